@@ -1,0 +1,343 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: published
+known-answer vectors, closed forms (view factors, spectrum moments, the flat
+surface's exact expectation), textbook distributions, brute force on tiny
+inputs, and conservation identities.  None of these need a GPU.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate, stats
+
+import oracle as O
+from paper_1806_00205_gb300 import inputs as I
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+TABLE = I.see_table()
+E47 = float(TABLE.energy_grid()[47])          # a grid energy (about 290.6 eV)
+
+
+def _kat_rows():
+    rows = []
+    with open(os.path.join(HERE, "golden", "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                w = [int(x, 16) for x in line.split()]
+                rows.append((w[0:4], w[4:6], w[6:10]))
+    return rows
+
+
+@pytest.mark.parametrize("ctr,key,expect", _kat_rows())
+def test_philox_known_answers(ctr, key, expect):
+    # Salmon et al. SC'11; vectors shipped with Random123 (tests/golden)
+    assert list(O.philox(ctr, key)) == expect
+
+
+# ---------------------------------------------------------------- geometry --
+
+def test_flat_plane_closed_form_hit():
+    """A vertical ray onto the 2-triangle plane: t, triangle and (u, v) are known."""
+    fp = I.flat_plane(160.0)
+    L = 160.0
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        x, y = rng.uniform(0, L, 2)
+        z0 = rng.uniform(1, 5)
+        t, j, u, v = O.closest_hit(fp, [x, y, z0], [0, 0, -1])
+        assert math.isclose(t, z0, rel_tol=1e-14)
+        if y < x:    # triangle 0: (0,0) (L,0) (L,L); P = u V1 + v V2
+            assert j == 0
+            assert math.isclose(v, y / L, abs_tol=1e-13) and math.isclose(u, (x - y) / L, abs_tol=1e-13)
+        else:        # triangle 1: (0,0) (L,L) (0,L)
+            assert j == 1
+            assert math.isclose(u, x / L, abs_tol=1e-13) and math.isclose(v, (y - x) / L, abs_tol=1e-13)
+        # back-face culling (Section 2.1 check 1): from below the plane the ray sees nothing
+        t2, j2, _, _ = O.closest_hit(fp, [x, y, -z0], [0, 0, 1])
+        assert j2 == -1 and math.isinf(t2)
+
+
+def test_watertight_matches_paper_moller_trumbore_on_foam():
+    """Watertight FP64 scan vs the paper's M-T solve with its four checks."""
+    mesh = I.grf_foam(8, 0.5, 1.5, seed=11)
+    rng = np.random.default_rng(5)
+    box = mesh.box
+    agree = 0
+    n = 400
+    for _ in range(n):
+        o = np.array([rng.uniform(0, box.lx), rng.uniform(0, box.ly), box.z_top])
+        d = rng.normal(size=3)
+        d[2] = -abs(d[2]) - 0.2
+        d /= np.linalg.norm(d)
+        a = O.closest_hit(mesh, o, d)
+        b = O.closest_hit(mesh, o, d, method="mt", eps=1e-12)
+        if a[1] == b[1]:
+            agree += 1
+            if a[1] >= 0:
+                assert math.isclose(a[0], b[0], rel_tol=1e-10)
+                assert abs(a[2] - b[2]) < 1e-9 and abs(a[3] - b[3]) < 1e-9
+    assert agree >= n - 1
+
+
+def test_hit_point_lies_on_ray_and_facet():
+    mesh = I.grf_foam(8, 0.5, 1.5, seed=12)
+    rng = np.random.default_rng(6)
+    tri = mesh.tri.astype(np.float64)
+    hits = 0
+    for _ in range(300):
+        o = np.array([rng.uniform(0, mesh.box.lx), rng.uniform(0, mesh.box.ly), mesh.box.z_top])
+        d = np.array([rng.normal(), rng.normal(), -3.0])
+        d /= np.linalg.norm(d)
+        t, j, u, v = O.closest_hit(mesh, o, d)
+        if j < 0:
+            continue
+        hits += 1
+        p = (1 - u - v) * tri[j, 0] + u * tri[j, 1] + v * tri[j, 2]
+        assert np.allclose(o + t * d, p, atol=1e-9)
+        assert u >= 0 and v >= 0 and u + v <= 1 + 1e-12
+        # no other front-facing triangle is hit closer (brute force over all of them)
+        n = np.cross(tri[:, 1] - tri[:, 0], tri[:, 2] - tri[:, 0])
+        assert np.dot(n[j], d) < 0
+    assert hits > 50
+
+
+def test_closest_hit_is_minimum_over_single_triangles():
+    """Brute force on a tiny mesh: the scan's answer is the min over one-triangle scans."""
+    mesh = I.grf_foam(6, 0.5, 1.2, seed=13)
+    rng = np.random.default_rng(7)
+    for _ in range(40):
+        o = np.array([rng.uniform(0, mesh.box.lx), rng.uniform(0, mesh.box.ly), mesh.box.z_top * 0.7])
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        t, j, _, _ = O.closest_hit(mesh, o, d)
+        best, bj = math.inf, -1
+        for k in range(mesh.n_tri):
+            one = I.Mesh(mesh.tri[k:k + 1], mesh.box)
+            tk, jk, _, _ = O.closest_hit(one, o, d)
+            if jk == 0 and tk < best:
+                best, bj = tk, k
+        assert bj == j and (j < 0 or best == t)
+
+
+def test_periodic_walk_counts_wraps():
+    """A daughter leaving the flat plane crosses the lateral faces a known number of times."""
+    fp = I.flat_plane(160.0)        # z_top = 10
+    L, H = 160.0, 10.0
+    for dx, dy, dz in [(3.0, 0.5, 0.01), (-2.0, 1.0, 0.05), (0.3, -4.0, 0.02), (1.0, 1.0, 2.0)]:
+        d = np.array([dx, dy, dz]) / math.sqrt(dx * dx + dy * dy + dz * dz)
+        o = np.array([17.0, 33.0, 0.0])
+        r = O.trace_ray(fp, o, d, origin_tri=0, max_wraps=100000)
+        assert r["fate"] == O.ESCAPED
+        t_top = H / d[2]
+        xf, yf = o[0] + t_top * d[0], o[1] + t_top * d[1]
+        expect = abs(math.floor(xf / L)) + abs(math.floor(yf / L))
+        assert r["wraps"] == expect
+        # the last segment ends on z_top at the wrapped exit point
+        end = r["o_last"] + r["t"] * d
+        assert math.isclose(end[2], H, abs_tol=1e-9)
+        assert math.isclose(end[0], xf - L * math.floor(xf / L), abs_tol=1e-6)
+        assert math.isclose(end[1], yf - L * math.floor(yf / L), abs_tol=1e-6)
+    # too many wraps -> lost
+    d = np.array([1.0, 0.0, 1e-4]); d /= np.linalg.norm(d)
+    r = O.trace_ray(fp, [5.0, 5.0, 0.0], d, origin_tri=0, max_wraps=8)
+    assert r["fate"] == O.LOST and r["wraps"] == 9
+
+
+# ---------------------------------------------------------------- sampling --
+
+def test_delta_lookup_grid_nodes_and_bilinearity():
+    g = TABLE.energy_grid()
+    for i in (0, 10, 47, 63):
+        for j in (0, 7, 17):
+            val = O.lookup_delta(TABLE, g[i], math.radians(5.0 * j))
+            assert math.isclose(val, float(TABLE.delta[i, j]), rel_tol=1e-9)
+    # midpoint in (ln E, theta) is the mean of the four corners
+    e_mid = math.sqrt(g[20] * g[21])
+    val = O.lookup_delta(TABLE, e_mid, math.radians(12.5))
+    corners = TABLE.delta[20:22, 2:4].astype(np.float64).mean()
+    assert math.isclose(val, corners, rel_tol=1e-9)
+    # interpolation error against the analytic curve is small off-grid
+    for e in (55.0, 300.0, 777.0):
+        for th in (0.0, 33.0, 71.0):
+            exact = float(I.lin_joy_delta(e, math.radians(th)))
+            assert abs(O.lookup_delta(TABLE, e, math.radians(th)) - exact) < 4e-3
+    # clamping outside the grid
+    assert math.isclose(O.lookup_delta(TABLE, 1e4, math.radians(89.0)),
+                        float(TABLE.delta[63, 17]), rel_tol=1e-9)
+
+
+def test_poisson_inversion_matches_pmf():
+    m = 200000
+    u = (np.arange(m) + 0.5) / m
+    for lam in (0.3, 1.078, 3.7):
+        ks = np.array([O.poisson(lam, x)[0] for x in u])
+        freq = np.bincount(ks, minlength=16)[:16] / m
+        pmf = stats.poisson.pmf(np.arange(16), lam)
+        assert np.abs(freq - pmf).max() < 2.0 / m
+    k, capped = O.poisson(40.0, 0.999)
+    assert k == 15 and capped == 1
+    k, capped = O.poisson(1.0, 0.5)
+    assert capped == 0
+
+
+def test_energy_sampler_inverts_the_spectrum_cdf():
+    phi, ecut = 4.55, 50.0
+    pdf = lambda e: e / (e + phi) ** 4
+    z = integrate.quad(pdf, 0, ecut)[0]
+    for u in (1e-6, 0.01, 0.25, 0.5, 0.9, 0.999999):
+        e = O.sample_energy(u)
+        assert 0.0 <= e <= ecut
+        assert math.isclose(integrate.quad(pdf, 0, e, epsabs=1e-14, epsrel=1e-12)[0] / z, u,
+                            rel_tol=1e-9, abs_tol=1e-12)
+
+
+def test_cosine_direction_law_and_basis():
+    rng = np.random.default_rng(9)
+    normals = [np.array([0, 0, 1.0]), np.array([0, 0, -1.0]), np.array([1.0, 0, 0])]
+    normals += [v / np.linalg.norm(v) for v in rng.normal(size=(20, 3))]
+    m = 64
+    for n in normals:
+        cos_sum = 0.0
+        for i in range(m):
+            for j in range(m):
+                u1, u2 = (i + 0.5) / m, (j + 0.5) / m
+                d = O.cosine_dir(n, u1, u2)
+                assert math.isclose(np.linalg.norm(d), 1.0, rel_tol=1e-12)
+                assert math.isclose(float(d @ n), math.sqrt(1 - u1), rel_tol=1e-9, abs_tol=1e-12)
+                cos_sum += float(d @ n)
+        # Malley: <cos theta'> = 2/3 under the cosine law
+        assert abs(cos_sum / (m * m) - 2.0 / 3.0) < 1e-3
+
+
+# ------------------------------------------------------------ whole runs --
+
+def test_flat_plane_reproduces_table_yield():
+    """Section 3.1: on a flat surface RTMC returns the sampling function exactly."""
+    fp = I.flat_plane(160.0)
+    for theta, j in ((0.0, 0), (60.0, 12)):
+        r = O.run(fp, TABLE, E47, theta, 400000, seed=2024, item=j)
+        lam = float(TABLE.delta[47, j])
+        assert r["lost"] == 0 and r["absorbed_low"] == 0 and r["absorbed_other"] == 0
+        assert r["escaped"] == r["emitted"] == r["sum_k"]      # every daughter escapes
+        assert abs(r["sey"] - lam) < 3.0 * r["sey_se"], (r["sey"], lam, r["sey_se"])
+        # Poisson counts: variance equals the mean
+        assert abs(r["sey_se"] ** 2 * r["n_primaries"] / lam - 1.0) < 0.02
+
+
+def test_flat_plane_spectra():
+    fp = I.flat_plane(160.0)
+    r = O.run(fp, TABLE, E47, 0.0, 300000, seed=99)
+    n = r["escaped"]
+    phi, ecut = 4.55, 50.0
+    pdf = lambda e: e / (e + phi) ** 4
+    z = integrate.quad(pdf, 0, ecut)[0]
+    edges = np.linspace(0, ecut, 65)
+    pe = np.array([integrate.quad(pdf, a, b)[0] for a, b in zip(edges[:-1], edges[1:])]) / z
+    assert stats.chisquare(r["hist_e"], pe * n).pvalue > 1e-3
+    th = np.radians(np.linspace(0, 90, 19))
+    pa = np.diff(np.sin(th) ** 2)                        # cosine law about +z
+    assert stats.chisquare(r["hist_a"], pa * n).pvalue > 1e-3
+    mean = integrate.quad(lambda e: e * pdf(e), 0, ecut)[0] / z
+    m2 = integrate.quad(lambda e: e * e * pdf(e), 0, ecut)[0] / z
+    se = math.sqrt((m2 - mean * mean) / n)
+    assert abs(r["e_sum"] / n - mean) < 3 * se
+    assert math.isclose(mean, 7.148468, rel_tol=1e-6)
+
+
+def view_factor_squares(x):
+    """Parallel, coaxial equal squares, side a, gap h, X = a/h (textbook closed form)."""
+    s = math.sqrt(1 + x * x)
+    return (2.0 / (math.pi * x * x)) * (math.log((1 + x * x) / math.sqrt(1 + 2 * x * x))
+                                        + 2 * x * s * math.atan(x / s) - 2 * x * math.atan(x))
+
+
+@pytest.mark.parametrize("a_over_h", [0.5, 1.0, 2.0])
+def test_square_well_view_factor(a_over_h):
+    a = 100.0
+    well = I.square_well(a, a / a_over_h)
+    r = O.run(well, TABLE, E47, 0.0, 300000, seed=31, window=I.opening_window(a))
+    lam = float(TABLE.delta[47, 0])
+    expect = lam * view_factor_squares(a_over_h)
+    assert r["lost"] == 0
+    assert abs(r["sey"] - expect) < 3.0 * r["sey_se"], (r["sey"], expect, r["sey_se"])
+    # every daughter either escapes or is absorbed by a wall
+    assert r["emitted"] == r["escaped"] + r["absorbed_low"] + r["absorbed_other"]
+
+
+def test_view_factor_reference_values():
+    # tabulated values of the closed form (X = 0.5, 1, 2, 4)
+    for x, f in ((0.5, 0.068590), (1.0, 0.199825), (2.0, 0.415253), (4.0, 0.632036)):
+        assert abs(view_factor_squares(x) - f) < 2e-6
+
+
+def _conservation(r, n):
+    assert r["n_primaries"] == n
+    assert r["rays"] == n + r["emitted"]
+    assert r["rays"] == (r["escaped"] + r["absorbed_low"] + r["absorbed_other"]
+                         + r["emitters"] + r["lost"])
+    assert r["sum_k"] == r["escaped"]
+    assert r["hist_e"].sum() == r["escaped"] == r["hist_a"].sum()
+
+
+def test_foam_conservation_and_records():
+    mesh = I.grf_foam(16, 0.5)
+    n = 3000
+    r = O.run(mesh, TABLE, 300.0, 0.0, n, seed=5, records=True)
+    _conservation(r, n)
+    assert r["lost"] == 0                          # closed mesh: nothing leaks
+    assert 0.2 < r["sey"] < 1.0                    # a foam traps part of the yield
+    rec = r["records"]
+    assert rec.size == r["rays"]
+    # tree structure: one primary per id, daughters j < k of their parent
+    prim = rec[rec["gen"] == 0]
+    assert prim.size == n and np.all(prim["path"] == 1)
+    kids = {}
+    for x in rec[rec["gen"] == 1]:
+        kids.setdefault(int(x["prim"]), []).append(int(x["path"]) - 16)
+    for p in prim:
+        got = sorted(kids.get(int(p["prim"]), []))
+        assert got == list(range(int(p["k"])))
+    esc = rec[rec["fate"] == O.ESCAPED]
+    assert np.bincount(esc["e_bin"], minlength=64).tolist() == r["hist_e"].tolist()
+
+
+def test_foam_results_independent_of_threads():
+    mesh = I.grf_foam(16, 0.5)
+    a = O.run(mesh, TABLE, 500.0, 30.0, 1500, seed=8, n_threads=1)
+    b = O.run(mesh, TABLE, 500.0, 30.0, 1500, seed=8, n_threads=4)
+    for k in ("rays", "escaped", "sum_k2", "wraps", "e_sum"):
+        assert a[k] == b[k]
+    assert (a["hist_a"] == b["hist_a"]).all()
+
+
+def test_tertiaries_conserve():
+    mesh = I.grf_foam(16, 0.7, seed=4)
+    em = O.Emission(regen_min_ev=20.0, max_generation=2)
+    n = 3000
+    r = O.run(mesh, TABLE, 500.0, 0.0, n, seed=6, emission=em, records=True)
+    _conservation(r, n)
+    assert r["regenerated"] > 0
+    rec = r["records"]
+    assert (rec["gen"] == 2).any() and rec["gen"].max() == 2
+    regen = rec[(rec["gen"] == 1) & (rec["fate"] == O.EMITTER)]
+    assert np.all(regen["energy"] >= 20.0)
+
+
+def test_primary_ids_replay_the_same_trees():
+    """Counter-based streams: a subset of primaries replays exactly."""
+    mesh = I.grf_foam(16, 0.5)
+    full = O.run(mesh, TABLE, 300.0, 0.0, 400, seed=5, records=True)["records"]
+    ids = np.array([3, 77, 150, 399], dtype=np.uint64)
+    sub = O.run(mesh, TABLE, 300.0, 0.0, 0, seed=5, prim_ids=ids, records=True)["records"]
+    want = full[np.isin(full["prim"], ids)]
+    assert sub.tobytes() == want.tobytes()
+
+
+def test_paper_yield_fit_peak():
+    """Eq. 6 at normal incidence peaks near 1.49 (Section 3.2 quotes 1.49 for flat W)."""
+    e = np.linspace(50, 1000, 95001)
+    g = I.paper_delta(e, 0.0)
+    assert abs(g.max() - 1.49) < 0.005
+    assert 380 < e[np.argmax(g)] < 450
