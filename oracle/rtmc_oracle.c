@@ -35,7 +35,8 @@
  *  R6 Random streams: Philox4x32-10, key = (seed lo, seed hi), counter =
  *     (prim lo, prim hi, path, item).  Primary path = 1; daughter j of a ray
  *     with path p has path 16 p + j.  The four words w0..w3 of a ray's block
- *     map to uniforms u = ((w >> 8) + 0.5) 2^-24.  Primary: u0, u1 -> (x, y)
+ *     map to uniforms u = ((w >> 9) + 0.5) 2^-23, a 24-bit odd multiple of
+ *     2^-24 and so exact in FP32 as in FP64.  Primary: u0, u1 -> (x, y)
  *     in the source window, u2 -> azimuth when random, u3 -> its Poisson
  *     draw.  Daughter: u0 -> energy, u1, u2 -> direction, u3 -> its own
  *     Poisson draw if it re-emits.
@@ -85,7 +86,7 @@ static void ray_uniforms(uint64_t seed, uint64_t prim, uint32_t path, uint32_t i
     uint32_t w[4];
     orc_philox4x32_10(ctr, key, w);
     for (int i = 0; i < 4; ++i)
-        u[i] = ((double)(w[i] >> 8) + 0.5) * (1.0 / 16777216.0);
+        u[i] = ((double)(w[i] >> 9) + 0.5) * (1.0 / 8388608.0);
 }
 
 /* ------------------------------------------------------------------------ */
