@@ -1,0 +1,182 @@
+/*
+ * rtmc.h -- C ABI of librtmc, a GB300 (sm_103a) implementation of ray-tracing
+ * Monte Carlo (RTMC) secondary-electron yield from triangulated surfaces
+ * (Alvarado, Chang, Nadvornick, Ghoniem, Marian: "Monte Carlo Raytracing
+ * Method for Calculating Secondary Electron Emission from Micro-Architected
+ * Surfaces").
+ *
+ * Method (Sections 2.1-2.2, Fig. 1): primary rays start on the top plane and
+ * travel into a periodic triangle mesh; the closest front-facing facet is
+ * found (Section 2.1, four checks; here through a linear BVH); at a hit the
+ * local incidence angle and energy give the expected number of secondaries
+ * from a flat-surface yield table (Section 2.2); each daughter gets an energy
+ * and a cosine-law direction and is traced in turn; a ray that reaches the
+ * top plane moving up is an emission event, and the yield is
+ * emissions / primaries (Fig. 1, gamma_eff).
+ *
+ * Conventions for every entry point:
+ *  - return 0 on success or a negative RTMC_ERR_* code; rtmc_last_error()
+ *    then holds a one-line message for that context;
+ *  - input pointers may be host or device memory (unified addressing decides)
+ *    and are copied before the call returns; the caller keeps ownership;
+ *  - outputs go to caller-owned host memory unless stated otherwise;
+ *  - work is ordered on the context's stream and the call synchronises that
+ *    stream before it returns;
+ *  - a context is used by one host thread at a time.
+ */
+#ifndef RTMC_H
+#define RTMC_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RTMC_OK                 0
+#define RTMC_ERR_INVALID_ARG   -1
+#define RTMC_ERR_OOM           -2
+#define RTMC_ERR_CUDA          -3
+#define RTMC_ERR_NOT_LOADED    -4
+#define RTMC_ERR_NOT_BUILT     -5
+#define RTMC_ERR_CAPACITY      -6
+#define RTMC_ERR_TIMEOUT       -7
+#define RTMC_ERR_DEVICE_CHECK  -8
+
+#define RTMC_BVH_FP32 0     /* 64-byte nodes with FP32 child boxes */
+
+/* Ray fates (per-ray records) */
+#define RTMC_ESCAPED        0
+#define RTMC_EMITTER        1
+#define RTMC_ABSORBED_LOW   2
+#define RTMC_ABSORBED_OTHER 3
+#define RTMC_LOST           4
+
+typedef struct rtmc_ctx rtmc_ctx;
+
+/* Periodic cell (Section 2.2, last paragraph): x in [0, lx), y in [0, ly)
+   periodic; the substrate lies above z_min; z_top is the escape plane. */
+typedef struct { double lx, ly, z_min, z_top; } rtmc_box;
+
+/* Yield-table grid: E_i = e_lo * (e_hi/e_lo)^(i/(n_e-1)), theta_j = j * step. */
+typedef struct {
+    int32_t n_e, n_theta;
+    double e_lo_ev, e_hi_ev, theta_step_deg;
+} rtmc_grid;
+
+/* Secondary emission (Section 2.2).  A primary always emits at its first hit;
+   a daughter of generation g re-emits when g < max_generation and
+   E >= regen_min_ev, else it is absorbed (absorbed_low below absorb_min_ev).
+   Daughter energies follow E/(E+phi)^4 on [0, e_cut_ev]; counts are
+   Poisson(delta) capped at k_max (<= 15). */
+typedef struct {
+    double phi_ev, e_cut_ev, absorb_min_ev, regen_min_ev;
+    int32_t max_generation, k_max;
+} rtmc_emission;
+
+typedef struct {
+    int32_t n_ebins, n_abins;      /* escaped-energy bins on [0, hist_e_max); polar bins on [0, 90 deg) */
+    double hist_e_max_ev;
+    uint64_t primary_offset;       /* primary ids are offset .. offset + n - 1 */
+    int32_t random_azimuth;        /* 0: incidence in the x-z plane; 1: uniform azimuth */
+    int32_t max_wraps;             /* lateral re-entries before a ray counts as lost (0 -> 1024) */
+    double src_x0, src_x1, src_y0, src_y1;   /* primary source window; all 0 -> whole cell */
+    int64_t chunk;                 /* primaries per wavefront chunk (0 -> automatic) */
+    int32_t block_threads;         /* traversal block size (0 -> 128) */
+    int32_t blocks_per_sm;         /* persistent traversal blocks per SM (0 -> occupancy) */
+    uint64_t* prim_hash;           /* optional DEVICE array [n_primaries]: per-primary
+                                      sum of record hashes (see rtmc_record_hash) */
+    int32_t profile;               /* 1: time every kernel launch with CUDA events */
+    int32_t count_visits;          /* 1: count BVH node visits and triangle tests */
+} rtmc_run_desc;
+
+typedef struct {
+    int64_t n_primaries, rays, escaped, absorbed_low, absorbed_other;
+    int64_t emitters, emitted, regenerated, capped, lost, wraps;
+    int64_t sum_k, sum_k2;                     /* per-primary escape count k: sum, sum of squares */
+    double e_sum, e2_sum;                      /* escaped energy moments (eV, eV^2) */
+    double sey, sey_se;                        /* sum_k / N and its standard error */
+    double gpu_ms;                             /* device time of this (E, theta) item */
+    int64_t launches;                          /* kernels launched for this item */
+    int64_t node_visits, tri_tests;            /* with count_visits */
+    double ms_generate, ms_traverse, ms_shade, ms_finalize;   /* with profile */
+    int64_t traverse_launches;
+} rtmc_result;
+
+/* One traced ray: the integer event sequence used for parity checks. */
+typedef struct {
+    uint64_t prim;
+    uint32_t path;            /* primary 1; daughter j of path p: 16 p + j */
+    int32_t gen, fate, tri;   /* tri: original triangle id of the final hit or -1 */
+    int32_t k, e_bin, a_bin, wraps;
+    double t;                 /* length parameter of the final segment */
+    double energy;            /* eV */
+} rtmc_record;                /* 56 bytes */
+
+/* Closest-hit query result (rtmc_trace_rays). */
+typedef struct { float t, u, v; int32_t tri; } rtmc_hit;
+
+/* Create a context on CUDA `device`.  `cuda_stream` is a cudaStream_t to
+   order all work on, or NULL for a context-owned stream. */
+int rtmc_create(rtmc_ctx** out, int32_t device, void* cuda_stream);
+void rtmc_destroy(rtmc_ctx* ctx);
+const char* rtmc_last_error(const rtmc_ctx* ctx);
+
+/* Copy a triangle soup tri[n_tri][3][3] (FP32, vertices V0 V1 V2 with
+   (V1-V0) x (V2-V0) pointing into vacuum, Section 2.1) into the context.
+   All vertices must lie in [0,lx] x [0,ly] x (z_min, z_top).
+   Writes the new mesh id. */
+int rtmc_load_mesh(rtmc_ctx* ctx, const float* tri, int64_t n_tri, const rtmc_box* box,
+                   int32_t* mesh_id);
+
+/* Free the device memory of a mesh and its BVH; the id becomes invalid. */
+int rtmc_unload_mesh(rtmc_ctx* ctx, int32_t mesh_id);
+
+/* Copy the flat-surface yield table delta[n_e][n_theta] (FP32, energy-major;
+   Section 2.2 "pre-calculated tables") and the emission parameters. */
+int rtmc_load_see_tables(rtmc_ctx* ctx, const float* delta, const rtmc_grid* grid,
+                         const rtmc_emission* emission);
+
+/* Build the linear BVH of a loaded mesh on the device: Morton codes of the
+   triangle centroids, radix sort, Karras hierarchy, bottom-up box refit,
+   triangle repack.  `bvh_kind` is RTMC_BVH_FP32. */
+int rtmc_build_bvh(rtmc_ctx* ctx, int32_t mesh_id, int32_t bvh_kind);
+
+/* Run RTMC for every (energy, angle) pair: n_e * n_theta items, item
+   ie * n_theta + it.  Each item traces n_primaries primaries with seed `seed`
+   (Philox4x32-10 streams keyed by seed and indexed by primary id, ray path and
+   item).  Writes out[n_e * n_theta] and, when non-NULL, hist_e[item][n_ebins]
+   and hist_a[item][n_abins] (host memory).  desc may be NULL (defaults). */
+int rtmc_run(rtmc_ctx* ctx, int32_t mesh_id, const double* energies_ev, int32_t n_e,
+             const double* theta_deg, int32_t n_theta, int64_t n_primaries, uint64_t seed,
+             const rtmc_run_desc* desc, rtmc_result* out, uint64_t* hist_e, uint64_t* hist_a);
+
+/* As rtmc_run for one (energy, angle) item with index `item`, also writing one
+   record per traced ray (any order) into rec[rec_cap] (host memory); *n_rec
+   receives the count.  Fails with RTMC_ERR_CAPACITY when rec_cap is too small. */
+int rtmc_run_records(rtmc_ctx* ctx, int32_t mesh_id, double energy_ev, double theta_deg,
+                     uint32_t item, int64_t n_primaries, uint64_t seed,
+                     const rtmc_run_desc* desc, rtmc_result* out, rtmc_record* rec,
+                     int64_t rec_cap, int64_t* n_rec);
+
+/* Closest front-facing hit of n rays in the cell (no periodic walk) through
+   the BVH: origins o[n][3], directions d[n][3] (FP32), origin triangle ids
+   to skip (original ids, -1 = none, may be NULL).  hits[n] gets t, the
+   barycentrics (u, v) of V1 and V2, and the original triangle id (-1 on a
+   miss).  Section 2.1. */
+int rtmc_trace_rays(rtmc_ctx* ctx, int32_t mesh_id, const float* o, const float* d,
+                    const int32_t* skip_tri, int64_t n, rtmc_hit* hits);
+
+/* Philox4x32-10 on the device: out[i][4] = philox(ctr[i][4], key), for
+   checking the device generator against the published vectors. */
+int rtmc_philox(rtmc_ctx* ctx, const uint32_t* ctr, int64_t n, uint64_t key, uint32_t* out);
+
+/* Hash of one record (the per-primary hash is the sum mod 2^64 of the hashes
+   of that primary's records): h = sm(prim); h = sm(h ^ (path | fate << 32));
+   h = sm(h ^ (uint32 tri | uint32 k << 32)); h = sm(h ^ (uint32 e_bin |
+   uint32 a_bin << 32)); h = sm(h ^ uint32 wraps), sm = splitmix64. */
+uint64_t rtmc_record_hash(const rtmc_record* r);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

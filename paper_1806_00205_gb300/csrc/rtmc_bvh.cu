@@ -1,0 +1,380 @@
+// rtmc_bvh.cu -- linear BVH construction on the device (sm_103a).
+//
+// The paper scans every element per ray (Section 2.1: "must scan through all
+// elements ... rapidly become prohibitive"); this library replaces the scan
+// by a binary BVH so a ray visits O(log n) boxes.  Construction follows the
+// Karras (HPG 2012) formulation:
+//   1. 30-bit Morton code of each triangle centroid, quantised on the cell box;
+//   2. stable LSD radix sort of (code, triangle id), 4 passes of 8 bits;
+//   3. one thread per inner node finds its key range and split (Karras);
+//   4. bottom-up box refit: one thread per leaf climbs, the second thread to
+//      reach a node (atomic counter) writes it;
+//   5. triangles and normals repacked in leaf order as 16-byte aligned float4.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+
+#include "rtmc_internal.h"
+
+namespace rtmc {
+namespace {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 4;
+constexpr int kSortTile = kSortThreads * kSortItems;
+
+__device__ __forceinline__ unsigned expand_bits10(unsigned v)
+{
+    v = (v * 0x00010001u) & 0xFF0000FFu;
+    v = (v * 0x00000101u) & 0x0F00F00Fu;
+    v = (v * 0x00000011u) & 0xC30C30C3u;
+    v = (v * 0x00000005u) & 0x49249249u;
+    return v;
+}
+
+__device__ __forceinline__ unsigned quant10(float x)
+{
+    float q = fminf(fmaxf(x * 1024.0f, 0.0f), 1023.0f);
+    return (unsigned)q;
+}
+
+__global__ void k_morton(const float* __restrict__ tri, int n, float4 box_lo, float4 box_inv,
+                         unsigned* __restrict__ keys, unsigned* __restrict__ vals)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float* t = tri + 9ll * i;
+    const float cx = (t[0] + t[3] + t[6]) * (1.0f / 3.0f);
+    const float cy = (t[1] + t[4] + t[7]) * (1.0f / 3.0f);
+    const float cz = (t[2] + t[5] + t[8]) * (1.0f / 3.0f);
+    const unsigned x = quant10((cx - box_lo.x) * box_inv.x);
+    const unsigned y = quant10((cy - box_lo.y) * box_inv.y);
+    const unsigned z = quant10((cz - box_lo.z) * box_inv.z);
+    keys[i] = (expand_bits10(x) << 2) | (expand_bits10(y) << 1) | expand_bits10(z);
+    vals[i] = (unsigned)i;
+}
+
+// ---- radix sort: per-tile digit histogram --------------------------------
+__global__ void k_radix_hist(const unsigned* __restrict__ keys, int n, int shift, int n_tiles,
+                             unsigned* __restrict__ hist)
+{
+    __shared__ unsigned cnt[256];
+    cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const long long base = (long long)blockIdx.x * kSortTile;
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        const long long e = base + it * kSortThreads + threadIdx.x;
+        if (e < n) atomicAdd(&cnt[(keys[e] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(long long)threadIdx.x * n_tiles + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// ---- radix sort: exclusive scan of the digit-major histogram (one block) --
+__global__ void k_radix_scan(unsigned* __restrict__ hist, long long total)
+{
+    __shared__ unsigned sums[1024];
+    const long long per = (total + blockDim.x - 1) / blockDim.x;
+    const long long lo = threadIdx.x * per;
+    const long long hi = lo + per < total ? lo + per : total;
+    unsigned s = 0;
+    for (long long i = lo; i < hi; ++i) s += hist[i];
+    sums[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+        unsigned v = threadIdx.x >= (unsigned)off ? sums[threadIdx.x - off] : 0u;
+        __syncthreads();
+        sums[threadIdx.x] += v;
+        __syncthreads();
+    }
+    unsigned run = sums[threadIdx.x] - s;       // exclusive prefix of this segment
+    for (long long i = lo; i < hi; ++i) {
+        const unsigned v = hist[i];
+        hist[i] = run;
+        run += v;
+    }
+}
+
+// ---- radix sort: stable scatter ------------------------------------------
+// Element e = tile*1024 + it*256 + warp*32 + lane.  Its rank among equal
+// digits of the tile = (equal digits in earlier (it, warp) slots) + (equal
+// digits in lower lanes of its own warp, from __match_any_sync).
+__global__ void __launch_bounds__(kSortThreads)
+k_radix_scatter(const unsigned* __restrict__ kin, const unsigned* __restrict__ vin,
+                unsigned* __restrict__ kout, unsigned* __restrict__ vout, int n, int shift,
+                int n_tiles, const unsigned* __restrict__ hist)
+{
+    constexpr int kSlots = kSortItems * (kSortThreads / 32);
+    __shared__ unsigned cnt[kSlots][256];
+    for (int i = threadIdx.x; i < kSlots * 256; i += kSortThreads) (&cnt[0][0])[i] = 0u;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const long long base = (long long)blockIdx.x * kSortTile;
+    unsigned key[kSortItems], val[kSortItems], dig[kSortItems], rank[kSortItems];
+    bool ok[kSortItems];
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        const long long e = base + it * kSortThreads + threadIdx.x;
+        ok[it] = e < n;
+        key[it] = ok[it] ? kin[e] : 0u;
+        val[it] = ok[it] ? vin[e] : 0u;
+        dig[it] = (key[it] >> shift) & 255u;
+        const unsigned tag = ok[it] ? dig[it] : 0x100u;
+        const unsigned peers = __match_any_sync(0xFFFFFFFFu, tag);
+        rank[it] = __popc(peers & lt);
+        if (ok[it] && (peers & lt) == 0u) cnt[it * (kSortThreads / 32) + warp][dig[it]] = __popc(peers);
+    }
+    __syncthreads();
+    {   // exclusive prefix over the (it, warp) slots, one digit per thread
+        const int d = threadIdx.x;
+        unsigned run = 0;
+        for (int s = 0; s < kSlots; ++s) {
+            const unsigned v = cnt[s][d];
+            cnt[s][d] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        if (!ok[it]) continue;
+        const unsigned pos = hist[(long long)dig[it] * n_tiles + blockIdx.x] +
+                             cnt[it * (kSortThreads / 32) + warp][dig[it]] + rank[it];
+        kout[pos] = key[it];
+        vout[pos] = val[it];
+    }
+}
+
+// ---- Karras hierarchy ------------------------------------------------------
+__device__ __forceinline__ int common_prefix(const unsigned* __restrict__ k, int n, int i, int j)
+{
+    if (j < 0 || j >= n) return -1;
+    const unsigned a = k[i], b = k[j];
+    if (a == b) return 32 + __clz((unsigned)(i ^ j));
+    return __clz(a ^ b);
+}
+
+__global__ void k_karras(const unsigned* __restrict__ keys, int n, int2* __restrict__ child,
+                         int* __restrict__ parent, int* __restrict__ leaf_parent)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    const int d = (common_prefix(keys, n, i, i + 1) - common_prefix(keys, n, i, i - 1)) >= 0 ? 1 : -1;
+    const int dmin = common_prefix(keys, n, i, i - d);
+    int lmax = 2;
+    while (common_prefix(keys, n, i, i + lmax * d) > dmin) lmax *= 2;
+    int l = 0;
+    for (int t = lmax / 2; t >= 1; t /= 2)
+        if (common_prefix(keys, n, i, i + (l + t) * d) > dmin) l += t;
+    const int j = i + l * d;
+    const int dnode = common_prefix(keys, n, i, j);
+    int s = 0;
+    for (int div = 2;; div *= 2) {
+        const int t = (l + div - 1) / div;
+        if (common_prefix(keys, n, i, i + (s + t) * d) > dnode) s += t;
+        if (t <= 1) break;
+    }
+    const int gamma = i + s * d + min(d, 0);
+    const int lo = min(i, j), hi = max(i, j);
+    const int left = (lo == gamma) ? ~gamma : gamma;
+    const int right = (hi == gamma + 1) ? ~(gamma + 1) : gamma + 1;
+    child[i] = make_int2(left, right);
+    if (left < 0) leaf_parent[~left] = i; else parent[left] = i;
+    if (right < 0) leaf_parent[~right] = i; else parent[right] = i;
+    if (i == 0) parent[0] = -1;
+}
+
+struct Box3 { float3 lo, hi; };
+
+__device__ __forceinline__ Box3 tri_box(const float* __restrict__ tri, unsigned t)
+{
+    const float* p = tri + 9ll * t;
+    Box3 b;
+    b.lo = make_float3(fminf(fminf(p[0], p[3]), p[6]), fminf(fminf(p[1], p[4]), p[7]),
+                       fminf(fminf(p[2], p[5]), p[8]));
+    b.hi = make_float3(fmaxf(fmaxf(p[0], p[3]), p[6]), fmaxf(fmaxf(p[1], p[4]), p[7]),
+                       fmaxf(fmaxf(p[2], p[5]), p[8]));
+    return b;
+}
+
+__device__ __forceinline__ void store_node(float4* __restrict__ nodes, int i, const Box3& b0,
+                                           const Box3& b1, int c0, int c1)
+{
+    float4* nd = nodes + 4ll * i;
+    nd[0] = make_float4(b0.lo.x, b0.hi.x, b0.lo.y, b0.hi.y);
+    nd[1] = make_float4(b1.lo.x, b1.hi.x, b1.lo.y, b1.hi.y);
+    nd[2] = make_float4(b0.lo.z, b0.hi.z, b1.lo.z, b1.hi.z);
+    nd[3] = make_float4(__int_as_float(c0), __int_as_float(c1), 0.f, 0.f);
+}
+
+__global__ void k_refit(const float* __restrict__ tri, const unsigned* __restrict__ order, int n,
+                        const int2* __restrict__ child, const int* __restrict__ parent,
+                        const int* __restrict__ leaf_parent, unsigned* __restrict__ flag,
+                        float4* __restrict__ aabb, float4* __restrict__ nodes)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int node = leaf_parent[j];
+    for (int level = 0; node >= 0 && level < 256; ++level) {   // depth is far below 256
+        if (atomicAdd(&flag[node], 1u) == 0u) return;    // the sibling is not done yet
+        const int2 c = child[node];
+        Box3 b[2];
+        const int cc[2] = {c.x, c.y};
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            if (cc[s] < 0) {
+                b[s] = tri_box(tri, order[~cc[s]]);
+            } else {
+                const float4 lo = __ldcg(aabb + 2ll * cc[s]);
+                const float4 hi = __ldcg(aabb + 2ll * cc[s] + 1);
+                b[s].lo = make_float3(lo.x, lo.y, lo.z);
+                b[s].hi = make_float3(hi.x, hi.y, hi.z);
+            }
+        }
+        store_node(nodes, node, b[0], b[1], c.x, c.y);
+        __stcg(aabb + 2ll * node, make_float4(fminf(b[0].lo.x, b[1].lo.x), fminf(b[0].lo.y, b[1].lo.y),
+                                              fminf(b[0].lo.z, b[1].lo.z), 0.f));
+        __stcg(aabb + 2ll * node + 1, make_float4(fmaxf(b[0].hi.x, b[1].hi.x), fmaxf(b[0].hi.y, b[1].hi.y),
+                                                  fmaxf(b[0].hi.z, b[1].hi.z), 0.f));
+        __threadfence();
+        node = parent[node];
+    }
+}
+
+// A one-triangle mesh: the root's two children are the same leaf (the repeat
+// test cannot change the closest hit).
+__global__ void k_single_leaf(const float* __restrict__ tri, float4* __restrict__ nodes)
+{
+    const Box3 b = tri_box(tri, 0);
+    store_node(nodes, 0, b, b, ~0, ~0);
+}
+
+__global__ void k_pack(const float* __restrict__ tri, const unsigned* __restrict__ order, int n,
+                       float4* __restrict__ tris, float4* __restrict__ normals,
+                       int* __restrict__ inv_order)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const unsigned i = order[j];
+    const float* p = tri + 9ll * i;
+    tris[3ll * j + 0] = make_float4(p[0], p[1], p[2], __int_as_float((int)i));
+    tris[3ll * j + 1] = make_float4(p[3], p[4], p[5], 0.f);
+    tris[3ll * j + 2] = make_float4(p[6], p[7], p[8], 0.f);
+    const float l1x = p[3] - p[0], l1y = p[4] - p[1], l1z = p[5] - p[2];
+    const float l2x = p[6] - p[0], l2y = p[7] - p[1], l2z = p[8] - p[2];
+    const float nx = l1y * l2z - l1z * l2y, ny = l1z * l2x - l1x * l2z, nz = l1x * l2y - l1y * l2x;
+    const float inv = 1.0f / sqrtf(nx * nx + ny * ny + nz * nz);
+    normals[j] = make_float4(nx * inv, ny * inv, nz * inv, 0.f);
+    inv_order[i] = j;
+}
+
+__global__ void k_depth(const int* __restrict__ parent, const int* __restrict__ leaf_parent, int n,
+                        int* __restrict__ depth)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int d = 1, node = leaf_parent[j];
+    while (node >= 0 && d < 1000) { ++d; node = parent[node]; }
+    atomicMax(depth, d);
+}
+
+struct DevBuf {
+    void* p = nullptr;
+    ~DevBuf() { if (p) cudaFree(p); }
+    cudaError_t alloc(size_t bytes) { return cudaMalloc(&p, bytes ? bytes : 16); }
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+}  // namespace
+
+int build_lbvh(rtmc_ctx* ctx, DeviceMesh& m)
+{
+    cudaStream_t s = ctx->stream;
+    const int n = (int)m.n_tri;
+    if (m.n_tri <= 0 || m.n_tri > (int64_t)1 << 30)
+        return ctx->fail(RTMC_ERR_INVALID_ARG, "build_bvh: triangle count out of range");
+    if (m.nodes) { cudaFree(m.nodes); m.nodes = nullptr; }
+    if (m.tris) { cudaFree(m.tris); m.tris = nullptr; }
+    if (m.normals) { cudaFree(m.normals); m.normals = nullptr; }
+    if (m.inv_order) { cudaFree(m.inv_order); m.inv_order = nullptr; }
+    m.built = false;
+    const int64_t n_nodes = n > 1 ? n - 1 : 1;
+    cudaError_t e = cudaMalloc(&m.nodes, n_nodes * 64);
+    if (e == cudaSuccess) e = cudaMalloc(&m.tris, (size_t)n * 48);
+    if (e == cudaSuccess) e = cudaMalloc(&m.normals, (size_t)n * 16);
+    if (e == cudaSuccess) e = cudaMalloc(&m.inv_order, (size_t)n * 4);
+    if (e != cudaSuccess) return ctx->fail(RTMC_ERR_OOM, std::string("build_bvh: ") + cudaGetErrorString(e));
+    m.n_nodes = n_nodes;
+
+    cudaEvent_t ev0, ev1;
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+    cudaEventRecord(ev0, s);
+
+    const int n_tiles = (n + kSortTile - 1) / kSortTile;
+    DevBuf k0, k1, v0, v1, hist, child, parent, leafp, flag, aabb, depth;
+    e = k0.alloc(4ull * n);
+    if (e == cudaSuccess) e = k1.alloc(4ull * n);
+    if (e == cudaSuccess) e = v0.alloc(4ull * n);
+    if (e == cudaSuccess) e = v1.alloc(4ull * n);
+    if (e == cudaSuccess) e = hist.alloc(4ull * 256 * n_tiles);
+    if (e == cudaSuccess) e = child.alloc(8ull * n_nodes);
+    if (e == cudaSuccess) e = parent.alloc(4ull * n_nodes);
+    if (e == cudaSuccess) e = leafp.alloc(4ull * n);
+    if (e == cudaSuccess) e = flag.alloc(4ull * n_nodes);
+    if (e == cudaSuccess) e = aabb.alloc(32ull * n_nodes);
+    if (e == cudaSuccess) e = depth.alloc(4);
+    if (e != cudaSuccess) return ctx->fail(RTMC_ERR_OOM, std::string("build_bvh scratch: ") + cudaGetErrorString(e));
+
+    const rtmc_box& bx = m.box;
+    const float4 lo = make_float4(0.f, 0.f, (float)bx.z_min, 0.f);
+    const float4 inv = make_float4((float)(1.0 / bx.lx), (float)(1.0 / bx.ly),
+                                   (float)(1.0 / (bx.z_top - bx.z_min)), 0.f);
+    const int tb = 256, gb = (n + tb - 1) / tb;
+    k_morton<<<gb, tb, 0, s>>>(m.tri_in, n, lo, inv, k0.as<unsigned>(), v0.as<unsigned>());
+    unsigned *ki = k0.as<unsigned>(), *ko = k1.as<unsigned>();
+    unsigned *vi = v0.as<unsigned>(), *vo = v1.as<unsigned>();
+    for (int pass = 0; pass < 4; ++pass) {
+        const int shift = 8 * pass;
+        k_radix_hist<<<n_tiles, kSortThreads, 0, s>>>(ki, n, shift, n_tiles, hist.as<unsigned>());
+        k_radix_scan<<<1, 1024, 0, s>>>(hist.as<unsigned>(), 256ll * n_tiles);
+        k_radix_scatter<<<n_tiles, kSortThreads, 0, s>>>(ki, vi, ko, vo, n, shift, n_tiles, hist.as<unsigned>());
+        unsigned* t = ki; ki = ko; ko = t;
+        t = vi; vi = vo; vo = t;
+    }
+    // after 4 passes the sorted data is back in (k0, v0)
+    cudaMemsetAsync(depth.p, 0, 4, s);
+    if (n == 1) {
+        k_single_leaf<<<1, 1, 0, s>>>(m.tri_in, m.nodes);
+        int one = 1;
+        cudaMemcpyAsync(depth.p, &one, 4, cudaMemcpyHostToDevice, s);
+    } else {
+        cudaMemsetAsync(flag.p, 0, 4ull * n_nodes, s);
+        const int gi = (n - 1 + tb - 1) / tb;
+        k_karras<<<gi, tb, 0, s>>>(ki, n, child.as<int2>(), parent.as<int>(), leafp.as<int>());
+        k_refit<<<gb, tb, 0, s>>>(m.tri_in, vi, n, child.as<int2>(), parent.as<int>(), leafp.as<int>(),
+                                  flag.as<unsigned>(), aabb.as<float4>(), m.nodes);
+        k_depth<<<gb, tb, 0, s>>>(parent.as<int>(), leafp.as<int>(), n, depth.as<int>());
+    }
+    k_pack<<<gb, tb, 0, s>>>(m.tri_in, vi, n, m.tris, m.normals, m.inv_order);
+    int h_depth = 0;
+    cudaMemcpyAsync(&h_depth, depth.p, 4, cudaMemcpyDeviceToHost, s);
+    cudaEventRecord(ev1, s);
+    e = cudaStreamSynchronize(s);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return ctx->fail(RTMC_ERR_CUDA, std::string("build_bvh: ") + cudaGetErrorString(e));
+    m.depth = h_depth;
+    m.build_ms = ms;
+    if (h_depth >= kStackMax)
+        return ctx->fail(RTMC_ERR_DEVICE_CHECK, "build_bvh: hierarchy deeper than the traversal stack");
+    m.built = true;
+    return RTMC_OK;
+}
+
+}  // namespace rtmc

@@ -1,0 +1,113 @@
+// rtmc_internal.h -- host-side state shared by the translation units of librtmc.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/rtmc.h"
+#include "rtmc_device.cuh"
+
+namespace rtmc {
+
+struct DeviceMesh {
+    int64_t n_tri = 0;
+    rtmc_box box{};
+    float* tri_in = nullptr;       // n_tri * 9, original order
+    bool built = false;
+    int kind = RTMC_BVH_FP32;
+    int64_t n_nodes = 0;
+    float4* nodes = nullptr;       // n_nodes * 4 float4 (64 B each)
+    float4* tris = nullptr;        // n_tri * 3 float4, BVH leaf order
+    float4* normals = nullptr;     // n_tri float4
+    int* inv_order = nullptr;      // original id -> leaf-order index
+    int depth = 0;                 // hierarchy depth (root = 1)
+    double build_ms = 0.0;
+};
+
+// Growable device scratch owned by the context.
+struct Scratch {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+struct Tuning {
+    int block_threads = 128;
+    int blocks_per_sm = 0;         // 0: from occupancy
+};
+
+}  // namespace rtmc
+
+struct rtmc_ctx {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<rtmc::DeviceMesh> meshes;
+    float* delta = nullptr;
+    rtmc_grid grid{};
+    rtmc_emission emission{};
+    bool table_loaded = false;
+    // run buffers
+    rtmc::Scratch q_oe[2], q_dt[2], q_id[2], hits, kcount, ctl, tally, hist, wraps, records, tmp;
+    std::string err;
+    int fail(int code, const std::string& msg) { err = msg; return code; }
+};
+
+namespace rtmc {
+
+// Ensure a scratch buffer holds at least `bytes`; returns cudaSuccess or the error.
+cudaError_t scratch_reserve(Scratch& s, size_t bytes);
+void scratch_free(Scratch& s);
+
+// LBVH build (rtmc_bvh.cu).
+int build_lbvh(rtmc_ctx* ctx, DeviceMesh& m);
+
+// Wavefront launchers (rtmc_trace.cu).
+struct RunParams {
+    unsigned long long seed;
+    unsigned item;
+    float energy, theta_rad;
+    int random_azimuth;
+    float src_x0, src_x1, src_y0, src_y1;
+    float lx, ly, z_min, z_top;
+    int max_wraps;
+    int n_ebins, n_abins;
+    float ebin_w;                // eV per energy bin
+    float inv_abin;              // bins per radian of polar angle
+    unsigned long long prim_offset;
+};
+
+struct Queues {
+    float4* oe[2];
+    float4* dt[2];
+    uint4* id[2];
+    float4* hits;
+    int* wraps;                  // record mode only
+    unsigned* kcount;
+    Control* ctl;
+    Tally* tally;
+    unsigned long long* hist_e;  // device, n_ebins
+    unsigned long long* hist_a;  // device, n_abins
+    unsigned long long* prim_hash;  // optional
+    rtmc_record* records;        // optional (device)
+    unsigned long long rec_cap;
+    unsigned cap[2];
+};
+
+cudaError_t launch_generate(const RunParams& p, const Queues& q, int buf, unsigned long long first,
+                            unsigned n, cudaStream_t s);
+cudaError_t launch_traverse(const DeviceMesh& m, const RunParams& p, const Queues& q, int buf,
+                            int gen, int num_sms, const Tuning& tune, bool record, bool count,
+                            cudaStream_t s);
+cudaError_t launch_shade(const DeviceMesh& m, const RunParams& p, const TableDesc& tab,
+                         const Emission& em, const Queues& q, int buf, int gen,
+                         unsigned long long chunk_first, int num_sms, bool record, cudaStream_t s);
+cudaError_t launch_finalize(const Queues& q, unsigned n, cudaStream_t s);
+cudaError_t launch_trace_rays(const DeviceMesh& m, const float* o, const float* d, const int* skip,
+                              int64_t n, rtmc_hit* hits, unsigned* status, cudaStream_t s);
+cudaError_t launch_philox(const uint32_t* ctr, int64_t n, unsigned long long key, uint32_t* out,
+                          cudaStream_t s);
+
+}  // namespace rtmc

@@ -1,0 +1,646 @@
+// rtmc_trace.cu -- wavefront RTMC kernels (sm_103a).
+//
+// One chunk of primaries is processed as generations of rays held in
+// structure-of-arrays queues in HBM (paper Section 2.2: daughters are
+// appended to the end of the ray tree; here a whole generation is one queue):
+//   generate  : primaries from Philox streams           -> queue 0
+//   traverse  : persistent warps pull 32-ray tiles; BVH closest hit with a
+//               shared-memory short stack; periodic cell walk  -> hits
+//   shade     : escape tallies / yield-table lookup / Poisson count; a block
+//               prefix over the counts compacts the daughters, which are then
+//               expanded one per thread into queue g+1
+//   finalize  : per-primary escape counts -> sum k, sum k^2
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstdint>
+
+#include "rtmc_internal.h"
+
+namespace rtmc {
+namespace {
+
+constexpr int kShadeThreads = 256;
+constexpr int kSmemStack = 16;        // stack entries held in shared memory per ray
+constexpr float kRobust = 1.0000004f; // 1 + 2 gamma_3 (Ize 2013): conservative slab test
+
+__device__ __forceinline__ float4 ldg4(const float4* p) { return __ldg(p); }
+
+// --------------------------------------------------------------------------
+// generate
+// --------------------------------------------------------------------------
+__global__ void k_generate(RunParams p, float sin_t, float cos_t, unsigned long long first,
+                           unsigned n, float4* __restrict__ oe, float4* __restrict__ dt,
+                           uint4* __restrict__ id, Control* __restrict__ ctl)
+{
+    const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) ctl->count[0] = n;
+    if (i >= n) return;
+    const unsigned long long prim = p.prim_offset + first + i;
+    const unsigned plo = (unsigned)prim, phi = (unsigned)(prim >> 32);
+    const uint4 w = ray_block(p.seed, plo, phi, 1u, p.item);
+    const float x = p.src_x0 + u01(w.x) * (p.src_x1 - p.src_x0);
+    const float y = p.src_y0 + u01(w.y) * (p.src_y1 - p.src_y0);
+    float ca = 1.f, sa = 0.f;
+    if (p.random_azimuth) sincospif(2.0f * u01(w.z), &sa, &ca);
+    oe[i] = make_float4(x, y, p.z_top, p.energy);
+    dt[i] = make_float4(sin_t * ca, sin_t * sa, -cos_t, __int_as_float(-1));
+    id[i] = make_uint4(plo, phi, 1u, 0u);
+}
+
+// --------------------------------------------------------------------------
+// traverse: BVH closest hit in one cell + periodic walk
+// --------------------------------------------------------------------------
+struct StackRef {
+    int2* smem;       // [kSmemStack][blockDim]
+    int stride;
+    int tid;
+};
+
+__device__ __forceinline__ void slab2(const float4 n0, const float4 n1, const float4 n2, const RaySetup& r,
+                                      float t_best, float& tmin0, float& tmin1, bool& h0, bool& h1)
+{
+    const float lx0 = (n0.x - r.o.x) * r.inv.x, hx0 = (n0.y - r.o.x) * r.inv.x;
+    const float ly0 = (n0.z - r.o.y) * r.inv.y, hy0 = (n0.w - r.o.y) * r.inv.y;
+    const float lz0 = (n2.x - r.o.z) * r.inv.z, hz0 = (n2.y - r.o.z) * r.inv.z;
+    const float lx1 = (n1.x - r.o.x) * r.inv.x, hx1 = (n1.y - r.o.x) * r.inv.x;
+    const float ly1 = (n1.z - r.o.y) * r.inv.y, hy1 = (n1.w - r.o.y) * r.inv.y;
+    const float lz1 = (n2.z - r.o.z) * r.inv.z, hz1 = (n2.w - r.o.z) * r.inv.z;
+    tmin0 = fmaxf(fmaxf(fminf(lx0, hx0), fminf(ly0, hy0)), fmaxf(fminf(lz0, hz0), 0.f));
+    const float tmax0 = fminf(fminf(fmaxf(lx0, hx0), fmaxf(ly0, hy0)), fminf(fmaxf(lz0, hz0), t_best));
+    tmin1 = fmaxf(fmaxf(fminf(lx1, hx1), fminf(ly1, hy1)), fmaxf(fminf(lz1, hz1), 0.f));
+    const float tmax1 = fminf(fminf(fmaxf(lx1, hx1), fmaxf(ly1, hy1)), fminf(fmaxf(lz1, hz1), t_best));
+    h0 = tmin0 <= tmax0 * kRobust;
+    h1 = tmin1 <= tmax1 * kRobust;
+}
+
+struct Counts { unsigned visits = 0, tests = 0; };
+
+// Closest front-facing triangle (leaf order index) with t > 0, skipping `skip`.
+template <bool COUNT = false>
+__device__ __forceinline__ int bvh_closest(const float4* __restrict__ nodes, const float4* __restrict__ tris,
+                                           const RaySetup& r, int skip, StackRef st, float& t_best,
+                                           float& bu, float& bv, unsigned& status, Counts* cnt = nullptr)
+{
+    int2 lstack[kStackMax - kSmemStack];
+    int sp = 0;
+    int node = 0;
+    int best = -1, best_orig = INT_MAX;
+    t_best = INFINITY;
+    bu = bv = 0.f;
+    for (int visits = 0;; ++visits) {
+        if (visits >= kMaxVisits) { status |= ST_LOOP_LIMIT; break; }
+        if (COUNT) ++cnt->visits;
+        const float4* np = nodes + 4ll * node;
+        const float4 n0 = ldg4(np), n1 = ldg4(np + 1), n2 = ldg4(np + 2), n3 = ldg4(np + 3);
+        float tmin0, tmin1;
+        bool h0, h1;
+        slab2(n0, n1, n2, r, t_best, tmin0, tmin1, h0, h1);
+        const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+        if (h0 && c0 < 0) {
+            const int j = ~c0;
+            if (j != skip) {
+                if (COUNT) ++cnt->tests;
+                const float4* tp = tris + 3ll * j;
+                if (intersect_tri(r, ldg4(tp), ldg4(tp + 1), ldg4(tp + 2), t_best, best_orig, bu, bv)) best = j;
+            }
+            h0 = false;
+        }
+        if (h1 && c1 < 0) {
+            const int j = ~c1;
+            if (j != skip) {
+                if (COUNT) ++cnt->tests;
+                const float4* tp = tris + 3ll * j;
+                if (intersect_tri(r, ldg4(tp), ldg4(tp + 1), ldg4(tp + 2), t_best, best_orig, bu, bv)) best = j;
+            }
+            h1 = false;
+        }
+        if (h0 && h1) {
+            int near = c0, far = c1;
+            float tfar = tmin1;
+            if (tmin1 < tmin0) { near = c1; far = c0; tfar = tmin0; }
+            const int2 e = make_int2(far, __float_as_int(tfar));
+            if (sp < kSmemStack) st.smem[sp * st.stride + st.tid] = e;
+            else if (sp < kStackMax) lstack[sp - kSmemStack] = e;
+            else { status |= ST_STACK_OVERFLOW; sp = kStackMax - 1; }
+            ++sp;
+            node = near;
+            continue;
+        }
+        if (h0) { node = c0; continue; }
+        if (h1) { node = c1; continue; }
+        bool found = false;
+        while (sp > 0) {
+            --sp;
+            const int2 e = sp < kSmemStack ? st.smem[sp * st.stride + st.tid] : lstack[sp - kSmemStack];
+            if (__int_as_float(e.y) <= t_best * kRobust) { node = e.x; found = true; break; }
+        }
+        if (!found) break;
+    }
+    return best;
+}
+
+struct Cell { float lx, ly, z_min, z_top; int max_wraps; };
+
+// Trace one ray segment by segment through the periodic cell (Section 2.2,
+// last paragraph).  Returns the hit record; *wraps gets the lateral re-entries.
+template <bool COUNT>
+__device__ __forceinline__ float4 trace_ray(const float4* __restrict__ nodes, const float4* __restrict__ tris,
+                                            float3 o, const float3 d, int skip, const Cell& c, StackRef st,
+                                            int& wraps, unsigned& status, Counts* cnt)
+{
+    wraps = 0;
+    for (;;) {
+        const RaySetup rs = setup_ray(o, d);
+        float t, u, v;
+        const int j = bvh_closest<COUNT>(nodes, tris, rs, skip, st, t, u, v, status, cnt);
+        if (j >= 0) return make_float4(t, u, v, __int_as_float(j));
+        float tx = INFINITY, ty = INFINITY, tz = INFINITY;
+        if (d.x > 0.f) tx = (c.lx - o.x) / d.x; else if (d.x < 0.f) tx = (0.f - o.x) / d.x;
+        if (d.y > 0.f) ty = (c.ly - o.y) / d.y; else if (d.y < 0.f) ty = (0.f - o.y) / d.y;
+        if (d.z > 0.f) tz = (c.z_top - o.z) / d.z; else if (d.z < 0.f) tz = (c.z_min - o.z) / d.z;
+        if (tz < tx && tz < ty)
+            return make_float4(tz, 0.f, 0.f, __int_as_float(d.z > 0.f ? HIT_ESCAPE : HIT_LOST));
+        if (++wraps > c.max_wraps) return make_float4(fminf(tx, ty), 0.f, 0.f, __int_as_float(HIT_LOST));
+        if (tx <= ty) {
+            o.y = o.y + tx * d.y;
+            o.z = o.z + tx * d.z;
+            o.x = d.x > 0.f ? 0.f : c.lx;
+        } else {
+            o.x = o.x + ty * d.x;
+            o.z = o.z + ty * d.z;
+            o.y = d.y > 0.f ? 0.f : c.ly;
+        }
+        skip = -1;
+    }
+}
+
+template <bool RECORD, bool COUNT>
+__global__ void __launch_bounds__(128)
+k_traverse(const float4* __restrict__ nodes, const float4* __restrict__ tris, Cell cell,
+           const float4* __restrict__ oe, const float4* __restrict__ dt, float4* __restrict__ hits,
+           int* __restrict__ wraps_out, Control* __restrict__ ctl, int gen, unsigned cap,
+           Tally* __restrict__ tally)
+{
+    extern __shared__ int2 s_stack[];
+    const StackRef st{s_stack, (int)blockDim.x, (int)threadIdx.x};
+    const unsigned n = min(*((volatile unsigned*)&ctl->count[gen]), cap);
+    const int lane = threadIdx.x & 31;
+    unsigned long long my_wraps = 0;
+    unsigned status = 0;
+    Counts cnt;
+    for (;;) {
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(&ctl->next[gen], 32u);
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        if (base >= n) break;
+        const unsigned i = base + lane;
+        if (i < n) {
+            const float4 a = oe[i], b = dt[i];
+            int w;
+            const float4 h = trace_ray<COUNT>(nodes, tris, make_float3(a.x, a.y, a.z), make_float3(b.x, b.y, b.z),
+                                              __float_as_int(b.w), cell, st, w, status, &cnt);
+            hits[i] = h;
+            my_wraps += (unsigned)w;
+            if (RECORD) wraps_out[i] = w;
+        }
+    }
+    for (int off = 16; off; off >>= 1) {
+        my_wraps += __shfl_xor_sync(0xFFFFFFFFu, my_wraps, off);
+        status |= __shfl_xor_sync(0xFFFFFFFFu, status, off);
+    }
+    if (COUNT) {
+        unsigned long long v = cnt.visits, t = cnt.tests;
+        for (int off = 16; off; off >>= 1) {
+            v += __shfl_xor_sync(0xFFFFFFFFu, v, off);
+            t += __shfl_xor_sync(0xFFFFFFFFu, t, off);
+        }
+        if (lane == 0) { atomicAdd(&tally->node_visits, v); atomicAdd(&tally->tri_tests, t); }
+    }
+    if (lane == 0) {
+        if (my_wraps) atomicAdd(&tally->wraps, my_wraps);
+        if (status) atomicOr(&tally->status, (unsigned long long)status);
+    }
+}
+
+// --------------------------------------------------------------------------
+// shade
+// --------------------------------------------------------------------------
+__device__ __forceinline__ float lookup_delta(const TableDesc& t, float e, float alpha)
+{
+    float x = (__logf(e) - t.log_e_lo) * t.inv_log_span;
+    x = fminf(fmaxf(x, 0.f), (float)(t.n_e - 1));
+    int i = min((int)x, t.n_e - 2);
+    const float fx = x - (float)i;
+    float y = alpha * 57.295779513082321f * t.inv_theta_step_deg;
+    y = fminf(fmaxf(y, 0.f), (float)(t.n_theta - 1));
+    const int j = min((int)y, t.n_theta - 2);
+    const float fy = y - (float)j;
+    const float* r0 = t.delta + i * t.n_theta + j;
+    const float* r1 = r0 + t.n_theta;
+    const float t00 = __ldg(r0), t01 = __ldg(r0 + 1), t10 = __ldg(r1), t11 = __ldg(r1 + 1);
+    return (1.f - fx) * ((1.f - fy) * t00 + fy * t01) + fx * ((1.f - fy) * t10 + fy * t11);
+}
+
+__device__ __forceinline__ int poisson_inv(float lam, float u, int k_max, int& capped)
+{
+    float p = expf(-lam);
+    float cdf = p;
+    capped = 0;
+    for (int k = 0; k < k_max; ++k) {
+        if (u < cdf) return k;
+        p *= lam / (float)(k + 1);
+        cdf += p;
+    }
+    if (!(u < cdf)) capped = 1;
+    return k_max;
+}
+
+// Inverse of the truncated spectrum CDF 1 - 3 s^2 + 2 s^3, s = phi/(E+phi):
+// smoothstep(s) = 3 s^2 - 2 s^3 = 1 - y, solved as s = 1/2 - sin(asin(2y - 1)/3).
+__device__ __forceinline__ float sample_energy(const Emission& em, float u)
+{
+    const float y = u * em.spec_norm;
+    const float s = 0.5f - sinf(asinf(fmaf(2.f, y, -1.f)) * (1.0f / 3.0f));
+    return fminf(em.phi * (1.0f / s - 1.0f), em.e_cut);
+}
+
+// Cosine-law direction about n in the basis of Duff et al. (JCGT 2017).
+__device__ __forceinline__ float3 cosine_dir(float3 n, float u1, float u2)
+{
+    const float sgn = n.z >= 0.f ? 1.f : -1.f;
+    const float a = -1.0f / (sgn + n.z);
+    const float b = n.x * n.y * a;
+    const float3 t1 = make_float3(1.f + sgn * n.x * n.x * a, sgn * b, -sgn * n.x);
+    const float3 t2 = make_float3(b, sgn + n.y * n.y * a, -n.y);
+    const float st = sqrtf(u1), ct = sqrtf(1.f - u1);
+    float sp, cp;
+    sincospif(2.0f * u2, &sp, &cp);
+    const float x = st * cp, y = st * sp;
+    return make_float3(x * t1.x + y * t2.x + ct * n.x, x * t1.y + y * t2.y + ct * n.y,
+                       x * t1.z + y * t2.z + ct * n.z);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+    for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, off);
+    return v;
+}
+
+struct ShadeOut {
+    float4* oe;
+    float4* dt;
+    uint4* id;
+    unsigned cap;
+};
+
+template <bool RECORD>
+__global__ void __launch_bounds__(kShadeThreads)
+k_shade(const float4* __restrict__ tris, const float4* __restrict__ normals, TableDesc tab, Emission em,
+        RunParams p, const float4* __restrict__ oe, const float4* __restrict__ dt, const uint4* __restrict__ id,
+        const float4* __restrict__ hits, const int* __restrict__ wraps_in, ShadeOut out,
+        Control* __restrict__ ctl, int gen, unsigned cap_in, Tally* __restrict__ tally,
+        unsigned long long* __restrict__ hist_e, unsigned long long* __restrict__ hist_a,
+        unsigned* __restrict__ kcount, unsigned long long chunk_first,
+        unsigned long long* __restrict__ prim_hash, rtmc_record* __restrict__ records,
+        unsigned long long rec_cap)
+{
+    extern __shared__ unsigned s_hist[];              // n_ebins + n_abins
+    __shared__ unsigned s_excl[kShadeThreads + 1];
+    __shared__ unsigned s_warp[kShadeThreads / 32];
+    __shared__ float s_px[kShadeThreads], s_py[kShadeThreads], s_pz[kShadeThreads];
+    __shared__ float s_nx[kShadeThreads], s_ny[kShadeThreads], s_nz[kShadeThreads];
+    __shared__ uint4 s_id[kShadeThreads];
+    __shared__ int s_tri[kShadeThreads];
+    __shared__ unsigned s_base;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int b = tid; b < p.n_ebins + p.n_abins; b += kShadeThreads) s_hist[b] = 0u;
+    unsigned *sh_e = s_hist, *sh_a = s_hist + p.n_ebins;
+    const unsigned n = min(*((volatile unsigned*)&ctl->count[gen]), cap_in);
+    unsigned c_rays = 0, c_esc = 0, c_lost = 0, c_low = 0, c_other = 0, c_emit = 0, c_regen = 0,
+             c_emitted = 0, c_capped = 0;
+    double e_sum = 0.0, e2_sum = 0.0;
+    __syncthreads();
+
+    for (unsigned tile = blockIdx.x; tile * kShadeThreads < n; tile += gridDim.x) {
+        const unsigned i = tile * kShadeThreads + tid;
+        unsigned k = 0;
+        if (i < n) {
+            const float4 a = oe[i], b = dt[i], h = hits[i];
+            const uint4 rid = id[i];
+            const int tri = __float_as_int(h.w);
+            const unsigned g = rid.w;
+            const float E = a.w;
+            int fate, orig = -1, e_bin = -1, a_bin = -1, kk = 0;
+            ++c_rays;
+            if (tri == HIT_ESCAPE && g > 0) {
+                fate = RTMC_ESCAPED;
+                ++c_esc;
+                e_bin = max(0, min((int)(E / p.ebin_w), p.n_ebins - 1));
+                const float pol = acosf(fminf(1.f, b.z));
+                a_bin = max(0, min((int)(pol * p.inv_abin), p.n_abins - 1));
+                atomicAdd(&sh_e[e_bin], 1u);
+                atomicAdd(&sh_a[a_bin], 1u);
+                const unsigned long long prim = ((unsigned long long)rid.y << 32) | rid.x;
+                atomicAdd(&kcount[prim - p.prim_offset - chunk_first], 1u);
+                e_sum += (double)E;
+                e2_sum += (double)E * (double)E;
+            } else if (tri < 0) {
+                fate = RTMC_LOST;
+                ++c_lost;
+            } else {
+                const float4 w0 = ldg4(tris + 3ll * tri);
+                orig = __float_as_int(w0.w);
+                const bool emits = g == 0 || ((int)g < em.max_generation && E >= em.regen_min);
+                if (!emits) {
+                    if (E < em.absorb_min) { fate = RTMC_ABSORBED_LOW; ++c_low; }
+                    else { fate = RTMC_ABSORBED_OTHER; ++c_other; }
+                } else {
+                    fate = RTMC_EMITTER;
+                    ++c_emit;
+                    if (g > 0) ++c_regen;
+                    const float4 nr = ldg4(normals + tri);
+                    const float cosa = -(b.x * nr.x + b.y * nr.y + b.z * nr.z);
+                    const float alpha = acosf(fminf(1.f, cosa));
+                    const float lam = lookup_delta(tab, E, alpha);
+                    const uint4 w = ray_block(p.seed, rid.x, rid.y, rid.z, p.item);
+                    int capped;
+                    kk = poisson_inv(lam, u01(w.w), em.k_max, capped);
+                    c_capped += capped;
+                    c_emitted += kk;
+                    k = kk;
+                    const float4 w1 = ldg4(tris + 3ll * tri + 1), w2 = ldg4(tris + 3ll * tri + 2);
+                    const float bw = 1.f - h.y - h.z;
+                    s_px[tid] = bw * w0.x + h.y * w1.x + h.z * w2.x;
+                    s_py[tid] = bw * w0.y + h.y * w1.y + h.z * w2.y;
+                    s_pz[tid] = bw * w0.z + h.y * w1.z + h.z * w2.z;
+                    s_nx[tid] = nr.x; s_ny[tid] = nr.y; s_nz[tid] = nr.z;
+                    s_id[tid] = make_uint4(rid.x, rid.y, rid.z, g + 1);
+                    s_tri[tid] = tri;
+                }
+            }
+            if (RECORD || prim_hash) {
+                const unsigned long long prim = ((unsigned long long)rid.y << 32) | rid.x;
+                const int wr = wraps_in ? wraps_in[i] : 0;
+                if (prim_hash)
+                    atomicAdd(&prim_hash[prim - p.prim_offset],
+                              record_hash_fields(prim, rid.z, fate, orig, kk, e_bin, a_bin, wr));
+                if (RECORD) {
+                    const unsigned long long slot = atomicAdd(&tally->rays_recorded, 1ull);
+                    if (slot < rec_cap) {
+                        rtmc_record r;
+                        r.prim = prim; r.path = rid.z; r.gen = (int)g; r.fate = fate; r.tri = orig;
+                        r.k = kk; r.e_bin = e_bin; r.a_bin = a_bin; r.wraps = wr;
+                        r.t = (double)h.x; r.energy = (double)E;
+                        records[slot] = r;
+                    } else {
+                        atomicOr(&tally->status, (unsigned long long)ST_RECORD_OVERFLOW);
+                    }
+                }
+            }
+        }
+        // block exclusive prefix of the daughter counts (warp shuffles + warp totals)
+        unsigned incl = k;
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned v = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+            if (lane >= off) incl += v;
+        }
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned v = lane < kShadeThreads / 32 ? s_warp[lane] : 0u;
+            for (int off = 1; off < 32; off <<= 1) {
+                const unsigned u = __shfl_up_sync(0xFFFFFFFFu, v, off);
+                if (lane >= off) v += u;
+            }
+            if (lane < kShadeThreads / 32) s_warp[lane] = v;     // inclusive warp totals
+        }
+        __syncthreads();
+        const unsigned warp_off = warp ? s_warp[warp - 1] : 0u;
+        s_excl[tid] = warp_off + incl - k;
+        const unsigned total = s_warp[kShadeThreads / 32 - 1];
+        if (tid == 0) {
+            s_excl[kShadeThreads] = total;
+            s_base = total ? atomicAdd(&ctl->count[gen + 1], total) : 0u;
+        }
+        __syncthreads();
+        // expand: daughter slot s belongs to the last parent with excl <= s
+        const unsigned base = s_base;
+        for (unsigned s = tid; s < total; s += kShadeThreads) {
+            int lo = 0, hi = kShadeThreads - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_excl[mid] <= s) lo = mid; else hi = mid - 1;
+            }
+            const int par = lo;
+            const unsigned j = s - s_excl[par];
+            const uint4 pid = s_id[par];
+            const unsigned path = pid.z * 16u + j;
+            const uint4 w = ray_block(p.seed, pid.x, pid.y, path, p.item);
+            const float e = sample_energy(em, u01(w.x));
+            const float3 dd = cosine_dir(make_float3(s_nx[par], s_ny[par], s_nz[par]), u01(w.y), u01(w.z));
+            const unsigned slot = base + s;
+            if (slot < out.cap) {
+                out.oe[slot] = make_float4(s_px[par], s_py[par], s_pz[par], e);
+                out.dt[slot] = make_float4(dd.x, dd.y, dd.z, __int_as_float(s_tri[par]));
+                out.id[slot] = make_uint4(pid.x, pid.y, path, pid.w);
+            } else {
+                atomicOr(&tally->status, (unsigned long long)ST_QUEUE_OVERFLOW);
+            }
+        }
+        __syncthreads();
+    }
+    // block reduction of the counters -> one atomic per counter per block
+    __shared__ unsigned long long s_red[9][kShadeThreads / 32];
+    __shared__ double s_dred[2][kShadeThreads / 32];
+    const unsigned cs[9] = {c_rays, c_esc, c_lost, c_low, c_other, c_emit, c_regen, c_emitted, c_capped};
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        const unsigned v = warp_sum(cs[q]);
+        if (lane == 0) s_red[q][warp] = v;
+    }
+    const double es = warp_sum(e_sum), e2 = warp_sum(e2_sum);
+    if (lane == 0) { s_dred[0][warp] = es; s_dred[1][warp] = e2; }
+    __syncthreads();
+    if (tid < 9) {
+        unsigned long long v = 0;
+        for (int w = 0; w < kShadeThreads / 32; ++w) v += s_red[tid][w];
+        if (v) {
+            unsigned long long* dst[9] = {&tally->rays, &tally->escaped, &tally->lost, &tally->absorbed_low,
+                                          &tally->absorbed_other, &tally->emitters, &tally->regenerated,
+                                          &tally->emitted, &tally->capped};
+            atomicAdd(dst[tid], v);
+        }
+    } else if (tid < 11) {
+        double v = 0.0;
+        for (int w = 0; w < kShadeThreads / 32; ++w) v += s_dred[tid - 9][w];
+        if (v != 0.0) atomicAdd(tid == 9 ? &tally->e_sum : &tally->e2_sum, v);
+    }
+    for (int b = tid; b < p.n_ebins; b += kShadeThreads)
+        if (sh_e[b]) atomicAdd(&hist_e[b], (unsigned long long)sh_e[b]);
+    for (int b = tid; b < p.n_abins; b += kShadeThreads)
+        if (sh_a[b]) atomicAdd(&hist_a[b], (unsigned long long)sh_a[b]);
+}
+
+// --------------------------------------------------------------------------
+// finalize: per-primary escape counts -> sum k, sum k^2; resets the counts
+// --------------------------------------------------------------------------
+__global__ void k_finalize(unsigned* __restrict__ kcount, unsigned n, Tally* __restrict__ tally)
+{
+    unsigned long long s1 = 0, s2 = 0;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const unsigned k = kcount[i];
+        if (k) {
+            s1 += k;
+            s2 += (unsigned long long)k * k;
+            kcount[i] = 0u;
+        }
+    }
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    __shared__ unsigned long long r1[8], r2[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { r1[warp] = s1; r2[warp] = s2; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long a = 0, b = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += r1[w]; b += r2[w]; }
+        if (a) { atomicAdd(&tally->sum_k, a); atomicAdd(&tally->sum_k2, b); }
+    }
+}
+
+// --------------------------------------------------------------------------
+// test hooks
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(128)
+k_trace_rays(const float4* __restrict__ nodes, const float4* __restrict__ tris, const int* __restrict__ inv_order,
+             int n_tri, const float* __restrict__ o, const float* __restrict__ d, const int* __restrict__ skip,
+             int64_t n, rtmc_hit* __restrict__ hits, unsigned* __restrict__ status_out)
+{
+    extern __shared__ int2 s_stack[];
+    const StackRef st{s_stack, (int)blockDim.x, (int)threadIdx.x};
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float3 oo = make_float3(o[3 * i], o[3 * i + 1], o[3 * i + 2]);
+    const float3 dd = make_float3(d[3 * i], d[3 * i + 1], d[3 * i + 2]);
+    const int sk = (skip && skip[i] >= 0 && skip[i] < n_tri) ? inv_order[skip[i]] : -1;
+    unsigned status = 0;
+    float t, u, v;
+    const int j = bvh_closest(nodes, tris, setup_ray(oo, dd), sk, st, t, u, v, status);
+    rtmc_hit h;
+    h.t = t; h.u = u; h.v = v;
+    h.tri = j >= 0 ? __float_as_int(__ldg(tris + 3ll * j).w) : -1;
+    hits[i] = h;
+    if (status) atomicOr(status_out, status);
+}
+
+__global__ void k_philox(const uint4* __restrict__ ctr, int64_t n, unsigned long long key, uint4* __restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] = philox4x32_10(ctr[i], make_uint2((unsigned)key, (unsigned)(key >> 32)));
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------
+// launchers
+// ----------------------------------------------------------------------------
+cudaError_t launch_generate(const RunParams& p, const Queues& q, int buf, unsigned long long first,
+                            unsigned n, cudaStream_t s)
+{
+    const double th = (double)p.theta_rad;
+    const int tb = 256;
+    const unsigned gb = n ? (n + tb - 1) / tb : 1;
+    k_generate<<<gb, tb, 0, s>>>(p, (float)sin(th), (float)cos(th), first, n, q.oe[buf], q.dt[buf],
+                                 q.id[buf], q.ctl);
+    return cudaGetLastError();
+}
+
+template <bool R, bool C>
+static int traverse_blocks_t(int num_sms, const Tuning& tune)
+{
+    if (tune.blocks_per_sm > 0) return num_sms * tune.blocks_per_sm;
+    int per_sm = 0;
+    const size_t smem = (size_t)kSmemStack * tune.block_threads * sizeof(int2);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse<R, C>, tune.block_threads, smem);
+    return num_sms * (per_sm > 0 ? per_sm : 1);
+}
+
+template <bool R, bool C>
+static cudaError_t traverse_t(const DeviceMesh& m, const RunParams& p, const Queues& q, int buf, int gen,
+                              int num_sms, const Tuning& tune, cudaStream_t s)
+{
+    const Cell cell{p.lx, p.ly, p.z_min, p.z_top, p.max_wraps};
+    const int blocks = traverse_blocks_t<R, C>(num_sms, tune);
+    const size_t smem = (size_t)kSmemStack * tune.block_threads * sizeof(int2);
+    k_traverse<R, C><<<blocks, tune.block_threads, smem, s>>>(m.nodes, m.tris, cell, q.oe[buf], q.dt[buf], q.hits,
+                                                              R ? q.wraps : nullptr, q.ctl, gen, q.cap[buf], q.tally);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_traverse(const DeviceMesh& m, const RunParams& p, const Queues& q, int buf, int gen,
+                            int num_sms, const Tuning& tune, bool record, bool count, cudaStream_t s)
+{
+    if (record) return count ? traverse_t<true, true>(m, p, q, buf, gen, num_sms, tune, s)
+                             : traverse_t<true, false>(m, p, q, buf, gen, num_sms, tune, s);
+    return count ? traverse_t<false, true>(m, p, q, buf, gen, num_sms, tune, s)
+                 : traverse_t<false, false>(m, p, q, buf, gen, num_sms, tune, s);
+}
+
+cudaError_t launch_shade(const DeviceMesh& m, const RunParams& p, const TableDesc& tab, const Emission& em,
+                         const Queues& q, int buf, int gen, unsigned long long chunk_first, int num_sms,
+                         bool record, cudaStream_t s)
+{
+    const int nb = 1 - buf;
+    const ShadeOut out{q.oe[nb], q.dt[nb], q.id[nb], q.cap[nb]};
+    const size_t smem = (size_t)(p.n_ebins + p.n_abins) * sizeof(unsigned);
+    const int blocks = num_sms * 4;
+    if (record)
+        k_shade<true><<<blocks, kShadeThreads, smem, s>>>(m.tris, m.normals, tab, em, p, q.oe[buf], q.dt[buf],
+                                                          q.id[buf], q.hits, q.wraps, out, q.ctl, gen, q.cap[buf], q.tally,
+                                                          q.hist_e, q.hist_a, q.kcount, chunk_first, q.prim_hash,
+                                                          q.records, q.rec_cap);
+    else
+        k_shade<false><<<blocks, kShadeThreads, smem, s>>>(m.tris, m.normals, tab, em, p, q.oe[buf], q.dt[buf],
+                                                           q.id[buf], q.hits, nullptr, out, q.ctl, gen, q.cap[buf], q.tally,
+                                                           q.hist_e, q.hist_a, q.kcount, chunk_first, q.prim_hash,
+                                                           nullptr, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const Queues& q, unsigned n, cudaStream_t s)
+{
+    const int tb = 256;
+    int gb = (int)((n + tb - 1) / tb);
+    if (gb > 4096) gb = 4096;
+    if (gb < 1) gb = 1;
+    k_finalize<<<gb, tb, 0, s>>>(q.kcount, n, q.tally);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trace_rays(const DeviceMesh& m, const float* o, const float* d, const int* skip, int64_t n,
+                              rtmc_hit* hits, unsigned* status, cudaStream_t s)
+{
+    const int tb = 128;
+    const size_t smem = (size_t)kSmemStack * tb * sizeof(int2);
+    const int64_t gb = (n + tb - 1) / tb;
+    if (gb > 0)
+        k_trace_rays<<<(unsigned)gb, tb, smem, s>>>(m.nodes, m.tris, m.inv_order, (int)m.n_tri, o, d, skip, n,
+                                                    hits, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_philox(const uint32_t* ctr, int64_t n, unsigned long long key, uint32_t* out, cudaStream_t s)
+{
+    const int tb = 256;
+    const int64_t gb = (n + tb - 1) / tb;
+    if (gb > 0)
+        k_philox<<<(unsigned)gb, tb, 0, s>>>(reinterpret_cast<const uint4*>(ctr), n, key,
+                                             reinterpret_cast<uint4*>(out));
+    return cudaGetLastError();
+}
+
+}  // namespace rtmc

@@ -1,0 +1,71 @@
+"""C-ABI checks that need no GPU: the library builds, loads and exports every
+declared entry point; host-only helpers behave as documented."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    src = open(os.path.join(ROOT, "include", "rtmc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rtmc_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_1806_00205_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    syms = _declared_symbols()
+    for s in ("rtmc_create", "rtmc_load_mesh", "rtmc_load_see_tables", "rtmc_build_bvh", "rtmc_run"):
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\s[TW]\s+(rtmc_\w+)", out))
+    missing = [s for s in _declared_symbols() if s not in exported]
+    assert not missing, missing
+
+
+def test_binding_loads_and_lists_exports(lib_path):
+    from paper_1806_00205_gb300 import rtmc
+    L = rtmc.lib()
+    assert set(rtmc.EXPORTS) == set(_declared_symbols())
+    for s in rtmc.EXPORTS:
+        assert hasattr(L, s)
+
+
+def test_record_hash_matches_documented_formula(lib_path):
+    from paper_1806_00205_gb300 import rtmc
+    from tests.parity import record_hashes
+    rng = np.random.default_rng(0)
+    rec = np.zeros(50, dtype=rtmc.RECORD_DTYPE)
+    rec["prim"] = rng.integers(0, 1 << 40, 50, dtype=np.uint64)
+    rec["path"] = rng.integers(1, 1 << 20, 50)
+    rec["fate"] = rng.integers(0, 5, 50)
+    rec["tri"] = rng.integers(-1, 10000, 50)
+    rec["k"] = rng.integers(0, 16, 50)
+    rec["e_bin"] = rng.integers(-1, 64, 50)
+    rec["a_bin"] = rng.integers(-1, 18, 50)
+    rec["wraps"] = rng.integers(0, 100, 50)
+    want = record_hashes(rec)
+    got = np.array([rtmc.record_hash(r) for r in rec], dtype=np.uint64)
+    assert np.array_equal(got, want)
+
+
+def test_create_without_gpu_fails_cleanly(lib_path):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1806_00205_gb300 import rtmc
+    with pytest.raises(rtmc.RtmcError):
+        rtmc.Context(0)

@@ -1,0 +1,259 @@
+"""CUDA path vs the FP64 oracle, through the C ABI (needs a GB300)."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1806_00205_gb300 import inputs as I
+from tests.parity import compare_records, primary_hashes
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+TABLE = I.see_table()
+E47 = float(TABLE.energy_grid()[47])
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1806_00205_gb300 import rtmc
+    c = rtmc.Context(0)
+    c.load_see_tables(TABLE)
+    yield c
+    c.close()
+
+
+def _mesh_id(ctx, mesh):
+    mid = ctx.load_mesh(mesh.tri, mesh.box)
+    ctx.build_bvh(mid)
+    return mid
+
+
+@pytest.fixture(scope="module")
+def tiny(ctx):
+    m = I.grf_foam(16, 0.5)
+    return m, _mesh_id(ctx, m)
+
+
+# ------------------------------------------------------------------ RNG ----
+
+def test_device_philox_known_answers(ctx):
+    rows = []
+    for line in open(os.path.join(HERE, "golden", "philox4x32_10_kat.txt")):
+        if line.strip() and not line.startswith("#"):
+            rows.append([int(x, 16) for x in line.split()])
+    for r in rows:
+        key = r[4] | (r[5] << 32)
+        out = ctx.philox(np.array(r[0:4], dtype=np.uint32), key)
+        assert list(out[0]) == r[6:10]
+
+
+def test_device_philox_matches_oracle(ctx):
+    rng = np.random.default_rng(1)
+    ctr = rng.integers(0, 1 << 32, (2000, 4), dtype=np.uint64).astype(np.uint32)
+    key = 0x123456789ABCDEF
+    dev = ctx.philox(ctr, key)
+    for i in range(0, 2000, 97):
+        want = O.philox(ctr[i], [key & 0xFFFFFFFF, key >> 32])
+        assert list(dev[i]) == list(want)
+
+
+# ------------------------------------------------------------- BVH hits ----
+
+def _rays_for(mesh, n, rng):
+    box = mesh.box
+    o = np.stack([rng.uniform(0, box.lx, n), rng.uniform(0, box.ly, n),
+                  rng.uniform(box.z_min + 0.3 * (box.z_top - box.z_min), box.z_top, n)], axis=1)
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    # rays aimed at vertices and edge midpoints (the edge cases of the test)
+    tri = mesh.tri.astype(np.float64)
+    k = n // 4
+    pick = rng.integers(0, mesh.n_tri, k)
+    tgt = np.where(rng.random(k)[:, None] < 0.5, tri[pick, 0], 0.5 * (tri[pick, 0] + tri[pick, 1]))
+    o2 = tgt + rng.normal(size=(k, 3)) * 5.0
+    d2 = tgt - o2
+    d2 /= np.linalg.norm(d2, axis=1)[:, None]
+    return np.concatenate([o, o2]).astype(np.float32), np.concatenate([d, d2]).astype(np.float32)
+
+
+@pytest.mark.parametrize("which", ["tiny", "flat", "well", "single", "foam8"])
+def test_bvh_closest_hit_matches_brute_force(ctx, which):
+    mesh = {"tiny": lambda: I.grf_foam(16, 0.5), "flat": lambda: I.flat_plane(),
+            "well": lambda: I.square_well(100.0, 60.0),
+            "single": lambda: I.Mesh(I.flat_plane().tri[:1], I.flat_plane().box),
+            "foam8": lambda: I.grf_foam(8, 0.7, 1.5, 3)}[which]()
+    mid = _mesh_id(ctx, mesh)
+    rng = np.random.default_rng(42)
+    o, d = _rays_for(mesh, 4000, rng)
+    skip = rng.integers(-1, mesh.n_tri, o.shape[0]).astype(np.int32)
+    skip[rng.random(o.shape[0]) < 0.5] = -1
+    hits = ctx.trace_rays(mid, o, d, skip)
+    same = 0
+    tri = mesh.tri.astype(np.float64)
+    for i in range(o.shape[0]):
+        t, j, u, v = O.closest_hit(mesh, o[i].astype(np.float64), d[i].astype(np.float64), int(skip[i]))
+        g = hits[i]
+        if g["tri"] == j:
+            same += 1
+            if j >= 0:
+                assert abs(g["t"] - t) <= 1e-5 * t + 1e-6, (i, g, t)
+        else:
+            # only a near-tie between two facets at the same point may differ
+            assert j >= 0 and g["tri"] >= 0, (i, g, j)
+            assert abs(g["t"] - t) <= 1e-4 * t + 1e-4, (i, g, t)
+    assert same >= 0.999 * o.shape[0]
+
+
+# ---------------------------------------------------------- full runs ------
+
+def test_tiny_config_records_match_oracle(ctx, tiny):
+    """Tiny config: 16^3 foam, 1e5 primaries at 300 eV, normal incidence."""
+    mesh, mid = tiny
+    n = 100_000
+    g = ctx.run_records(mid, 300.0, 0.0, n, seed=1806)
+    o = O.run(mesh, TABLE, 300.0, 0.0, n, seed=1806, records=True)
+    st = compare_records(g["records"], o["records"])
+    assert st["frac_same"] >= 0.9999, {k: v for k, v in st.items() if k != "mismatch"}
+    assert st["t_rel_max"] <= 1e-5 or st["t_rel_p9999"] <= 1e-5
+    for k in ("rays", "escaped", "emitted", "sum_k"):
+        assert abs(g[k] - o[k]) <= 2e-4 * max(1, o[k]) + 2, k
+    se = math.hypot(g["sey_se"], o["sey_se"])
+    assert abs(g["sey"] - o["sey"]) < min(3 * se, 1e-3)
+    assert g["lost"] == 0
+    assert g["rays"] == n + g["emitted"]
+    assert g["rays"] == g["escaped"] + g["absorbed_low"] + g["absorbed_other"] + g["emitters"] + g["lost"]
+
+
+def test_run_tallies_equal_record_tallies(ctx, tiny):
+    _, mid = tiny
+    n = 20_000
+    res, he, ha = ctx.run(mid, [300.0], [0.0], n, seed=5)
+    rr = ctx.run_records(mid, 300.0, 0.0, n, seed=5)
+    r = res[0]
+    for k in ("rays", "escaped", "emitted", "sum_k", "sum_k2", "wraps", "absorbed_low"):
+        assert r[k] == rr[k], k
+    esc = rr["records"][rr["records"]["fate"] == O.ESCAPED]
+    assert np.array_equal(np.bincount(esc["e_bin"], minlength=64), he[0].astype(np.int64))
+    assert np.array_equal(np.bincount(esc["a_bin"], minlength=18), ha[0].astype(np.int64))
+
+
+def test_flat_plane_gpu(ctx):
+    fp = I.flat_plane()
+    mid = _mesh_id(ctx, fp)
+    res, he, ha = ctx.run(mid, [E47], [0.0, 60.0], 1_000_000, seed=77)
+    for r, j in zip(res, (0, 12)):
+        lam = float(TABLE.delta[47, j])
+        assert r["lost"] == 0 and r["escaped"] == r["emitted"]
+        assert abs(r["sey"] - lam) < 3 * r["sey_se"], (r["sey"], lam)
+
+
+def test_square_well_view_factor_gpu(ctx):
+    from tests.test_oracle_pins import view_factor_squares
+    from paper_1806_00205_gb300 import rtmc
+    w = I.square_well(100.0, 100.0)
+    mid = _mesh_id(ctx, w)
+    res, _, _ = ctx.run(mid, [E47], [0.0], 2_000_000, seed=3,
+                        desc=rtmc.run_desc(window=I.opening_window(100.0)))
+    expect = float(TABLE.delta[47, 0]) * view_factor_squares(1.0)
+    assert abs(res[0]["sey"] - expect) < 3 * res[0]["sey_se"]
+
+
+def test_multi_item_run_equals_single_items(ctx, tiny):
+    _, mid = tiny
+    res, he, _ = ctx.run(mid, [100.0, 700.0], [0.0, 45.0], 5000, seed=9)
+    for item, (e, th) in enumerate([(100.0, 0.0), (100.0, 45.0), (700.0, 0.0), (700.0, 45.0)]):
+        one = ctx.run_records(mid, e, th, 5000, seed=9, item=item)
+        assert res[item]["sum_k"] == one["sum_k"] and res[item]["rays"] == one["rays"]
+
+
+def test_chunking_and_edge_sizes(ctx, tiny):
+    from paper_1806_00205_gb300 import rtmc
+    _, mid = tiny
+    ref, _, _ = ctx.run(mid, [300.0], [0.0], 2500, seed=4)
+    for chunk in (1000, 999, 2500, 4096):
+        r, _, _ = ctx.run(mid, [300.0], [0.0], 2500, seed=4, desc=rtmc.run_desc(chunk=chunk))
+        assert r[0]["sum_k"] == ref[0]["sum_k"] and r[0]["rays"] == ref[0]["rays"]
+    z, _, _ = ctx.run(mid, [300.0], [0.0], 0, seed=4)
+    assert z[0]["rays"] == 0 and z[0]["sey"] == 0.0
+    one = ctx.run_records(mid, 300.0, 0.0, 1, seed=4)
+    assert one["records"].size == one["rays"] >= 1
+
+
+def test_tertiaries_match_oracle(ctx):
+    from paper_1806_00205_gb300 import rtmc
+    mesh = I.grf_foam(16, 0.7, seed=4)
+    em = rtmc.Emission(regen_min_ev=20.0, max_generation=2)
+    c2 = rtmc.Context(0)
+    try:
+        c2.load_see_tables(TABLE, em)
+        mid = _mesh_id(c2, mesh)
+        n = 20_000
+        g = c2.run_records(mid, 500.0, 0.0, n, seed=6)
+        o = O.run(mesh, TABLE, 500.0, 0.0, n, seed=6, records=True,
+                  emission=O.Emission(regen_min_ev=20.0, max_generation=2))
+        st = compare_records(g["records"], o["records"])
+        assert st["frac_same"] >= 0.9999, {k: v for k, v in st.items() if k != "mismatch"}
+        assert g["regenerated"] > 0
+    finally:
+        c2.close()
+
+
+def test_random_azimuth_and_window_match_oracle(ctx, tiny):
+    from paper_1806_00205_gb300 import rtmc
+    mesh, mid = tiny
+    win = (20.0, 90.0, 30.0, 150.0)
+    n = 20_000
+    g = ctx.run_records(mid, 200.0, 50.0, n, seed=11, item=3,
+                        desc=rtmc.run_desc(random_azimuth=True, window=win))
+    o = O.run(mesh, TABLE, 200.0, 50.0, n, seed=11, item=3, random_azimuth=True, window=win, records=True)
+    st = compare_records(g["records"], o["records"])
+    assert st["frac_same"] >= 0.9999, {k: v for k, v in st.items() if k != "mismatch"}
+
+
+def test_wrap_limit_counts_lost(ctx):
+    from paper_1806_00205_gb300 import rtmc
+    fp = I.flat_plane(160.0, height=400.0)      # tall slab: many daughters need wraps
+    mid = _mesh_id(ctx, fp)
+    n = 20_000
+    g = ctx.run_records(mid, E47, 0.0, n, seed=2, desc=rtmc.run_desc(max_wraps=2))
+    o = O.run(fp, TABLE, E47, 0.0, n, seed=2, max_wraps=2, records=True)
+    assert g["lost"] > 0
+    st = compare_records(g["records"], o["records"])
+    assert st["frac_same"] >= 0.9999
+
+
+def test_prim_hash_matches_oracle(ctx, tiny):
+    import torch
+    from paper_1806_00205_gb300 import rtmc
+    mesh, mid = tiny
+    n = 50_000
+    h = torch.zeros(n, dtype=torch.int64, device="cuda")
+    ctx.run(mid, [300.0], [0.0], n, seed=21, desc=rtmc.run_desc(prim_hash=h))
+    dev = h.cpu().numpy().view(np.uint64)
+    ids = np.arange(0, n, 7, dtype=np.uint64)
+    o = O.run(mesh, TABLE, 300.0, 0.0, 0, seed=21, prim_ids=ids, records=True)
+    want = primary_hashes(o["records"], ids)
+    assert np.mean(dev[ids.astype(np.int64)] == want) >= 0.9995
+
+
+def test_errors_are_reported_not_faulted(ctx):
+    from paper_1806_00205_gb300 import rtmc
+    with pytest.raises(rtmc.RtmcError) as e:
+        ctx.run(12345, [300.0], [0.0], 10, seed=1)
+    assert e.value.code == -4
+    mid = ctx.load_mesh(I.flat_plane().tri, I.flat_plane().box)
+    with pytest.raises(rtmc.RtmcError) as e:
+        ctx.run(mid, [300.0], [0.0], 10, seed=1)
+    assert e.value.code == -5
+    ctx.build_bvh(mid)
+    with pytest.raises(rtmc.RtmcError) as e:
+        ctx.run(mid, [300.0], [95.0], 10, seed=1)
+    assert e.value.code == -1
+    with pytest.raises(rtmc.RtmcError):
+        ctx.run(mid, [-3.0], [0.0], 10, seed=1)
