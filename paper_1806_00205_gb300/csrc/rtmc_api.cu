@@ -91,6 +91,7 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
     cudaStream_t s = ctx->stream;
     const rtmc_emission& em = ctx->emission;
     const bool record = o.rec != nullptr;
+    const bool need_wraps = record || d.prim_hash != nullptr;   // wrap counts enter records and hashes
 
     RunParams p;
     p.seed = seed;
@@ -158,7 +159,7 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
             if (ce == cudaSuccess) ce = scratch_reserve(ctx->q_id[b], (size_t)c * 16);
         }
         if (ce == cudaSuccess) ce = scratch_reserve(ctx->hits, (size_t)capmax * 16);
-        if (ce == cudaSuccess && record) ce = scratch_reserve(ctx->wraps, (size_t)capmax * 4);
+        if (ce == cudaSuccess && need_wraps) ce = scratch_reserve(ctx->wraps, (size_t)capmax * 4);
         const bool kc_new = ctx->kcount.bytes < (size_t)chunk * 4;
         if (ce == cudaSuccess) ce = scratch_reserve(ctx->kcount, (size_t)chunk * 4);
         if (ce == cudaSuccess && kc_new) ce = cudaMemsetAsync(ctx->kcount.ptr, 0, ctx->kcount.bytes, s);
@@ -177,7 +178,7 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
         q.cap[0] = (unsigned)cap0;
         q.cap[1] = (unsigned)cap1;
         q.hits = (float4*)ctx->hits.ptr;
-        q.wraps = record ? (int*)ctx->wraps.ptr : nullptr;
+        q.wraps = need_wraps ? (int*)ctx->wraps.ptr : nullptr;
         q.kcount = (unsigned*)ctx->kcount.ptr;
         q.ctl = (Control*)ctx->ctl.ptr;
         q.tally = (Tally*)ctx->tally.ptr;
@@ -217,7 +218,7 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
             for (int g = 0; g <= em.max_generation && ce == cudaSuccess; ++g) {
                 const int buf = g & 1;
                 h = tick(1);
-                ce = launch_traverse(m, p, q, buf, g, ctx->num_sms, tune, record, d.count_visits != 0, s);
+                ce = launch_traverse(m, p, q, buf, g, ctx->num_sms, tune, need_wraps, d.count_visits != 0, s);
                 tock(h);
                 h = tick(2);
                 if (ce == cudaSuccess)

@@ -144,33 +144,39 @@ struct Cell { float lx, ly, z_min, z_top; int max_wraps; };
 
 // Trace one ray segment by segment through the periodic cell (Section 2.2,
 // last paragraph).  Returns the hit record; *wraps gets the lateral re-entries.
+// The re-entry point is carried in FP64 (a few operations per wrap) so that a
+// ray that wraps many times does not accumulate FP32 rounding in its origin;
+// each cell query uses that point rounded to FP32.
 template <bool COUNT>
 __device__ __forceinline__ float4 trace_ray(const float4* __restrict__ nodes, const float4* __restrict__ tris,
-                                            float3 o, const float3 d, int skip, const Cell& c, StackRef st,
+                                            const float3 o32, const float3 d, int skip, const Cell& c, StackRef st,
                                             int& wraps, unsigned& status, Counts* cnt)
 {
     wraps = 0;
+    double ox = o32.x, oy = o32.y, oz = o32.z;
+    float3 o = o32;
     for (;;) {
         const RaySetup rs = setup_ray(o, d);
         float t, u, v;
         const int j = bvh_closest<COUNT>(nodes, tris, rs, skip, st, t, u, v, status, cnt);
         if (j >= 0) return make_float4(t, u, v, __int_as_float(j));
-        float tx = INFINITY, ty = INFINITY, tz = INFINITY;
-        if (d.x > 0.f) tx = (c.lx - o.x) / d.x; else if (d.x < 0.f) tx = (0.f - o.x) / d.x;
-        if (d.y > 0.f) ty = (c.ly - o.y) / d.y; else if (d.y < 0.f) ty = (0.f - o.y) / d.y;
-        if (d.z > 0.f) tz = (c.z_top - o.z) / d.z; else if (d.z < 0.f) tz = (c.z_min - o.z) / d.z;
+        double tx = INFINITY, ty = INFINITY, tz = INFINITY;
+        if (d.x > 0.f) tx = ((double)c.lx - ox) / d.x; else if (d.x < 0.f) tx = (0.0 - ox) / d.x;
+        if (d.y > 0.f) ty = ((double)c.ly - oy) / d.y; else if (d.y < 0.f) ty = (0.0 - oy) / d.y;
+        if (d.z > 0.f) tz = ((double)c.z_top - oz) / d.z; else if (d.z < 0.f) tz = ((double)c.z_min - oz) / d.z;
         if (tz < tx && tz < ty)
-            return make_float4(tz, 0.f, 0.f, __int_as_float(d.z > 0.f ? HIT_ESCAPE : HIT_LOST));
-        if (++wraps > c.max_wraps) return make_float4(fminf(tx, ty), 0.f, 0.f, __int_as_float(HIT_LOST));
+            return make_float4((float)tz, 0.f, 0.f, __int_as_float(d.z > 0.f ? HIT_ESCAPE : HIT_LOST));
+        if (++wraps > c.max_wraps) return make_float4((float)fmin(tx, ty), 0.f, 0.f, __int_as_float(HIT_LOST));
         if (tx <= ty) {
-            o.y = o.y + tx * d.y;
-            o.z = o.z + tx * d.z;
-            o.x = d.x > 0.f ? 0.f : c.lx;
+            oy = oy + tx * d.y;
+            oz = oz + tx * d.z;
+            ox = d.x > 0.f ? 0.0 : (double)c.lx;
         } else {
-            o.x = o.x + ty * d.x;
-            o.z = o.z + ty * d.z;
-            o.y = d.y > 0.f ? 0.f : c.ly;
+            ox = ox + ty * d.x;
+            oz = oz + ty * d.z;
+            oy = d.y > 0.f ? 0.0 : (double)c.ly;
         }
+        o = make_float3((float)ox, (float)oy, (float)oz);
         skip = -1;
     }
 }
@@ -605,7 +611,7 @@ cudaError_t launch_shade(const DeviceMesh& m, const RunParams& p, const TableDes
                                                           q.records, q.rec_cap);
     else
         k_shade<false><<<blocks, kShadeThreads, smem, s>>>(m.tris, m.normals, tab, em, p, q.oe[buf], q.dt[buf],
-                                                           q.id[buf], q.hits, nullptr, out, q.ctl, gen, q.cap[buf], q.tally,
+                                                           q.id[buf], q.hits, q.prim_hash ? q.wraps : nullptr, out, q.ctl, gen, q.cap[buf], q.tally,
                                                            q.hist_e, q.hist_a, q.kcount, chunk_first, q.prim_hash,
                                                            nullptr, 0);
     return cudaGetLastError();
