@@ -170,6 +170,38 @@ int rtmc_trace_rays(rtmc_ctx* ctx, int32_t mesh_id, const float* o, const float*
    checking the device generator against the published vectors. */
 int rtmc_philox(rtmc_ctx* ctx, const uint32_t* ctr, int64_t n, uint64_t key, uint32_t* out);
 
+/* Scratch-free run of one (energy, angle) item.  The paper has no
+   counterpart: this entry point serves callers that must not allocate device
+   memory while they run, for example a process whose allocator reserved the
+   whole device up front so that nothing can fail for lack of memory later, or
+   a latency-bound loop that cannot afford cudaMalloc/cudaFree, which may
+   synchronise the device and stall other streams.  It computes what rtmc_run
+   computes for one item (same kernels, same random streams, same outputs)
+   but allocates nothing: it calls no cudaMalloc, cudaFree or allocating
+   library routine.  Its scratch (ray queues, hits, counters, histograms,
+   about 4.5 MiB) is one static device array compiled into librtmc, which
+   every GPU that loads the library keeps until the process exits.  The mesh,
+   BVH and tables still come from the context (loaded beforehand).
+   Limits, rejected with RTMC_ERR_INVALID_ARG and a message:
+     n_primaries <= RTMC_NOALLOC_MAX_PRIMARIES per call (advance
+       desc->primary_offset and call again for more primaries);
+     the loaded emission parameters must have max_generation == 1;
+     n_ebins + n_abins <= 1024.
+   desc->profile is ignored; desc->prim_hash (device, n_primaries entries)
+   and desc->count_visits work as in rtmc_run.
+   The first call on a device looks up the array's device address
+   (cudaGetSymbolAddress) with that device current; make that first call
+   before any stream capture.  Every call on a device uses the same array and
+   clears the counters it needs before it starts; calls whose GPU work
+   overlaps (other host threads, other contexts or streams on the same
+   device) race on the array and must be serialised by the caller.
+   Writes *out and, when non-NULL, hist_e[n_ebins] / hist_a[n_abins] (host). */
+#define RTMC_NOALLOC_MAX_PRIMARIES 4096
+int rtmc_run_noalloc(rtmc_ctx* ctx, int32_t mesh_id, double energy_ev, double theta_deg,
+                     uint32_t item, int64_t n_primaries, uint64_t seed,
+                     const rtmc_run_desc* desc, rtmc_result* out, uint64_t* hist_e,
+                     uint64_t* hist_a);
+
 /* Hash of one record (the per-primary hash is the sum mod 2^64 of the hashes
    of that primary's records): h = sm(prim); h = sm(h ^ (path | fate << 32));
    h = sm(h ^ (uint32 tri | uint32 k << 32)); h = sm(h ^ (uint32 e_bin |

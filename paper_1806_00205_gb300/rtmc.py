@@ -25,7 +25,8 @@ ESCAPED, EMITTER, ABSORBED_LOW, ABSORBED_OTHER, LOST = 0, 1, 2, 3, 4
 EXPORTS = ["rtmc_create", "rtmc_destroy", "rtmc_last_error", "rtmc_load_mesh", "rtmc_unload_mesh",
            "rtmc_load_see_tables",
            "rtmc_build_bvh", "rtmc_run", "rtmc_run_records", "rtmc_trace_rays", "rtmc_philox",
-           "rtmc_record_hash"]
+           "rtmc_record_hash", "rtmc_run_noalloc"]
+NOALLOC_MAX_PRIMARIES = 4096
 
 
 class RtmcError(RuntimeError):
@@ -103,6 +104,8 @@ def lib():
     L.rtmc_run_records.argtypes = [vp, i32, C.c_double, C.c_double, C.c_uint32, i64, u64, C.POINTER(RunDesc),
                                    C.POINTER(Result), vp, i64, C.POINTER(i64)]
     L.rtmc_trace_rays.argtypes = [vp, i32, vp, vp, vp, i64, vp]
+    L.rtmc_run_noalloc.argtypes = [vp, i32, C.c_double, C.c_double, C.c_uint32, i64, u64, C.POINTER(RunDesc),
+                                   C.POINTER(Result), vp, vp]
     L.rtmc_philox.argtypes = [vp, vp, i64, u64, vp]
     L.rtmc_record_hash.argtypes = [C.POINTER(Record)]
     L.rtmc_record_hash.restype = u64
@@ -232,6 +235,19 @@ class Context:
         out = result_dict(res)
         out["records"] = np.sort(rec[:n.value], order=["prim", "gen", "path"])
         return out
+
+    def run_noalloc(self, mesh_id, energy, theta, n_primaries, seed, item=0, desc=None):
+        """One item through rtmc_run_noalloc (static device scratch, no allocation).
+
+        Returns (result dict, hist_e, hist_a)."""
+        d = desc or run_desc()
+        res = Result()
+        he = np.zeros(d.n_ebins, dtype=np.uint64)
+        ha = np.zeros(d.n_abins, dtype=np.uint64)
+        self._check(self._L.rtmc_run_noalloc(self.h, int(mesh_id), float(energy), float(theta), int(item),
+                                             int(n_primaries), int(seed), C.byref(d), C.byref(res), _ptr(he),
+                                             _ptr(ha)))
+        return result_dict(res), he, ha
 
     def trace_rays(self, mesh_id, o, d, skip=None):
         o = np.ascontiguousarray(o, dtype=np.float32)
