@@ -43,6 +43,8 @@ extern "C" {
 #define RTMC_ERR_DEVICE_CHECK  -8
 
 #define RTMC_BVH_FP32 0     /* 64-byte nodes with FP32 child boxes */
+/* bvh_kind = node format | RTMC_BVH_LEAF(n): leaves of up to n (1..8) triangles, default 4 */
+#define RTMC_BVH_LEAF(n) ((n) << 8)
 
 /* Ray fates (per-ray records) */
 #define RTMC_ESCAPED        0
@@ -87,6 +89,8 @@ typedef struct {
                                       sum of record hashes (see rtmc_record_hash) */
     int32_t profile;               /* 1: time every kernel launch with CUDA events */
     int32_t count_visits;          /* 1: count BVH node visits and triangle tests */
+    int32_t traversal;             /* 0: default; 1: one ray per lane per 32-ray tile;
+                                      2: while-while loop with per-lane ray refill */
 } rtmc_run_desc;
 
 typedef struct {
@@ -138,7 +142,9 @@ int rtmc_load_see_tables(rtmc_ctx* ctx, const float* delta, const rtmc_grid* gri
 
 /* Build the linear BVH of a loaded mesh on the device: Morton codes of the
    triangle centroids, radix sort, Karras hierarchy, bottom-up box refit,
-   triangle repack.  `bvh_kind` is RTMC_BVH_FP32. */
+   triangle repack.  `bvh_kind` is RTMC_BVH_FP32, optionally or-ed with
+   RTMC_BVH_LEAF(n) to cap leaves at n triangles (subtrees with at most n
+   triangles become one leaf). */
 int rtmc_build_bvh(rtmc_ctx* ctx, int32_t mesh_id, int32_t bvh_kind);
 
 /* Run RTMC for every (energy, angle) pair: n_e * n_theta items, item

@@ -145,6 +145,7 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
     Tuning tune;
     if (d.block_threads > 0) tune.block_threads = d.block_threads;
     tune.blocks_per_sm = d.blocks_per_sm;
+    tune.traversal = d.traversal;
 
     for (int attempt = 0;; ++attempt) {
         const int64_t cap0 = chunk * mult[0], cap1 = chunk * mult[1];
@@ -320,8 +321,9 @@ int check_run_args(rtmc_ctx* ctx, int32_t mesh_id, int64_t n_primaries, const rt
     if (n_primaries < 0 || n_primaries > ((int64_t)1 << 40)) return ctx->fail(RTMC_ERR_INVALID_ARG, "run: n_primaries out of range");
     if (d.n_ebins <= 0 || d.n_ebins > 4096 || d.n_abins <= 0 || d.n_abins > 4096 || !(d.hist_e_max_ev > 0.0))
         return ctx->fail(RTMC_ERR_INVALID_ARG, "run: histogram shape");
-    if (d.block_threads != 0 && (d.block_threads % 32 != 0 || d.block_threads < 32 || d.block_threads > 1024))
-        return ctx->fail(RTMC_ERR_INVALID_ARG, "run: block_threads must be a multiple of 32 in [32, 1024]");
+    if (d.block_threads != 0 && (d.block_threads % 32 != 0 || d.block_threads < 32 || d.block_threads > 128))
+        return ctx->fail(RTMC_ERR_INVALID_ARG, "run: block_threads must be a multiple of 32 in [32, 128]");
+    if (d.traversal < 0 || d.traversal > 2) return ctx->fail(RTMC_ERR_INVALID_ARG, "run: unknown traversal variant");
     if (d.chunk < 0 || d.chunk > ((int64_t)1 << 28)) return ctx->fail(RTMC_ERR_INVALID_ARG, "run: chunk out of range");
     if (d.max_wraps < 0 || d.max_wraps > (1 << 20)) return ctx->fail(RTMC_ERR_INVALID_ARG, "run: max_wraps out of range");
     if (d.blocks_per_sm < 0 || d.blocks_per_sm > 64) return ctx->fail(RTMC_ERR_INVALID_ARG, "run: blocks_per_sm out of range");
@@ -450,10 +452,13 @@ int rtmc_build_bvh(rtmc_ctx* ctx, int32_t mesh_id, int32_t bvh_kind)
     if (!ctx) return RTMC_ERR_INVALID_ARG;
     if (mesh_id < 0 || mesh_id >= (int)ctx->meshes.size() || !ctx->meshes[mesh_id].tri_in)
         return ctx->fail(RTMC_ERR_NOT_LOADED, "build_bvh: unknown mesh id");
-    if (bvh_kind != RTMC_BVH_FP32) return ctx->fail(RTMC_ERR_INVALID_ARG, "build_bvh: unknown bvh kind");
+    const int format = bvh_kind & 0xFF, leaf = (bvh_kind >> 8) & 0xFF;
+    if (format != RTMC_BVH_FP32 || (bvh_kind >> 16) != 0 || leaf > 8)
+        return ctx->fail(RTMC_ERR_INVALID_ARG, "build_bvh: unknown bvh kind or leaf size > 8");
     DeviceGuard g(ctx->device);
     DeviceMesh& m = ctx->meshes[mesh_id];
-    m.kind = bvh_kind;
+    m.kind = format;
+    m.leaf_max = leaf ? leaf : 4;
     return rtmc::build_lbvh(ctx, m);
 }
 

@@ -157,7 +157,7 @@ __device__ __forceinline__ int common_prefix(const unsigned* __restrict__ k, int
 }
 
 __global__ void k_karras(const unsigned* __restrict__ keys, int n, int2* __restrict__ child,
-                         int* __restrict__ parent, int* __restrict__ leaf_parent)
+                         int2* __restrict__ range, int* __restrict__ parent, int* __restrict__ leaf_parent)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n - 1) return;
@@ -181,6 +181,7 @@ __global__ void k_karras(const unsigned* __restrict__ keys, int n, int2* __restr
     const int left = (lo == gamma) ? ~gamma : gamma;
     const int right = (hi == gamma + 1) ? ~(gamma + 1) : gamma + 1;
     child[i] = make_int2(left, right);
+    range[i] = make_int2(lo, hi);
     if (left < 0) leaf_parent[~left] = i; else parent[left] = i;
     if (right < 0) leaf_parent[~right] = i; else parent[right] = i;
     if (i == 0) parent[0] = -1;
@@ -209,10 +210,25 @@ __device__ __forceinline__ void store_node(float4* __restrict__ nodes, int i, co
     nd[3] = make_float4(__int_as_float(c0), __int_as_float(c1), 0.f, 0.f);
 }
 
+// Child reference stored in a node: an inner node index (>= 0), or a leaf
+// ~((first << 3) | (count - 1)) covering `count` <= 8 consecutive triangles of
+// the leaf order.  A Karras inner node covers a contiguous key range, so an
+// inner child whose range holds at most `leaf_max` triangles is stored as one
+// leaf over that range.
+__device__ __forceinline__ int child_ref(int c, const int2* __restrict__ range, int leaf_max)
+{
+    if (c < 0) return ~((~c) << 3);
+    const int2 r = range[c];
+    const int cnt = r.y - r.x + 1;
+    if (cnt <= leaf_max) return ~((r.x << 3) | (cnt - 1));
+    return c;
+}
+
 __global__ void k_refit(const float* __restrict__ tri, const unsigned* __restrict__ order, int n,
-                        const int2* __restrict__ child, const int* __restrict__ parent,
-                        const int* __restrict__ leaf_parent, unsigned* __restrict__ flag,
-                        float4* __restrict__ aabb, float4* __restrict__ nodes)
+                        const int2* __restrict__ child, const int2* __restrict__ range,
+                        const int* __restrict__ parent, const int* __restrict__ leaf_parent,
+                        unsigned* __restrict__ flag, float4* __restrict__ aabb, float4* __restrict__ nodes,
+                        int leaf_max)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
@@ -233,7 +249,7 @@ __global__ void k_refit(const float* __restrict__ tri, const unsigned* __restric
                 b[s].hi = make_float3(hi.x, hi.y, hi.z);
             }
         }
-        store_node(nodes, node, b[0], b[1], c.x, c.y);
+        store_node(nodes, node, b[0], b[1], child_ref(c.x, range, leaf_max), child_ref(c.y, range, leaf_max));
         __stcg(aabb + 2ll * node, make_float4(fminf(b[0].lo.x, b[1].lo.x), fminf(b[0].lo.y, b[1].lo.y),
                                               fminf(b[0].lo.z, b[1].lo.z), 0.f));
         __stcg(aabb + 2ll * node + 1, make_float4(fmaxf(b[0].hi.x, b[1].hi.x), fmaxf(b[0].hi.y, b[1].hi.y),
@@ -293,7 +309,7 @@ int build_lbvh(rtmc_ctx* ctx, DeviceMesh& m)
 {
     cudaStream_t s = ctx->stream;
     const int n = (int)m.n_tri;
-    if (m.n_tri <= 0 || m.n_tri > (int64_t)1 << 30)
+    if (m.n_tri <= 0 || m.n_tri >= (int64_t)1 << 28)
         return ctx->fail(RTMC_ERR_INVALID_ARG, "build_bvh: triangle count out of range");
     if (m.nodes) { cudaFree(m.nodes); m.nodes = nullptr; }
     if (m.tris) { cudaFree(m.tris); m.tris = nullptr; }
@@ -314,13 +330,14 @@ int build_lbvh(rtmc_ctx* ctx, DeviceMesh& m)
     cudaEventRecord(ev0, s);
 
     const int n_tiles = (n + kSortTile - 1) / kSortTile;
-    DevBuf k0, k1, v0, v1, hist, child, parent, leafp, flag, aabb, depth;
+    DevBuf k0, k1, v0, v1, hist, child, range, parent, leafp, flag, aabb, depth;
     e = k0.alloc(4ull * n);
     if (e == cudaSuccess) e = k1.alloc(4ull * n);
     if (e == cudaSuccess) e = v0.alloc(4ull * n);
     if (e == cudaSuccess) e = v1.alloc(4ull * n);
     if (e == cudaSuccess) e = hist.alloc(4ull * 256 * n_tiles);
     if (e == cudaSuccess) e = child.alloc(8ull * n_nodes);
+    if (e == cudaSuccess) e = range.alloc(8ull * n_nodes);
     if (e == cudaSuccess) e = parent.alloc(4ull * n_nodes);
     if (e == cudaSuccess) e = leafp.alloc(4ull * n);
     if (e == cudaSuccess) e = flag.alloc(4ull * n_nodes);
@@ -353,9 +370,9 @@ int build_lbvh(rtmc_ctx* ctx, DeviceMesh& m)
     } else {
         cudaMemsetAsync(flag.p, 0, 4ull * n_nodes, s);
         const int gi = (n - 1 + tb - 1) / tb;
-        k_karras<<<gi, tb, 0, s>>>(ki, n, child.as<int2>(), parent.as<int>(), leafp.as<int>());
-        k_refit<<<gb, tb, 0, s>>>(m.tri_in, vi, n, child.as<int2>(), parent.as<int>(), leafp.as<int>(),
-                                  flag.as<unsigned>(), aabb.as<float4>(), m.nodes);
+        k_karras<<<gi, tb, 0, s>>>(ki, n, child.as<int2>(), range.as<int2>(), parent.as<int>(), leafp.as<int>());
+        k_refit<<<gb, tb, 0, s>>>(m.tri_in, vi, n, child.as<int2>(), range.as<int2>(), parent.as<int>(),
+                                  leafp.as<int>(), flag.as<unsigned>(), aabb.as<float4>(), m.nodes, m.leaf_max);
         k_depth<<<gb, tb, 0, s>>>(parent.as<int>(), leafp.as<int>(), n, depth.as<int>());
     }
     k_pack<<<gb, tb, 0, s>>>(m.tri_in, vi, n, m.tris, m.normals, m.inv_order);

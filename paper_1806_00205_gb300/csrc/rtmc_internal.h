@@ -23,6 +23,7 @@ struct DeviceMesh {
     float4* normals = nullptr;     // n_tri float4
     int* inv_order = nullptr;      // original id -> leaf-order index
     int depth = 0;                 // hierarchy depth (root = 1)
+    int leaf_max = 4;              // triangles per leaf (1..8)
     double build_ms = 0.0;
 };
 
@@ -35,6 +36,7 @@ struct Scratch {
 struct Tuning {
     int block_threads = 128;
     int blocks_per_sm = 0;         // 0: from occupancy
+    int traversal = 0;             // 0/2: while-while with ray refill, 1: one ray per lane per tile
 };
 
 }  // namespace rtmc

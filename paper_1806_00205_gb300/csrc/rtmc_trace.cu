@@ -76,7 +76,25 @@ __device__ __forceinline__ void slab2(const float4 n0, const float4 n1, const fl
 
 struct Counts { unsigned visits = 0, tests = 0; };
 
-// Closest front-facing triangle (leaf order index) with t > 0, skipping `skip`.
+// Test the triangles of leaf `code` (~((first << 3) | (count - 1))).
+template <bool COUNT>
+__device__ __forceinline__ void test_leaf(const float4* __restrict__ tris, const RaySetup& r, int code, int skip,
+                                          float& t_best, int& best, int& best_orig, float& bu, float& bv,
+                                          Counts* cnt)
+{
+    const int v = ~code;
+    const int first = v >> 3, count = (v & 7) + 1;
+    for (int k = 0; k < count; ++k) {
+        const int j = first + k;
+        if (j == skip) continue;
+        if (COUNT) ++cnt->tests;
+        const float4* tp = tris + 3ll * j;
+        if (intersect_tri(r, ldg4(tp), ldg4(tp + 1), ldg4(tp + 2), t_best, best_orig, bu, bv)) best = j;
+    }
+}
+
+// Closest front-facing triangle (leaf order index) with t > 0, skipping `skip`:
+// one ray per lane, leaves tested as soon as their box is hit.
 template <bool COUNT = false>
 __device__ __forceinline__ int bvh_closest(const float4* __restrict__ nodes, const float4* __restrict__ tris,
                                            const RaySetup& r, int skip, StackRef st, float& t_best,
@@ -98,21 +116,11 @@ __device__ __forceinline__ int bvh_closest(const float4* __restrict__ nodes, con
         slab2(n0, n1, n2, r, t_best, tmin0, tmin1, h0, h1);
         const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
         if (h0 && c0 < 0) {
-            const int j = ~c0;
-            if (j != skip) {
-                if (COUNT) ++cnt->tests;
-                const float4* tp = tris + 3ll * j;
-                if (intersect_tri(r, ldg4(tp), ldg4(tp + 1), ldg4(tp + 2), t_best, best_orig, bu, bv)) best = j;
-            }
+            test_leaf<COUNT>(tris, r, c0, skip, t_best, best, best_orig, bu, bv, cnt);
             h0 = false;
         }
         if (h1 && c1 < 0) {
-            const int j = ~c1;
-            if (j != skip) {
-                if (COUNT) ++cnt->tests;
-                const float4* tp = tris + 3ll * j;
-                if (intersect_tri(r, ldg4(tp), ldg4(tp + 1), ldg4(tp + 2), t_best, best_orig, bu, bv)) best = j;
-            }
+            test_leaf<COUNT>(tris, r, c1, skip, t_best, best, best_orig, bu, bv, cnt);
             h1 = false;
         }
         if (h0 && h1) {
@@ -210,6 +218,178 @@ k_traverse(const float4* __restrict__ nodes, const float4* __restrict__ tris, Ce
             my_wraps += (unsigned)w;
             if (RECORD) wraps_out[i] = w;
         }
+    }
+    for (int off = 16; off; off >>= 1) {
+        my_wraps += __shfl_xor_sync(0xFFFFFFFFu, my_wraps, off);
+        status |= __shfl_xor_sync(0xFFFFFFFFu, status, off);
+    }
+    if (COUNT) {
+        unsigned long long v = cnt.visits, t = cnt.tests;
+        for (int off = 16; off; off >>= 1) {
+            v += __shfl_xor_sync(0xFFFFFFFFu, v, off);
+            t += __shfl_xor_sync(0xFFFFFFFFu, t, off);
+        }
+        if (lane == 0) { atomicAdd(&tally->node_visits, v); atomicAdd(&tally->tri_tests, t); }
+    }
+    if (lane == 0) {
+        if (my_wraps) atomicAdd(&tally->wraps, my_wraps);
+        if (status) atomicOr(&tally->status, (unsigned long long)status);
+    }
+}
+
+// --------------------------------------------------------------------------
+// traverse, while-while form (Aila & Laine, HPG 2009): inner nodes and leaf
+// triangles run in separate loops so the lanes of a warp stay in the same
+// phase; the first leaf a lane meets is postponed until every active lane
+// has one.  A lane whose ray finishes takes a new ray from the generation's
+// queue (one atomic per warp refill) instead of idling until the whole tile
+// is done.  The FP64 re-entry point of each lane lives in shared memory.
+// --------------------------------------------------------------------------
+constexpr int kEntrySentinel = 0x76543210;   // "stack empty" (never a node index)
+constexpr int kFetchThreshold = 20;          // refill when fewer lanes than this are active
+
+template <bool RECORD, bool COUNT>
+__global__ void __launch_bounds__(128)
+k_traverse_ww(const float4* __restrict__ nodes, const float4* __restrict__ tris, Cell cell,
+              const float4* __restrict__ oe, const float4* __restrict__ dt, float4* __restrict__ hits,
+              int* __restrict__ wraps_out, Control* __restrict__ ctl, int gen, unsigned cap,
+              Tally* __restrict__ tally)
+{
+    extern __shared__ int2 s_stack[];                                   // [kSmemStack][blockDim]
+    const int B = blockDim.x, tid = threadIdx.x, lane = tid & 31;
+    double* s_o = reinterpret_cast<double*>(s_stack + kSmemStack * B);   // [3][blockDim]
+    const unsigned lt = (1u << lane) - 1u;
+    const unsigned n = min(*((volatile unsigned*)&ctl->count[gen]), cap);
+    int2 lstack[kStackMax - kSmemStack];
+
+    int ray = -1;
+    bool exhausted = false, drained = false;
+    float3 o = make_float3(0.f, 0.f, 0.f), d = make_float3(0.f, 0.f, 1.f);
+    RaySetup rs = setup_ray(o, d);
+    float t_best = INFINITY, bu = 0.f, bv = 0.f;
+    int best = -1, best_orig = INT_MAX, node = kEntrySentinel, leaf = 0, sp = 0, skip = -1, wraps = 0, visits = 0;
+    unsigned status = 0;
+    unsigned long long my_wraps = 0;
+    Counts cnt;
+
+    auto push = [&](int node_ref, float tmin) {
+        const int2 e = make_int2(node_ref, __float_as_int(tmin));
+        if (sp < kSmemStack) s_stack[sp * B + tid] = e;
+        else if (sp < kStackMax) lstack[sp - kSmemStack] = e;
+        else { status |= ST_STACK_OVERFLOW; sp = kStackMax - 1; }
+        ++sp;
+    };
+    auto pop = [&]() -> int {
+        while (sp > 0) {
+            --sp;
+            const int2 e = sp < kSmemStack ? s_stack[sp * B + tid] : lstack[sp - kSmemStack];
+            if (__int_as_float(e.y) <= t_best * kRobust) return e.x;
+        }
+        return kEntrySentinel;
+    };
+    auto restart = [&]() {      // new cell traversal from the current origin
+        rs = setup_ray(o, d);
+        node = 0; leaf = 0; sp = 0; visits = 0;
+        t_best = INFINITY; best = -1; best_orig = INT_MAX; bu = bv = 0.f;
+    };
+
+    for (;;) {
+        const bool need = ray < 0 && !exhausted;
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, need);
+        if (m) {
+            const int leader = __ffs(m) - 1;
+            unsigned base = 0;
+            if (lane == leader) base = atomicAdd(&ctl->next[gen], (unsigned)__popc(m));
+            base = __shfl_sync(0xFFFFFFFFu, base, leader);
+            if (base + (unsigned)__popc(m) >= n) drained = true;
+            if (need) {
+                const unsigned idx = base + __popc(m & lt);
+                if (idx < n) {
+                    ray = (int)idx;
+                    const float4 a = oe[idx], b = dt[idx];
+                    o = make_float3(a.x, a.y, a.z);
+                    d = make_float3(b.x, b.y, b.z);
+                    skip = __float_as_int(b.w);
+                    s_o[tid] = a.x; s_o[B + tid] = a.y; s_o[2 * B + tid] = a.z;
+                    wraps = 0;
+                    restart();
+                } else {
+                    exhausted = true;
+                }
+            }
+        }
+        if (__all_sync(0xFFFFFFFFu, ray < 0)) break;
+        if (ray < 0) continue;
+
+        bool cell_done = false;
+        for (;;) {
+            while (node >= 0 && node != kEntrySentinel) {
+                if (++visits > kMaxVisits) { status |= ST_LOOP_LIMIT; node = kEntrySentinel; leaf = 0; sp = 0; break; }
+                if (COUNT) ++cnt.visits;
+                const float4* np = nodes + 4ll * node;
+                const float4 n0 = ldg4(np), n1 = ldg4(np + 1), n2 = ldg4(np + 2), n3 = ldg4(np + 3);
+                float tmin0, tmin1;
+                bool h0, h1;
+                slab2(n0, n1, n2, rs, t_best, tmin0, tmin1, h0, h1);
+                const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+                if (h0 && h1) {
+                    const bool first0 = tmin0 <= tmin1;
+                    push(first0 ? c1 : c0, first0 ? tmin1 : tmin0);
+                    node = first0 ? c0 : c1;
+                } else if (h0 || h1) {
+                    node = h0 ? c0 : c1;
+                } else {
+                    node = pop();
+                }
+                if (node < 0 && leaf == 0) { leaf = node; node = pop(); }
+                if (!__any_sync(__activemask(), leaf == 0)) break;
+            }
+            while (leaf < 0) {
+                test_leaf<COUNT>(tris, rs, leaf, skip, t_best, best, best_orig, bu, bv, &cnt);
+                leaf = 0;
+                if (node < 0) { leaf = node; node = pop(); }
+            }
+            if (node == kEntrySentinel) { cell_done = true; break; }
+            if (!drained && __popc(__activemask()) < kFetchThreshold) break;
+        }
+        if (!cell_done) continue;
+
+        if (best >= 0) {
+            hits[ray] = make_float4(t_best, bu, bv, __int_as_float(best));
+        } else {
+            // no facet in this cell: leave through a face (FP64 re-entry point)
+            double ox = s_o[tid], oy = s_o[B + tid], oz = s_o[2 * B + tid];
+            double tx = INFINITY, ty = INFINITY, tz = INFINITY;
+            if (d.x > 0.f) tx = ((double)cell.lx - ox) / d.x; else if (d.x < 0.f) tx = (0.0 - ox) / d.x;
+            if (d.y > 0.f) ty = ((double)cell.ly - oy) / d.y; else if (d.y < 0.f) ty = (0.0 - oy) / d.y;
+            if (d.z > 0.f) tz = ((double)cell.z_top - oz) / d.z; else if (d.z < 0.f) tz = ((double)cell.z_min - oz) / d.z;
+            int code = 0;
+            float tout = 0.f;
+            if (tz < tx && tz < ty) {
+                code = d.z > 0.f ? HIT_ESCAPE : HIT_LOST;
+                tout = (float)tz;
+            } else if (++wraps > cell.max_wraps) {
+                code = HIT_LOST;
+                tout = (float)fmin(tx, ty);
+            }
+            if (code) {
+                hits[ray] = make_float4(tout, 0.f, 0.f, __int_as_float(code));
+            } else {
+                if (tx <= ty) {
+                    oy = oy + tx * d.y; oz = oz + tx * d.z; ox = d.x > 0.f ? 0.0 : (double)cell.lx;
+                } else {
+                    ox = ox + ty * d.x; oz = oz + ty * d.z; oy = d.y > 0.f ? 0.0 : (double)cell.ly;
+                }
+                s_o[tid] = ox; s_o[B + tid] = oy; s_o[2 * B + tid] = oz;
+                o = make_float3((float)ox, (float)oy, (float)oz);
+                skip = -1;
+                restart();
+                continue;
+            }
+        }
+        my_wraps += (unsigned)wraps;
+        if (RECORD) wraps_out[ray] = wraps;
+        ray = -1;
     }
     for (int off = 16; off; off >>= 1) {
         my_wraps += __shfl_xor_sync(0xFFFFFFFFu, my_wraps, off);
@@ -566,24 +746,25 @@ cudaError_t launch_generate(const RunParams& p, const Queues& q, int buf, unsign
 }
 
 template <bool R, bool C>
-static int traverse_blocks_t(int num_sms, const Tuning& tune)
-{
-    if (tune.blocks_per_sm > 0) return num_sms * tune.blocks_per_sm;
-    int per_sm = 0;
-    const size_t smem = (size_t)kSmemStack * tune.block_threads * sizeof(int2);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse<R, C>, tune.block_threads, smem);
-    return num_sms * (per_sm > 0 ? per_sm : 1);
-}
-
-template <bool R, bool C>
 static cudaError_t traverse_t(const DeviceMesh& m, const RunParams& p, const Queues& q, int buf, int gen,
                               int num_sms, const Tuning& tune, cudaStream_t s)
 {
     const Cell cell{p.lx, p.ly, p.z_min, p.z_top, p.max_wraps};
-    const int blocks = traverse_blocks_t<R, C>(num_sms, tune);
-    const size_t smem = (size_t)kSmemStack * tune.block_threads * sizeof(int2);
-    k_traverse<R, C><<<blocks, tune.block_threads, smem, s>>>(m.nodes, m.tris, cell, q.oe[buf], q.dt[buf], q.hits,
-                                                              R ? q.wraps : nullptr, q.ctl, gen, q.cap[buf], q.tally);
+    const int bt = tune.block_threads;
+    int per_sm = tune.blocks_per_sm;
+    if (tune.traversal == 1) {
+        const size_t smem = (size_t)kSmemStack * bt * sizeof(int2);
+        if (per_sm <= 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse<R, C>, bt, smem);
+        k_traverse<R, C><<<num_sms * (per_sm > 0 ? per_sm : 1), bt, smem, s>>>(
+            m.nodes, m.tris, cell, q.oe[buf], q.dt[buf], q.hits, R ? q.wraps : nullptr, q.ctl, gen, q.cap[buf],
+            q.tally);
+    } else {
+        const size_t smem = (size_t)kSmemStack * bt * sizeof(int2) + 3 * (size_t)bt * sizeof(double);
+        if (per_sm <= 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse_ww<R, C>, bt, smem);
+        k_traverse_ww<R, C><<<num_sms * (per_sm > 0 ? per_sm : 1), bt, smem, s>>>(
+            m.nodes, m.tris, cell, q.oe[buf], q.dt[buf], q.hits, R ? q.wraps : nullptr, q.ctl, gen, q.cap[buf],
+            q.tally);
+    }
     return cudaGetLastError();
 }
 

@@ -54,7 +54,8 @@ class RunDesc(C.Structure):
                 ("primary_offset", C.c_uint64), ("random_azimuth", C.c_int32), ("max_wraps", C.c_int32),
                 ("src_x0", C.c_double), ("src_x1", C.c_double), ("src_y0", C.c_double), ("src_y1", C.c_double),
                 ("chunk", C.c_int64), ("block_threads", C.c_int32), ("blocks_per_sm", C.c_int32),
-                ("prim_hash", C.c_void_p), ("profile", C.c_int32), ("count_visits", C.c_int32)]
+                ("prim_hash", C.c_void_p), ("profile", C.c_int32), ("count_visits", C.c_int32),
+                ("traversal", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -137,12 +138,12 @@ class Emission:
 
 def run_desc(n_ebins=64, n_abins=18, hist_e_max_ev=50.0, primary_offset=0, random_azimuth=False,
              max_wraps=1024, window=None, chunk=0, block_threads=0, blocks_per_sm=0, prim_hash=None,
-             profile=False, count_visits=False):
+             profile=False, count_visits=False, traversal=0):
     x0, x1, y0, y1 = window if window is not None else (0.0, 0.0, 0.0, 0.0)
     return RunDesc(int(n_ebins), int(n_abins), float(hist_e_max_ev), int(primary_offset),
                    int(bool(random_azimuth)), int(max_wraps), x0, x1, y0, y1, int(chunk), int(block_threads),
                    int(blocks_per_sm), prim_hash.data_ptr() if prim_hash is not None else None,
-                   int(bool(profile)), int(bool(count_visits)))
+                   int(bool(profile)), int(bool(count_visits)), int(traversal))
 
 
 def result_dict(r: Result):
@@ -206,8 +207,8 @@ class Context:
         e = EmissionC(em.phi_ev, em.e_cut_ev, em.absorb_min_ev, em.regen_min_ev, em.max_generation, em.k_max)
         self._check(self._L.rtmc_load_see_tables(self.h, _ptr(delta), C.byref(g), C.byref(e)))
 
-    def build_bvh(self, mesh_id: int, kind: int = BVH_FP32):
-        self._check(self._L.rtmc_build_bvh(self.h, int(mesh_id), int(kind)))
+    def build_bvh(self, mesh_id: int, kind: int = BVH_FP32, leaf: int = 0):
+        self._check(self._L.rtmc_build_bvh(self.h, int(mesh_id), int(kind) | (int(leaf) << 8)))
 
     def run(self, mesh_id, energies, thetas, n_primaries, seed, desc: RunDesc | None = None):
         """All (energy, angle) items; returns (results list, hist_e [items, nE], hist_a [items, nA])."""
