@@ -43,6 +43,7 @@ extern "C" {
 #define RTMC_ERR_DEVICE_CHECK  -8
 
 #define RTMC_BVH_FP32 0     /* 64-byte nodes with FP32 child boxes */
+#define RTMC_BVH_Q8   1     /* 32-byte nodes with 8-bit outward-rounded child boxes */
 /* bvh_kind = node format | RTMC_BVH_LEAF(n): leaves of up to n (1..8) triangles, default 4 */
 #define RTMC_BVH_LEAF(n) ((n) << 8)
 
@@ -91,6 +92,9 @@ typedef struct {
     int32_t count_visits;          /* 1: count BVH node visits and triangle tests */
     int32_t traversal;             /* 0: default; 1: one ray per lane per 32-ray tile;
                                       2: while-while loop with per-lane ray refill */
+    int32_t fp64_retest;           /* 1: re-test hits within 1e-5 (barycentric) of an edge
+                                      or with cos(incidence) < 1e-3 using FP64 triangle
+                                      tests (while-while traversal only) */
 } rtmc_run_desc;
 
 typedef struct {
@@ -104,6 +108,7 @@ typedef struct {
     int64_t node_visits, tri_tests;            /* with count_visits */
     double ms_generate, ms_traverse, ms_shade, ms_finalize;   /* with profile */
     int64_t traverse_launches;
+    int64_t retested;                          /* rays re-tested in FP64 */
 } rtmc_result;
 
 /* One traced ray: the integer event sequence used for parity checks. */
@@ -142,7 +147,9 @@ int rtmc_load_see_tables(rtmc_ctx* ctx, const float* delta, const rtmc_grid* gri
 
 /* Build the linear BVH of a loaded mesh on the device: Morton codes of the
    triangle centroids, radix sort, Karras hierarchy, bottom-up box refit,
-   triangle repack.  `bvh_kind` is RTMC_BVH_FP32, optionally or-ed with
+   triangle repack; RTMC_BVH_Q8 also quantises each node's two child boxes to
+   8 bits per coordinate in the node's own frame (origin + q 2^e, rounded
+   outward).  `bvh_kind` is RTMC_BVH_FP32 or RTMC_BVH_Q8, optionally or-ed with
    RTMC_BVH_LEAF(n) to cap leaves at n triangles (subtrees with at most n
    triangles become one leaf). */
 int rtmc_build_bvh(rtmc_ctx* ctx, int32_t mesh_id, int32_t bvh_kind);
@@ -171,6 +178,14 @@ int rtmc_run_records(rtmc_ctx* ctx, int32_t mesh_id, double energy_ev, double th
    miss).  Section 2.1. */
 int rtmc_trace_rays(rtmc_ctx* ctx, int32_t mesh_id, const float* o, const float* d,
                     const int32_t* skip_tri, int64_t n, rtmc_hit* hits);
+
+/* Copy a built BVH to host memory for inspection: which = 0 FP32 nodes
+   (n_nodes x 64 B), 1 Q8 nodes (n_nodes x 32 B, RTMC_BVH_Q8 meshes only),
+   2 triangles in leaf order (n_tri x 48 B).  Layouts as in the library's
+   device code.  With out == NULL only *bytes_needed is written; otherwise
+   bytes must be at least that size. */
+int rtmc_export_bvh(rtmc_ctx* ctx, int32_t mesh_id, int32_t which, void* out, int64_t bytes,
+                    int64_t* bytes_needed);
 
 /* Philox4x32-10 on the device: out[i][4] = philox(ctr[i][4], key), for
    checking the device generator against the published vectors. */

@@ -161,6 +161,7 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
         }
         if (ce == cudaSuccess) ce = scratch_reserve(ctx->hits, (size_t)capmax * 16);
         if (ce == cudaSuccess && need_wraps) ce = scratch_reserve(ctx->wraps, (size_t)capmax * 4);
+        if (ce == cudaSuccess && d.fp64_retest) ce = scratch_reserve(ctx->retest, (size_t)capmax * 4);
         const bool kc_new = ctx->kcount.bytes < (size_t)chunk * 4;
         if (ce == cudaSuccess) ce = scratch_reserve(ctx->kcount, (size_t)chunk * 4);
         if (ce == cudaSuccess && kc_new) ce = cudaMemsetAsync(ctx->kcount.ptr, 0, ctx->kcount.bytes, s);
@@ -181,6 +182,7 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
         q.hits = (float4*)ctx->hits.ptr;
         q.wraps = need_wraps ? (int*)ctx->wraps.ptr : nullptr;
         q.kcount = (unsigned*)ctx->kcount.ptr;
+        q.retest = d.fp64_retest ? (unsigned*)ctx->retest.ptr : nullptr;
         q.ctl = (Control*)ctx->ctl.ptr;
         q.tally = (Tally*)ctx->tally.ptr;
         q.hist_e = (unsigned long long*)ctx->hist.ptr;
@@ -219,7 +221,8 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
             for (int g = 0; g <= em.max_generation && ce == cudaSuccess; ++g) {
                 const int buf = g & 1;
                 h = tick(1);
-                ce = launch_traverse(m, p, q, buf, g, ctx->num_sms, tune, need_wraps, d.count_visits != 0, s);
+                ce = launch_traverse(m, p, q, buf, g, ctx->num_sms, tune, need_wraps, d.count_visits != 0,
+                                     d.fp64_retest != 0, s);
                 tock(h);
                 h = tick(2);
                 if (ce == cudaSuccess)
@@ -298,6 +301,7 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
         r.ms_traverse = kms[1];
         r.ms_shade = kms[2];
         r.ms_finalize = kms[3];
+        r.retested = (int64_t)t.retested;
         if (o.hist_e) for (int b = 0; b < d.n_ebins; ++b) o.hist_e[b] = hist[b];
         if (o.hist_a) for (int b = 0; b < d.n_abins; ++b) o.hist_a[b] = hist[d.n_ebins + b];
         if (record) {
@@ -324,6 +328,8 @@ int check_run_args(rtmc_ctx* ctx, int32_t mesh_id, int64_t n_primaries, const rt
     if (d.block_threads != 0 && (d.block_threads % 32 != 0 || d.block_threads < 32 || d.block_threads > 128))
         return ctx->fail(RTMC_ERR_INVALID_ARG, "run: block_threads must be a multiple of 32 in [32, 128]");
     if (d.traversal < 0 || d.traversal > 2) return ctx->fail(RTMC_ERR_INVALID_ARG, "run: unknown traversal variant");
+    if (d.fp64_retest && d.traversal == 1)
+        return ctx->fail(RTMC_ERR_INVALID_ARG, "run: fp64_retest needs the while-while traversal");
     if (d.chunk < 0 || d.chunk > ((int64_t)1 << 28)) return ctx->fail(RTMC_ERR_INVALID_ARG, "run: chunk out of range");
     if (d.max_wraps < 0 || d.max_wraps > (1 << 20)) return ctx->fail(RTMC_ERR_INVALID_ARG, "run: max_wraps out of range");
     if (d.blocks_per_sm < 0 || d.blocks_per_sm > 64) return ctx->fail(RTMC_ERR_INVALID_ARG, "run: blocks_per_sm out of range");
@@ -369,11 +375,12 @@ void rtmc_destroy(rtmc_ctx* ctx)
         cudaFree(m.tris);
         cudaFree(m.normals);
         cudaFree(m.inv_order);
+        cudaFree(m.q8);
     }
     cudaFree(ctx->delta);
     rtmc::Scratch* all[] = {&ctx->q_oe[0], &ctx->q_oe[1], &ctx->q_dt[0], &ctx->q_dt[1], &ctx->q_id[0],
                             &ctx->q_id[1], &ctx->hits, &ctx->kcount, &ctx->ctl, &ctx->tally, &ctx->hist,
-                            &ctx->wraps, &ctx->records, &ctx->tmp};
+                            &ctx->wraps, &ctx->records, &ctx->tmp, &ctx->retest};
     for (auto* s : all) rtmc::scratch_free(*s);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -421,6 +428,7 @@ int rtmc_unload_mesh(rtmc_ctx* ctx, int32_t mesh_id)
     cudaFree(m.tris);
     cudaFree(m.normals);
     cudaFree(m.inv_order);
+    cudaFree(m.q8);
     m = DeviceMesh();
     return RTMC_OK;
 }
@@ -453,7 +461,7 @@ int rtmc_build_bvh(rtmc_ctx* ctx, int32_t mesh_id, int32_t bvh_kind)
     if (mesh_id < 0 || mesh_id >= (int)ctx->meshes.size() || !ctx->meshes[mesh_id].tri_in)
         return ctx->fail(RTMC_ERR_NOT_LOADED, "build_bvh: unknown mesh id");
     const int format = bvh_kind & 0xFF, leaf = (bvh_kind >> 8) & 0xFF;
-    if (format != RTMC_BVH_FP32 || (bvh_kind >> 16) != 0 || leaf > 8)
+    if ((format != RTMC_BVH_FP32 && format != RTMC_BVH_Q8) || (bvh_kind >> 16) != 0 || leaf > 8)
         return ctx->fail(RTMC_ERR_INVALID_ARG, "build_bvh: unknown bvh kind or leaf size > 8");
     DeviceGuard g(ctx->device);
     DeviceMesh& m = ctx->meshes[mesh_id];
@@ -543,6 +551,29 @@ int rtmc_trace_rays(rtmc_ctx* ctx, int32_t mesh_id, const float* o, const float*
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "trace_rays");
     if (status) return ctx->fail(RTMC_ERR_DEVICE_CHECK, "trace_rays: traversal stack overflow");
+    return RTMC_OK;
+}
+
+int rtmc_export_bvh(rtmc_ctx* ctx, int32_t mesh_id, int32_t which, void* out, int64_t bytes, int64_t* bytes_needed)
+{
+    if (!ctx) return RTMC_ERR_INVALID_ARG;
+    if (mesh_id < 0 || mesh_id >= (int)ctx->meshes.size() || !ctx->meshes[mesh_id].tri_in)
+        return ctx->fail(RTMC_ERR_NOT_LOADED, "export_bvh: unknown mesh id");
+    const DeviceMesh& m = ctx->meshes[mesh_id];
+    if (!m.built) return ctx->fail(RTMC_ERR_NOT_BUILT, "export_bvh: build_bvh first");
+    const void* src = nullptr;
+    int64_t need = 0;
+    if (which == 0) { src = m.nodes; need = m.n_nodes * 64; }
+    else if (which == 1 && m.q8) { src = m.q8; need = m.n_nodes * 32; }
+    else if (which == 2) { src = m.tris; need = m.n_tri * 48; }
+    else return ctx->fail(RTMC_ERR_INVALID_ARG, "export_bvh: unknown array or not built in this format");
+    if (bytes_needed) *bytes_needed = need;
+    if (!out) return RTMC_OK;
+    if (bytes < need) return ctx->fail(RTMC_ERR_INVALID_ARG, "export_bvh: output buffer too small");
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaMemcpyAsync(out, src, (size_t)need, cudaMemcpyDefault, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "export_bvh");
     return RTMC_OK;
 }
 

@@ -267,11 +267,121 @@ __global__ void k_single_leaf(const float* __restrict__ tri, float4* __restrict_
     store_node(nodes, 0, b, b, ~0, ~0);
 }
 
+// ---- Q8 nodes: 8-bit child boxes, outward rounded -------------------------
+// The frame of node i is its own box: origin = box lo, per-axis scale 2^e with
+// fmaf(255, 2^e, origin) >= box hi.  A child bound decodes to fmaf(q, 2^e,
+// origin); lower bounds are rounded down and upper bounds up, checked with the
+// same FP32 decode the traversal uses, so a decoded child box always contains
+// the exact one.
+__device__ int frame_exponent(float lo, float hi)
+{
+    const float ext = hi - lo;
+    int e = -126;
+    if (ext > 0.f) {
+        e = (int)ceilf(log2f(ext / 255.0f));
+        e = max(-126, min(e, 127));
+    }
+    while (e < 127 && fmaf(255.0f, exp2_int(e), lo) < hi) ++e;
+    return e;
+}
+
+__device__ unsigned quant_lo(float v, float o, float sc)
+{
+    int q = (int)floorf((v - o) / sc);
+    q = max(0, min(q, 255));
+    while (q > 0 && fmaf((float)q, sc, o) > v) --q;
+    return (unsigned)q;
+}
+
+__device__ unsigned quant_hi(float v, float o, float sc)
+{
+    int q = (int)ceilf((v - o) / sc);
+    q = max(0, min(q, 255));
+    while (q < 255 && fmaf((float)q, sc, o) < v) ++q;
+    return (unsigned)q;
+}
+
+__device__ void child_info(int raw, const float* __restrict__ tri, const unsigned* __restrict__ order,
+                           const int2* __restrict__ range, const float4* __restrict__ aabb, int leaf_max,
+                           Box3& b, bool& leaf, int& count)
+{
+    if (raw < 0) {
+        b = tri_box(tri, order[~raw]);
+        leaf = true;
+        count = 1;
+        return;
+    }
+    const float4 lo = __ldcg(aabb + 2ll * raw), hi = __ldcg(aabb + 2ll * raw + 1);
+    b.lo = make_float3(lo.x, lo.y, lo.z);
+    b.hi = make_float3(hi.x, hi.y, hi.z);
+    const int2 r = range[raw];
+    count = r.y - r.x + 1;
+    leaf = count <= leaf_max;
+}
+
+__global__ void k_quantize(const float* __restrict__ tri, const unsigned* __restrict__ order, int n_inner,
+                           const int2* __restrict__ child, const int2* __restrict__ range,
+                           const float4* __restrict__ aabb, int leaf_max, uint4* __restrict__ q8)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_inner) return;
+    const int2 c = child[i];
+    Box3 b[2];
+    bool leaf[2];
+    int count[2];
+    child_info(c.x, tri, order, range, aabb, leaf_max, b[0], leaf[0], count[0]);
+    child_info(c.y, tri, order, range, aabb, leaf_max, b[1], leaf[1], count[1]);
+    const int gamma = c.x < 0 ? ~c.x : c.x;
+    const float3 plo = make_float3(fminf(b[0].lo.x, b[1].lo.x), fminf(b[0].lo.y, b[1].lo.y), fminf(b[0].lo.z, b[1].lo.z));
+    const float3 phi = make_float3(fmaxf(b[0].hi.x, b[1].hi.x), fmaxf(b[0].hi.y, b[1].hi.y), fmaxf(b[0].hi.z, b[1].hi.z));
+    const int ex = frame_exponent(plo.x, phi.x), ey = frame_exponent(plo.y, phi.y), ez = frame_exponent(plo.z, phi.z);
+    const float sx = exp2_int(ex), sy = exp2_int(ey), sz = exp2_int(ez);
+    unsigned qb[12];
+    for (int k = 0; k < 2; ++k) {
+        qb[6 * k + 0] = quant_lo(b[k].lo.x, plo.x, sx);
+        qb[6 * k + 1] = quant_lo(b[k].lo.y, plo.y, sy);
+        qb[6 * k + 2] = quant_lo(b[k].lo.z, plo.z, sz);
+        qb[6 * k + 3] = quant_hi(b[k].hi.x, plo.x, sx);
+        qb[6 * k + 4] = quant_hi(b[k].hi.y, plo.y, sy);
+        qb[6 * k + 5] = quant_hi(b[k].hi.z, plo.z, sz);
+    }
+    const unsigned meta = (leaf[0] ? 1u : 0u) | ((unsigned)(leaf[0] ? count[0] - 1 : 0) << 1) |
+                          (leaf[1] ? 16u : 0u) | ((unsigned)(leaf[1] ? count[1] - 1 : 0) << 5);
+    const unsigned packed = (unsigned)(ex & 255) | ((unsigned)(ey & 255) << 8) | ((unsigned)(ez & 255) << 16) |
+                            (meta << 24);
+    q8[2ll * i] = make_uint4(__float_as_uint(plo.x), __float_as_uint(plo.y), __float_as_uint(plo.z), packed);
+    q8[2ll * i + 1] = make_uint4(qb[0] | qb[1] << 8 | qb[2] << 16 | qb[3] << 24,
+                                 qb[4] | qb[5] << 8 | qb[6] << 16 | qb[7] << 24,
+                                 qb[8] | qb[9] << 8 | qb[10] << 16 | qb[11] << 24, (unsigned)gamma);
+}
+
+// One-triangle mesh in Q8 form: left leaf = triangle 0, right leaf = the
+// degenerate padding triangle 1 (never hit).
+__global__ void k_quantize_single(const float* __restrict__ tri, uint4* __restrict__ q8)
+{
+    const Box3 b = tri_box(tri, 0);
+    const int ex = frame_exponent(b.lo.x, b.hi.x), ey = frame_exponent(b.lo.y, b.hi.y), ez = frame_exponent(b.lo.z, b.hi.z);
+    const unsigned meta = 1u | 16u;
+    const unsigned packed = (unsigned)(ex & 255) | ((unsigned)(ey & 255) << 8) | ((unsigned)(ez & 255) << 16) |
+                            (meta << 24);
+    q8[0] = make_uint4(__float_as_uint(b.lo.x), __float_as_uint(b.lo.y), __float_as_uint(b.lo.z), packed);
+    q8[1] = make_uint4(0xFF000000u, 0x0000FFFFu, 0x00000000u, 0u);   // c0 = [0,255]^3, c1 = [0,0]^3
+}
+
 __global__ void k_pack(const float* __restrict__ tri, const unsigned* __restrict__ order, int n,
                        float4* __restrict__ tris, float4* __restrict__ normals,
                        int* __restrict__ inv_order)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j == n) {   // degenerate padding triangle after the last leaf (never hit)
+        const float* p0 = tri;
+        const float4 v = make_float4(p0[0], p0[1], p0[2], __int_as_float(-1));
+        tris[3ll * n + 0] = v;
+        tris[3ll * n + 1] = make_float4(v.x, v.y, v.z, 0.f);
+        tris[3ll * n + 2] = make_float4(v.x, v.y, v.z, 0.f);
+        normals[n] = make_float4(0.f, 0.f, 1.f, 0.f);
+        return;
+    }
     if (j >= n) return;
     const unsigned i = order[j];
     const float* p = tri + 9ll * i;
@@ -315,11 +425,13 @@ int build_lbvh(rtmc_ctx* ctx, DeviceMesh& m)
     if (m.tris) { cudaFree(m.tris); m.tris = nullptr; }
     if (m.normals) { cudaFree(m.normals); m.normals = nullptr; }
     if (m.inv_order) { cudaFree(m.inv_order); m.inv_order = nullptr; }
+    if (m.q8) { cudaFree(m.q8); m.q8 = nullptr; }
     m.built = false;
     const int64_t n_nodes = n > 1 ? n - 1 : 1;
     cudaError_t e = cudaMalloc(&m.nodes, n_nodes * 64);
-    if (e == cudaSuccess) e = cudaMalloc(&m.tris, (size_t)n * 48);
-    if (e == cudaSuccess) e = cudaMalloc(&m.normals, (size_t)n * 16);
+    if (e == cudaSuccess) e = cudaMalloc(&m.tris, (size_t)(n + 1) * 48);
+    if (e == cudaSuccess) e = cudaMalloc(&m.normals, (size_t)(n + 1) * 16);
+    if (e == cudaSuccess && m.kind == FMT_Q8) e = cudaMalloc(&m.q8, n_nodes * 32);
     if (e == cudaSuccess) e = cudaMalloc(&m.inv_order, (size_t)n * 4);
     if (e != cudaSuccess) return ctx->fail(RTMC_ERR_OOM, std::string("build_bvh: ") + cudaGetErrorString(e));
     m.n_nodes = n_nodes;
@@ -365,6 +477,7 @@ int build_lbvh(rtmc_ctx* ctx, DeviceMesh& m)
     cudaMemsetAsync(depth.p, 0, 4, s);
     if (n == 1) {
         k_single_leaf<<<1, 1, 0, s>>>(m.tri_in, m.nodes);
+        if (m.kind == FMT_Q8) k_quantize_single<<<1, 1, 0, s>>>(m.tri_in, reinterpret_cast<uint4*>(m.q8));
         int one = 1;
         cudaMemcpyAsync(depth.p, &one, 4, cudaMemcpyHostToDevice, s);
     } else {
@@ -374,8 +487,12 @@ int build_lbvh(rtmc_ctx* ctx, DeviceMesh& m)
         k_refit<<<gb, tb, 0, s>>>(m.tri_in, vi, n, child.as<int2>(), range.as<int2>(), parent.as<int>(),
                                   leafp.as<int>(), flag.as<unsigned>(), aabb.as<float4>(), m.nodes, m.leaf_max);
         k_depth<<<gb, tb, 0, s>>>(parent.as<int>(), leafp.as<int>(), n, depth.as<int>());
+        if (m.kind == FMT_Q8)
+            k_quantize<<<gi, tb, 0, s>>>(m.tri_in, vi, n - 1, child.as<int2>(), range.as<int2>(), aabb.as<float4>(),
+                                         m.leaf_max, reinterpret_cast<uint4*>(m.q8));
     }
-    k_pack<<<gb, tb, 0, s>>>(m.tri_in, vi, n, m.tris, m.normals, m.inv_order);
+    const int gp = (n + 1 + tb - 1) / tb;
+    k_pack<<<gp, tb, 0, s>>>(m.tri_in, vi, n, m.tris, m.normals, m.inv_order);
     int h_depth = 0;
     cudaMemcpyAsync(&h_depth, depth.p, 4, cudaMemcpyDeviceToHost, s);
     cudaEventRecord(ev1, s);

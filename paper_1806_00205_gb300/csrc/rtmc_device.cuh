@@ -6,6 +6,11 @@
 //                    float4 c = (c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z)
 //                    int4   d = (child0, child1, 0, 0); child >= 0: inner node,
 //                               child < 0: leaf holding sorted triangle ~child.
+//   Q8 node (32 B): float4 (frame origin xyz, packed: ex | ey << 8 | ez << 16 | meta << 24)
+//                   uint4  (12 quantised bytes: c0 lo.xyz hi.xyz, c1 lo.xyz hi.xyz; gamma)
+//                   a child coordinate decodes to fmaf(q, 2^e, origin) (outward rounded);
+//                   children are gamma and gamma + 1: inner node indices, or leaves
+//                   ending at gamma / starting at gamma + 1 (meta: leaf bit + count - 1).
 //   triangle (48 B): float4 V0 (w = original id bits), float4 V1, float4 V2
 //   normal   (16 B): float4 (unit normal, 0)
 //   ray queue (SoA, 48 B per ray):
@@ -38,11 +43,13 @@ struct Tally {                    // one (energy, angle) item, device resident
     unsigned long long rays_recorded;
     unsigned long long status;    // ST_* bits raised by any kernel of the item
     unsigned long long node_visits, tri_tests;   // counting variant of traverse only
+    unsigned long long retested;                 // rays re-tested in FP64
 };
 
 struct Control {                  // per chunk
     unsigned int count[8];        // rays in queue of generation g
     unsigned int next[8];         // persistent-traversal work counter per generation
+    unsigned int n_retest[8];     // rays flagged for the FP64 re-test per generation
 };
 
 struct Emission {
@@ -58,6 +65,21 @@ struct TableDesc {
     float log_e_lo;
     float inv_theta_step_deg;
 };
+
+constexpr int FMT_FP32 = 0;
+constexpr int FMT_Q8 = 1;
+
+// Leaf reference used by both node formats: ~((first << 3) | (count - 1)).
+__host__ __device__ inline int leaf_ref(int first, int count) { return ~((first << 3) | (count - 1)); }
+
+// 2^e for e in [-126, 127] (a normal float built from its exponent field).
+__device__ __forceinline__ float exp2_int(int e) { return __int_as_float((e + 127) << 23); }
+
+// Byte k of w as a float (exact): 0x4B0000qq is 2^23 + q.
+__device__ __forceinline__ float byte_f(unsigned w, int k)
+{
+    return __int_as_float(__byte_perm(w, 0x4B000000u, (unsigned)k | 0x7540u)) - 8388608.0f;
+}
 
 // --------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11).  Counter (prim lo, prim hi, path,

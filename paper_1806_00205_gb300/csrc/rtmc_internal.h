@@ -22,6 +22,7 @@ struct DeviceMesh {
     float4* tris = nullptr;        // n_tri * 3 float4, BVH leaf order
     float4* normals = nullptr;     // n_tri float4
     int* inv_order = nullptr;      // original id -> leaf-order index
+    void* q8 = nullptr;            // n_nodes * 32 B quantised nodes (RTMC_BVH_Q8)
     int depth = 0;                 // hierarchy depth (root = 1)
     int leaf_max = 4;              // triangles per leaf (1..8)
     double build_ms = 0.0;
@@ -52,7 +53,7 @@ struct rtmc_ctx {
     rtmc_emission emission{};
     bool table_loaded = false;
     // run buffers
-    rtmc::Scratch q_oe[2], q_dt[2], q_id[2], hits, kcount, ctl, tally, hist, wraps, records, tmp;
+    rtmc::Scratch q_oe[2], q_dt[2], q_id[2], hits, kcount, ctl, tally, hist, wraps, records, tmp, retest;
     std::string err;
     int fail(int code, const std::string& msg) { err = msg; return code; }
 };
@@ -88,6 +89,7 @@ struct Queues {
     float4* hits;
     int* wraps;                  // record mode only
     unsigned* kcount;
+    unsigned* retest;            // flagged ray indices (FP64 re-test), capacity max(cap)
     Control* ctl;
     Tally* tally;
     unsigned long long* hist_e;  // device, n_ebins
@@ -102,7 +104,7 @@ cudaError_t launch_generate(const RunParams& p, const Queues& q, int buf, unsign
                             unsigned n, cudaStream_t s);
 cudaError_t launch_traverse(const DeviceMesh& m, const RunParams& p, const Queues& q, int buf,
                             int gen, int num_sms, const Tuning& tune, bool record, bool count,
-                            cudaStream_t s);
+                            bool retest, cudaStream_t s);
 cudaError_t launch_shade(const DeviceMesh& m, const RunParams& p, const TableDesc& tab,
                          const Emission& em, const Queues& q, int buf, int gen,
                          unsigned long long chunk_first, int num_sms, bool record, cudaStream_t s);

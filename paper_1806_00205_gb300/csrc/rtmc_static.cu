@@ -180,6 +180,7 @@ extern "C" int rtmc_run_noalloc(rtmc_ctx* ctx, int32_t mesh_id, double energy_ev
     const bool hashing = d.prim_hash != nullptr;
     q.wraps = hashing ? reinterpret_cast<int*>(base + kWraps) : nullptr;
     q.kcount = reinterpret_cast<unsigned*>(base + kKcount);
+    q.retest = nullptr;
     q.ctl = reinterpret_cast<Control*>(base + kCtl);
     q.tally = reinterpret_cast<Tally*>(base + kTally);
     q.hist_e = reinterpret_cast<unsigned long long*>(base + kHist);
@@ -201,7 +202,7 @@ extern "C" int rtmc_run_noalloc(rtmc_ctx* ctx, int32_t mesh_id, double energy_ev
     const unsigned n = (unsigned)n_primaries;
     if (ce == cudaSuccess) ce = launch_generate(p, q, 0, 0ull, n, s);
     for (int g = 0; g <= 1 && ce == cudaSuccess; ++g) {
-        ce = launch_traverse(m, p, q, g, g, ctx->num_sms, tune, hashing, d.count_visits != 0, s);
+        ce = launch_traverse(m, p, q, g, g, ctx->num_sms, tune, hashing, d.count_visits != 0, false, s);
         if (ce == cudaSuccess) ce = launch_shade(m, p, tab, e, q, g, g, 0ull, ctx->num_sms, false, s);
     }
     if (ce == cudaSuccess) ce = launch_finalize(q, n, s);

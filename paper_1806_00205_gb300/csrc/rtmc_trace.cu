@@ -57,30 +57,119 @@ struct StackRef {
     int tid;
 };
 
-__device__ __forceinline__ void slab2(const float4 n0, const float4 n1, const float4 n2, const RaySetup& r,
-                                      float t_best, float& tmin0, float& tmin1, bool& h0, bool& h1)
+// Slab test of one box (Ize 2013 form: difference first, then the reciprocal,
+// tmax widened by 1 + 2 gamma_3 so the test is conservative).
+__device__ __forceinline__ void slab_box(float lox, float hix, float loy, float hiy, float loz, float hiz,
+                                         const RaySetup& r, float t_best, float& tmin, bool& hit)
 {
-    const float lx0 = (n0.x - r.o.x) * r.inv.x, hx0 = (n0.y - r.o.x) * r.inv.x;
-    const float ly0 = (n0.z - r.o.y) * r.inv.y, hy0 = (n0.w - r.o.y) * r.inv.y;
-    const float lz0 = (n2.x - r.o.z) * r.inv.z, hz0 = (n2.y - r.o.z) * r.inv.z;
-    const float lx1 = (n1.x - r.o.x) * r.inv.x, hx1 = (n1.y - r.o.x) * r.inv.x;
-    const float ly1 = (n1.z - r.o.y) * r.inv.y, hy1 = (n1.w - r.o.y) * r.inv.y;
-    const float lz1 = (n2.z - r.o.z) * r.inv.z, hz1 = (n2.w - r.o.z) * r.inv.z;
-    tmin0 = fmaxf(fmaxf(fminf(lx0, hx0), fminf(ly0, hy0)), fmaxf(fminf(lz0, hz0), 0.f));
-    const float tmax0 = fminf(fminf(fmaxf(lx0, hx0), fmaxf(ly0, hy0)), fminf(fmaxf(lz0, hz0), t_best));
-    tmin1 = fmaxf(fmaxf(fminf(lx1, hx1), fminf(ly1, hy1)), fmaxf(fminf(lz1, hz1), 0.f));
-    const float tmax1 = fminf(fminf(fmaxf(lx1, hx1), fmaxf(ly1, hy1)), fminf(fmaxf(lz1, hz1), t_best));
-    h0 = tmin0 <= tmax0 * kRobust;
-    h1 = tmin1 <= tmax1 * kRobust;
+    const float lx = (lox - r.o.x) * r.inv.x, hx = (hix - r.o.x) * r.inv.x;
+    const float ly = (loy - r.o.y) * r.inv.y, hy = (hiy - r.o.y) * r.inv.y;
+    const float lz = (loz - r.o.z) * r.inv.z, hz = (hiz - r.o.z) * r.inv.z;
+    tmin = fmaxf(fmaxf(fminf(lx, hx), fminf(ly, hy)), fmaxf(fminf(lz, hz), 0.f));
+    const float tmax = fminf(fminf(fmaxf(lx, hx), fmaxf(ly, hy)), fminf(fmaxf(lz, hz), t_best));
+    hit = tmin <= tmax * kRobust;
+}
+
+// Fetch node `node` and test its two child boxes; c0/c1 get the child refs
+// (inner node index >= 0 or leaf_ref(first, count) < 0).
+template <int FMT>
+__device__ __forceinline__ void node_children(const void* __restrict__ nodes, int node, const RaySetup& r,
+                                              float t_best, float& tmin0, float& tmin1, bool& h0, bool& h1,
+                                              int& c0, int& c1)
+{
+    if (FMT == FMT_FP32) {
+        const float4* np = reinterpret_cast<const float4*>(nodes) + 4ll * node;
+        const float4 n0 = ldg4(np), n1 = ldg4(np + 1), n2 = ldg4(np + 2), n3 = ldg4(np + 3);
+        slab_box(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, r, t_best, tmin0, h0);
+        slab_box(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, r, t_best, tmin1, h1);
+        c0 = __float_as_int(n3.x);
+        c1 = __float_as_int(n3.y);
+    } else {
+        const uint4* np = reinterpret_cast<const uint4*>(nodes) + 2ll * node;
+        const uint4 w0 = __ldg(np), w1 = __ldg(np + 1);
+        const float ox = __uint_as_float(w0.x), oy = __uint_as_float(w0.y), oz = __uint_as_float(w0.z);
+        const unsigned pk = w0.w;
+        const float sx = exp2_int((int)(signed char)(pk & 255u));
+        const float sy = exp2_int((int)(signed char)((pk >> 8) & 255u));
+        const float sz = exp2_int((int)(signed char)((pk >> 16) & 255u));
+        const unsigned meta = pk >> 24;
+        slab_box(fmaf(byte_f(w1.x, 0), sx, ox), fmaf(byte_f(w1.x, 3), sx, ox),
+                 fmaf(byte_f(w1.x, 1), sy, oy), fmaf(byte_f(w1.y, 0), sy, oy),
+                 fmaf(byte_f(w1.x, 2), sz, oz), fmaf(byte_f(w1.y, 1), sz, oz), r, t_best, tmin0, h0);
+        slab_box(fmaf(byte_f(w1.y, 2), sx, ox), fmaf(byte_f(w1.z, 1), sx, ox),
+                 fmaf(byte_f(w1.y, 3), sy, oy), fmaf(byte_f(w1.z, 2), sy, oy),
+                 fmaf(byte_f(w1.z, 0), sz, oz), fmaf(byte_f(w1.z, 3), sz, oz), r, t_best, tmin1, h1);
+        const int g = (int)w1.w;
+        c0 = (meta & 1u) ? leaf_ref(g - (int)((meta >> 1) & 7u), (int)((meta >> 1) & 7u) + 1) : g;
+        c1 = (meta & 16u) ? leaf_ref(g + 1, (int)((meta >> 5) & 7u) + 1) : g + 1;
+    }
 }
 
 struct Counts { unsigned visits = 0, tests = 0; };
 
-// Test the triangles of leaf `code` (~((first << 3) | (count - 1))).
-template <bool COUNT>
-__device__ __forceinline__ void test_leaf(const float4* __restrict__ tris, const RaySetup& r, int code, int skip,
-                                          float& t_best, int& best, int& best_orig, float& bu, float& bv,
-                                          Counts* cnt)
+// FP64 form of the watertight test on the same (FP32-valued) ray: used to
+// re-test hits the FP32 pass flags as near an edge or grazing.
+struct RaySetup64 {
+    double ox, oy, oz;
+    int kx, ky, kz;
+    double sx, sy, sz;
+};
+
+__device__ __forceinline__ RaySetup64 setup_ray64(float3 o, float3 d)
+{
+    RaySetup64 r;
+    r.ox = o.x; r.oy = o.y; r.oz = o.z;
+    const double dv[3] = {d.x, d.y, d.z};
+    int kz = 0;
+    if (fabs(dv[1]) > fabs(dv[kz])) kz = 1;
+    if (fabs(dv[2]) > fabs(dv[kz])) kz = 2;
+    int kx = kz == 2 ? 0 : kz + 1;
+    int ky = kx == 2 ? 0 : kx + 1;
+    if (dv[kz] < 0.0) { const int t = kx; kx = ky; ky = t; }
+    r.kx = kx; r.ky = ky; r.kz = kz;
+    r.sx = dv[kx] / dv[kz];
+    r.sy = dv[ky] / dv[kz];
+    r.sz = 1.0 / dv[kz];
+    return r;
+}
+
+__device__ __forceinline__ double comp(double x, double y, double z, int k) { return k == 0 ? x : (k == 1 ? y : z); }
+
+__device__ __forceinline__ bool intersect_tri64(const RaySetup64& r, float4 w0, float4 w1, float4 w2, double& t_best,
+                                                int& best_orig, float& bu, float& bv)
+{
+    const double a0 = w0.x - r.ox, a1 = w0.y - r.oy, a2 = w0.z - r.oz;
+    const double b0 = w1.x - r.ox, b1 = w1.y - r.oy, b2 = w1.z - r.oz;
+    const double c0 = w2.x - r.ox, c1 = w2.y - r.oy, c2 = w2.z - r.oz;
+    const double akz = comp(a0, a1, a2, r.kz), bkz = comp(b0, b1, b2, r.kz), ckz = comp(c0, c1, c2, r.kz);
+    const double ax = comp(a0, a1, a2, r.kx) - r.sx * akz, ay = comp(a0, a1, a2, r.ky) - r.sy * akz;
+    const double bx = comp(b0, b1, b2, r.kx) - r.sx * bkz, by = comp(b0, b1, b2, r.ky) - r.sy * bkz;
+    const double cx = comp(c0, c1, c2, r.kx) - r.sx * ckz, cy = comp(c0, c1, c2, r.ky) - r.sy * ckz;
+    const double U = cx * by - cy * bx, V = ax * cy - ay * cx, W = bx * ay - by * ax;
+    if (U < 0.0 || V < 0.0 || W < 0.0) return false;
+    const double det = U + V + W;
+    if (det == 0.0) return false;
+    const double T = U * (r.sz * akz) + V * (r.sz * bkz) + W * (r.sz * ckz);
+    if (T <= 0.0) return false;
+    if (T > t_best * det * (1.0 + 1e-12)) return false;     // cannot beat the best hit (det > 0)
+    const double t = T / det;                               // divisions only for candidates
+    const int orig = __float_as_int(w0.w);
+    if (t < t_best || (t == t_best && orig < best_orig)) {
+        t_best = t;
+        best_orig = orig;
+        const double inv = 1.0 / det;
+        bu = (float)(V * inv);
+        bv = (float)(W * inv);
+        return true;
+    }
+    return false;
+}
+
+// Test the triangles of a leaf ref.
+template <bool COUNT, bool TRI64>
+__device__ __forceinline__ void test_leaf(const float4* __restrict__ tris, const RaySetup& r, const RaySetup64& r64,
+                                          int code, int skip, float& t_best, double& t_best64, int& best,
+                                          int& best_orig, float& bu, float& bv, Counts* cnt)
 {
     const int v = ~code;
     const int first = v >> 3, count = (v & 7) + 1;
@@ -89,38 +178,45 @@ __device__ __forceinline__ void test_leaf(const float4* __restrict__ tris, const
         if (j == skip) continue;
         if (COUNT) ++cnt->tests;
         const float4* tp = tris + 3ll * j;
-        if (intersect_tri(r, ldg4(tp), ldg4(tp + 1), ldg4(tp + 2), t_best, best_orig, bu, bv)) best = j;
+        if (TRI64) {
+            if (intersect_tri64(r64, ldg4(tp), ldg4(tp + 1), ldg4(tp + 2), t_best64, best_orig, bu, bv)) {
+                best = j;
+                t_best = (float)t_best64;
+            }
+        } else {
+            if (intersect_tri(r, ldg4(tp), ldg4(tp + 1), ldg4(tp + 2), t_best, best_orig, bu, bv)) best = j;
+        }
     }
 }
 
-// Closest front-facing triangle (leaf order index) with t > 0, skipping `skip`:
-// one ray per lane, leaves tested as soon as their box is hit.
-template <bool COUNT = false>
-__device__ __forceinline__ int bvh_closest(const float4* __restrict__ nodes, const float4* __restrict__ tris,
-                                           const RaySetup& r, int skip, StackRef st, float& t_best,
-                                           float& bu, float& bv, unsigned& status, Counts* cnt = nullptr)
+// Closest front-facing triangle (leaf order index) with t > 0, skipping
+// `skip`: one ray per lane, leaves tested as soon as their box is hit.
+template <int FMT, bool COUNT = false, bool TRI64 = false>
+__device__ __forceinline__ int bvh_closest(const void* __restrict__ nodes, const float4* __restrict__ tris,
+                                           const RaySetup& r, const RaySetup64& r64, int skip, StackRef st,
+                                           float& t_best, float& bu, float& bv, unsigned& status,
+                                           Counts* cnt = nullptr)
 {
     int2 lstack[kStackMax - kSmemStack];
     int sp = 0;
     int node = 0;
     int best = -1, best_orig = INT_MAX;
+    double t_best64 = INFINITY;
     t_best = INFINITY;
     bu = bv = 0.f;
     for (int visits = 0;; ++visits) {
         if (visits >= kMaxVisits) { status |= ST_LOOP_LIMIT; break; }
         if (COUNT) ++cnt->visits;
-        const float4* np = nodes + 4ll * node;
-        const float4 n0 = ldg4(np), n1 = ldg4(np + 1), n2 = ldg4(np + 2), n3 = ldg4(np + 3);
         float tmin0, tmin1;
         bool h0, h1;
-        slab2(n0, n1, n2, r, t_best, tmin0, tmin1, h0, h1);
-        const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+        int c0, c1;
+        node_children<FMT>(nodes, node, r, t_best, tmin0, tmin1, h0, h1, c0, c1);
         if (h0 && c0 < 0) {
-            test_leaf<COUNT>(tris, r, c0, skip, t_best, best, best_orig, bu, bv, cnt);
+            test_leaf<COUNT, TRI64>(tris, r, r64, c0, skip, t_best, t_best64, best, best_orig, bu, bv, cnt);
             h0 = false;
         }
         if (h1 && c1 < 0) {
-            test_leaf<COUNT>(tris, r, c1, skip, t_best, best, best_orig, bu, bv, cnt);
+            test_leaf<COUNT, TRI64>(tris, r, r64, c1, skip, t_best, t_best64, best, best_orig, bu, bv, cnt);
             h1 = false;
         }
         if (h0 && h1) {
@@ -145,6 +241,7 @@ __device__ __forceinline__ int bvh_closest(const float4* __restrict__ nodes, con
         }
         if (!found) break;
     }
+    if (TRI64 && best >= 0) t_best = (float)t_best64;
     return best;
 }
 
@@ -152,11 +249,11 @@ struct Cell { float lx, ly, z_min, z_top; int max_wraps; };
 
 // Trace one ray segment by segment through the periodic cell (Section 2.2,
 // last paragraph).  Returns the hit record; *wraps gets the lateral re-entries.
-// The re-entry point is carried in FP64 (a few operations per wrap) so that a
-// ray that wraps many times does not accumulate FP32 rounding in its origin;
-// each cell query uses that point rounded to FP32.
-template <bool COUNT>
-__device__ __forceinline__ float4 trace_ray(const float4* __restrict__ nodes, const float4* __restrict__ tris,
+// The re-entry point is carried in FP64 (a few operations per wrap) so a ray
+// that wraps many times does not accumulate FP32 rounding in its origin; each
+// cell query uses that point rounded to FP32.
+template <int FMT, bool COUNT, bool TRI64>
+__device__ __forceinline__ float4 trace_ray(const void* __restrict__ nodes, const float4* __restrict__ tris,
                                             const float3 o32, const float3 d, int skip, const Cell& c, StackRef st,
                                             int& wraps, unsigned& status, Counts* cnt)
 {
@@ -165,8 +262,10 @@ __device__ __forceinline__ float4 trace_ray(const float4* __restrict__ nodes, co
     float3 o = o32;
     for (;;) {
         const RaySetup rs = setup_ray(o, d);
+        RaySetup64 r64;
+        if (TRI64) r64 = setup_ray64(o, d);
         float t, u, v;
-        const int j = bvh_closest<COUNT>(nodes, tris, rs, skip, st, t, u, v, status, cnt);
+        const int j = bvh_closest<FMT, COUNT, TRI64>(nodes, tris, rs, r64, skip, st, t, u, v, status, cnt);
         if (j >= 0) return make_float4(t, u, v, __int_as_float(j));
         double tx = INFINITY, ty = INFINITY, tz = INFINITY;
         if (d.x > 0.f) tx = ((double)c.lx - ox) / d.x; else if (d.x < 0.f) tx = (0.0 - ox) / d.x;
@@ -189,9 +288,9 @@ __device__ __forceinline__ float4 trace_ray(const float4* __restrict__ nodes, co
     }
 }
 
-template <bool RECORD, bool COUNT>
+template <int FMT, bool RECORD, bool COUNT>
 __global__ void __launch_bounds__(128)
-k_traverse(const float4* __restrict__ nodes, const float4* __restrict__ tris, Cell cell,
+k_traverse(const void* __restrict__ nodes, const float4* __restrict__ tris, Cell cell,
            const float4* __restrict__ oe, const float4* __restrict__ dt, float4* __restrict__ hits,
            int* __restrict__ wraps_out, Control* __restrict__ ctl, int gen, unsigned cap,
            Tally* __restrict__ tally)
@@ -212,8 +311,9 @@ k_traverse(const float4* __restrict__ nodes, const float4* __restrict__ tris, Ce
         if (i < n) {
             const float4 a = oe[i], b = dt[i];
             int w;
-            const float4 h = trace_ray<COUNT>(nodes, tris, make_float3(a.x, a.y, a.z), make_float3(b.x, b.y, b.z),
-                                              __float_as_int(b.w), cell, st, w, status, &cnt);
+            const float4 h = trace_ray<FMT, COUNT, false>(nodes, tris, make_float3(a.x, a.y, a.z),
+                                                          make_float3(b.x, b.y, b.z), __float_as_int(b.w), cell,
+                                                          st, w, status, &cnt);
             hits[i] = h;
             my_wraps += (unsigned)w;
             if (RECORD) wraps_out[i] = w;
@@ -244,16 +344,20 @@ k_traverse(const float4* __restrict__ nodes, const float4* __restrict__ tris, Ce
 // has one.  A lane whose ray finishes takes a new ray from the generation's
 // queue (one atomic per warp refill) instead of idling until the whole tile
 // is done.  The FP64 re-entry point of each lane lives in shared memory.
+// With RETEST, hits closer than kEdgeEps (barycentric) to an edge or with
+// cos(incidence) below kGrazeCos are listed for the FP64 re-test kernel.
 // --------------------------------------------------------------------------
 constexpr int kEntrySentinel = 0x76543210;   // "stack empty" (never a node index)
 constexpr int kFetchThreshold = 20;          // refill when fewer lanes than this are active
+constexpr float kEdgeEps = 1e-5f;
+constexpr float kGrazeCos = 1e-3f;
 
-template <bool RECORD, bool COUNT>
+template <int FMT, bool RECORD, bool COUNT, bool RETEST>
 __global__ void __launch_bounds__(128)
-k_traverse_ww(const float4* __restrict__ nodes, const float4* __restrict__ tris, Cell cell,
-              const float4* __restrict__ oe, const float4* __restrict__ dt, float4* __restrict__ hits,
+k_traverse_ww(const void* __restrict__ nodes, const float4* __restrict__ tris, const float4* __restrict__ normals,
+              Cell cell, const float4* __restrict__ oe, const float4* __restrict__ dt, float4* __restrict__ hits,
               int* __restrict__ wraps_out, Control* __restrict__ ctl, int gen, unsigned cap,
-              Tally* __restrict__ tally)
+              unsigned* __restrict__ retest_list, Tally* __restrict__ tally)
 {
     extern __shared__ int2 s_stack[];                                   // [kSmemStack][blockDim]
     const int B = blockDim.x, tid = threadIdx.x, lane = tid & 31;
@@ -266,7 +370,9 @@ k_traverse_ww(const float4* __restrict__ nodes, const float4* __restrict__ tris,
     bool exhausted = false, drained = false;
     float3 o = make_float3(0.f, 0.f, 0.f), d = make_float3(0.f, 0.f, 1.f);
     RaySetup rs = setup_ray(o, d);
+    RaySetup64 r64;
     float t_best = INFINITY, bu = 0.f, bv = 0.f;
+    double t_best64 = INFINITY;
     int best = -1, best_orig = INT_MAX, node = kEntrySentinel, leaf = 0, sp = 0, skip = -1, wraps = 0, visits = 0;
     unsigned status = 0;
     unsigned long long my_wraps = 0;
@@ -326,12 +432,10 @@ k_traverse_ww(const float4* __restrict__ nodes, const float4* __restrict__ tris,
             while (node >= 0 && node != kEntrySentinel) {
                 if (++visits > kMaxVisits) { status |= ST_LOOP_LIMIT; node = kEntrySentinel; leaf = 0; sp = 0; break; }
                 if (COUNT) ++cnt.visits;
-                const float4* np = nodes + 4ll * node;
-                const float4 n0 = ldg4(np), n1 = ldg4(np + 1), n2 = ldg4(np + 2), n3 = ldg4(np + 3);
                 float tmin0, tmin1;
                 bool h0, h1;
-                slab2(n0, n1, n2, rs, t_best, tmin0, tmin1, h0, h1);
-                const int c0 = __float_as_int(n3.x), c1 = __float_as_int(n3.y);
+                int c0, c1;
+                node_children<FMT>(nodes, node, rs, t_best, tmin0, tmin1, h0, h1, c0, c1);
                 if (h0 && h1) {
                     const bool first0 = tmin0 <= tmin1;
                     push(first0 ? c1 : c0, first0 ? tmin1 : tmin0);
@@ -345,7 +449,7 @@ k_traverse_ww(const float4* __restrict__ nodes, const float4* __restrict__ tris,
                 if (!__any_sync(__activemask(), leaf == 0)) break;
             }
             while (leaf < 0) {
-                test_leaf<COUNT>(tris, rs, leaf, skip, t_best, best, best_orig, bu, bv, &cnt);
+                test_leaf<COUNT, false>(tris, rs, r64, leaf, skip, t_best, t_best64, best, best_orig, bu, bv, &cnt);
                 leaf = 0;
                 if (node < 0) { leaf = node; node = pop(); }
             }
@@ -356,6 +460,17 @@ k_traverse_ww(const float4* __restrict__ nodes, const float4* __restrict__ tris,
 
         if (best >= 0) {
             hits[ray] = make_float4(t_best, bu, bv, __int_as_float(best));
+            if (RETEST) {
+                bool flag = fminf(fminf(bu, bv), 1.f - bu - bv) < kEdgeEps;
+                if (!flag) {
+                    const float4 nr = ldg4(normals + best);
+                    flag = -(d.x * nr.x + d.y * nr.y + d.z * nr.z) < kGrazeCos;
+                }
+                if (flag) {
+                    const unsigned slot = atomicAdd(&ctl->n_retest[gen], 1u);
+                    if (slot < cap) retest_list[slot] = (unsigned)ray;
+                }
+            }
         } else {
             // no facet in this cell: leave through a face (FP64 re-entry point)
             double ox = s_o[tid], oy = s_o[B + tid], oz = s_o[2 * B + tid];
@@ -407,6 +522,39 @@ k_traverse_ww(const float4* __restrict__ nodes, const float4* __restrict__ tris,
         if (my_wraps) atomicAdd(&tally->wraps, my_wraps);
         if (status) atomicOr(&tally->status, (unsigned long long)status);
     }
+}
+
+// FP64 re-test of the flagged rays of one generation: the whole ray is traced
+// again (same FP32 ray, same FP32 boxes, triangle tests in FP64) and its hit
+// record (and wrap count) replaced.
+template <int FMT, bool RECORD>
+__global__ void __launch_bounds__(128)
+k_retest(const void* __restrict__ nodes, const float4* __restrict__ tris, Cell cell, const float4* __restrict__ oe,
+         const float4* __restrict__ dt, float4* __restrict__ hits, int* __restrict__ wraps_out,
+         Control* __restrict__ ctl, int gen, unsigned cap, const unsigned* __restrict__ retest_list,
+         Tally* __restrict__ tally)
+{
+    extern __shared__ int2 s_stack[];
+    const StackRef st{s_stack, (int)blockDim.x, (int)threadIdx.x};
+    const unsigned n = min(*((volatile unsigned*)&ctl->n_retest[gen]), cap);
+    unsigned status = 0;
+    long long wdelta = 0;
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const unsigned i = retest_list[k];
+        const float4 a = oe[i], b = dt[i];
+        int w;
+        const float4 h = trace_ray<FMT, false, true>(nodes, tris, make_float3(a.x, a.y, a.z),
+                                                     make_float3(b.x, b.y, b.z), __float_as_int(b.w), cell, st, w,
+                                                     status, nullptr);
+        hits[i] = h;
+        if (RECORD) {
+            wdelta += (long long)w - (long long)wraps_out[i];
+            wraps_out[i] = w;
+        }
+    }
+    if (status) atomicOr(&tally->status, (unsigned long long)status);
+    if (RECORD && wdelta) atomicAdd(&tally->wraps, (unsigned long long)wdelta);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && n) atomicAdd(&tally->retested, (unsigned long long)n);
 }
 
 // --------------------------------------------------------------------------
@@ -700,8 +848,9 @@ __global__ void k_finalize(unsigned* __restrict__ kcount, unsigned n, Tally* __r
 // --------------------------------------------------------------------------
 // test hooks
 // --------------------------------------------------------------------------
+template <int FMT>
 __global__ void __launch_bounds__(128)
-k_trace_rays(const float4* __restrict__ nodes, const float4* __restrict__ tris, const int* __restrict__ inv_order,
+k_trace_rays(const void* __restrict__ nodes, const float4* __restrict__ tris, const int* __restrict__ inv_order,
              int n_tri, const float* __restrict__ o, const float* __restrict__ d, const int* __restrict__ skip,
              int64_t n, rtmc_hit* __restrict__ hits, unsigned* __restrict__ status_out)
 {
@@ -714,7 +863,8 @@ k_trace_rays(const float4* __restrict__ nodes, const float4* __restrict__ tris, 
     const int sk = (skip && skip[i] >= 0 && skip[i] < n_tri) ? inv_order[skip[i]] : -1;
     unsigned status = 0;
     float t, u, v;
-    const int j = bvh_closest(nodes, tris, setup_ray(oo, dd), sk, st, t, u, v, status);
+    RaySetup64 r64;
+    const int j = bvh_closest<FMT>(nodes, tris, setup_ray(oo, dd), r64, sk, st, t, u, v, status);
     rtmc_hit h;
     h.t = t; h.u = u; h.v = v;
     h.tri = j >= 0 ? __float_as_int(__ldg(tris + 3ll * j).w) : -1;
@@ -745,36 +895,62 @@ cudaError_t launch_generate(const RunParams& p, const Queues& q, int buf, unsign
     return cudaGetLastError();
 }
 
-template <bool R, bool C>
+template <int F, bool R, bool C>
 static cudaError_t traverse_t(const DeviceMesh& m, const RunParams& p, const Queues& q, int buf, int gen,
-                              int num_sms, const Tuning& tune, cudaStream_t s)
+                              int num_sms, const Tuning& tune, bool retest, cudaStream_t s)
 {
     const Cell cell{p.lx, p.ly, p.z_min, p.z_top, p.max_wraps};
+    const void* nodes = F == FMT_Q8 ? m.q8 : (const void*)m.nodes;
     const int bt = tune.block_threads;
     int per_sm = tune.blocks_per_sm;
     if (tune.traversal == 1) {
         const size_t smem = (size_t)kSmemStack * bt * sizeof(int2);
-        if (per_sm <= 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse<R, C>, bt, smem);
-        k_traverse<R, C><<<num_sms * (per_sm > 0 ? per_sm : 1), bt, smem, s>>>(
-            m.nodes, m.tris, cell, q.oe[buf], q.dt[buf], q.hits, R ? q.wraps : nullptr, q.ctl, gen, q.cap[buf],
+        if (per_sm <= 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse<F, R, C>, bt, smem);
+        k_traverse<F, R, C><<<num_sms * (per_sm > 0 ? per_sm : 1), bt, smem, s>>>(
+            nodes, m.tris, cell, q.oe[buf], q.dt[buf], q.hits, R ? q.wraps : nullptr, q.ctl, gen, q.cap[buf],
             q.tally);
     } else {
         const size_t smem = (size_t)kSmemStack * bt * sizeof(int2) + 3 * (size_t)bt * sizeof(double);
-        if (per_sm <= 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse_ww<R, C>, bt, smem);
-        k_traverse_ww<R, C><<<num_sms * (per_sm > 0 ? per_sm : 1), bt, smem, s>>>(
-            m.nodes, m.tris, cell, q.oe[buf], q.dt[buf], q.hits, R ? q.wraps : nullptr, q.ctl, gen, q.cap[buf],
-            q.tally);
+        if (retest) {
+            if (per_sm <= 0)
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse_ww<F, R, C, true>, bt, smem);
+            k_traverse_ww<F, R, C, true><<<num_sms * (per_sm > 0 ? per_sm : 1), bt, smem, s>>>(
+                nodes, m.tris, m.normals, cell, q.oe[buf], q.dt[buf], q.hits, R ? q.wraps : nullptr, q.ctl, gen,
+                q.cap[buf], q.retest, q.tally);
+        } else {
+            if (per_sm <= 0)
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse_ww<F, R, C, false>, bt, smem);
+            k_traverse_ww<F, R, C, false><<<num_sms * (per_sm > 0 ? per_sm : 1), bt, smem, s>>>(
+                nodes, m.tris, m.normals, cell, q.oe[buf], q.dt[buf], q.hits, R ? q.wraps : nullptr, q.ctl, gen,
+                q.cap[buf], nullptr, q.tally);
+        }
     }
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && retest && tune.traversal != 1) {
+        const int tb = 64;
+        const size_t smem = (size_t)kSmemStack * tb * sizeof(int2);
+        k_retest<F, R><<<num_sms, tb, smem, s>>>(nodes, m.tris, cell, q.oe[buf], q.dt[buf], q.hits,
+                                                 R ? q.wraps : nullptr, q.ctl, gen, q.cap[buf], q.retest, q.tally);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+template <int F>
+static cudaError_t traverse_f(const DeviceMesh& m, const RunParams& p, const Queues& q, int buf, int gen,
+                              int num_sms, const Tuning& tune, bool record, bool count, bool retest, cudaStream_t s)
+{
+    if (record) return count ? traverse_t<F, true, true>(m, p, q, buf, gen, num_sms, tune, retest, s)
+                             : traverse_t<F, true, false>(m, p, q, buf, gen, num_sms, tune, retest, s);
+    return count ? traverse_t<F, false, true>(m, p, q, buf, gen, num_sms, tune, retest, s)
+                 : traverse_t<F, false, false>(m, p, q, buf, gen, num_sms, tune, retest, s);
 }
 
 cudaError_t launch_traverse(const DeviceMesh& m, const RunParams& p, const Queues& q, int buf, int gen,
-                            int num_sms, const Tuning& tune, bool record, bool count, cudaStream_t s)
+                            int num_sms, const Tuning& tune, bool record, bool count, bool retest, cudaStream_t s)
 {
-    if (record) return count ? traverse_t<true, true>(m, p, q, buf, gen, num_sms, tune, s)
-                             : traverse_t<true, false>(m, p, q, buf, gen, num_sms, tune, s);
-    return count ? traverse_t<false, true>(m, p, q, buf, gen, num_sms, tune, s)
-                 : traverse_t<false, false>(m, p, q, buf, gen, num_sms, tune, s);
+    if (m.kind == FMT_Q8) return traverse_f<FMT_Q8>(m, p, q, buf, gen, num_sms, tune, record, count, retest, s);
+    return traverse_f<FMT_FP32>(m, p, q, buf, gen, num_sms, tune, record, count, retest, s);
 }
 
 cudaError_t launch_shade(const DeviceMesh& m, const RunParams& p, const TableDesc& tab, const Emission& em,
@@ -814,9 +990,12 @@ cudaError_t launch_trace_rays(const DeviceMesh& m, const float* o, const float* 
     const int tb = 128;
     const size_t smem = (size_t)kSmemStack * tb * sizeof(int2);
     const int64_t gb = (n + tb - 1) / tb;
-    if (gb > 0)
-        k_trace_rays<<<(unsigned)gb, tb, smem, s>>>(m.nodes, m.tris, m.inv_order, (int)m.n_tri, o, d, skip, n,
-                                                    hits, status);
+    if (gb > 0 && m.kind == FMT_Q8)
+        k_trace_rays<FMT_Q8><<<(unsigned)gb, tb, smem, s>>>(m.q8, m.tris, m.inv_order, (int)m.n_tri, o, d, skip, n,
+                                                            hits, status);
+    else if (gb > 0)
+        k_trace_rays<FMT_FP32><<<(unsigned)gb, tb, smem, s>>>(m.nodes, m.tris, m.inv_order, (int)m.n_tri, o, d, skip,
+                                                              n, hits, status);
     return cudaGetLastError();
 }
 

@@ -20,12 +20,13 @@ OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NOT_LOADED", -5: "NOT_BUILT",
           -6: "CAPACITY", -7: "TIMEOUT", -8: "DEVICE_CHECK"}
 BVH_FP32 = 0
+BVH_Q8 = 1
 ESCAPED, EMITTER, ABSORBED_LOW, ABSORBED_OTHER, LOST = 0, 1, 2, 3, 4
 
 EXPORTS = ["rtmc_create", "rtmc_destroy", "rtmc_last_error", "rtmc_load_mesh", "rtmc_unload_mesh",
            "rtmc_load_see_tables",
            "rtmc_build_bvh", "rtmc_run", "rtmc_run_records", "rtmc_trace_rays", "rtmc_philox",
-           "rtmc_record_hash", "rtmc_run_noalloc"]
+           "rtmc_record_hash", "rtmc_run_noalloc", "rtmc_export_bvh"]
 NOALLOC_MAX_PRIMARIES = 4096
 
 
@@ -55,7 +56,7 @@ class RunDesc(C.Structure):
                 ("src_x0", C.c_double), ("src_x1", C.c_double), ("src_y0", C.c_double), ("src_y1", C.c_double),
                 ("chunk", C.c_int64), ("block_threads", C.c_int32), ("blocks_per_sm", C.c_int32),
                 ("prim_hash", C.c_void_p), ("profile", C.c_int32), ("count_visits", C.c_int32),
-                ("traversal", C.c_int32)]
+                ("traversal", C.c_int32), ("fp64_retest", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -65,7 +66,7 @@ class Result(C.Structure):
         (n, C.c_double) for n in ("e_sum", "e2_sum", "sey", "sey_se", "gpu_ms")] + [
         (n, C.c_int64) for n in ("launches", "node_visits", "tri_tests")] + [
         (n, C.c_double) for n in ("ms_generate", "ms_traverse", "ms_shade", "ms_finalize")] + [
-        ("traverse_launches", C.c_int64)]
+        ("traverse_launches", C.c_int64), ("retested", C.c_int64)]
 
 
 class Record(C.Structure):
@@ -108,6 +109,7 @@ def lib():
     L.rtmc_run_noalloc.argtypes = [vp, i32, C.c_double, C.c_double, C.c_uint32, i64, u64, C.POINTER(RunDesc),
                                    C.POINTER(Result), vp, vp]
     L.rtmc_philox.argtypes = [vp, vp, i64, u64, vp]
+    L.rtmc_export_bvh.argtypes = [vp, i32, i32, vp, i64, C.POINTER(i64)]
     L.rtmc_record_hash.argtypes = [C.POINTER(Record)]
     L.rtmc_record_hash.restype = u64
     for name in EXPORTS:
@@ -138,12 +140,12 @@ class Emission:
 
 def run_desc(n_ebins=64, n_abins=18, hist_e_max_ev=50.0, primary_offset=0, random_azimuth=False,
              max_wraps=1024, window=None, chunk=0, block_threads=0, blocks_per_sm=0, prim_hash=None,
-             profile=False, count_visits=False, traversal=0):
+             profile=False, count_visits=False, traversal=0, fp64_retest=False):
     x0, x1, y0, y1 = window if window is not None else (0.0, 0.0, 0.0, 0.0)
     return RunDesc(int(n_ebins), int(n_abins), float(hist_e_max_ev), int(primary_offset),
                    int(bool(random_azimuth)), int(max_wraps), x0, x1, y0, y1, int(chunk), int(block_threads),
                    int(blocks_per_sm), prim_hash.data_ptr() if prim_hash is not None else None,
-                   int(bool(profile)), int(bool(count_visits)), int(traversal))
+                   int(bool(profile)), int(bool(count_visits)), int(traversal), int(bool(fp64_retest)))
 
 
 def result_dict(r: Result):
@@ -258,6 +260,14 @@ class Context:
         hits = np.zeros(n, dtype=HIT_DTYPE)
         self._check(self._L.rtmc_trace_rays(self.h, int(mesh_id), _ptr(o), _ptr(d), _ptr(sk), n, _ptr(hits)))
         return hits
+
+    def export_bvh(self, mesh_id, which):
+        """Raw bytes of a built BVH array (0 FP32 nodes, 1 Q8 nodes, 2 triangles)."""
+        need = C.c_int64()
+        self._check(self._L.rtmc_export_bvh(self.h, int(mesh_id), int(which), None, 0, C.byref(need)))
+        buf = np.zeros(need.value, dtype=np.uint8)
+        self._check(self._L.rtmc_export_bvh(self.h, int(mesh_id), int(which), _ptr(buf), need.value, C.byref(need)))
+        return buf
 
     def philox(self, ctr, key):
         c = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)

@@ -82,13 +82,15 @@ def _rays_for(mesh, n, rng):
     return np.concatenate([o, o2]).astype(np.float32), np.concatenate([d, d2]).astype(np.float32)
 
 
+@pytest.mark.parametrize("kind,leaf", [(0, 4), (0, 1), (1, 4), (1, 8)])
 @pytest.mark.parametrize("which", ["tiny", "flat", "well", "single", "foam8"])
-def test_bvh_closest_hit_matches_brute_force(ctx, which):
+def test_bvh_closest_hit_matches_brute_force(ctx, which, kind, leaf):
     mesh = {"tiny": lambda: I.grf_foam(16, 0.5), "flat": lambda: I.flat_plane(),
             "well": lambda: I.square_well(100.0, 60.0),
             "single": lambda: I.Mesh(I.flat_plane().tri[:1], I.flat_plane().box),
             "foam8": lambda: I.grf_foam(8, 0.7, 1.5, 3)}[which]()
-    mid = _mesh_id(ctx, mesh)
+    mid = ctx.load_mesh(mesh.tri, mesh.box)
+    ctx.build_bvh(mid, kind=kind, leaf=leaf)
     rng = np.random.default_rng(42)
     o, d = _rays_for(mesh, 4000, rng)
     skip = rng.integers(-1, mesh.n_tri, o.shape[0]).astype(np.int32)

@@ -1,0 +1,125 @@
+"""Precision form: 8-bit quantised 32-byte nodes and the FP64 re-test (GB300)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1806_00205_gb300 import inputs as I
+from tests.parity import compare_records, primary_hashes
+
+pytestmark = pytest.mark.gpu
+TABLE = I.see_table()
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1806_00205_gb300 import rtmc
+    c = rtmc.Context(0)
+    c.load_see_tables(TABLE)
+    yield c
+    c.close()
+
+
+def _decode_q8(raw):
+    """Decode Q8 nodes (float32 arithmetic as on the device: origin + q 2^e, one rounding)."""
+    w = raw.view(np.uint32).reshape(-1, 8)
+    origin = w[:, 0:3].view(np.float32)
+    pk = w[:, 3]
+    exps = np.stack([(pk >> (8 * k)) & 255 for k in range(3)], axis=1).astype(np.uint8).view(np.int8)
+    scale = np.ldexp(np.float32(1.0), exps.astype(np.int32)).astype(np.float32)
+    meta = (pk >> 24) & 255
+    qb = np.stack([(w[:, 4 + k // 4] >> (8 * (k % 4))) & 255 for k in range(12)], axis=1).astype(np.float32)
+    gamma = w[:, 7].view(np.int32)
+    boxes = np.empty((w.shape[0], 2, 2, 3), dtype=np.float32)      # node, child, lo/hi, axis
+    for c in range(2):
+        for lh in range(2):
+            for ax in range(3):
+                q = qb[:, 6 * c + 3 * lh + ax]
+                boxes[:, c, lh, ax] = origin[:, ax] + q * scale[:, ax]     # q * 2^e is exact
+    cnt0 = ((meta >> 1) & 7).astype(np.int64)
+    cnt1 = ((meta >> 5) & 7).astype(np.int64)
+    g = gamma.astype(np.int64)
+    ref0 = np.where(meta & 1, ~(((g - cnt0) << 3) | cnt0), g)
+    ref1 = np.where(meta & 16, ~(((g + 1) << 3) | cnt1), g + 1)
+    return boxes, ref0.astype(np.int32), ref1.astype(np.int32)
+
+
+def _decode_fp32(raw):
+    f = raw.view(np.float32).reshape(-1, 16)
+    i = raw.view(np.int32).reshape(-1, 16)
+    boxes = np.empty((f.shape[0], 2, 2, 3), dtype=np.float32)
+    boxes[:, 0, 0] = np.stack([f[:, 0], f[:, 2], f[:, 8]], axis=1)
+    boxes[:, 0, 1] = np.stack([f[:, 1], f[:, 3], f[:, 9]], axis=1)
+    boxes[:, 1, 0] = np.stack([f[:, 4], f[:, 6], f[:, 10]], axis=1)
+    boxes[:, 1, 1] = np.stack([f[:, 5], f[:, 7], f[:, 11]], axis=1)
+    return boxes, i[:, 12], i[:, 13]
+
+
+@pytest.mark.parametrize("n,p,leaf", [(16, 0.5, 4), (48, 0.3, 1), (128, 0.6, 4)])
+def test_q8_boxes_contain_fp32_boxes(ctx, n, p, leaf):
+    """Exhaustive: every decoded 8-bit child box contains its exact FP32 box."""
+    from paper_1806_00205_gb300 import rtmc
+    mesh = I.grf_foam(n, p)
+    mid = ctx.load_mesh(mesh.tri, mesh.box)
+    ctx.build_bvh(mid, kind=rtmc.BVH_Q8, leaf=leaf)
+    qb, q0, q1 = _decode_q8(ctx.export_bvh(mid, 1))
+    fb, f0, f1 = _decode_fp32(ctx.export_bvh(mid, 0))
+    ctx.unload_mesh(mid)
+    assert qb.shape == fb.shape
+    assert np.all(qb[:, :, 0] <= fb[:, :, 0]) and np.all(qb[:, :, 1] >= fb[:, :, 1])
+    assert np.array_equal(q0, f0) and np.array_equal(q1, f1)
+    # the quantised boxes stay tight: at most a few quanta looser per side
+    ext = np.maximum(fb[:, :, 1] - fb[:, :, 0], 1e-6)
+    grow = ((qb[:, :, 1] - qb[:, :, 0]) - (fb[:, :, 1] - fb[:, :, 0])) / ext
+    assert np.median(grow) < 0.05
+
+
+@pytest.mark.parametrize("kind,retest", [(1, False), (1, True), (0, True)])
+def test_precision_form_records_match_oracle(ctx, kind, retest):
+    from paper_1806_00205_gb300 import rtmc
+    mesh = I.grf_foam(16, 0.5)
+    mid = ctx.load_mesh(mesh.tri, mesh.box)
+    ctx.build_bvh(mid, kind=kind)
+    n = 100_000
+    g = ctx.run_records(mid, 300.0, 0.0, n, seed=1806, desc=rtmc.run_desc(fp64_retest=retest))
+    ctx.unload_mesh(mid)
+    o = O.run(mesh, TABLE, 300.0, 0.0, n, seed=1806, records=True)
+    st = compare_records(g["records"], o["records"])
+    assert st["frac_same"] >= 0.9999, {k: v for k, v in st.items() if k != "mismatch"}
+    assert st["t_rel_p999"] <= 1e-5
+    if retest:
+        assert 0 < g["retested"] <= 1e-3 * g["rays"]
+    else:
+        assert g["retested"] == 0
+
+
+def test_precision_config_sey_vs_plain_and_oracle(ctx):
+    """Precision config: 128^3 foams at porosity 0.4 / 0.6 / 0.8, E in {100, 300, 700} eV,
+    incidence 0 and 60 deg.  Q8 nodes + FP64 re-test against FP32 nodes (same streams),
+    and sampled primaries against the oracle."""
+    import torch
+    from paper_1806_00205_gb300 import rtmc
+    n = 1_000_000
+    for porosity in (0.4, 0.6, 0.8):
+        mesh = I.grf_foam(128, porosity)
+        m32 = ctx.load_mesh(mesh.tri, mesh.box)
+        ctx.build_bvh(m32, kind=rtmc.BVH_FP32)
+        mq = ctx.load_mesh(mesh.tri, mesh.box)
+        ctx.build_bvh(mq, kind=rtmc.BVH_Q8)
+        plain, _, _ = ctx.run(m32, [100.0, 300.0, 700.0], [0.0, 60.0], n, 1806)
+        prec, _, _ = ctx.run(mq, [100.0, 300.0, 700.0], [0.0, 60.0], n, 1806, desc=rtmc.run_desc(fp64_retest=True))
+        for a, b in zip(plain, prec):
+            assert abs(a["sey"] - b["sey"]) <= 1e-3
+            assert b["retested"] <= 1e-3 * b["rays"]
+        h = torch.zeros(n, dtype=torch.int64, device="cuda")
+        ctx.run(mq, [300.0], [60.0], n, 1806, desc=rtmc.run_desc(fp64_retest=True, prim_hash=h))
+        ids = np.sort(np.random.default_rng(3).choice(n, 150, replace=False)).astype(np.uint64)
+        o = O.run(mesh, TABLE, 300.0, 60.0, 0, seed=1806, prim_ids=ids, records=True)
+        dev = h.cpu().numpy().view(np.uint64)[ids.astype(np.int64)]
+        assert np.sum(dev != primary_hashes(o["records"], ids)) <= 1
+        ctx.unload_mesh(m32)
+        ctx.unload_mesh(mq)
