@@ -164,10 +164,86 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def l2_copy_gbs(torch, dev):
+    """Achievable L2 bandwidth: device copy between two 24 MiB buffers (both stay in L2)."""
+    a = torch.empty(6 * 1024 * 1024, dtype=torch.float32, device=dev)
+    b = torch.empty_like(a)
+    a.fill_(1.0)
+    for _ in range(5):
+        b.copy_(a)
+    best = float("inf")
+    for _ in range(20):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            b.copy_(a)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        best = min(best, e0.elapsed_time(e1) / 10)
+    return 2 * a.numel() * 4 / (best / 1e3) / 1e9
+
+
+def run_forms(ctx, rtmc, autotune, n_prim):
+    """Batched config: 16 foams (48^3..128^3, porosity 0.3..0.9) x 20 energies x 9 angles.
+
+    Compares the batched form (multi-item queues, one CUDA graph, autotuned,
+    Q8 or FP32 nodes) with the plain form (rtmc_run item by item, FP32 nodes)."""
+    import torch
+    from paper_1806_00205_gb300 import inputs as I
+    cfg = I.batched_foams()
+    meshes = [I.grf_foam(g, p, CORR, sd) for g, p, sd in cfg]
+    energies = [50.0 * i for i in range(1, 21)]
+    thetas = [10.0 * j for j in range(9)]
+    ids32, idsq = [], []
+    for m in meshes:
+        a = ctx.load_mesh(m.tri, m.box)
+        ctx.build_bvh(a, kind=rtmc.BVH_FP32)
+        ids32.append(a)
+        b = ctx.load_mesh(m.tri, m.box)
+        ctx.build_bvh(b, kind=rtmc.BVH_Q8)
+        idsq.append(b)
+    ntri = [m.n_tri for m in meshes]
+    pq = autotune.tune(ctx, idsq, ntri, energies, thetas, kind=1, cache_path=None, device_name="gb300")
+    p32 = autotune.tune(ctx, ids32, ntri, energies, thetas, kind=0, cache_path=None, device_name="gb300")
+    per_mesh = len(energies) * len(thetas)
+
+    def plain():
+        out = []
+        for mi, mid in enumerate(ids32):
+            r, _, _ = ctx.run(mid, energies, thetas, n_prim, SEED, desc=rtmc.run_desc(item_base=mi * per_mesh))
+            out += r
+        return out
+
+    forms = {}
+    results = {}
+    for name, fn in (("batched_q8", lambda: ctx.run_batch(idsq, energies, thetas, n_prim, SEED,
+                                                          desc=rtmc.run_desc(**pq))[0]),
+                     ("batched_fp32", lambda: ctx.run_batch(ids32, energies, thetas, n_prim, SEED,
+                                                            desc=rtmc.run_desc(**p32))[0]),
+                     ("plain_fp32", plain)):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        rays = sum(x["rays"] for x in r)
+        forms[name] = {"rays_per_s": rays / dt, "primaries_per_s": len(r) * n_prim / dt, "s": dt}
+        results[name] = r
+    d_sey = max(abs(a["sey"] - b["sey"]) for a, b in zip(results["batched_q8"], results["plain_fp32"]))
+    for mid in ids32 + idsq:
+        ctx.unload_mesh(mid)
+    return {"workload": f"16 GRF foams (grids 48^3..128^3, porosity 0.30..0.90, {min(ntri)}..{max(ntri)} "
+                        f"triangles) x 20 energies (50..1000 eV) x 9 angles (0..80 deg) x {n_prim:.0e} primaries",
+            "forms": forms, "max_abs_sey_diff_batched_q8_vs_plain_fp32": d_sey,
+            "speedup_batched_q8_vs_plain_fp32": forms["plain_fp32"]["s"] / forms["batched_q8"]["s"],
+            "autotuned": {"batched_q8": pq, "batched_fp32": p32}}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
-    from paper_1806_00205_gb300 import rtmc
+    from paper_1806_00205_gb300 import autotune, rtmc
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -186,15 +262,17 @@ def run_ours(args):
     mid = ctx.load_mesh(mesh.tri, mesh.box)
     ctx.build_bvh(mid)
     offset = rank * n_prim * len(energies)      # weak scaling: each rank its own primary ids
-    desc = rtmc.run_desc(primary_offset=offset, profile=True)
+    tuned = autotune.tune(ctx, [mid], [mesh.n_tri], energies, [0.0], kind=0, cache_path=None,
+                          device_name=torch.cuda.get_device_name(dev))
+    desc = rtmc.run_desc(primary_offset=offset, profile=True, no_graph=True, **tuned)
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    def step():
-        return ctx.run(mid, energies, [0.0], n_prim, SEED, desc=desc)
+    def step(d=desc):
+        return ctx.run_batch([mid], energies, [0.0], n_prim, SEED, desc=d)
 
     for _ in range(args.warmup):
         step()
@@ -208,12 +286,11 @@ def run_ours(args):
     results = None
     for _ in range(args.steps):
         results, _, _ = step()
-        for r in results:
-            rays += r["rays"]
-            prims += r["n_primaries"]
-            launches += r["launches"]
-            trav_launches += r["traverse_launches"]
-            trav_ms += r["ms_traverse"]
+        rays += sum(r["rays"] for r in results)
+        prims += sum(r["n_primaries"] for r in results)
+        launches += results[0]["launches"]
+        trav_launches += results[0]["traverse_launches"]
+        trav_ms += results[0]["ms_traverse"]
     ev1.record(stream)
     barrier()
     clk = clocks.stop()
@@ -227,31 +304,52 @@ def run_ours(args):
         ms, rays, prims = tmax.item(), tsum[0].item(), tsum[1].item()
     value = rays / (ms / 1e3)
 
+    # the same steps replayed from the captured CUDA graph
+    gdesc = rtmc.run_desc(primary_offset=offset, **tuned)
+    step(gdesc)
+    barrier()
+    g0 = time.perf_counter()
+    for _ in range(args.steps):
+        step(gdesc)
+    barrier()
+    graph_ms = (time.perf_counter() - g0) * 1e3 / args.steps
+
+    # plain form (rtmc_run item by item) on the same workload
+    pdesc = rtmc.run_desc(primary_offset=offset)
+    ctx.run(mid, energies, [0.0], n_prim, SEED, desc=pdesc)
+    barrier()
+    p0 = time.perf_counter()
+    pres, _, _ = ctx.run(mid, energies, [0.0], n_prim, SEED, desc=pdesc)
+    barrier()
+    plain_s = time.perf_counter() - p0
+    assert all(a["sum_k"] == b["sum_k"] for a, b in zip(pres, results)), "batched and plain tallies differ"
+
     # node-visit counts of the same workload (counting variant, untimed) -> algorithmic bytes
-    cres, _, _ = ctx.run(mid, energies, [0.0], n_prim, SEED,
-                         desc=rtmc.run_desc(primary_offset=offset, count_visits=True))
+    cres, _, _ = ctx.run_batch([mid], energies, [0.0], n_prim, SEED,
+                               desc=rtmc.run_desc(primary_offset=offset, count_visits=True, no_graph=True, **tuned))
     c_rays = sum(r["rays"] for r in cres)
-    visits = sum(r["node_visits"] for r in cres) / c_rays
-    tests = sum(r["tri_tests"] for r in cres) / c_rays
+    visits = cres[0]["node_visits"] / c_rays
+    tests = cres[0]["tri_tests"] / c_rays
     b_ray = visits * NODE_BYTES + tests * TRI_BYTES + RAY_BYTES
     local_rays = sum(r["rays"] for r in results) * args.steps
     achieved = local_rays * b_ray / (trav_ms / 1e3) / 1e9
     pk, pk_kind = peaks()
     peak = float(pk.get("hbm_gbs", 6800.0))
     traffic = measured_traffic()
+    l2_gbs = l2_copy_gbs(torch, dev)
 
     # end to end through the C ABI from pinned host memory
     tri_host = torch.from_numpy(mesh.tri.reshape(-1, 9)).pin_memory()
     h2d = tri_host.numel() * 4 + table.delta.nbytes + 8 * (len(energies) + 1)
     d2h = len(energies) * (rtmc.C.sizeof(rtmc.Result) + 8 * (64 + 18))
-    e2e_desc = rtmc.run_desc(primary_offset=offset)
+    e2e_desc = rtmc.run_desc(primary_offset=offset, no_graph=True, **tuned)
     barrier()
     e_t0 = time.perf_counter()
     e_rays = 0
     for _ in range(args.e2e_steps):
         m2 = ctx.load_mesh(tri_host, mesh.box)
         ctx.build_bvh(m2)
-        rr, _, _ = ctx.run(m2, energies, [0.0], n_prim, SEED, desc=e2e_desc)
+        rr, _, _ = ctx.run_batch([m2], energies, [0.0], n_prim, SEED, desc=e2e_desc)
         ctx.unload_mesh(m2)
         e_rays += sum(r["rays"] for r in rr)
     barrier()
@@ -261,6 +359,10 @@ def run_ours(args):
         a = et[:1].clone(); dist.all_reduce(a, op=dist.ReduceOp.MAX)
         b = et[1:].clone(); dist.all_reduce(b, op=dist.ReduceOp.SUM)
         e_dt, e_rays = a.item(), b.item()
+
+    forms = None
+    if rank == 0 and not args.no_forms:
+        forms = run_forms(ctx, rtmc, autotune, args.forms_primaries)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -279,22 +381,28 @@ def run_ours(args):
             "config": {"workload": workload_name(mesh.n_tri, n_prim), "n_tri": mesh.n_tri,
                        "energies_ev": energies, "theta_deg": [0.0], "primaries_per_energy": n_prim,
                        "primaries_per_step": n_prim * len(energies) * world,
+                       "engine": "rtmc_run_batch (multi-item queues), FP32 BVH nodes, autotuned",
+                       "autotuned": tuned,
                        "l2": "inputs larger than L2 (BVH nodes + triangles + normals "
                              f"{(mesh.n_tri - 1) * 64 / 1e6 + mesh.n_tri * 64 / 1e6:.0f} MB, ray queues > 1 GB)"},
+            "graph_ms_per_step": graph_ms,
+            "plain_form_rays_per_s": sum(r["rays"] for r in pres) / plain_s,
             "sey": [round(r["sey"], 6) for r in results],
             "sey_se_max": max(r["sey_se"] for r in results),
             "sey_error": "GPU vs FP64 oracle: event records bit-exact on >= 99.99% of rays and SEY within "
                          "min(3 SE, 1e-3) (tests/test_gpu_parity.py); statistical SE per energy above",
-            "roofline": {"bound": "hbm", "kernel": "k_traverse", "achieved": achieved, "peak": peak,
+            "roofline": {"bound": "hbm", "kernel": "k_traverse_ww", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": f"{pk_kind} hbm_gbs", "bytes_per_ray": b_ray,
                          "node_visits_per_ray": visits, "tri_tests_per_ray": tests,
-                         "traverse_ms_per_launch": trav_ms / max(1, trav_launches)},
+                         "traverse_ms_per_launch": trav_ms / max(1, trav_launches),
+                         "l2_copy_gbs": l2_gbs, "frac_of_l2_copy": achieved / l2_gbs},
             "e2e": {"value": e_rays / e_dt, "unit": "rays/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "clocks": clk,
             "cpu_baseline": cpu,
+            "batched_config": forms,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -314,6 +422,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=1024)
     ap.add_argument("--ref-sample", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched-config form comparison")
+    ap.add_argument("--forms-primaries", type=int, default=1_000_000)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -95,6 +95,10 @@ typedef struct {
     int32_t fp64_retest;           /* 1: re-test hits within 1e-5 (barycentric) of an edge
                                       or with cos(incidence) < 1e-3 using FP64 triangle
                                       tests (while-while traversal only) */
+    uint32_t item_base;            /* added to every item index (Philox counter word 3) */
+    int32_t no_graph;              /* rtmc_run_batch: 1 = launch eagerly, no CUDA graph */
+    int32_t stack_depth;           /* shared-memory traversal stack entries: 8, 16 or 32 (0 -> 16) */
+    int32_t fetch_threshold;       /* warp refills rays when fewer lanes than this are busy (0 -> 20) */
 } rtmc_run_desc;
 
 typedef struct {
@@ -162,6 +166,32 @@ int rtmc_build_bvh(rtmc_ctx* ctx, int32_t mesh_id, int32_t bvh_kind);
 int rtmc_run(rtmc_ctx* ctx, int32_t mesh_id, const double* energies_ev, int32_t n_e,
              const double* theta_deg, int32_t n_theta, int64_t n_primaries, uint64_t seed,
              const rtmc_run_desc* desc, rtmc_result* out, uint64_t* hist_e, uint64_t* hist_a);
+
+/* Batched form: every (mesh, energy, angle) combination of the batch as one
+   item, item = (m * n_e + ie) * n_theta + it (plus desc->item_base), each with
+   n_primaries primaries.  The rays of all items of a mesh share the wavefront
+   queues (a chunk spans items), and the whole launch sequence over all meshes
+   is captured once into a CUDA graph and replayed on later calls with the same
+   batch shape (desc->no_graph = 1 launches eagerly instead).  Item k uses the
+   same random streams as rtmc_run with item_base = k, so its tallies are
+   identical to that run's.  Requires max_generation == 1.  Writes
+   out[n_items]; hist_e / hist_a as in rtmc_run.  gpu_ms of every result is
+   the device time of the whole batch, and node_visits / tri_tests / retested
+   are batch totals (the traversal does not tell items apart); launches counts
+   the batch's kernels; with no_graph and profile the ms_* fields hold the
+   batch's per-kernel totals. */
+typedef struct {
+    const int32_t* mesh_ids;
+    int32_t n_meshes;
+    const double* energies_ev;
+    int32_t n_e;
+    const double* theta_deg;
+    int32_t n_theta;
+    int64_t n_primaries;           /* per item */
+    uint64_t seed;
+} rtmc_batch;
+int rtmc_run_batch(rtmc_ctx* ctx, const rtmc_batch* batch, const rtmc_run_desc* desc,
+                   rtmc_result* out, uint64_t* hist_e, uint64_t* hist_a);
 
 /* As rtmc_run for one (energy, angle) item with index `item`, also writing one
    record per traced ray (any order) into rec[rec_cap] (host memory); *n_rec

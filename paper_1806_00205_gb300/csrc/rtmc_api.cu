@@ -74,25 +74,13 @@ double spectrum_cdf(double e, double phi)
     return 1.0 - 3.0 * s * s + 2.0 * s * s * s;
 }
 
-struct ItemOut {
-    rtmc_result* res;
-    uint64_t* hist_e;   // host, n_ebins or NULL
-    uint64_t* hist_a;
-    rtmc_record* rec;   // host or NULL
-    int64_t rec_cap;
-    int64_t* n_rec;
-};
+}  // namespace
 
-// Run one (energy, angle) item through the wavefront loop.
-int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsigned item,
-             int64_t n_prim, uint64_t seed, const rtmc_run_desc& d, ItemOut o)
+namespace rtmc {
+
+RunParams make_params(const DeviceMesh& m, const rtmc_run_desc& d, uint64_t seed, unsigned item, double energy,
+                      double theta_deg)
 {
-    using namespace rtmc;
-    cudaStream_t s = ctx->stream;
-    const rtmc_emission& em = ctx->emission;
-    const bool record = o.rec != nullptr;
-    const bool need_wraps = record || d.prim_hash != nullptr;   // wrap counts enter records and hashes
-
     RunParams p;
     p.seed = seed;
     p.item = item;
@@ -114,7 +102,11 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
     p.ebin_w = (float)(d.hist_e_max_ev / d.n_ebins);
     p.inv_abin = (float)(d.n_abins / (0.5 * kPi));
     p.prim_offset = d.primary_offset;
+    return p;
+}
 
+TableDesc make_table(const rtmc_ctx* ctx)
+{
     TableDesc tab;
     tab.delta = ctx->delta;
     tab.n_e = ctx->grid.n_e;
@@ -122,7 +114,11 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
     tab.inv_log_span = (float)((ctx->grid.n_e - 1) / std::log(ctx->grid.e_hi_ev / ctx->grid.e_lo_ev));
     tab.log_e_lo = (float)std::log(ctx->grid.e_lo_ev);
     tab.inv_theta_step_deg = (float)(1.0 / ctx->grid.theta_step_deg);
+    return tab;
+}
 
+Emission make_emission(const rtmc_emission& em)
+{
     Emission e;
     e.phi = (float)em.phi_ev;
     e.e_cut = (float)em.e_cut_ev;
@@ -130,7 +126,69 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
     e.regen_min = std::isinf(em.regen_min_ev) ? INFINITY : (float)em.regen_min_ev;
     e.max_generation = em.max_generation;
     e.k_max = em.k_max;
-    e.spec_norm = (float)spectrum_cdf(em.e_cut_ev, em.phi_ev);
+    const double sn = em.phi_ev / (em.e_cut_ev + em.phi_ev);
+    e.spec_norm = (float)(1.0 - 3.0 * sn * sn + 2.0 * sn * sn * sn);
+    return e;
+}
+
+void fill_result(rtmc_result& r, const Tally& t, int64_t n_prim)
+{
+    std::memset(&r, 0, sizeof r);
+    r.n_primaries = n_prim;
+    r.rays = (int64_t)t.rays;
+    r.escaped = (int64_t)t.escaped;
+    r.absorbed_low = (int64_t)t.absorbed_low;
+    r.absorbed_other = (int64_t)t.absorbed_other;
+    r.emitters = (int64_t)t.emitters;
+    r.emitted = (int64_t)t.emitted;
+    r.regenerated = (int64_t)t.regenerated;
+    r.capped = (int64_t)t.capped;
+    r.lost = (int64_t)t.lost;
+    r.wraps = (int64_t)t.wraps;
+    r.sum_k = (int64_t)t.sum_k;
+    r.sum_k2 = (int64_t)t.sum_k2;
+    r.e_sum = t.e_sum;
+    r.e2_sum = t.e2_sum;
+    r.node_visits = (int64_t)t.node_visits;
+    r.tri_tests = (int64_t)t.tri_tests;
+    r.retested = (int64_t)t.retested;
+    if (n_prim > 0) r.sey = (double)r.sum_k / (double)n_prim;
+    if (n_prim > 1) {
+        const double var = ((double)r.sum_k2 / (double)n_prim - r.sey * r.sey) / (double)(n_prim - 1);
+        r.sey_se = var > 0.0 ? std::sqrt(var) : 0.0;
+    }
+}
+
+}  // namespace rtmc
+
+namespace {
+
+using rtmc::make_params;
+using rtmc::make_table;
+using rtmc::make_emission;
+
+struct ItemOut {
+    rtmc_result* res;
+    uint64_t* hist_e;   // host, n_ebins or NULL
+    uint64_t* hist_a;
+    rtmc_record* rec;   // host or NULL
+    int64_t rec_cap;
+    int64_t* n_rec;
+};
+
+// Run one (energy, angle) item through the wavefront loop.
+int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsigned item,
+             int64_t n_prim, uint64_t seed, const rtmc_run_desc& d, ItemOut o)
+{
+    using namespace rtmc;
+    cudaStream_t s = ctx->stream;
+    const rtmc_emission& em = ctx->emission;
+    const bool record = o.rec != nullptr;
+    const bool need_wraps = record || d.prim_hash != nullptr;   // wrap counts enter records and hashes
+
+    const RunParams p = make_params(m, d, seed, item, energy, theta_deg);
+    const TableDesc tab = make_table(ctx);
+    const Emission e = make_emission(em);
 
     // Queue capacities: generation g holds at most k_max^g rays per primary.
     // Buffer 0 holds even generations, buffer 1 odd ones; deep trees use a
@@ -146,6 +204,8 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
     if (d.block_threads > 0) tune.block_threads = d.block_threads;
     tune.blocks_per_sm = d.blocks_per_sm;
     tune.traversal = d.traversal;
+    if (d.stack_depth > 0) tune.stack_depth = d.stack_depth;
+    tune.fetch_threshold = d.fetch_threshold;
 
     for (int attempt = 0;; ++attempt) {
         const int64_t cap0 = chunk * mult[0], cap1 = chunk * mult[1];
@@ -271,37 +331,14 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
             return ctx->fail(RTMC_ERR_CAPACITY, "run_records: record buffer too small");
 
         rtmc_result& r = *o.res;
-        std::memset(&r, 0, sizeof r);
-        r.n_primaries = n_prim;
-        r.rays = (int64_t)t.rays;
-        r.escaped = (int64_t)t.escaped;
-        r.absorbed_low = (int64_t)t.absorbed_low;
-        r.absorbed_other = (int64_t)t.absorbed_other;
-        r.emitters = (int64_t)t.emitters;
-        r.emitted = (int64_t)t.emitted;
-        r.regenerated = (int64_t)t.regenerated;
-        r.capped = (int64_t)t.capped;
-        r.lost = (int64_t)t.lost;
-        r.wraps = (int64_t)t.wraps;
-        r.sum_k = (int64_t)t.sum_k;
-        r.sum_k2 = (int64_t)t.sum_k2;
-        r.e_sum = t.e_sum;
-        r.e2_sum = t.e2_sum;
-        if (n_prim > 0) r.sey = (double)r.sum_k / (double)n_prim;
-        if (n_prim > 1) {
-            const double var = ((double)r.sum_k2 / (double)n_prim - r.sey * r.sey) / (double)(n_prim - 1);
-            r.sey_se = var > 0.0 ? std::sqrt(var) : 0.0;
-        }
+        rtmc::fill_result(r, t, n_prim);
         r.gpu_ms = ms;
         r.launches = launches;
         r.traverse_launches = trav_launches;
-        r.node_visits = (int64_t)t.node_visits;
-        r.tri_tests = (int64_t)t.tri_tests;
         r.ms_generate = kms[0];
         r.ms_traverse = kms[1];
         r.ms_shade = kms[2];
         r.ms_finalize = kms[3];
-        r.retested = (int64_t)t.retested;
         if (o.hist_e) for (int b = 0; b < d.n_ebins; ++b) o.hist_e[b] = hist[b];
         if (o.hist_a) for (int b = 0; b < d.n_abins; ++b) o.hist_a[b] = hist[d.n_ebins + b];
         if (record) {
@@ -323,11 +360,22 @@ int check_run_args(rtmc_ctx* ctx, int32_t mesh_id, int64_t n_primaries, const rt
     if (!ctx->meshes[mesh_id].built) return ctx->fail(RTMC_ERR_NOT_BUILT, "run: build_bvh first");
     if (!ctx->table_loaded) return ctx->fail(RTMC_ERR_NOT_LOADED, "run: load_see_tables first");
     if (n_primaries < 0 || n_primaries > ((int64_t)1 << 40)) return ctx->fail(RTMC_ERR_INVALID_ARG, "run: n_primaries out of range");
+    return rtmc::check_run_desc(ctx, d);
+}
+
+}  // namespace
+
+int rtmc::check_run_desc(rtmc_ctx* ctx, const rtmc_run_desc& d)
+{
     if (d.n_ebins <= 0 || d.n_ebins > 4096 || d.n_abins <= 0 || d.n_abins > 4096 || !(d.hist_e_max_ev > 0.0))
         return ctx->fail(RTMC_ERR_INVALID_ARG, "run: histogram shape");
     if (d.block_threads != 0 && (d.block_threads % 32 != 0 || d.block_threads < 32 || d.block_threads > 128))
         return ctx->fail(RTMC_ERR_INVALID_ARG, "run: block_threads must be a multiple of 32 in [32, 128]");
     if (d.traversal < 0 || d.traversal > 2) return ctx->fail(RTMC_ERR_INVALID_ARG, "run: unknown traversal variant");
+    if (d.stack_depth != 0 && d.stack_depth != 8 && d.stack_depth != 16 && d.stack_depth != 32)
+        return ctx->fail(RTMC_ERR_INVALID_ARG, "run: stack_depth must be 8, 16 or 32");
+    if (d.fetch_threshold < 0 || d.fetch_threshold > 32)
+        return ctx->fail(RTMC_ERR_INVALID_ARG, "run: fetch_threshold must be in [0, 32]");
     if (d.fp64_retest && d.traversal == 1)
         return ctx->fail(RTMC_ERR_INVALID_ARG, "run: fp64_retest needs the while-while traversal");
     if (d.chunk < 0 || d.chunk > ((int64_t)1 << 28)) return ctx->fail(RTMC_ERR_INVALID_ARG, "run: chunk out of range");
@@ -335,8 +383,6 @@ int check_run_args(rtmc_ctx* ctx, int32_t mesh_id, int64_t n_primaries, const rt
     if (d.blocks_per_sm < 0 || d.blocks_per_sm > 64) return ctx->fail(RTMC_ERR_INVALID_ARG, "run: blocks_per_sm out of range");
     return RTMC_OK;
 }
-
-}  // namespace
 
 extern "C" {
 
@@ -378,9 +424,10 @@ void rtmc_destroy(rtmc_ctx* ctx)
         cudaFree(m.q8);
     }
     cudaFree(ctx->delta);
+    if (ctx->batch_graph) cudaGraphExecDestroy(ctx->batch_graph);
     rtmc::Scratch* all[] = {&ctx->q_oe[0], &ctx->q_oe[1], &ctx->q_dt[0], &ctx->q_dt[1], &ctx->q_id[0],
                             &ctx->q_id[1], &ctx->hits, &ctx->kcount, &ctx->ctl, &ctx->tally, &ctx->hist,
-                            &ctx->wraps, &ctx->records, &ctx->tmp, &ctx->retest};
+                            &ctx->wraps, &ctx->records, &ctx->tmp, &ctx->retest, &ctx->items};
     for (auto* s : all) rtmc::scratch_free(*s);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -494,7 +541,8 @@ int rtmc_run(rtmc_ctx* ctx, int32_t mesh_id, const double* energies_ev, int32_t 
             const int item = ie * n_theta + it;
             ItemOut o{&out[item], hist_e ? hist_e + (size_t)item * d.n_ebins : nullptr,
                       hist_a ? hist_a + (size_t)item * d.n_abins : nullptr, nullptr, 0, nullptr};
-            rc = run_item(ctx, m, energies_ev[ie], theta_deg[it], (unsigned)item, n_primaries, seed, d, o);
+            rc = run_item(ctx, m, energies_ev[ie], theta_deg[it], d.item_base + (unsigned)item, n_primaries, seed,
+                          d, o);
             if (rc) return rc;
         }
     }

@@ -1,0 +1,342 @@
+// rtmc_batch.cu -- rtmc_run_batch: many (mesh, energy, angle) items in one
+// captured CUDA graph.
+//
+// Items of one mesh share the wavefront queues: the chunk-linear index g runs
+// over (item, primary) pairs, item-major, so a chunk can span several items
+// and the persistent traversal kernels stay full up to the last item.  The
+// whole launch sequence (per mesh, per chunk: generate, traverse [+ FP64
+// re-test] and shade per generation, finalize) is recorded once by stream
+// capture and replayed as one graph launch on later calls with the same batch
+// shape and the same scratch buffers.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rtmc_internal.h"
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// Per-kernel CUDA-event timing of an eager batch (kind 0 generate, 1
+// traverse, 2 shade, 3 finalize).
+struct KernelTimer {
+    bool on = false;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
+    int tick(int kind, cudaStream_t s)
+    {
+        if (!on) return -1;
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        cudaEventRecord(a, s);
+        ev.push_back({kind, {a, b}});
+        return (int)ev.size() - 1;
+    }
+    void tock(int h, cudaStream_t s) { if (h >= 0) cudaEventRecord(ev[h].second.second, s); }
+    void collect(double ms[4], int64_t& trav_launches)
+    {
+        for (auto& k : ev) {
+            float x = 0.f;
+            if (cudaEventElapsedTime(&x, k.second.first, k.second.second) == cudaSuccess) ms[k.first] += x;
+            if (k.first == 1) ++trav_launches;
+            cudaEventDestroy(k.second.first);
+            cudaEventDestroy(k.second.second);
+        }
+        ev.clear();
+    }
+};
+
+// Record the launch sequence of the whole batch on `s`.
+cudaError_t record_batch(rtmc_ctx* ctx, const rtmc_batch& b, const rtmc_run_desc& d, const rtmc::Queues& q,
+                         rtmc::ItemDev* d_items, rtmc::Tally* d_tallies, unsigned long long* d_hists,
+                         int64_t chunk, const rtmc::Tuning& tune, int64_t n_items, cudaStream_t s,
+                         KernelTimer& kt, int64_t& launches)
+{
+    using namespace rtmc;
+    const int nbins = d.n_ebins + d.n_abins;
+    cudaError_t ce = cudaMemsetAsync(d_tallies, 0, (size_t)(n_items + 1) * sizeof(Tally), s);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(d_hists, 0, (size_t)n_items * nbins * 8, s);
+    const TableDesc tab = make_table(ctx);
+    const Emission em = make_emission(ctx->emission);
+    const int64_t per_mesh = (int64_t)b.n_e * b.n_theta;
+    for (int mi = 0; mi < b.n_meshes && ce == cudaSuccess; ++mi) {
+        const DeviceMesh& m = ctx->meshes[b.mesh_ids[mi]];
+        const RunParams p = make_params(m, d, b.seed, 0u, 1.0, 0.0);
+        ItemCtx ic;
+        ic.items = d_items + mi * per_mesh;
+        ic.n_per_item = (unsigned long long)b.n_primaries;
+        ic.tallies = d_tallies;
+        ic.hists = d_hists;
+        const int64_t total = per_mesh * b.n_primaries;
+        for (int64_t g0 = 0; g0 < total && ce == cudaSuccess; g0 += chunk) {
+            const unsigned n = (unsigned)std::min<int64_t>(chunk, total - g0);
+            ic.g0 = (unsigned long long)g0;
+            ic.it_lo = (unsigned)(g0 / b.n_primaries);
+            ic.n_items = (unsigned)((g0 + n - 1) / b.n_primaries) - ic.it_lo + 1;
+            Queues qq = q;
+            qq.tally = d_tallies + n_items;   // traversal-side counters and status: the batch slot
+            ce = cudaMemsetAsync(q.ctl, 0, sizeof(Control), s);
+            int h = kt.tick(0, s);
+            if (ce == cudaSuccess) ce = launch_generate_items(p, ic, qq, n, s);
+            kt.tock(h, s);
+            launches += 1;
+            for (int g = 0; g <= ctx->emission.max_generation && ce == cudaSuccess; ++g) {
+                const int buf = g & 1;
+                h = kt.tick(1, s);
+                ce = launch_traverse(m, p, qq, buf, g, ctx->num_sms, tune, true, d.count_visits != 0,
+                                     d.fp64_retest != 0, s);
+                kt.tock(h, s);
+                h = kt.tick(2, s);
+                if (ce == cudaSuccess) ce = launch_shade_items(m, p, tab, em, ic, qq, buf, g, ctx->num_sms, s);
+                kt.tock(h, s);
+                launches += 2 + (d.fp64_retest ? 1 : 0);
+            }
+            h = kt.tick(3, s);
+            if (ce == cudaSuccess) ce = launch_finalize_items(ic, qq, n, ctx->num_sms, s);
+            kt.tock(h, s);
+            launches += 1;
+        }
+    }
+    return ce;
+}
+
+}  // namespace
+
+extern "C" int rtmc_run_batch(rtmc_ctx* ctx, const rtmc_batch* batch, const rtmc_run_desc* desc, rtmc_result* out,
+                              uint64_t* hist_e, uint64_t* hist_a)
+{
+    using namespace rtmc;
+    if (!ctx) return RTMC_ERR_INVALID_ARG;
+    if (!batch || !out || !batch->mesh_ids || !batch->energies_ev || !batch->theta_deg || batch->n_meshes <= 0 ||
+        batch->n_e <= 0 || batch->n_theta <= 0 || batch->n_primaries < 0 ||
+        batch->n_primaries > ((int64_t)1 << 32))
+        return ctx->fail(RTMC_ERR_INVALID_ARG, "run_batch: bad batch description");
+    rtmc_run_desc d;
+    std::memset(&d, 0, sizeof d);
+    if (desc) {
+        d = *desc;
+    } else {
+        d.n_ebins = 64;
+        d.n_abins = 18;
+        d.hist_e_max_ev = 50.0;
+    }
+    int rc = check_run_desc(ctx, d);
+    if (rc) return rc;
+    if (!ctx->table_loaded) return ctx->fail(RTMC_ERR_NOT_LOADED, "run_batch: load_see_tables first");
+    if (ctx->emission.max_generation != 1)
+        return ctx->fail(RTMC_ERR_INVALID_ARG, "run_batch: the batched form needs max_generation == 1");
+    if (d.prim_hash) return ctx->fail(RTMC_ERR_INVALID_ARG, "run_batch: per-primary hashes are not supported");
+    if (d.n_ebins + d.n_abins > 512)
+        return ctx->fail(RTMC_ERR_INVALID_ARG, "run_batch: n_ebins + n_abins must be <= 512");
+    for (int i = 0; i < batch->n_meshes; ++i) {
+        const int mid = batch->mesh_ids[i];
+        if (mid < 0 || mid >= (int)ctx->meshes.size() || !ctx->meshes[mid].tri_in)
+            return ctx->fail(RTMC_ERR_NOT_LOADED, "run_batch: unknown mesh id");
+        if (!ctx->meshes[mid].built) return ctx->fail(RTMC_ERR_NOT_BUILT, "run_batch: build_bvh first");
+    }
+    for (int i = 0; i < batch->n_e; ++i)
+        if (!(batch->energies_ev[i] > 0.0)) return ctx->fail(RTMC_ERR_INVALID_ARG, "run_batch: energies must be > 0");
+    for (int i = 0; i < batch->n_theta; ++i)
+        if (!(batch->theta_deg[i] >= 0.0 && batch->theta_deg[i] < 90.0))
+            return ctx->fail(RTMC_ERR_INVALID_ARG, "run_batch: incidence angles must be in [0, 90) degrees");
+
+    DeviceGuard guard(ctx->device);
+    cudaStream_t s = ctx->stream;
+    const int64_t per_mesh = (int64_t)batch->n_e * batch->n_theta;
+    const int64_t n_items = per_mesh * batch->n_meshes;
+    const int nbins = d.n_ebins + d.n_abins;
+
+    // item table (host -> device every call: energies and angles may change)
+    std::vector<ItemDev> items((size_t)n_items);
+    for (int mi = 0; mi < batch->n_meshes; ++mi)
+        for (int ie = 0; ie < batch->n_e; ++ie)
+            for (int it = 0; it < batch->n_theta; ++it) {
+                const int64_t k = (mi * (int64_t)batch->n_e + ie) * batch->n_theta + it;
+                ItemDev& x = items[(size_t)k];
+                const double th = batch->theta_deg[it] * kPi / 180.0;
+                x.energy = (float)batch->energies_ev[ie];
+                x.sin_t = (float)std::sin(th);
+                x.cos_t = (float)std::cos(th);
+                x.philox_item = d.item_base + (unsigned)k;
+                x.prim_offset = d.primary_offset;
+                x.tally = (int)k;
+                x.pad = 0;
+            }
+
+    // scratch: queues for one chunk (worst case k_max daughters per primary)
+    const int kmax = std::max(1, ctx->emission.k_max);
+    int64_t chunk = d.chunk > 0 ? d.chunk : ((int64_t)1 << 23);
+    chunk = std::min<int64_t>(chunk, std::max<int64_t>(per_mesh * batch->n_primaries, 1));
+    const int64_t cap0 = chunk, cap1 = chunk * kmax;
+    if (cap1 > 0xFFFFFFF0ll) return ctx->fail(RTMC_ERR_CAPACITY, "run_batch: chunk too large");
+    cudaError_t ce = cudaSuccess;
+    const void* before[14] = {ctx->q_oe[0].ptr, ctx->q_oe[1].ptr, ctx->q_dt[0].ptr, ctx->q_dt[1].ptr,
+                              ctx->q_id[0].ptr, ctx->q_id[1].ptr, ctx->hits.ptr, ctx->kcount.ptr,
+                              ctx->ctl.ptr, ctx->tally.ptr, ctx->hist.ptr, ctx->items.ptr, ctx->wraps.ptr,
+                              ctx->retest.ptr};
+    for (int bb = 0; bb < 2 && ce == cudaSuccess; ++bb) {
+        const int64_t c = bb ? cap1 : cap0;
+        ce = scratch_reserve(ctx->q_oe[bb], (size_t)c * 16);
+        if (ce == cudaSuccess) ce = scratch_reserve(ctx->q_dt[bb], (size_t)c * 16);
+        if (ce == cudaSuccess) ce = scratch_reserve(ctx->q_id[bb], (size_t)c * 16);
+    }
+    if (ce == cudaSuccess) ce = scratch_reserve(ctx->hits, (size_t)cap1 * 16);
+    const bool kc_new = ctx->kcount.bytes < (size_t)chunk * 4;
+    if (ce == cudaSuccess) ce = scratch_reserve(ctx->kcount, (size_t)chunk * 4);
+    if (ce == cudaSuccess && kc_new) ce = cudaMemsetAsync(ctx->kcount.ptr, 0, ctx->kcount.bytes, s);
+    if (ce == cudaSuccess) ce = scratch_reserve(ctx->ctl, sizeof(Control));
+    if (ce == cudaSuccess) ce = scratch_reserve(ctx->tally, (size_t)(n_items + 1) * sizeof(Tally));
+    if (ce == cudaSuccess) ce = scratch_reserve(ctx->wraps, (size_t)cap1 * 4);
+    if (ce == cudaSuccess) ce = scratch_reserve(ctx->hist, (size_t)n_items * nbins * 8);
+    if (ce == cudaSuccess) ce = scratch_reserve(ctx->items, (size_t)n_items * sizeof(ItemDev));
+    if (ce == cudaSuccess && d.fp64_retest) ce = scratch_reserve(ctx->retest, (size_t)cap1 * 4);
+    if (ce != cudaSuccess) return ctx->fail(RTMC_ERR_OOM, std::string("run_batch: scratch: ") + cudaGetErrorString(ce));
+    const void* after[14] = {ctx->q_oe[0].ptr, ctx->q_oe[1].ptr, ctx->q_dt[0].ptr, ctx->q_dt[1].ptr,
+                             ctx->q_id[0].ptr, ctx->q_id[1].ptr, ctx->hits.ptr, ctx->kcount.ptr,
+                             ctx->ctl.ptr, ctx->tally.ptr, ctx->hist.ptr, ctx->items.ptr, ctx->wraps.ptr,
+                             ctx->retest.ptr};
+    const bool moved = std::memcmp(before, after, sizeof before) != 0;
+
+    Queues q;
+    for (int bb = 0; bb < 2; ++bb) {
+        q.oe[bb] = (float4*)ctx->q_oe[bb].ptr;
+        q.dt[bb] = (float4*)ctx->q_dt[bb].ptr;
+        q.id[bb] = (uint4*)ctx->q_id[bb].ptr;
+    }
+    q.cap[0] = (unsigned)cap0;
+    q.cap[1] = (unsigned)cap1;
+    q.hits = (float4*)ctx->hits.ptr;
+    q.wraps = (int*)ctx->wraps.ptr;
+    q.kcount = (unsigned*)ctx->kcount.ptr;
+    q.retest = d.fp64_retest ? (unsigned*)ctx->retest.ptr : nullptr;
+    q.ctl = (Control*)ctx->ctl.ptr;
+    q.tally = (Tally*)ctx->tally.ptr;
+    q.hist_e = nullptr;
+    q.hist_a = nullptr;
+    q.prim_hash = nullptr;
+    q.records = nullptr;
+    q.rec_cap = 0;
+    Tuning tune;
+    if (d.block_threads > 0) tune.block_threads = d.block_threads;
+    tune.blocks_per_sm = d.blocks_per_sm;
+    tune.traversal = d.traversal;
+    if (d.stack_depth > 0) tune.stack_depth = d.stack_depth;
+    tune.fetch_threshold = d.fetch_threshold;
+
+    ce = cudaMemcpyAsync(ctx->items.ptr, items.data(), items.size() * sizeof(ItemDev), cudaMemcpyHostToDevice, s);
+    if (ce != cudaSuccess) return ctx->fail(RTMC_ERR_CUDA, std::string("run_batch: ") + cudaGetErrorString(ce));
+
+    // graph key: everything the recorded launch parameters depend on
+    std::string key;
+    {
+        char buf[512];
+        std::snprintf(buf, sizeof buf, "%d|%d|%d|%lld|%llu|%lld|%d|%d|%d|%d|%d|%d|%d|%d|%u|%.17g|%llu|%.17g|%.17g|%.17g|%.17g",
+                      batch->n_meshes, batch->n_e, batch->n_theta, (long long)batch->n_primaries,
+                      (unsigned long long)batch->seed, (long long)chunk, d.n_ebins, d.n_abins, d.random_azimuth,
+                      d.max_wraps, d.block_threads, d.blocks_per_sm, d.traversal * 10000 + d.stack_depth * 100 + d.fetch_threshold, d.fp64_retest, d.item_base,
+                      d.hist_e_max_ev, (unsigned long long)d.primary_offset, d.src_x0, d.src_x1, d.src_y0, d.src_y1);
+        key = buf;
+        for (int i = 0; i < batch->n_meshes; ++i) {
+            const DeviceMesh& m = ctx->meshes[batch->mesh_ids[i]];
+            std::snprintf(buf, sizeof buf, "|%d:%p:%p:%d", batch->mesh_ids[i], (const void*)m.nodes, m.q8, m.kind);
+            key += buf;
+        }
+        std::snprintf(buf, sizeof buf, "|cv%d|%p", d.count_visits, (const void*)ctx->delta);
+        key += buf;
+    }
+    if (moved || key != ctx->batch_key) {
+        if (ctx->batch_graph) { cudaGraphExecDestroy(ctx->batch_graph); ctx->batch_graph = nullptr; }
+        ctx->batch_key.clear();
+        ctx->batch_launches = 0;
+    }
+
+    cudaEvent_t ev0, ev1;
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+    KernelTimer kt;
+    kt.on = d.no_graph && d.profile;
+    int64_t launches = 0;
+    cudaEventRecord(ev0, s);
+    if (d.no_graph) {
+        ce = record_batch(ctx, *batch, d, q, (ItemDev*)ctx->items.ptr, (Tally*)ctx->tally.ptr,
+                          (unsigned long long*)ctx->hist.ptr, chunk, tune, n_items, s, kt, launches);
+    } else {
+        if (!ctx->batch_graph) {
+            cudaGraph_t graph = nullptr;
+            ce = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+            if (ce == cudaSuccess) {
+                KernelTimer none;
+                const cudaError_t rec = record_batch(ctx, *batch, d, q, (ItemDev*)ctx->items.ptr,
+                                                     (Tally*)ctx->tally.ptr, (unsigned long long*)ctx->hist.ptr,
+                                                     chunk, tune, n_items, s, none, ctx->batch_launches);
+                ce = cudaStreamEndCapture(s, &graph);
+                if (ce == cudaSuccess) ce = rec;
+            }
+            if (ce == cudaSuccess) ce = cudaGraphInstantiate(&ctx->batch_graph, graph, 0);
+            if (ce != cudaSuccess) ctx->batch_launches = 0;
+            if (graph) cudaGraphDestroy(graph);
+            if (ce == cudaSuccess) ctx->batch_key = key;
+            else ctx->batch_graph = nullptr;
+        }
+        if (ce == cudaSuccess) ce = cudaGraphLaunch(ctx->batch_graph, s);
+        launches = ctx->batch_launches;
+    }
+    cudaEventRecord(ev1, s);
+    std::vector<Tally> t((size_t)n_items + 1);
+    std::vector<unsigned long long> h((size_t)n_items * nbins);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(t.data(), ctx->tally.ptr, t.size() * sizeof(Tally), cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(h.data(), ctx->hist.ptr, h.size() * 8, cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    float ms = 0.f;
+    if (ce == cudaSuccess) cudaEventElapsedTime(&ms, ev0, ev1);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    double kms[4] = {0.0, 0.0, 0.0, 0.0};
+    int64_t trav_launches = 0;
+    kt.collect(kms, trav_launches);
+    if (ce != cudaSuccess) return ctx->fail(RTMC_ERR_CUDA, std::string("run_batch: ") + cudaGetErrorString(ce));
+    unsigned long long status = 0;
+    for (const Tally& x : t) status |= x.status;
+    if (status & ST_QUEUE_OVERFLOW) return ctx->fail(RTMC_ERR_CAPACITY, "run_batch: daughter queue overflow");
+    if (status & (ST_STACK_OVERFLOW | ST_LOOP_LIMIT))
+        return ctx->fail(RTMC_ERR_DEVICE_CHECK, "run_batch: traversal stack overflow or iteration bound");
+    const Tally& all = t[(size_t)n_items];
+    for (int64_t k = 0; k < n_items; ++k) {
+        fill_result(out[k], t[(size_t)k], batch->n_primaries);
+        out[k].gpu_ms = ms;
+        out[k].node_visits = (int64_t)all.node_visits;     // traversal counters: batch totals
+        out[k].tri_tests = (int64_t)all.tri_tests;
+        out[k].retested = (int64_t)all.retested;
+        out[k].launches = launches;
+        out[k].traverse_launches = trav_launches;
+        out[k].ms_generate = kms[0];
+        out[k].ms_traverse = kms[1];
+        out[k].ms_shade = kms[2];
+        out[k].ms_finalize = kms[3];
+        if (hist_e)
+            for (int bb = 0; bb < d.n_ebins; ++bb) hist_e[k * d.n_ebins + bb] = h[(size_t)k * nbins + bb];
+        if (hist_a)
+            for (int bb = 0; bb < d.n_abins; ++bb) hist_a[k * d.n_abins + bb] = h[(size_t)k * nbins + d.n_ebins + bb];
+    }
+    return RTMC_OK;
+}

@@ -52,6 +52,28 @@ struct Control {                  // per chunk
     unsigned int n_retest[8];     // rays flagged for the FP64 re-test per generation
 };
 
+// One (energy, angle) item of a batched launch.
+struct ItemDev {
+    float energy, sin_t, cos_t;
+    unsigned philox_item;            // Philox counter word 3
+    unsigned long long prim_offset;  // global id of the item's primary 0
+    int tally;                       // slot in the tally / histogram arrays
+    int pad;
+};
+
+// Where the rays of a multi-item chunk come from: chunk-linear index g (from
+// g0) is local primary g % n_per_item of item g / n_per_item.
+struct ItemCtx {
+    const ItemDev* items;
+    unsigned long long n_per_item;
+    unsigned long long g0;
+    Tally* tallies;
+    unsigned long long* hists;       // [slot][n_ebins + n_abins]
+    unsigned it_lo, n_items;         // items this chunk touches: it_lo .. it_lo + n_items - 1
+};
+
+constexpr int kChunkItems = 16;      // per-block shared accumulators for up to this many items
+
 struct Emission {
     float phi, e_cut, absorb_min, regen_min;
     int max_generation, k_max;

@@ -38,6 +38,8 @@ struct Tuning {
     int block_threads = 128;
     int blocks_per_sm = 0;         // 0: from occupancy
     int traversal = 0;             // 0/2: while-while with ray refill, 1: one ray per lane per tile
+    int stack_depth = 16;          // shared-memory stack entries per ray (8, 16, 32)
+    int fetch_threshold = 0;       // refill when fewer lanes are active (0: default 20)
 };
 
 }  // namespace rtmc
@@ -54,11 +56,23 @@ struct rtmc_ctx {
     bool table_loaded = false;
     // run buffers
     rtmc::Scratch q_oe[2], q_dt[2], q_id[2], hits, kcount, ctl, tally, hist, wraps, records, tmp, retest;
+    rtmc::Scratch items;                      // batched item table
+    cudaGraphExec_t batch_graph = nullptr;    // captured batch launch sequence
+    std::string batch_key;                    // what the captured graph was built for
+    int64_t batch_launches = 0;               // kernel launches in the captured graph
     std::string err;
     int fail(int code, const std::string& msg) { err = msg; return code; }
 };
 
 namespace rtmc {
+
+struct RunParams;
+RunParams make_params(const DeviceMesh& m, const rtmc_run_desc& d, uint64_t seed, unsigned item, double energy,
+                      double theta_deg);
+TableDesc make_table(const rtmc_ctx* ctx);
+Emission make_emission(const rtmc_emission& em);
+void fill_result(rtmc_result& r, const Tally& t, int64_t n_prim);
+int check_run_desc(rtmc_ctx* ctx, const rtmc_run_desc& d);
 
 // Ensure a scratch buffer holds at least `bytes`; returns cudaSuccess or the error.
 cudaError_t scratch_reserve(Scratch& s, size_t bytes);
@@ -109,6 +123,11 @@ cudaError_t launch_shade(const DeviceMesh& m, const RunParams& p, const TableDes
                          const Emission& em, const Queues& q, int buf, int gen,
                          unsigned long long chunk_first, int num_sms, bool record, cudaStream_t s);
 cudaError_t launch_finalize(const Queues& q, unsigned n, cudaStream_t s);
+cudaError_t launch_generate_items(const RunParams& p, const ItemCtx& ic, const Queues& q, unsigned n,
+                                  cudaStream_t s);
+cudaError_t launch_shade_items(const DeviceMesh& m, const RunParams& p, const TableDesc& tab, const Emission& em,
+                               const ItemCtx& ic, const Queues& q, int buf, int gen, int num_sms, cudaStream_t s);
+cudaError_t launch_finalize_items(const ItemCtx& ic, const Queues& q, unsigned n, int num_sms, cudaStream_t s);
 cudaError_t launch_trace_rays(const DeviceMesh& m, const float* o, const float* d, const int* skip,
                               int64_t n, rtmc_hit* hits, unsigned* status, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t* ctr, int64_t n, unsigned long long key, uint32_t* out,

@@ -12,6 +12,7 @@
 //   finalize  : per-primary escape counts -> sum k, sum k^2
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <climits>
 #include <cstdint>
 
@@ -46,6 +47,29 @@ __global__ void k_generate(RunParams p, float sin_t, float cos_t, unsigned long 
     oe[i] = make_float4(x, y, p.z_top, p.energy);
     dt[i] = make_float4(sin_t * ca, sin_t * sa, -cos_t, __int_as_float(-1));
     id[i] = make_uint4(plo, phi, 1u, 0u);
+}
+
+// Multi-item chunk: slot i is local primary (g0 + i) % N of item (g0 + i) / N.
+// Ray id = (local primary, item index, path, generation).
+__global__ void k_generate_items(RunParams p, ItemCtx ic, unsigned n, float4* __restrict__ oe,
+                                 float4* __restrict__ dt, uint4* __restrict__ id, Control* __restrict__ ctl)
+{
+    const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) ctl->count[0] = n;
+    if (i >= n) return;
+    const unsigned long long g = ic.g0 + i;
+    const unsigned it = (unsigned)(g / ic.n_per_item);
+    const unsigned pl = (unsigned)(g - (unsigned long long)it * ic.n_per_item);
+    const ItemDev item = ic.items[it];
+    const unsigned long long prim = item.prim_offset + pl;
+    const uint4 w = ray_block(p.seed, (unsigned)prim, (unsigned)(prim >> 32), 1u, item.philox_item);
+    const float x = p.src_x0 + u01(w.x) * (p.src_x1 - p.src_x0);
+    const float y = p.src_y0 + u01(w.y) * (p.src_y1 - p.src_y0);
+    float ca = 1.f, sa = 0.f;
+    if (p.random_azimuth) sincospif(2.0f * u01(w.z), &sa, &ca);
+    oe[i] = make_float4(x, y, p.z_top, item.energy);
+    dt[i] = make_float4(item.sin_t * ca, item.sin_t * sa, -item.cos_t, __int_as_float(-1));
+    id[i] = make_uint4(pl, it, 1u, 0u);
 }
 
 // --------------------------------------------------------------------------
@@ -348,23 +372,23 @@ k_traverse(const void* __restrict__ nodes, const float4* __restrict__ tris, Cell
 // cos(incidence) below kGrazeCos are listed for the FP64 re-test kernel.
 // --------------------------------------------------------------------------
 constexpr int kEntrySentinel = 0x76543210;   // "stack empty" (never a node index)
-constexpr int kFetchThreshold = 20;          // refill when fewer lanes than this are active
+constexpr int kFetchThreshold = 20;          // default: refill when fewer lanes than this are active
 constexpr float kEdgeEps = 1e-5f;
 constexpr float kGrazeCos = 1e-3f;
 
-template <int FMT, bool RECORD, bool COUNT, bool RETEST>
+template <int FMT, bool RECORD, bool COUNT, bool RETEST, int SSTACK>
 __global__ void __launch_bounds__(128)
 k_traverse_ww(const void* __restrict__ nodes, const float4* __restrict__ tris, const float4* __restrict__ normals,
               Cell cell, const float4* __restrict__ oe, const float4* __restrict__ dt, float4* __restrict__ hits,
               int* __restrict__ wraps_out, Control* __restrict__ ctl, int gen, unsigned cap,
-              unsigned* __restrict__ retest_list, Tally* __restrict__ tally)
+              unsigned* __restrict__ retest_list, Tally* __restrict__ tally, int fetch_threshold)
 {
-    extern __shared__ int2 s_stack[];                                   // [kSmemStack][blockDim]
+    extern __shared__ int2 s_stack[];                                   // [SSTACK][blockDim]
     const int B = blockDim.x, tid = threadIdx.x, lane = tid & 31;
-    double* s_o = reinterpret_cast<double*>(s_stack + kSmemStack * B);   // [3][blockDim]
+    double* s_o = reinterpret_cast<double*>(s_stack + SSTACK * B);       // [3][blockDim]
     const unsigned lt = (1u << lane) - 1u;
     const unsigned n = min(*((volatile unsigned*)&ctl->count[gen]), cap);
-    int2 lstack[kStackMax - kSmemStack];
+    int2 lstack[kStackMax - SSTACK];
 
     int ray = -1;
     bool exhausted = false, drained = false;
@@ -380,15 +404,15 @@ k_traverse_ww(const void* __restrict__ nodes, const float4* __restrict__ tris, c
 
     auto push = [&](int node_ref, float tmin) {
         const int2 e = make_int2(node_ref, __float_as_int(tmin));
-        if (sp < kSmemStack) s_stack[sp * B + tid] = e;
-        else if (sp < kStackMax) lstack[sp - kSmemStack] = e;
+        if (sp < SSTACK) s_stack[sp * B + tid] = e;
+        else if (sp < kStackMax) lstack[sp - SSTACK] = e;
         else { status |= ST_STACK_OVERFLOW; sp = kStackMax - 1; }
         ++sp;
     };
     auto pop = [&]() -> int {
         while (sp > 0) {
             --sp;
-            const int2 e = sp < kSmemStack ? s_stack[sp * B + tid] : lstack[sp - kSmemStack];
+            const int2 e = sp < SSTACK ? s_stack[sp * B + tid] : lstack[sp - SSTACK];
             if (__int_as_float(e.y) <= t_best * kRobust) return e.x;
         }
         return kEntrySentinel;
@@ -454,7 +478,7 @@ k_traverse_ww(const void* __restrict__ nodes, const float4* __restrict__ tris, c
                 if (node < 0) { leaf = node; node = pop(); }
             }
             if (node == kEntrySentinel) { cell_done = true; break; }
-            if (!drained && __popc(__activemask()) < kFetchThreshold) break;
+            if (!drained && __popc(__activemask()) < fetch_threshold) break;
         }
         if (!cell_done) continue;
 
@@ -629,81 +653,191 @@ struct ShadeOut {
     unsigned cap;
 };
 
-template <bool RECORD>
+// Per-ray contribution to the tallies.
+struct Acc {
+    unsigned rays = 0, esc = 0, lost = 0, low = 0, other = 0, emit = 0, regen = 0, emitted = 0, capped = 0;
+    unsigned wraps = 0;               // multi-item chunks only (the traversal cannot tell items apart)
+    double es = 0.0, e2 = 0.0;
+    __device__ void add(const Acc& a)
+    {
+        rays += a.rays; esc += a.esc; lost += a.lost; low += a.low; other += a.other; emit += a.emit;
+        regen += a.regen; emitted += a.emitted; capped += a.capped; wraps += a.wraps; es += a.es; e2 += a.e2;
+    }
+};
+
+__device__ __forceinline__ void acc_atomic(Tally* t, const Acc& a)
+{
+    if (a.rays) atomicAdd(&t->rays, (unsigned long long)a.rays);
+    if (a.esc) atomicAdd(&t->escaped, (unsigned long long)a.esc);
+    if (a.lost) atomicAdd(&t->lost, (unsigned long long)a.lost);
+    if (a.low) atomicAdd(&t->absorbed_low, (unsigned long long)a.low);
+    if (a.other) atomicAdd(&t->absorbed_other, (unsigned long long)a.other);
+    if (a.emit) atomicAdd(&t->emitters, (unsigned long long)a.emit);
+    if (a.regen) atomicAdd(&t->regenerated, (unsigned long long)a.regen);
+    if (a.emitted) atomicAdd(&t->emitted, (unsigned long long)a.emitted);
+    if (a.capped) atomicAdd(&t->capped, (unsigned long long)a.capped);
+    if (a.wraps) atomicAdd(&t->wraps, (unsigned long long)a.wraps);
+    if (a.es != 0.0) atomicAdd(&t->e_sum, a.es);
+    if (a.e2 != 0.0) atomicAdd(&t->e2_sum, a.e2);
+}
+
+// With ITEMS the queue holds rays of several items (ray id.y is the item
+// index in ic.items).  Daughters of different items interleave in the next
+// queue tile by tile, so each block keeps per-item counters and histograms
+// in shared memory for every item the chunk touches (at most kChunkItems);
+// a warp whose rays share one item (the common case) adds one reduced value
+// per counter.  The block flushes to global memory once, at its end.
+template <bool RECORD, bool ITEMS>
 __global__ void __launch_bounds__(kShadeThreads)
 k_shade(const float4* __restrict__ tris, const float4* __restrict__ normals, TableDesc tab, Emission em,
-        RunParams p, const float4* __restrict__ oe, const float4* __restrict__ dt, const uint4* __restrict__ id,
-        const float4* __restrict__ hits, const int* __restrict__ wraps_in, ShadeOut out,
-        Control* __restrict__ ctl, int gen, unsigned cap_in, Tally* __restrict__ tally,
+        RunParams p, ItemCtx ic, const float4* __restrict__ oe, const float4* __restrict__ dt,
+        const uint4* __restrict__ id, const float4* __restrict__ hits, const int* __restrict__ wraps_in,
+        ShadeOut out, Control* __restrict__ ctl, int gen, unsigned cap_in, Tally* __restrict__ tally,
         unsigned long long* __restrict__ hist_e, unsigned long long* __restrict__ hist_a,
         unsigned* __restrict__ kcount, unsigned long long chunk_first,
         unsigned long long* __restrict__ prim_hash, rtmc_record* __restrict__ records,
         unsigned long long rec_cap)
 {
-    extern __shared__ unsigned s_hist[];              // n_ebins + n_abins
+    extern __shared__ unsigned s_hist[];              // [ITEMS ? kChunkItems : 1][n_ebins + n_abins]
     __shared__ unsigned s_excl[kShadeThreads + 1];
     __shared__ unsigned s_warp[kShadeThreads / 32];
     __shared__ float s_px[kShadeThreads], s_py[kShadeThreads], s_pz[kShadeThreads];
     __shared__ float s_nx[kShadeThreads], s_ny[kShadeThreads], s_nz[kShadeThreads];
-    __shared__ uint4 s_id[kShadeThreads];
+    __shared__ uint4 s_id[kShadeThreads];             // child id: (x, y, parent path, gen + 1)
+    __shared__ uint3 s_key[kShadeThreads];            // Philox: (prim lo, prim hi, item)
     __shared__ int s_tri[kShadeThreads];
     __shared__ unsigned s_base;
+    __shared__ unsigned long long s_red[10][kShadeThreads / 32];
+    __shared__ double s_dred[2][kShadeThreads / 32];
+    __shared__ unsigned s_icnt[kChunkItems][10];      // multi-item chunks: per-item counters
+    __shared__ double s_isum[kChunkItems][2];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int b = tid; b < p.n_ebins + p.n_abins; b += kShadeThreads) s_hist[b] = 0u;
+    const int nbins = p.n_ebins + p.n_abins;
+    // multi-item chunks touching at most kChunkItems items accumulate per item in
+    // shared memory; wider chunks (tiny items) send every ray to global atomics
+    const bool shared_items = ITEMS && ic.n_items <= (unsigned)kChunkItems;
+    const int hist_rows = ITEMS ? (shared_items ? (int)ic.n_items : 0) : 1;
+    for (int b = tid; b < hist_rows * nbins; b += kShadeThreads) s_hist[b] = 0u;
+    if (ITEMS)
+        for (int b = tid; b < kChunkItems * 10; b += kShadeThreads) {
+            (&s_icnt[0][0])[b] = 0u;
+            if (b < kChunkItems * 2) (&s_isum[0][0])[b] = 0.0;
+        }
     unsigned *sh_e = s_hist, *sh_a = s_hist + p.n_ebins;
     const unsigned n = min(*((volatile unsigned*)&ctl->count[gen]), cap_in);
-    unsigned c_rays = 0, c_esc = 0, c_lost = 0, c_low = 0, c_other = 0, c_emit = 0, c_regen = 0,
-             c_emitted = 0, c_capped = 0;
-    double e_sum = 0.0, e2_sum = 0.0;
+    Acc acc;                                          // single-item runs: this thread's share
+    Tally* home_tally = tally;
+    unsigned long long* home_he = hist_e;
     __syncthreads();
+
+    // block reduction of `acc` and the shared histogram into the home item
+    auto flush = [&]() {
+        const unsigned cs[10] = {acc.rays, acc.esc, acc.lost, acc.low, acc.other, acc.emit, acc.regen,
+                                 acc.emitted, acc.capped, acc.wraps};
+#pragma unroll
+        for (int q = 0; q < 10; ++q) {
+            const unsigned v = warp_sum(cs[q]);
+            if (lane == 0) s_red[q][warp] = v;
+        }
+        const double es = warp_sum(acc.es), e2 = warp_sum(acc.e2);
+        if (lane == 0) { s_dred[0][warp] = es; s_dred[1][warp] = e2; }
+        __syncthreads();
+        if (tid < 10) {
+            unsigned long long v = 0;
+            for (int w = 0; w < kShadeThreads / 32; ++w) v += s_red[tid][w];
+            if (v) {
+                unsigned long long* dst[10] = {&home_tally->rays, &home_tally->escaped, &home_tally->lost,
+                                               &home_tally->absorbed_low, &home_tally->absorbed_other,
+                                               &home_tally->emitters, &home_tally->regenerated,
+                                               &home_tally->emitted, &home_tally->capped, &home_tally->wraps};
+                atomicAdd(dst[tid], v);
+            }
+        } else if (tid >= 32 && tid < 34) {
+            double v = 0.0;
+            for (int w = 0; w < kShadeThreads / 32; ++w) v += s_dred[tid - 32][w];
+            if (v != 0.0) atomicAdd(tid == 32 ? &home_tally->e_sum : &home_tally->e2_sum, v);
+        }
+        for (int b = tid; b < nbins; b += kShadeThreads) {
+            if (s_hist[b]) atomicAdd(&home_he[b], (unsigned long long)s_hist[b]);
+            s_hist[b] = 0u;
+        }
+        acc = Acc();
+        __syncthreads();
+    };
 
     for (unsigned tile = blockIdx.x; tile * kShadeThreads < n; tile += gridDim.x) {
         const unsigned i = tile * kShadeThreads + tid;
         unsigned k = 0;
+        Acc r;
+        int jslot = -1;                               // multi-item: item index - ic.it_lo
         if (i < n) {
             const float4 a = oe[i], b = dt[i], h = hits[i];
             const uint4 rid = id[i];
             const int tri = __float_as_int(h.w);
             const unsigned g = rid.w;
             const float E = a.w;
+            unsigned long long prim;
+            unsigned pitem;
+            int slot = 0;
+            if (ITEMS) {
+                const ItemDev item = ic.items[rid.y];
+                prim = item.prim_offset + rid.x;
+                pitem = item.philox_item;
+                slot = item.tally;
+                jslot = (int)(rid.y - ic.it_lo);
+            } else {
+                prim = ((unsigned long long)rid.y << 32) | rid.x;
+                pitem = p.item;
+            }
             int fate, orig = -1, e_bin = -1, a_bin = -1, kk = 0;
-            ++c_rays;
+            r.rays = 1;
+            if (ITEMS && wraps_in) r.wraps = (unsigned)wraps_in[i];
             if (tri == HIT_ESCAPE && g > 0) {
                 fate = RTMC_ESCAPED;
-                ++c_esc;
+                r.esc = 1;
                 e_bin = max(0, min((int)(E / p.ebin_w), p.n_ebins - 1));
                 const float pol = acosf(fminf(1.f, b.z));
                 a_bin = max(0, min((int)(pol * p.inv_abin), p.n_abins - 1));
-                atomicAdd(&sh_e[e_bin], 1u);
-                atomicAdd(&sh_a[a_bin], 1u);
-                const unsigned long long prim = ((unsigned long long)rid.y << 32) | rid.x;
-                atomicAdd(&kcount[prim - p.prim_offset - chunk_first], 1u);
-                e_sum += (double)E;
-                e2_sum += (double)E * (double)E;
+                if (!ITEMS) {
+                    atomicAdd(&sh_e[e_bin], 1u);
+                    atomicAdd(&sh_a[a_bin], 1u);
+                } else if (shared_items) {
+                    atomicAdd(&s_hist[jslot * nbins + e_bin], 1u);
+                    atomicAdd(&s_hist[jslot * nbins + p.n_ebins + a_bin], 1u);
+                } else {
+                    unsigned long long* hh = ic.hists + (size_t)slot * nbins;
+                    atomicAdd(&hh[e_bin], 1ull);
+                    atomicAdd(&hh[p.n_ebins + a_bin], 1ull);
+                }
+                const unsigned long long ks = ITEMS ? (unsigned long long)rid.y * ic.n_per_item + rid.x - ic.g0
+                                                    : prim - p.prim_offset - chunk_first;
+                atomicAdd(&kcount[ks], 1u);
+                r.es = (double)E;
+                r.e2 = (double)E * (double)E;
             } else if (tri < 0) {
                 fate = RTMC_LOST;
-                ++c_lost;
+                r.lost = 1;
             } else {
                 const float4 w0 = ldg4(tris + 3ll * tri);
                 orig = __float_as_int(w0.w);
                 const bool emits = g == 0 || ((int)g < em.max_generation && E >= em.regen_min);
                 if (!emits) {
-                    if (E < em.absorb_min) { fate = RTMC_ABSORBED_LOW; ++c_low; }
-                    else { fate = RTMC_ABSORBED_OTHER; ++c_other; }
+                    if (E < em.absorb_min) { fate = RTMC_ABSORBED_LOW; r.low = 1; }
+                    else { fate = RTMC_ABSORBED_OTHER; r.other = 1; }
                 } else {
                     fate = RTMC_EMITTER;
-                    ++c_emit;
-                    if (g > 0) ++c_regen;
+                    r.emit = 1;
+                    if (g > 0) r.regen = 1;
                     const float4 nr = ldg4(normals + tri);
                     const float cosa = -(b.x * nr.x + b.y * nr.y + b.z * nr.z);
                     const float alpha = acosf(fminf(1.f, cosa));
                     const float lam = lookup_delta(tab, E, alpha);
-                    const uint4 w = ray_block(p.seed, rid.x, rid.y, rid.z, p.item);
+                    const uint4 w = ray_block(p.seed, (unsigned)prim, (unsigned)(prim >> 32), rid.z, pitem);
                     int capped;
                     kk = poisson_inv(lam, u01(w.w), em.k_max, capped);
-                    c_capped += capped;
-                    c_emitted += kk;
+                    r.capped = capped;
+                    r.emitted = kk;
                     k = kk;
                     const float4 w1 = ldg4(tris + 3ll * tri + 1), w2 = ldg4(tris + 3ll * tri + 2);
                     const float bw = 1.f - h.y - h.z;
@@ -712,27 +846,51 @@ k_shade(const float4* __restrict__ tris, const float4* __restrict__ normals, Tab
                     s_pz[tid] = bw * w0.z + h.y * w1.z + h.z * w2.z;
                     s_nx[tid] = nr.x; s_ny[tid] = nr.y; s_nz[tid] = nr.z;
                     s_id[tid] = make_uint4(rid.x, rid.y, rid.z, g + 1);
+                    s_key[tid] = make_uint3((unsigned)prim, (unsigned)(prim >> 32), pitem);
                     s_tri[tid] = tri;
                 }
             }
-            if (RECORD || prim_hash) {
-                const unsigned long long prim = ((unsigned long long)rid.y << 32) | rid.x;
+            if (!ITEMS) acc.add(r);
+            else if (!shared_items) acc_atomic(ic.tallies + slot, r);
+            if (!ITEMS && (RECORD || prim_hash)) {
                 const int wr = wraps_in ? wraps_in[i] : 0;
                 if (prim_hash)
                     atomicAdd(&prim_hash[prim - p.prim_offset],
                               record_hash_fields(prim, rid.z, fate, orig, kk, e_bin, a_bin, wr));
                 if (RECORD) {
-                    const unsigned long long slot = atomicAdd(&tally->rays_recorded, 1ull);
-                    if (slot < rec_cap) {
-                        rtmc_record r;
-                        r.prim = prim; r.path = rid.z; r.gen = (int)g; r.fate = fate; r.tri = orig;
-                        r.k = kk; r.e_bin = e_bin; r.a_bin = a_bin; r.wraps = wr;
-                        r.t = (double)h.x; r.energy = (double)E;
-                        records[slot] = r;
+                    const unsigned long long rs = atomicAdd(&tally->rays_recorded, 1ull);
+                    if (rs < rec_cap) {
+                        rtmc_record rec;
+                        rec.prim = prim; rec.path = rid.z; rec.gen = (int)g; rec.fate = fate; rec.tri = orig;
+                        rec.k = kk; rec.e_bin = e_bin; rec.a_bin = a_bin; rec.wraps = wr;
+                        rec.t = (double)h.x; rec.energy = (double)E;
+                        records[rs] = rec;
                     } else {
                         atomicOr(&tally->status, (unsigned long long)ST_RECORD_OVERFLOW);
                     }
                 }
+            }
+        }
+        if (ITEMS && shared_items) {
+            // warps are almost always single-item: reduce the warp, one shared add per counter
+            const int j0 = __shfl_sync(0xFFFFFFFFu, jslot, 0);
+            if (__all_sync(0xFFFFFFFFu, jslot == j0 || jslot < 0) && j0 >= 0) {
+                const unsigned cs[10] = {r.rays, r.esc, r.lost, r.low, r.other, r.emit, r.regen, r.emitted,
+                                         r.capped, r.wraps};
+#pragma unroll
+                for (int c = 0; c < 10; ++c) {
+                    const unsigned v = __reduce_add_sync(0xFFFFFFFFu, cs[c]);
+                    if (lane == 0 && v) atomicAdd(&s_icnt[j0][c], v);
+                }
+                const double es = warp_sum(r.es), e2 = warp_sum(r.e2);
+                if (lane == 0 && es != 0.0) { atomicAdd(&s_isum[j0][0], es); atomicAdd(&s_isum[j0][1], e2); }
+            } else if (jslot >= 0) {
+                const unsigned cs[10] = {r.rays, r.esc, r.lost, r.low, r.other, r.emit, r.regen, r.emitted,
+                                         r.capped, r.wraps};
+#pragma unroll
+                for (int c = 0; c < 10; ++c)
+                    if (cs[c]) atomicAdd(&s_icnt[jslot][c], cs[c]);
+                if (r.es != 0.0) { atomicAdd(&s_isum[jslot][0], r.es); atomicAdd(&s_isum[jslot][1], r.e2); }
             }
         }
         // block exclusive prefix of the daughter counts (warp shuffles + warp totals)
@@ -771,8 +929,9 @@ k_shade(const float4* __restrict__ tris, const float4* __restrict__ normals, Tab
             const int par = lo;
             const unsigned j = s - s_excl[par];
             const uint4 pid = s_id[par];
+            const uint3 key = s_key[par];
             const unsigned path = pid.z * 16u + j;
-            const uint4 w = ray_block(p.seed, pid.x, pid.y, path, p.item);
+            const uint4 w = ray_block(p.seed, key.x, key.y, path, key.z);
             const float e = sample_energy(em, u01(w.x));
             const float3 dd = cosine_dir(make_float3(s_nx[par], s_ny[par], s_nz[par]), u01(w.y), u01(w.z));
             const unsigned slot = base + s;
@@ -786,36 +945,30 @@ k_shade(const float4* __restrict__ tris, const float4* __restrict__ normals, Tab
         }
         __syncthreads();
     }
-    // block reduction of the counters -> one atomic per counter per block
-    __shared__ unsigned long long s_red[9][kShadeThreads / 32];
-    __shared__ double s_dred[2][kShadeThreads / 32];
-    const unsigned cs[9] = {c_rays, c_esc, c_lost, c_low, c_other, c_emit, c_regen, c_emitted, c_capped};
-#pragma unroll
-    for (int q = 0; q < 9; ++q) {
-        const unsigned v = warp_sum(cs[q]);
-        if (lane == 0) s_red[q][warp] = v;
-    }
-    const double es = warp_sum(e_sum), e2 = warp_sum(e2_sum);
-    if (lane == 0) { s_dred[0][warp] = es; s_dred[1][warp] = e2; }
-    __syncthreads();
-    if (tid < 9) {
-        unsigned long long v = 0;
-        for (int w = 0; w < kShadeThreads / 32; ++w) v += s_red[tid][w];
-        if (v) {
-            unsigned long long* dst[9] = {&tally->rays, &tally->escaped, &tally->lost, &tally->absorbed_low,
-                                          &tally->absorbed_other, &tally->emitters, &tally->regenerated,
-                                          &tally->emitted, &tally->capped};
-            atomicAdd(dst[tid], v);
+    if (!ITEMS) {
+        flush();
+    } else if (shared_items) {
+        __syncthreads();
+        for (int j = 0; j < (int)ic.n_items; ++j) {
+            const int slot = ic.items[ic.it_lo + j].tally;
+            Tally* t = ic.tallies + slot;
+            if (tid < 10) {
+                const unsigned v = s_icnt[j][tid];
+                if (v) {
+                    unsigned long long* dst[10] = {&t->rays, &t->escaped, &t->lost, &t->absorbed_low,
+                                                   &t->absorbed_other, &t->emitters, &t->regenerated, &t->emitted,
+                                                   &t->capped, &t->wraps};
+                    atomicAdd(dst[tid], (unsigned long long)v);
+                }
+            } else if (tid == 32 || tid == 33) {
+                const double v = s_isum[j][tid - 32];
+                if (v != 0.0) atomicAdd(tid == 32 ? &t->e_sum : &t->e2_sum, v);
+            }
+            unsigned long long* hh = ic.hists + (size_t)slot * nbins;
+            for (int b = tid; b < nbins; b += kShadeThreads)
+                if (s_hist[j * nbins + b]) atomicAdd(&hh[b], (unsigned long long)s_hist[j * nbins + b]);
         }
-    } else if (tid < 11) {
-        double v = 0.0;
-        for (int w = 0; w < kShadeThreads / 32; ++w) v += s_dred[tid - 9][w];
-        if (v != 0.0) atomicAdd(tid == 9 ? &tally->e_sum : &tally->e2_sum, v);
     }
-    for (int b = tid; b < p.n_ebins; b += kShadeThreads)
-        if (sh_e[b]) atomicAdd(&hist_e[b], (unsigned long long)sh_e[b]);
-    for (int b = tid; b < p.n_abins; b += kShadeThreads)
-        if (sh_a[b]) atomicAdd(&hist_a[b], (unsigned long long)sh_a[b]);
 }
 
 // --------------------------------------------------------------------------
@@ -842,6 +995,46 @@ __global__ void k_finalize(unsigned* __restrict__ kcount, unsigned n, Tally* __r
         unsigned long long a = 0, b = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += r1[w]; b += r2[w]; }
         if (a) { atomicAdd(&tally->sum_k, a); atomicAdd(&tally->sum_k2, b); }
+    }
+}
+
+// Multi-item finalize: per-block shared sums per item of the chunk (at most
+// kChunkItems; wider chunks add per lane straight to global memory).
+__global__ void k_finalize_items(unsigned* __restrict__ kcount, unsigned n, ItemCtx ic)
+{
+    __shared__ unsigned long long s_sum[kChunkItems][2];
+    __shared__ unsigned s_end[kChunkItems];           // chunk-relative end of item it_lo + j
+    const bool shared_items = ic.n_items <= (unsigned)kChunkItems;
+    for (int b = threadIdx.x; b < kChunkItems * 2; b += blockDim.x) (&s_sum[0][0])[b] = 0ull;
+    if (shared_items && threadIdx.x < ic.n_items) {
+        const unsigned long long e = (unsigned long long)(ic.it_lo + threadIdx.x + 1) * ic.n_per_item - ic.g0;
+        s_end[threadIdx.x] = (unsigned)min(e, (unsigned long long)n);
+    }
+    __syncthreads();
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const unsigned k = kcount[i];
+        if (!k) continue;
+        kcount[i] = 0u;
+        if (shared_items) {
+            unsigned j = 0;
+            while (j + 1 < ic.n_items && i >= s_end[j]) ++j;
+            atomicAdd(&s_sum[j][0], (unsigned long long)k);
+            atomicAdd(&s_sum[j][1], (unsigned long long)k * k);
+        } else {
+            const unsigned it = (unsigned)((ic.g0 + i) / ic.n_per_item);
+            Tally* t = ic.tallies + ic.items[it].tally;
+            atomicAdd(&t->sum_k, (unsigned long long)k);
+            atomicAdd(&t->sum_k2, (unsigned long long)k * k);
+        }
+    }
+    __syncthreads();
+    if (shared_items && threadIdx.x < ic.n_items) {
+        const unsigned j = threadIdx.x;
+        if (s_sum[j][0]) {
+            Tally* t = ic.tallies + ic.items[ic.it_lo + j].tally;
+            atomicAdd(&t->sum_k, s_sum[j][0]);
+            atomicAdd(&t->sum_k2, s_sum[j][1]);
+        }
     }
 }
 
@@ -895,6 +1088,38 @@ cudaError_t launch_generate(const RunParams& p, const Queues& q, int buf, unsign
     return cudaGetLastError();
 }
 
+template <int F, bool R, bool C, int SS>
+static cudaError_t ww_launch(const DeviceMesh& m, const Cell& cell, const Queues& q, int buf, int gen, int num_sms,
+                             const Tuning& tune, bool retest, const void* nodes, cudaStream_t s)
+{
+    const int bt = tune.block_threads;
+    int per_sm = tune.blocks_per_sm;
+    const int thr = tune.fetch_threshold > 0 ? tune.fetch_threshold : kFetchThreshold;
+    const size_t smem = (size_t)SS * bt * sizeof(int2) + 3 * (size_t)bt * sizeof(double);
+    if (retest) {
+        if (per_sm <= 0)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse_ww<F, R, C, true, SS>, bt, smem);
+        k_traverse_ww<F, R, C, true, SS><<<num_sms * (per_sm > 0 ? per_sm : 1), bt, smem, s>>>(
+            nodes, m.tris, m.normals, cell, q.oe[buf], q.dt[buf], q.hits, R ? q.wraps : nullptr, q.ctl, gen,
+            q.cap[buf], q.retest, q.tally, thr);
+    } else {
+        if (per_sm <= 0)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse_ww<F, R, C, false, SS>, bt, smem);
+        k_traverse_ww<F, R, C, false, SS><<<num_sms * (per_sm > 0 ? per_sm : 1), bt, smem, s>>>(
+            nodes, m.tris, m.normals, cell, q.oe[buf], q.dt[buf], q.hits, R ? q.wraps : nullptr, q.ctl, gen,
+            q.cap[buf], nullptr, q.tally, thr);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && retest) {
+        const int tb = 64;
+        const size_t rs = (size_t)kSmemStack * tb * sizeof(int2);
+        k_retest<F, R><<<num_sms, tb, rs, s>>>(nodes, m.tris, cell, q.oe[buf], q.dt[buf], q.hits,
+                                               R ? q.wraps : nullptr, q.ctl, gen, q.cap[buf], q.retest, q.tally);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
 template <int F, bool R, bool C>
 static cudaError_t traverse_t(const DeviceMesh& m, const RunParams& p, const Queues& q, int buf, int gen,
                               int num_sms, const Tuning& tune, bool retest, cudaStream_t s)
@@ -910,30 +1135,12 @@ static cudaError_t traverse_t(const DeviceMesh& m, const RunParams& p, const Que
             nodes, m.tris, cell, q.oe[buf], q.dt[buf], q.hits, R ? q.wraps : nullptr, q.ctl, gen, q.cap[buf],
             q.tally);
     } else {
-        const size_t smem = (size_t)kSmemStack * bt * sizeof(int2) + 3 * (size_t)bt * sizeof(double);
-        if (retest) {
-            if (per_sm <= 0)
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse_ww<F, R, C, true>, bt, smem);
-            k_traverse_ww<F, R, C, true><<<num_sms * (per_sm > 0 ? per_sm : 1), bt, smem, s>>>(
-                nodes, m.tris, m.normals, cell, q.oe[buf], q.dt[buf], q.hits, R ? q.wraps : nullptr, q.ctl, gen,
-                q.cap[buf], q.retest, q.tally);
-        } else {
-            if (per_sm <= 0)
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse_ww<F, R, C, false>, bt, smem);
-            k_traverse_ww<F, R, C, false><<<num_sms * (per_sm > 0 ? per_sm : 1), bt, smem, s>>>(
-                nodes, m.tris, m.normals, cell, q.oe[buf], q.dt[buf], q.hits, R ? q.wraps : nullptr, q.ctl, gen,
-                q.cap[buf], nullptr, q.tally);
-        }
+        const int depth = tune.stack_depth;
+        if (C || depth == 16) return ww_launch<F, R, C, 16>(m, cell, q, buf, gen, num_sms, tune, retest, nodes, s);
+        if (depth == 8) return ww_launch<F, R, false, 8>(m, cell, q, buf, gen, num_sms, tune, retest, nodes, s);
+        return ww_launch<F, R, false, 32>(m, cell, q, buf, gen, num_sms, tune, retest, nodes, s);
     }
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess && retest && tune.traversal != 1) {
-        const int tb = 64;
-        const size_t smem = (size_t)kSmemStack * tb * sizeof(int2);
-        k_retest<F, R><<<num_sms, tb, smem, s>>>(nodes, m.tris, cell, q.oe[buf], q.dt[buf], q.hits,
-                                                 R ? q.wraps : nullptr, q.ctl, gen, q.cap[buf], q.retest, q.tally);
-        e = cudaGetLastError();
-    }
-    return e;
+    return cudaGetLastError();
 }
 
 template <int F>
@@ -961,16 +1168,49 @@ cudaError_t launch_shade(const DeviceMesh& m, const RunParams& p, const TableDes
     const ShadeOut out{q.oe[nb], q.dt[nb], q.id[nb], q.cap[nb]};
     const size_t smem = (size_t)(p.n_ebins + p.n_abins) * sizeof(unsigned);
     const int blocks = num_sms * 4;
+    const ItemCtx ic{};
     if (record)
-        k_shade<true><<<blocks, kShadeThreads, smem, s>>>(m.tris, m.normals, tab, em, p, q.oe[buf], q.dt[buf],
-                                                          q.id[buf], q.hits, q.wraps, out, q.ctl, gen, q.cap[buf], q.tally,
-                                                          q.hist_e, q.hist_a, q.kcount, chunk_first, q.prim_hash,
-                                                          q.records, q.rec_cap);
+        k_shade<true, false><<<blocks, kShadeThreads, smem, s>>>(m.tris, m.normals, tab, em, p, ic, q.oe[buf],
+                                                                 q.dt[buf], q.id[buf], q.hits, q.wraps, out, q.ctl,
+                                                                 gen, q.cap[buf], q.tally, q.hist_e, q.hist_a,
+                                                                 q.kcount, chunk_first, q.prim_hash, q.records,
+                                                                 q.rec_cap);
     else
-        k_shade<false><<<blocks, kShadeThreads, smem, s>>>(m.tris, m.normals, tab, em, p, q.oe[buf], q.dt[buf],
-                                                           q.id[buf], q.hits, q.prim_hash ? q.wraps : nullptr, out, q.ctl, gen, q.cap[buf], q.tally,
-                                                           q.hist_e, q.hist_a, q.kcount, chunk_first, q.prim_hash,
-                                                           nullptr, 0);
+        k_shade<false, false><<<blocks, kShadeThreads, smem, s>>>(m.tris, m.normals, tab, em, p, ic, q.oe[buf],
+                                                                  q.dt[buf], q.id[buf], q.hits,
+                                                                  q.prim_hash ? q.wraps : nullptr, out, q.ctl, gen,
+                                                                  q.cap[buf], q.tally, q.hist_e, q.hist_a, q.kcount,
+                                                                  chunk_first, q.prim_hash, nullptr, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_generate_items(const RunParams& p, const ItemCtx& ic, const Queues& q, unsigned n,
+                                  cudaStream_t s)
+{
+    const int tb = 256;
+    const unsigned gb = n ? (n + tb - 1) / tb : 1;
+    k_generate_items<<<gb, tb, 0, s>>>(p, ic, n, q.oe[0], q.dt[0], q.id[0], q.ctl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shade_items(const DeviceMesh& m, const RunParams& p, const TableDesc& tab, const Emission& em,
+                               const ItemCtx& ic, const Queues& q, int buf, int gen, int num_sms, cudaStream_t s)
+{
+    const int nb = 1 - buf;
+    const ShadeOut out{q.oe[nb], q.dt[nb], q.id[nb], q.cap[nb]};
+    const size_t smem = (size_t)kChunkItems * (p.n_ebins + p.n_abins) * sizeof(unsigned);
+    k_shade<false, true><<<num_sms * 4, kShadeThreads, smem, s>>>(m.tris, m.normals, tab, em, p, ic, q.oe[buf],
+                                                                  q.dt[buf], q.id[buf], q.hits, q.wraps, out, q.ctl,
+                                                                  gen, q.cap[buf], q.tally, nullptr, nullptr, q.kcount,
+                                                                  0ull, nullptr, nullptr, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_items(const ItemCtx& ic, const Queues& q, unsigned n, int num_sms, cudaStream_t s)
+{
+    int gb = (int)((n + 255) / 256);
+    gb = std::max(1, std::min(gb, num_sms * 8));
+    k_finalize_items<<<gb, 256, 0, s>>>(q.kcount, n, ic);
     return cudaGetLastError();
 }
 

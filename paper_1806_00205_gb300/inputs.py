@@ -367,3 +367,15 @@ def opening_window(a: float = 100.0, rim: float | None = None):
     """Source window (x0, x1, y0, y1) covering exactly the pit opening."""
     r = a / 16.0 if rim is None else float(rim)
     return (r, r + a, r, r + a)
+
+
+def batched_foams(n_foams: int = 16, p_lo: float = 0.30, p_hi: float = 0.90, g_lo: int = 48, g_hi: int = 128,
+                  seed: int = 1806):
+    """The batched workload's foams: porosity linspace(p_lo, p_hi, n) and grid
+    sizes linspace(g_lo, g_hi, n) rounded to multiples of 16, paired by a
+    seeded shuffle.  Returns a list of (grid, porosity, seed)."""
+    por = np.linspace(p_lo, p_hi, n_foams)
+    grids = (np.round(np.linspace(g_lo, g_hi, n_foams) / 16.0) * 16).astype(int)
+    rng = np.random.Generator(np.random.Philox(seed))
+    grids = grids[rng.permutation(n_foams)]
+    return [(int(g), float(p), int(seed + k)) for k, (g, p) in enumerate(zip(grids, por))]

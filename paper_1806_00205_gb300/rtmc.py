@@ -26,7 +26,7 @@ ESCAPED, EMITTER, ABSORBED_LOW, ABSORBED_OTHER, LOST = 0, 1, 2, 3, 4
 EXPORTS = ["rtmc_create", "rtmc_destroy", "rtmc_last_error", "rtmc_load_mesh", "rtmc_unload_mesh",
            "rtmc_load_see_tables",
            "rtmc_build_bvh", "rtmc_run", "rtmc_run_records", "rtmc_trace_rays", "rtmc_philox",
-           "rtmc_record_hash", "rtmc_run_noalloc", "rtmc_export_bvh"]
+           "rtmc_record_hash", "rtmc_run_noalloc", "rtmc_export_bvh", "rtmc_run_batch"]
 NOALLOC_MAX_PRIMARIES = 4096
 
 
@@ -56,7 +56,15 @@ class RunDesc(C.Structure):
                 ("src_x0", C.c_double), ("src_x1", C.c_double), ("src_y0", C.c_double), ("src_y1", C.c_double),
                 ("chunk", C.c_int64), ("block_threads", C.c_int32), ("blocks_per_sm", C.c_int32),
                 ("prim_hash", C.c_void_p), ("profile", C.c_int32), ("count_visits", C.c_int32),
-                ("traversal", C.c_int32), ("fp64_retest", C.c_int32)]
+                ("traversal", C.c_int32), ("fp64_retest", C.c_int32), ("item_base", C.c_uint32),
+                ("no_graph", C.c_int32), ("stack_depth", C.c_int32), ("fetch_threshold", C.c_int32)]
+
+
+class Batch(C.Structure):
+    _fields_ = [("mesh_ids", C.POINTER(C.c_int32)), ("n_meshes", C.c_int32),
+                ("energies_ev", C.POINTER(C.c_double)), ("n_e", C.c_int32),
+                ("theta_deg", C.POINTER(C.c_double)), ("n_theta", C.c_int32),
+                ("n_primaries", C.c_int64), ("seed", C.c_uint64)]
 
 
 class Result(C.Structure):
@@ -110,6 +118,7 @@ def lib():
                                    C.POINTER(Result), vp, vp]
     L.rtmc_philox.argtypes = [vp, vp, i64, u64, vp]
     L.rtmc_export_bvh.argtypes = [vp, i32, i32, vp, i64, C.POINTER(i64)]
+    L.rtmc_run_batch.argtypes = [vp, C.POINTER(Batch), C.POINTER(RunDesc), C.POINTER(Result), vp, vp]
     L.rtmc_record_hash.argtypes = [C.POINTER(Record)]
     L.rtmc_record_hash.restype = u64
     for name in EXPORTS:
@@ -140,12 +149,14 @@ class Emission:
 
 def run_desc(n_ebins=64, n_abins=18, hist_e_max_ev=50.0, primary_offset=0, random_azimuth=False,
              max_wraps=1024, window=None, chunk=0, block_threads=0, blocks_per_sm=0, prim_hash=None,
-             profile=False, count_visits=False, traversal=0, fp64_retest=False):
+             profile=False, count_visits=False, traversal=0, fp64_retest=False, item_base=0, no_graph=False,
+             stack_depth=0, fetch_threshold=0):
     x0, x1, y0, y1 = window if window is not None else (0.0, 0.0, 0.0, 0.0)
     return RunDesc(int(n_ebins), int(n_abins), float(hist_e_max_ev), int(primary_offset),
                    int(bool(random_azimuth)), int(max_wraps), x0, x1, y0, y1, int(chunk), int(block_threads),
                    int(blocks_per_sm), prim_hash.data_ptr() if prim_hash is not None else None,
-                   int(bool(profile)), int(bool(count_visits)), int(traversal), int(bool(fp64_retest)))
+                   int(bool(profile)), int(bool(count_visits)), int(traversal), int(bool(fp64_retest)),
+                   int(item_base), int(bool(no_graph)), int(stack_depth), int(fetch_threshold))
 
 
 def result_dict(r: Result):
@@ -238,6 +249,21 @@ class Context:
         out = result_dict(res)
         out["records"] = np.sort(rec[:n.value], order=["prim", "gen", "path"])
         return out
+
+    def run_batch(self, mesh_ids, energies, thetas, n_primaries, seed, desc: RunDesc | None = None):
+        """Batched form over meshes x energies x angles; returns (results, hist_e, hist_a)."""
+        ids = np.ascontiguousarray(np.atleast_1d(mesh_ids), dtype=np.int32)
+        e = np.ascontiguousarray(np.atleast_1d(energies), dtype=np.float64)
+        t = np.ascontiguousarray(np.atleast_1d(thetas), dtype=np.float64)
+        d = desc or run_desc()
+        b = Batch(ids.ctypes.data_as(C.POINTER(C.c_int32)), ids.size, e.ctypes.data_as(C.POINTER(C.c_double)),
+                  e.size, t.ctypes.data_as(C.POINTER(C.c_double)), t.size, int(n_primaries), int(seed))
+        n_items = ids.size * e.size * t.size
+        out = (Result * n_items)()
+        he = np.zeros((n_items, d.n_ebins), dtype=np.uint64)
+        ha = np.zeros((n_items, d.n_abins), dtype=np.uint64)
+        self._check(self._L.rtmc_run_batch(self.h, C.byref(b), C.byref(d), out, _ptr(he), _ptr(ha)))
+        return [result_dict(r) for r in out], he, ha
 
     def run_noalloc(self, mesh_id, energy, theta, n_primaries, seed, item=0, desc=None):
         """One item through rtmc_run_noalloc (static device scratch, no allocation).
