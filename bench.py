@@ -164,25 +164,6 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def l2_copy_gbs(torch, dev):
-    """Achievable L2 bandwidth: device copy between two 24 MiB buffers (both stay in L2)."""
-    a = torch.empty(6 * 1024 * 1024, dtype=torch.float32, device=dev)
-    b = torch.empty_like(a)
-    a.fill_(1.0)
-    for _ in range(5):
-        b.copy_(a)
-    best = float("inf")
-    for _ in range(20):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(10):
-            b.copy_(a)
-        e1.record()
-        torch.cuda.synchronize(dev)
-        best = min(best, e0.elapsed_time(e1) / 10)
-    return 2 * a.numel() * 4 / (best / 1e3) / 1e9
-
-
 def run_forms(ctx, rtmc, autotune, n_prim):
     """Batched config: 16 foams (48^3..128^3, porosity 0.3..0.9) x 20 energies x 9 angles.
 
@@ -262,8 +243,11 @@ def run_ours(args):
     mid = ctx.load_mesh(mesh.tri, mesh.box)
     ctx.build_bvh(mid)
     offset = rank * n_prim * len(energies)      # weak scaling: each rank its own primary ids
-    tuned = autotune.tune(ctx, [mid], [mesh.n_tri], energies, [0.0], kind=0, cache_path=None,
-                          device_name=torch.cuda.get_device_name(dev))
+    if args.no_autotune:
+        tuned = {}
+    else:
+        tuned = autotune.tune(ctx, [mid], [mesh.n_tri], energies, [0.0], kind=0, cache_path=None,
+                              device_name=torch.cuda.get_device_name(dev))
     desc = rtmc.run_desc(primary_offset=offset, profile=True, no_graph=True, **tuned)
 
     def barrier():
@@ -336,7 +320,8 @@ def run_ours(args):
     pk, pk_kind = peaks()
     peak = float(pk.get("hbm_gbs", 6800.0))
     traffic = measured_traffic()
-    l2_gbs = l2_copy_gbs(torch, dev)
+    l2_gbs = ctx.probe_bandwidth(32 << 20, 50)          # L2-resident streaming read (own probe)
+    hbm_read_gbs = ctx.probe_bandwidth(4 << 30, 5)      # HBM streaming read (own probe)
 
     # end to end through the C ABI from pinned host memory
     tri_host = torch.from_numpy(mesh.tri.reshape(-1, 9)).pin_memory()
@@ -396,7 +381,8 @@ def run_ours(args):
                          "peak_kind": f"{pk_kind} hbm_gbs", "bytes_per_ray": b_ray,
                          "node_visits_per_ray": visits, "tri_tests_per_ray": tests,
                          "traverse_ms_per_launch": trav_ms / max(1, trav_launches),
-                         "l2_copy_gbs": l2_gbs, "frac_of_l2_copy": achieved / l2_gbs},
+                         "l2_read_probe_gbs": l2_gbs, "frac_of_l2_read_probe": achieved / l2_gbs,
+                         "hbm_read_probe_gbs": hbm_read_gbs},
             "e2e": {"value": e_rays / e_dt, "unit": "rays/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
@@ -424,6 +410,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched-config form comparison")
     ap.add_argument("--forms-primaries", type=int, default=1_000_000)
+    ap.add_argument("--no-autotune", action="store_true", help="default launch parameters (profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

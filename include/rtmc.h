@@ -99,6 +99,9 @@ typedef struct {
     int32_t no_graph;              /* rtmc_run_batch: 1 = launch eagerly, no CUDA graph */
     int32_t stack_depth;           /* shared-memory traversal stack entries: 8, 16 or 32 (0 -> 16) */
     int32_t fetch_threshold;       /* warp refills rays when fewer lanes than this are busy (0 -> 20) */
+    int32_t id_order;              /* 1: queue primaries in id order; 0: order them by a
+                                      Morton-ordered 128 x 128 grid of entry points
+                                      (coherent traversal; results do not depend on order) */
 } rtmc_run_desc;
 
 typedef struct {
@@ -216,6 +219,12 @@ int rtmc_trace_rays(rtmc_ctx* ctx, int32_t mesh_id, const float* o, const float*
    bytes must be at least that size. */
 int rtmc_export_bvh(rtmc_ctx* ctx, int32_t mesh_id, int32_t which, void* out, int64_t bytes,
                     int64_t* bytes_needed);
+
+/* Read-bandwidth probe used as a roofline denominator: `iters` launches of a
+   kernel that streams `bytes` (a context-owned buffer, zero-filled) with
+   128-bit loads from every SM; *gbs receives bytes * iters / device time.
+   32 MiB stays in L2 after the first pass; a few GiB measures HBM. */
+int rtmc_probe_bandwidth(rtmc_ctx* ctx, int64_t bytes, int32_t iters, double* gbs);
 
 /* Philox4x32-10 on the device: out[i][4] = philox(ctr[i][4], key), for
    checking the device generator against the published vectors. */

@@ -226,6 +226,7 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
         if (ce == cudaSuccess) ce = scratch_reserve(ctx->kcount, (size_t)chunk * 4);
         if (ce == cudaSuccess && kc_new) ce = cudaMemsetAsync(ctx->kcount.ptr, 0, ctx->kcount.bytes, s);
         if (ce == cudaSuccess) ce = scratch_reserve(ctx->ctl, sizeof(Control));
+        if (ce == cudaSuccess && !d.id_order) ce = scratch_reserve(ctx->sort_counts, (size_t)kSortBucketsPerItem * 4);
         if (ce == cudaSuccess) ce = scratch_reserve(ctx->tally, sizeof(Tally));
         if (ce == cudaSuccess) ce = scratch_reserve(ctx->hist, (size_t)(d.n_ebins + d.n_abins) * 8);
         if (ce == cudaSuccess && record) ce = scratch_reserve(ctx->records, (size_t)std::max<int64_t>(o.rec_cap, 1) * sizeof(rtmc_record));
@@ -243,6 +244,7 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
         q.wraps = need_wraps ? (int*)ctx->wraps.ptr : nullptr;
         q.kcount = (unsigned*)ctx->kcount.ptr;
         q.retest = d.fp64_retest ? (unsigned*)ctx->retest.ptr : nullptr;
+        q.sort_counts = d.id_order ? nullptr : (unsigned*)ctx->sort_counts.ptr;
         q.ctl = (Control*)ctx->ctl.ptr;
         q.tally = (Tally*)ctx->tally.ptr;
         q.hist_e = (unsigned long long*)ctx->hist.ptr;
@@ -275,7 +277,9 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
             const unsigned nc = (unsigned)std::min<int64_t>(chunk, n_prim - first);
             ce = cudaMemsetAsync(q.ctl, 0, sizeof(Control), s);
             int h = tick(0);
-            if (ce == cudaSuccess) ce = launch_generate(p, q, 0, (unsigned long long)first, nc, s);
+            if (ce == cudaSuccess)
+                ce = d.id_order ? launch_generate(p, q, 0, (unsigned long long)first, nc, s)
+                                : launch_generate_sorted(p, q, (unsigned long long)first, nc, s);
             tock(h);
             ++launches;
             for (int g = 0; g <= em.max_generation && ce == cudaSuccess; ++g) {
@@ -427,7 +431,8 @@ void rtmc_destroy(rtmc_ctx* ctx)
     if (ctx->batch_graph) cudaGraphExecDestroy(ctx->batch_graph);
     rtmc::Scratch* all[] = {&ctx->q_oe[0], &ctx->q_oe[1], &ctx->q_dt[0], &ctx->q_dt[1], &ctx->q_id[0],
                             &ctx->q_id[1], &ctx->hits, &ctx->kcount, &ctx->ctl, &ctx->tally, &ctx->hist,
-                            &ctx->wraps, &ctx->records, &ctx->tmp, &ctx->retest, &ctx->items};
+                            &ctx->wraps, &ctx->records, &ctx->tmp, &ctx->retest, &ctx->items,
+                            &ctx->sort_counts};
     for (auto* s : all) rtmc::scratch_free(*s);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -622,6 +627,36 @@ int rtmc_export_bvh(rtmc_ctx* ctx, int32_t mesh_id, int32_t which, void* out, in
     cudaError_t e = cudaMemcpyAsync(out, src, (size_t)need, cudaMemcpyDefault, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "export_bvh");
+    return RTMC_OK;
+}
+
+int rtmc_probe_bandwidth(rtmc_ctx* ctx, int64_t bytes, int32_t iters, double* gbs)
+{
+    if (!ctx) return RTMC_ERR_INVALID_ARG;
+    if (!gbs || bytes < (1 << 20) || bytes > ((int64_t)64 << 30) || iters < 1 || iters > 10000)
+        return ctx->fail(RTMC_ERR_INVALID_ARG, "probe_bandwidth: bytes in [1 MiB, 64 GiB], iters in [1, 10000]");
+    DeviceGuard g(ctx->device);
+    bytes &= ~(int64_t)255;
+    cudaError_t e = rtmc::scratch_reserve(ctx->tmp, (size_t)bytes + 256);
+    if (e != cudaSuccess) return ctx->fail(RTMC_ERR_OOM, "probe_bandwidth: scratch");
+    cudaStream_t s = ctx->stream;
+    float* sink = reinterpret_cast<float*>(static_cast<char*>(ctx->tmp.ptr) + bytes);
+    e = cudaMemsetAsync(ctx->tmp.ptr, 0, (size_t)bytes, s);
+    if (e == cudaSuccess) e = rtmc::launch_read_probe(ctx->tmp.ptr, (size_t)bytes, ctx->num_sms, sink, s);
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, s);
+    for (int i = 0; i < iters && e == cudaSuccess; ++i)
+        e = rtmc::launch_read_probe(ctx->tmp.ptr, (size_t)bytes, ctx->num_sms, sink, s);
+    cudaEventRecord(b, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    float ms = 0.f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "probe_bandwidth");
+    *gbs = (double)bytes * iters / (ms / 1e3) / 1e9;
     return RTMC_OK;
 }
 

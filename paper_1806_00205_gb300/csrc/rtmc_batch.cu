@@ -97,7 +97,9 @@ cudaError_t record_batch(rtmc_ctx* ctx, const rtmc_batch& b, const rtmc_run_desc
             qq.tally = d_tallies + n_items;   // traversal-side counters and status: the batch slot
             ce = cudaMemsetAsync(q.ctl, 0, sizeof(Control), s);
             int h = kt.tick(0, s);
-            if (ce == cudaSuccess) ce = launch_generate_items(p, ic, qq, n, s);
+            const bool sorted = !d.id_order && ic.n_items <= (unsigned)kChunkItems;
+            if (ce == cudaSuccess)
+                ce = sorted ? launch_generate_items_sorted(p, ic, qq, n, s) : launch_generate_items(p, ic, qq, n, s);
             kt.tock(h, s);
             launches += 1;
             for (int g = 0; g <= ctx->emission.max_generation && ce == cudaSuccess; ++g) {
@@ -190,10 +192,10 @@ extern "C" int rtmc_run_batch(rtmc_ctx* ctx, const rtmc_batch* batch, const rtmc
     const int64_t cap0 = chunk, cap1 = chunk * kmax;
     if (cap1 > 0xFFFFFFF0ll) return ctx->fail(RTMC_ERR_CAPACITY, "run_batch: chunk too large");
     cudaError_t ce = cudaSuccess;
-    const void* before[14] = {ctx->q_oe[0].ptr, ctx->q_oe[1].ptr, ctx->q_dt[0].ptr, ctx->q_dt[1].ptr,
+    const void* before[15] = {ctx->q_oe[0].ptr, ctx->q_oe[1].ptr, ctx->q_dt[0].ptr, ctx->q_dt[1].ptr,
                               ctx->q_id[0].ptr, ctx->q_id[1].ptr, ctx->hits.ptr, ctx->kcount.ptr,
                               ctx->ctl.ptr, ctx->tally.ptr, ctx->hist.ptr, ctx->items.ptr, ctx->wraps.ptr,
-                              ctx->retest.ptr};
+                              ctx->retest.ptr, ctx->sort_counts.ptr};
     for (int bb = 0; bb < 2 && ce == cudaSuccess; ++bb) {
         const int64_t c = bb ? cap1 : cap0;
         ce = scratch_reserve(ctx->q_oe[bb], (size_t)c * 16);
@@ -210,11 +212,13 @@ extern "C" int rtmc_run_batch(rtmc_ctx* ctx, const rtmc_batch* batch, const rtmc
     if (ce == cudaSuccess) ce = scratch_reserve(ctx->hist, (size_t)n_items * nbins * 8);
     if (ce == cudaSuccess) ce = scratch_reserve(ctx->items, (size_t)n_items * sizeof(ItemDev));
     if (ce == cudaSuccess && d.fp64_retest) ce = scratch_reserve(ctx->retest, (size_t)cap1 * 4);
+    if (ce == cudaSuccess && !d.id_order)
+        ce = scratch_reserve(ctx->sort_counts, (size_t)kChunkItems * kSortBucketsPerItem * 4);
     if (ce != cudaSuccess) return ctx->fail(RTMC_ERR_OOM, std::string("run_batch: scratch: ") + cudaGetErrorString(ce));
-    const void* after[14] = {ctx->q_oe[0].ptr, ctx->q_oe[1].ptr, ctx->q_dt[0].ptr, ctx->q_dt[1].ptr,
+    const void* after[15] = {ctx->q_oe[0].ptr, ctx->q_oe[1].ptr, ctx->q_dt[0].ptr, ctx->q_dt[1].ptr,
                              ctx->q_id[0].ptr, ctx->q_id[1].ptr, ctx->hits.ptr, ctx->kcount.ptr,
                              ctx->ctl.ptr, ctx->tally.ptr, ctx->hist.ptr, ctx->items.ptr, ctx->wraps.ptr,
-                             ctx->retest.ptr};
+                             ctx->retest.ptr, ctx->sort_counts.ptr};
     const bool moved = std::memcmp(before, after, sizeof before) != 0;
 
     Queues q;
@@ -229,6 +233,7 @@ extern "C" int rtmc_run_batch(rtmc_ctx* ctx, const rtmc_batch* batch, const rtmc
     q.wraps = (int*)ctx->wraps.ptr;
     q.kcount = (unsigned*)ctx->kcount.ptr;
     q.retest = d.fp64_retest ? (unsigned*)ctx->retest.ptr : nullptr;
+    q.sort_counts = d.id_order ? nullptr : (unsigned*)ctx->sort_counts.ptr;
     q.ctl = (Control*)ctx->ctl.ptr;
     q.tally = (Tally*)ctx->tally.ptr;
     q.hist_e = nullptr;
@@ -261,7 +266,7 @@ extern "C" int rtmc_run_batch(rtmc_ctx* ctx, const rtmc_batch* batch, const rtmc
             std::snprintf(buf, sizeof buf, "|%d:%p:%p:%d", batch->mesh_ids[i], (const void*)m.nodes, m.q8, m.kind);
             key += buf;
         }
-        std::snprintf(buf, sizeof buf, "|cv%d|%p", d.count_visits, (const void*)ctx->delta);
+        std::snprintf(buf, sizeof buf, "|cv%d|io%d|%p", d.count_visits, d.id_order, (const void*)ctx->delta);
         key += buf;
     }
     if (moved || key != ctx->batch_key) {

@@ -57,6 +57,7 @@ struct rtmc_ctx {
     // run buffers
     rtmc::Scratch q_oe[2], q_dt[2], q_id[2], hits, kcount, ctl, tally, hist, wraps, records, tmp, retest;
     rtmc::Scratch items;                      // batched item table
+    rtmc::Scratch sort_counts;                // spatial sort of primaries
     cudaGraphExec_t batch_graph = nullptr;    // captured batch launch sequence
     std::string batch_key;                    // what the captured graph was built for
     int64_t batch_launches = 0;               // kernel launches in the captured graph
@@ -94,6 +95,7 @@ struct RunParams {
     float ebin_w;                // eV per energy bin
     float inv_abin;              // bins per radian of polar angle
     unsigned long long prim_offset;
+    float sin_t, cos_t;          // incidence (single-item runs)
 };
 
 struct Queues {
@@ -104,6 +106,7 @@ struct Queues {
     int* wraps;                  // record mode only
     unsigned* kcount;
     unsigned* retest;            // flagged ray indices (FP64 re-test), capacity max(cap)
+    unsigned* sort_counts;       // spatial sort of primaries: per-bucket counts / cursors
     Control* ctl;
     Tally* tally;
     unsigned long long* hist_e;  // device, n_ebins
@@ -125,11 +128,19 @@ cudaError_t launch_shade(const DeviceMesh& m, const RunParams& p, const TableDes
 cudaError_t launch_finalize(const Queues& q, unsigned n, cudaStream_t s);
 cudaError_t launch_generate_items(const RunParams& p, const ItemCtx& ic, const Queues& q, unsigned n,
                                   cudaStream_t s);
+// Spatially sorted primaries (Morton-ordered 128 x 128 entry cells; per item in
+// multi-item chunks, at most kChunkItems items).
+constexpr unsigned kSortBucketsPerItem = 1u << 14;
+cudaError_t launch_generate_sorted(const RunParams& p, const Queues& q, unsigned long long first, unsigned n,
+                                   cudaStream_t s);
+cudaError_t launch_generate_items_sorted(const RunParams& p, const ItemCtx& ic, const Queues& q, unsigned n,
+                                         cudaStream_t s);
 cudaError_t launch_shade_items(const DeviceMesh& m, const RunParams& p, const TableDesc& tab, const Emission& em,
                                const ItemCtx& ic, const Queues& q, int buf, int gen, int num_sms, cudaStream_t s);
 cudaError_t launch_finalize_items(const ItemCtx& ic, const Queues& q, unsigned n, int num_sms, cudaStream_t s);
 cudaError_t launch_trace_rays(const DeviceMesh& m, const float* o, const float* d, const int* skip,
                               int64_t n, rtmc_hit* hits, unsigned* status, cudaStream_t s);
+cudaError_t launch_read_probe(const void* buf, size_t bytes, int num_sms, float* sink, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t* ctr, int64_t n, unsigned long long key, uint32_t* out,
                           cudaStream_t s);
 

@@ -72,6 +72,120 @@ __global__ void k_generate_items(RunParams p, ItemCtx ic, unsigned n, float4* __
     id[i] = make_uint4(pl, it, 1u, 0u);
 }
 
+// Spatially ordered generation: primaries are counting-sorted by a
+// Morton-ordered 128 x 128 grid cell of their entry point (per item), so a
+// warp's lanes start close together and fetch the same BVH nodes.  The sort
+// is not stable (slots come from atomic cursors); per-ray results do not
+// depend on queue order because each ray's random numbers are keyed by its
+// identity.  Pass 1 counts, a single-block scan turns counts into cursors,
+// pass 2 writes each ray at its cursor.
+constexpr int kSortCellBits = 7;                        // 128 x 128 cells
+constexpr unsigned kSortCells = 1u << (2 * kSortCellBits);
+
+__device__ __forceinline__ unsigned spread7(unsigned v)   // bits 0..6 -> even bit positions
+{
+    v &= 0x7Fu;
+    v = (v | (v << 4)) & 0x0F0Fu;
+    v = (v | (v << 2)) & 0x3333u;
+    v = (v | (v << 1)) & 0x5555u;
+    return v;
+}
+
+template <bool ITEMS>
+__device__ __forceinline__ void primary_of(const RunParams& p, const ItemCtx& ic, unsigned long long first,
+                                           unsigned i, float4& oe, float4& dt, uint4& id, unsigned& bucket)
+{
+    unsigned long long prim;
+    unsigned pitem, it_rel = 0;
+    float energy, sin_t, cos_t;
+    uint2 idxy;
+    if (ITEMS) {
+        const unsigned long long g = ic.g0 + i;
+        const unsigned it = (unsigned)(g / ic.n_per_item);
+        const unsigned pl = (unsigned)(g - (unsigned long long)it * ic.n_per_item);
+        const ItemDev item = ic.items[it];
+        prim = item.prim_offset + pl;
+        pitem = item.philox_item;
+        energy = item.energy; sin_t = item.sin_t; cos_t = item.cos_t;
+        idxy = make_uint2(pl, it);
+        it_rel = it - ic.it_lo;
+    } else {
+        prim = p.prim_offset + first + i;
+        pitem = p.item;
+        energy = p.energy; sin_t = p.sin_t; cos_t = p.cos_t;
+        idxy = make_uint2((unsigned)prim, (unsigned)(prim >> 32));
+    }
+    const uint4 w = ray_block(p.seed, (unsigned)prim, (unsigned)(prim >> 32), 1u, pitem);
+    const float ux = u01(w.x), uy = u01(w.y);
+    const float x = p.src_x0 + ux * (p.src_x1 - p.src_x0);
+    const float y = p.src_y0 + uy * (p.src_y1 - p.src_y0);
+    float ca = 1.f, sa = 0.f;
+    if (p.random_azimuth) sincospif(2.0f * u01(w.z), &sa, &ca);
+    oe = make_float4(x, y, p.z_top, energy);
+    dt = make_float4(sin_t * ca, sin_t * sa, -cos_t, __int_as_float(-1));
+    id = make_uint4(idxy.x, idxy.y, 1u, 0u);
+    const unsigned cx = min((unsigned)(ux * (1 << kSortCellBits)), (1u << kSortCellBits) - 1);
+    const unsigned cy = min((unsigned)(uy * (1 << kSortCellBits)), (1u << kSortCellBits) - 1);
+    bucket = it_rel * kSortCells + (spread7(cx) | (spread7(cy) << 1));
+}
+
+template <bool ITEMS>
+__global__ void k_prim_count(RunParams p, ItemCtx ic, unsigned long long first, unsigned n,
+                             unsigned* __restrict__ counts)
+{
+    const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float4 a, b;
+    uint4 c;
+    unsigned bucket;
+    primary_of<ITEMS>(p, ic, first, i, a, b, c, bucket);
+    atomicAdd(&counts[bucket], 1u);
+}
+
+// Exclusive scan of `m` counts in place (one block of 1024 threads).
+__global__ void __launch_bounds__(1024) k_scan_counts(unsigned* __restrict__ c, unsigned m)
+{
+    __shared__ unsigned sums[1024];
+    const unsigned per = (m + blockDim.x - 1) / blockDim.x;
+    const unsigned lo = threadIdx.x * per, hi = min(lo + per, m);
+    unsigned t = 0;
+    for (unsigned i = lo; i < hi; ++i) t += c[i];
+    sums[threadIdx.x] = t;
+    __syncthreads();
+    for (unsigned off = 1; off < blockDim.x; off <<= 1) {
+        const unsigned v = threadIdx.x >= off ? sums[threadIdx.x - off] : 0u;
+        __syncthreads();
+        sums[threadIdx.x] += v;
+        __syncthreads();
+    }
+    unsigned run = sums[threadIdx.x] - t;
+    for (unsigned i = lo; i < hi; ++i) {
+        const unsigned v = c[i];
+        c[i] = run;
+        run += v;
+    }
+}
+
+template <bool ITEMS>
+__global__ void k_generate_sorted(RunParams p, ItemCtx ic, unsigned long long first, unsigned n,
+                                  unsigned* __restrict__ cursor, float4* __restrict__ oe, float4* __restrict__ dt,
+                                  uint4* __restrict__ id, Control* __restrict__ ctl)
+{
+    const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) ctl->count[0] = n;
+    if (i >= n) return;
+    float4 a, b;
+    uint4 c;
+    unsigned bucket;
+    primary_of<ITEMS>(p, ic, first, i, a, b, c, bucket);
+    const unsigned slot = atomicAdd(&cursor[bucket], 1u);
+    if (slot < n) {
+        oe[slot] = a;
+        dt[slot] = b;
+        id[slot] = c;
+    }
+}
+
 // --------------------------------------------------------------------------
 // traverse: BVH closest hit in one cell + periodic walk
 // --------------------------------------------------------------------------
@@ -1011,16 +1125,31 @@ __global__ void k_finalize_items(unsigned* __restrict__ kcount, unsigned n, Item
         s_end[threadIdx.x] = (unsigned)min(e, (unsigned long long)n);
     }
     __syncthreads();
-    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const unsigned k = kcount[i];
-        if (!k) continue;
-        kcount[i] = 0u;
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned stride = gridDim.x * blockDim.x;
+    for (unsigned base = blockIdx.x * blockDim.x; base < n; base += stride) {   // warp-uniform trip count
+        const unsigned i = base + threadIdx.x;
+        unsigned k = 0;
+        if (i < n) {
+            k = kcount[i];
+            if (k) kcount[i] = 0u;
+        }
         if (shared_items) {
             unsigned j = 0;
-            while (j + 1 < ic.n_items && i >= s_end[j]) ++j;
-            atomicAdd(&s_sum[j][0], (unsigned long long)k);
-            atomicAdd(&s_sum[j][1], (unsigned long long)k * k);
-        } else {
+            if (i < n) while (j + 1 < ic.n_items && i >= s_end[j]) ++j;
+            const unsigned j0 = __shfl_sync(0xFFFFFFFFu, j, 0);
+            if (__all_sync(0xFFFFFFFFu, j == j0 || i >= n)) {          // one item in this warp
+                const unsigned s1 = __reduce_add_sync(0xFFFFFFFFu, k);
+                const unsigned s2 = __reduce_add_sync(0xFFFFFFFFu, k * k);
+                if (lane == 0 && s1) {
+                    atomicAdd(&s_sum[j0][0], (unsigned long long)s1);
+                    atomicAdd(&s_sum[j0][1], (unsigned long long)s2);
+                }
+            } else if (k) {
+                atomicAdd(&s_sum[j][0], (unsigned long long)k);
+                atomicAdd(&s_sum[j][1], (unsigned long long)k * k);
+            }
+        } else if (k) {
             const unsigned it = (unsigned)((ic.g0 + i) / ic.n_per_item);
             Tally* t = ic.tallies + ic.items[it].tally;
             atomicAdd(&t->sum_k, (unsigned long long)k);
@@ -1063,6 +1192,24 @@ k_trace_rays(const void* __restrict__ nodes, const float4* __restrict__ tris, co
     h.tri = j >= 0 ? __float_as_int(__ldg(tris + 3ll * j).w) : -1;
     hits[i] = h;
     if (status) atomicOr(status_out, status);
+}
+
+// Streaming read of n float4 (bandwidth probe); the sum keeps the loads alive.
+__global__ void __launch_bounds__(256) k_read_probe(const float4* __restrict__ a, size_t n, float* __restrict__ sink)
+{
+    float acc = 0.f;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < n; i += 4 * stride) {
+        const float4 x = __ldcg(a + i), y = __ldcg(a + i + stride), z = __ldcg(a + i + 2 * stride),
+                     w = __ldcg(a + i + 3 * stride);
+        acc += x.x + x.y + x.z + x.w + y.x + y.y + y.z + y.w + z.x + z.y + z.z + z.w + w.x + w.y + w.z + w.w;
+    }
+    for (; i < n; i += stride) {
+        const float4 x = __ldcg(a + i);
+        acc += x.x + x.y + x.z + x.w;
+    }
+    if (acc == 1234.5f) sink[0] = acc;   // never true for the zero-filled buffer
 }
 
 __global__ void k_philox(const uint4* __restrict__ ctr, int64_t n, unsigned long long key, uint4* __restrict__ out)
@@ -1184,6 +1331,35 @@ cudaError_t launch_shade(const DeviceMesh& m, const RunParams& p, const TableDes
     return cudaGetLastError();
 }
 
+template <bool ITEMS>
+static cudaError_t generate_sorted(const RunParams& p, const ItemCtx& ic, const Queues& q,
+                                   unsigned long long first, unsigned n, unsigned buckets, cudaStream_t s)
+{
+    const int tb = 256;
+    const unsigned gb = n ? (n + tb - 1) / tb : 1;
+    cudaError_t e = cudaMemsetAsync(q.sort_counts, 0, (size_t)buckets * 4, s);
+    if (e == cudaSuccess && n) k_prim_count<ITEMS><<<gb, tb, 0, s>>>(p, ic, first, n, q.sort_counts);
+    if (e == cudaSuccess) k_scan_counts<<<1, 1024, 0, s>>>(q.sort_counts, buckets);
+    if (e == cudaSuccess)
+        k_generate_sorted<ITEMS><<<gb, tb, 0, s>>>(p, ic, first, n, q.sort_counts, q.oe[0], q.dt[0], q.id[0], q.ctl);
+    return e == cudaSuccess ? cudaGetLastError() : e;
+}
+
+cudaError_t launch_generate_sorted(const RunParams& p, const Queues& q, unsigned long long first, unsigned n,
+                                   cudaStream_t s)
+{
+    RunParams pp = p;
+    pp.sin_t = (float)sin((double)p.theta_rad);
+    pp.cos_t = (float)cos((double)p.theta_rad);
+    return generate_sorted<false>(pp, ItemCtx{}, q, first, n, kSortCells, s);
+}
+
+cudaError_t launch_generate_items_sorted(const RunParams& p, const ItemCtx& ic, const Queues& q, unsigned n,
+                                         cudaStream_t s)
+{
+    return generate_sorted<true>(p, ic, q, 0ull, n, ic.n_items * kSortCells, s);
+}
+
 cudaError_t launch_generate_items(const RunParams& p, const ItemCtx& ic, const Queues& q, unsigned n,
                                   cudaStream_t s)
 {
@@ -1236,6 +1412,12 @@ cudaError_t launch_trace_rays(const DeviceMesh& m, const float* o, const float* 
     else if (gb > 0)
         k_trace_rays<FMT_FP32><<<(unsigned)gb, tb, smem, s>>>(m.nodes, m.tris, m.inv_order, (int)m.n_tri, o, d, skip,
                                                               n, hits, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_read_probe(const void* buf, size_t bytes, int num_sms, float* sink, cudaStream_t s)
+{
+    k_read_probe<<<num_sms * 8, 256, 0, s>>>(reinterpret_cast<const float4*>(buf), bytes / 16, sink);
     return cudaGetLastError();
 }
 

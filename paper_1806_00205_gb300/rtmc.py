@@ -26,7 +26,8 @@ ESCAPED, EMITTER, ABSORBED_LOW, ABSORBED_OTHER, LOST = 0, 1, 2, 3, 4
 EXPORTS = ["rtmc_create", "rtmc_destroy", "rtmc_last_error", "rtmc_load_mesh", "rtmc_unload_mesh",
            "rtmc_load_see_tables",
            "rtmc_build_bvh", "rtmc_run", "rtmc_run_records", "rtmc_trace_rays", "rtmc_philox",
-           "rtmc_record_hash", "rtmc_run_noalloc", "rtmc_export_bvh", "rtmc_run_batch"]
+           "rtmc_record_hash", "rtmc_run_noalloc", "rtmc_export_bvh", "rtmc_run_batch",
+           "rtmc_probe_bandwidth"]
 NOALLOC_MAX_PRIMARIES = 4096
 
 
@@ -57,7 +58,8 @@ class RunDesc(C.Structure):
                 ("chunk", C.c_int64), ("block_threads", C.c_int32), ("blocks_per_sm", C.c_int32),
                 ("prim_hash", C.c_void_p), ("profile", C.c_int32), ("count_visits", C.c_int32),
                 ("traversal", C.c_int32), ("fp64_retest", C.c_int32), ("item_base", C.c_uint32),
-                ("no_graph", C.c_int32), ("stack_depth", C.c_int32), ("fetch_threshold", C.c_int32)]
+                ("no_graph", C.c_int32), ("stack_depth", C.c_int32), ("fetch_threshold", C.c_int32),
+                ("id_order", C.c_int32)]
 
 
 class Batch(C.Structure):
@@ -119,6 +121,7 @@ def lib():
     L.rtmc_philox.argtypes = [vp, vp, i64, u64, vp]
     L.rtmc_export_bvh.argtypes = [vp, i32, i32, vp, i64, C.POINTER(i64)]
     L.rtmc_run_batch.argtypes = [vp, C.POINTER(Batch), C.POINTER(RunDesc), C.POINTER(Result), vp, vp]
+    L.rtmc_probe_bandwidth.argtypes = [vp, i64, i32, C.POINTER(C.c_double)]
     L.rtmc_record_hash.argtypes = [C.POINTER(Record)]
     L.rtmc_record_hash.restype = u64
     for name in EXPORTS:
@@ -150,13 +153,14 @@ class Emission:
 def run_desc(n_ebins=64, n_abins=18, hist_e_max_ev=50.0, primary_offset=0, random_azimuth=False,
              max_wraps=1024, window=None, chunk=0, block_threads=0, blocks_per_sm=0, prim_hash=None,
              profile=False, count_visits=False, traversal=0, fp64_retest=False, item_base=0, no_graph=False,
-             stack_depth=0, fetch_threshold=0):
+             stack_depth=0, fetch_threshold=0, id_order=False):
     x0, x1, y0, y1 = window if window is not None else (0.0, 0.0, 0.0, 0.0)
     return RunDesc(int(n_ebins), int(n_abins), float(hist_e_max_ev), int(primary_offset),
                    int(bool(random_azimuth)), int(max_wraps), x0, x1, y0, y1, int(chunk), int(block_threads),
                    int(blocks_per_sm), prim_hash.data_ptr() if prim_hash is not None else None,
                    int(bool(profile)), int(bool(count_visits)), int(traversal), int(bool(fp64_retest)),
-                   int(item_base), int(bool(no_graph)), int(stack_depth), int(fetch_threshold))
+                   int(item_base), int(bool(no_graph)), int(stack_depth), int(fetch_threshold),
+                   int(bool(id_order)))
 
 
 def result_dict(r: Result):
@@ -294,6 +298,12 @@ class Context:
         buf = np.zeros(need.value, dtype=np.uint8)
         self._check(self._L.rtmc_export_bvh(self.h, int(mesh_id), int(which), _ptr(buf), need.value, C.byref(need)))
         return buf
+
+    def probe_bandwidth(self, nbytes, iters=20):
+        """Streaming read bandwidth (GB/s) over a buffer of `nbytes`."""
+        g = C.c_double()
+        self._check(self._L.rtmc_probe_bandwidth(self.h, int(nbytes), int(iters), C.byref(g)))
+        return g.value
 
     def philox(self, ctr, key):
         c = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
