@@ -99,7 +99,7 @@ class ClockSampler:
 
 def kernel_sha():
     h = hashlib.sha256()
-    for f in ("rtmc_trace.cu", "rtmc_device.cuh"):
+    for f in ("rtmc_traverse.cu", "rtmc_device.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1806_00205_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -221,6 +221,87 @@ def run_forms(ctx, rtmc, autotune, n_prim):
             "autotuned": {"batched_q8": pq, "batched_fp32": p32}}
 
 
+def run_large(args):
+    """Large config: 256^3 foam at porosity 0.7 (~8M triangles, Q8 BVH), tertiaries for
+    secondaries above 20 eV, 1e8 primaries at 500 eV x 9 incidence angles, 128 energy
+    bins and 36 angle bins, FP64 moments."""
+    import torch
+    from paper_1806_00205_gb300 import inputs as I
+    from paper_1806_00205_gb300 import rtmc
+    dev = torch.device("cuda", 0)
+    n_prim = args.primaries if args.primaries != N_PRIM else 100_000_000
+    thetas = [10.0 * j for j in range(9)]
+    mesh = I.grf_foam(256, 0.7, CORR, SEED)
+    table = I.see_table()
+    em = rtmc.Emission(regen_min_ev=20.0, max_generation=2)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = rtmc.Context(0, stream=stream)
+    ctx.load_see_tables(table, em)
+    mid = ctx.load_mesh(mesh.tri, mesh.box)
+    ctx.build_bvh(mid, kind=rtmc.BVH_Q8)
+    desc = rtmc.run_desc(n_ebins=128, n_abins=36, profile=True)
+    for _ in range(args.warmup):
+        ctx.run(mid, [500.0], thetas, n_prim // 10, SEED, desc=desc)
+    clocks = ClockSampler(0)
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    rays = prims = launches = 0
+    trav_ms, trav_l = 0.0, 0
+    for _ in range(args.steps):
+        res, he, ha = ctx.run(mid, [500.0], thetas, n_prim, SEED, desc=desc)
+        rays += sum(r["rays"] for r in res)
+        prims += sum(r["n_primaries"] for r in res)
+        launches += sum(r["launches"] for r in res)
+        trav_ms += sum(r["ms_traverse"] for r in res)
+        trav_l += sum(r["traverse_launches"] for r in res)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    cres, _, _ = ctx.run(mid, [500.0], thetas[:1], n_prim // 10, SEED,
+                         desc=rtmc.run_desc(n_ebins=128, n_abins=36, count_visits=True))
+    visits = cres[0]["node_visits"] / cres[0]["rays"]
+    tests = cres[0]["tri_tests"] / cres[0]["rays"]
+    b_ray = visits * 32 + tests * TRI_BYTES + RAY_BYTES
+    achieved = rays / args.steps * args.steps * b_ray / (trav_ms / 1e3) / 1e9
+    pk, pk_kind = peaks()
+    peak = float(pk.get("hbm_gbs", 6800.0))
+    tri_host = torch.from_numpy(mesh.tri.reshape(-1, 9)).pin_memory()
+    torch.cuda.synchronize(dev)
+    e0 = time.perf_counter()
+    m2 = ctx.load_mesh(tri_host, mesh.box)
+    ctx.build_bvh(m2, kind=rtmc.BVH_Q8)
+    rr, _, _ = ctx.run(m2, [500.0], thetas, n_prim, SEED, desc=rtmc.run_desc(n_ebins=128, n_abins=36))
+    ctx.unload_mesh(m2)
+    e_dt = time.perf_counter() - e0
+    cpu = None
+    if not args.no_cpu:
+        r, dt, threads = cpu_oracle_sample(mesh, table, 48)
+        cpu = {"value": r["rays"] / dt, "unit": "rays/s", "cores": threads, "kind": "oracle",
+               "sample": f"48 primaries at 500 eV, normal incidence, max_generation 1 (brute force over "
+                         f"{mesh.n_tri} triangles per segment); {dt:.1f} s"}
+    line = {"metric": METRIC, "value": rays / (ms / 1e3), "unit": "rays/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "primaries_per_s": prims / (ms / 1e3),
+            "config": {"workload": f"large: 256^3 periodic GRF foam (porosity 0.7) -> {mesh.n_tri} triangles, "
+                                   f"Q8 BVH; {n_prim:.0e} primaries at 500 eV x 9 angles (0..80 deg); "
+                                   "tertiaries above 20 eV (max_generation 2); 128 energy / 36 angle bins",
+                       "n_tri": mesh.n_tri, "l2": "inputs larger than L2 (Q8 nodes + triangles ~0.6 GB)"},
+            "sey": [round(r["sey"], 6) for r in res], "regenerated": sum(r["regenerated"] for r in res),
+            "roofline": {"bound": "hbm", "kernel": "k_traverse_ww (Q8)", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "peak_kind": f"{pk_kind} hbm_gbs", "bytes_per_ray": b_ray,
+                         "node_visits_per_ray": visits, "tri_tests_per_ray": tests},
+            "e2e": {"value": sum(r["rays"] for r in rr) / e_dt, "unit": "rays/s",
+                    "h2d_bytes_per_step": tri_host.numel() * 4 + table.delta.nbytes,
+                    "d2h_bytes_per_step": 9 * (rtmc.C.sizeof(rtmc.Result) + 8 * (128 + 36))},
+            "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -320,7 +401,7 @@ def run_ours(args):
     pk, pk_kind = peaks()
     peak = float(pk.get("hbm_gbs", 6800.0))
     traffic = measured_traffic()
-    l2_gbs = ctx.probe_bandwidth(32 << 20, 50)          # L2-resident streaming read (own probe)
+    l2_gbs = ctx.probe_bandwidth(32 << 20, 10)          # L2-resident streaming read (own probe)
     hbm_read_gbs = ctx.probe_bandwidth(4 << 30, 5)      # HBM streaming read (own probe)
 
     # end to end through the C ABI from pinned host memory
@@ -411,9 +492,13 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the batched-config form comparison")
     ap.add_argument("--forms-primaries", type=int, default=1_000_000)
     ap.add_argument("--no-autotune", action="store_true", help="default launch parameters (profiling runs)")
+    ap.add_argument("--config", choices=("paper", "large"), default="paper",
+                    help="paper: 128^3 foam, 20 energies x 1e7 (default); large: 256^3 foam, tertiaries")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "large":
+        run_large(args)
     else:
         run_ours(args)
 

@@ -222,8 +222,9 @@ int rtmc_export_bvh(rtmc_ctx* ctx, int32_t mesh_id, int32_t which, void* out, in
 
 /* Read-bandwidth probe used as a roofline denominator: `iters` launches of a
    kernel that streams `bytes` (a context-owned buffer, zero-filled) with
-   128-bit loads from every SM; *gbs receives bytes * iters / device time.
-   32 MiB stays in L2 after the first pass; a few GiB measures HBM. */
+   128-bit loads from every SM, repeating the pass so that each launch reads
+   at least 2 GiB; *gbs receives bytes read / device time.  32 MiB stays in
+   L2 after the first pass; a few GiB measures HBM. */
 int rtmc_probe_bandwidth(rtmc_ctx* ctx, int64_t bytes, int32_t iters, double* gbs);
 
 /* Philox4x32-10 on the device: out[i][4] = philox(ctr[i][4], key), for

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librtmc.so")
-SOURCES = ["rtmc_api.cu", "rtmc_bvh.cu", "rtmc_trace.cu", "rtmc_static.cu", "rtmc_batch.cu"]
+SOURCES = ["rtmc_api.cu", "rtmc_bvh.cu", "rtmc_trace.cu", "rtmc_traverse.cu", "rtmc_static.cu", "rtmc_batch.cu"]
 HEADERS = ["rtmc_device.cuh", "rtmc_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -641,14 +641,15 @@ int rtmc_probe_bandwidth(rtmc_ctx* ctx, int64_t bytes, int32_t iters, double* gb
     if (e != cudaSuccess) return ctx->fail(RTMC_ERR_OOM, "probe_bandwidth: scratch");
     cudaStream_t s = ctx->stream;
     float* sink = reinterpret_cast<float*>(static_cast<char*>(ctx->tmp.ptr) + bytes);
+    const int passes = (int)std::max<int64_t>(1, ((int64_t)2 << 30) / bytes);   // >= 2 GiB per launch
     e = cudaMemsetAsync(ctx->tmp.ptr, 0, (size_t)bytes, s);
-    if (e == cudaSuccess) e = rtmc::launch_read_probe(ctx->tmp.ptr, (size_t)bytes, ctx->num_sms, sink, s);
+    if (e == cudaSuccess) e = rtmc::launch_read_probe(ctx->tmp.ptr, (size_t)bytes, passes, ctx->num_sms, sink, s);
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
     cudaEventRecord(a, s);
     for (int i = 0; i < iters && e == cudaSuccess; ++i)
-        e = rtmc::launch_read_probe(ctx->tmp.ptr, (size_t)bytes, ctx->num_sms, sink, s);
+        e = rtmc::launch_read_probe(ctx->tmp.ptr, (size_t)bytes, passes, ctx->num_sms, sink, s);
     cudaEventRecord(b, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     float ms = 0.f;
@@ -656,7 +657,7 @@ int rtmc_probe_bandwidth(rtmc_ctx* ctx, int64_t bytes, int32_t iters, double* gb
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "probe_bandwidth");
-    *gbs = (double)bytes * iters / (ms / 1e3) / 1e9;
+    *gbs = (double)bytes * passes * iters / (ms / 1e3) / 1e9;
     return RTMC_OK;
 }
 

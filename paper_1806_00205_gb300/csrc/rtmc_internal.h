@@ -140,7 +140,7 @@ cudaError_t launch_shade_items(const DeviceMesh& m, const RunParams& p, const Ta
 cudaError_t launch_finalize_items(const ItemCtx& ic, const Queues& q, unsigned n, int num_sms, cudaStream_t s);
 cudaError_t launch_trace_rays(const DeviceMesh& m, const float* o, const float* d, const int* skip,
                               int64_t n, rtmc_hit* hits, unsigned* status, cudaStream_t s);
-cudaError_t launch_read_probe(const void* buf, size_t bytes, int num_sms, float* sink, cudaStream_t s);
+cudaError_t launch_read_probe(const void* buf, size_t bytes, int passes, int num_sms, float* sink, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t* ctr, int64_t n, unsigned long long key, uint32_t* out,
                           cudaStream_t s);
 

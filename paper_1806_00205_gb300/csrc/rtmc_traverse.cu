@@ -1,0 +1,644 @@
+// rtmc_traverse.cu -- ray traversal of the wavefront RTMC loop (sm_103a):
+// closest front-facing facet through the BVH (FP32 or Q8 nodes) with the
+// periodic cell walk, the FP64 re-test of flagged hits, and the closest-hit
+// query hook.  Section 2.1 of the paper (the four checks of the element scan)
+// and Section 2.2, last paragraph (periodic x/y, escape through z_max).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstdint>
+
+#include "rtmc_internal.h"
+
+namespace rtmc {
+namespace {
+
+constexpr int kSmemStack = 16;        // default stack entries held in shared memory per ray
+constexpr float kRobust = 1.0000004f; // 1 + 2 gamma_3 (Ize 2013): conservative slab test
+
+__device__ __forceinline__ float4 ldg4(const float4* p) { return __ldg(p); }
+
+// --------------------------------------------------------------------------
+// traverse: BVH closest hit in one cell + periodic walk
+// --------------------------------------------------------------------------
+struct StackRef {
+    int2* smem;       // [kSmemStack][blockDim]
+    int stride;
+    int tid;
+};
+
+// Slab test of one box (Ize 2013 form: difference first, then the reciprocal,
+// tmax widened by 1 + 2 gamma_3 so the test is conservative).
+__device__ __forceinline__ void slab_box(float lox, float hix, float loy, float hiy, float loz, float hiz,
+                                         const RaySetup& r, float t_best, float& tmin, bool& hit)
+{
+    const float lx = (lox - r.o.x) * r.inv.x, hx = (hix - r.o.x) * r.inv.x;
+    const float ly = (loy - r.o.y) * r.inv.y, hy = (hiy - r.o.y) * r.inv.y;
+    const float lz = (loz - r.o.z) * r.inv.z, hz = (hiz - r.o.z) * r.inv.z;
+    tmin = fmaxf(fmaxf(fminf(lx, hx), fminf(ly, hy)), fmaxf(fminf(lz, hz), 0.f));
+    const float tmax = fminf(fminf(fmaxf(lx, hx), fmaxf(ly, hy)), fminf(fmaxf(lz, hz), t_best));
+    hit = tmin <= tmax * kRobust;
+}
+
+// Fetch node `node` and test its two child boxes; c0/c1 get the child refs
+// (inner node index >= 0 or leaf_ref(first, count) < 0).
+template <int FMT>
+__device__ __forceinline__ void node_children(const void* __restrict__ nodes, int node, const RaySetup& r,
+                                              float t_best, float& tmin0, float& tmin1, bool& h0, bool& h1,
+                                              int& c0, int& c1)
+{
+    if (FMT == FMT_FP32) {
+        const float4* np = reinterpret_cast<const float4*>(nodes) + 4ll * node;
+        const float4 n0 = ldg4(np), n1 = ldg4(np + 1), n2 = ldg4(np + 2), n3 = ldg4(np + 3);
+        slab_box(n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, r, t_best, tmin0, h0);
+        slab_box(n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, r, t_best, tmin1, h1);
+        c0 = __float_as_int(n3.x);
+        c1 = __float_as_int(n3.y);
+    } else {
+        const uint4* np = reinterpret_cast<const uint4*>(nodes) + 2ll * node;
+        const uint4 w0 = __ldg(np), w1 = __ldg(np + 1);
+        const float ox = __uint_as_float(w0.x), oy = __uint_as_float(w0.y), oz = __uint_as_float(w0.z);
+        const unsigned pk = w0.w;
+        const float sx = exp2_int((int)(signed char)(pk & 255u));
+        const float sy = exp2_int((int)(signed char)((pk >> 8) & 255u));
+        const float sz = exp2_int((int)(signed char)((pk >> 16) & 255u));
+        const unsigned meta = pk >> 24;
+        slab_box(fmaf(byte_f(w1.x, 0), sx, ox), fmaf(byte_f(w1.x, 3), sx, ox),
+                 fmaf(byte_f(w1.x, 1), sy, oy), fmaf(byte_f(w1.y, 0), sy, oy),
+                 fmaf(byte_f(w1.x, 2), sz, oz), fmaf(byte_f(w1.y, 1), sz, oz), r, t_best, tmin0, h0);
+        slab_box(fmaf(byte_f(w1.y, 2), sx, ox), fmaf(byte_f(w1.z, 1), sx, ox),
+                 fmaf(byte_f(w1.y, 3), sy, oy), fmaf(byte_f(w1.z, 2), sy, oy),
+                 fmaf(byte_f(w1.z, 0), sz, oz), fmaf(byte_f(w1.z, 3), sz, oz), r, t_best, tmin1, h1);
+        const int g = (int)w1.w;
+        c0 = (meta & 1u) ? leaf_ref(g - (int)((meta >> 1) & 7u), (int)((meta >> 1) & 7u) + 1) : g;
+        c1 = (meta & 16u) ? leaf_ref(g + 1, (int)((meta >> 5) & 7u) + 1) : g + 1;
+    }
+}
+
+struct Counts { unsigned visits = 0, tests = 0; };
+
+// FP64 form of the watertight test on the same (FP32-valued) ray: used to
+// re-test hits the FP32 pass flags as near an edge or grazing.
+struct RaySetup64 {
+    double ox, oy, oz;
+    int kx, ky, kz;
+    double sx, sy, sz;
+};
+
+__device__ __forceinline__ RaySetup64 setup_ray64(float3 o, float3 d)
+{
+    RaySetup64 r;
+    r.ox = o.x; r.oy = o.y; r.oz = o.z;
+    const double dv[3] = {d.x, d.y, d.z};
+    int kz = 0;
+    if (fabs(dv[1]) > fabs(dv[kz])) kz = 1;
+    if (fabs(dv[2]) > fabs(dv[kz])) kz = 2;
+    int kx = kz == 2 ? 0 : kz + 1;
+    int ky = kx == 2 ? 0 : kx + 1;
+    if (dv[kz] < 0.0) { const int t = kx; kx = ky; ky = t; }
+    r.kx = kx; r.ky = ky; r.kz = kz;
+    r.sx = dv[kx] / dv[kz];
+    r.sy = dv[ky] / dv[kz];
+    r.sz = 1.0 / dv[kz];
+    return r;
+}
+
+__device__ __forceinline__ double comp(double x, double y, double z, int k) { return k == 0 ? x : (k == 1 ? y : z); }
+
+__device__ __forceinline__ bool intersect_tri64(const RaySetup64& r, float4 w0, float4 w1, float4 w2, double& t_best,
+                                                int& best_orig, float& bu, float& bv)
+{
+    const double a0 = w0.x - r.ox, a1 = w0.y - r.oy, a2 = w0.z - r.oz;
+    const double b0 = w1.x - r.ox, b1 = w1.y - r.oy, b2 = w1.z - r.oz;
+    const double c0 = w2.x - r.ox, c1 = w2.y - r.oy, c2 = w2.z - r.oz;
+    const double akz = comp(a0, a1, a2, r.kz), bkz = comp(b0, b1, b2, r.kz), ckz = comp(c0, c1, c2, r.kz);
+    const double ax = comp(a0, a1, a2, r.kx) - r.sx * akz, ay = comp(a0, a1, a2, r.ky) - r.sy * akz;
+    const double bx = comp(b0, b1, b2, r.kx) - r.sx * bkz, by = comp(b0, b1, b2, r.ky) - r.sy * bkz;
+    const double cx = comp(c0, c1, c2, r.kx) - r.sx * ckz, cy = comp(c0, c1, c2, r.ky) - r.sy * ckz;
+    const double U = cx * by - cy * bx, V = ax * cy - ay * cx, W = bx * ay - by * ax;
+    if (U < 0.0 || V < 0.0 || W < 0.0) return false;
+    const double det = U + V + W;
+    if (det == 0.0) return false;
+    const double T = U * (r.sz * akz) + V * (r.sz * bkz) + W * (r.sz * ckz);
+    if (T <= 0.0) return false;
+    if (T > t_best * det * (1.0 + 1e-12)) return false;     // cannot beat the best hit (det > 0)
+    const double t = T / det;                               // divisions only for candidates
+    const int orig = __float_as_int(w0.w);
+    if (t < t_best || (t == t_best && orig < best_orig)) {
+        t_best = t;
+        best_orig = orig;
+        const double inv = 1.0 / det;
+        bu = (float)(V * inv);
+        bv = (float)(W * inv);
+        return true;
+    }
+    return false;
+}
+
+// Test the triangles of a leaf ref.
+template <bool COUNT, bool TRI64>
+__device__ __forceinline__ void test_leaf(const float4* __restrict__ tris, const RaySetup& r, const RaySetup64& r64,
+                                          int code, int skip, float& t_best, double& t_best64, int& best,
+                                          int& best_orig, float& bu, float& bv, Counts* cnt)
+{
+    const int v = ~code;
+    const int first = v >> 3, count = (v & 7) + 1;
+    for (int k = 0; k < count; ++k) {
+        const int j = first + k;
+        if (j == skip) continue;
+        if (COUNT) ++cnt->tests;
+        const float4* tp = tris + 3ll * j;
+        if (TRI64) {
+            if (intersect_tri64(r64, ldg4(tp), ldg4(tp + 1), ldg4(tp + 2), t_best64, best_orig, bu, bv)) {
+                best = j;
+                t_best = (float)t_best64;
+            }
+        } else {
+            if (intersect_tri(r, ldg4(tp), ldg4(tp + 1), ldg4(tp + 2), t_best, best_orig, bu, bv)) best = j;
+        }
+    }
+}
+
+// Closest front-facing triangle (leaf order index) with t > 0, skipping
+// `skip`: one ray per lane, leaves tested as soon as their box is hit.
+template <int FMT, bool COUNT = false, bool TRI64 = false>
+__device__ __forceinline__ int bvh_closest(const void* __restrict__ nodes, const float4* __restrict__ tris,
+                                           const RaySetup& r, const RaySetup64& r64, int skip, StackRef st,
+                                           float& t_best, float& bu, float& bv, unsigned& status,
+                                           Counts* cnt = nullptr)
+{
+    int2 lstack[kStackMax - kSmemStack];
+    int sp = 0;
+    int node = 0;
+    int best = -1, best_orig = INT_MAX;
+    double t_best64 = INFINITY;
+    t_best = INFINITY;
+    bu = bv = 0.f;
+    for (int visits = 0;; ++visits) {
+        if (visits >= kMaxVisits) { status |= ST_LOOP_LIMIT; break; }
+        if (COUNT) ++cnt->visits;
+        float tmin0, tmin1;
+        bool h0, h1;
+        int c0, c1;
+        node_children<FMT>(nodes, node, r, t_best, tmin0, tmin1, h0, h1, c0, c1);
+        if (h0 && c0 < 0) {
+            test_leaf<COUNT, TRI64>(tris, r, r64, c0, skip, t_best, t_best64, best, best_orig, bu, bv, cnt);
+            h0 = false;
+        }
+        if (h1 && c1 < 0) {
+            test_leaf<COUNT, TRI64>(tris, r, r64, c1, skip, t_best, t_best64, best, best_orig, bu, bv, cnt);
+            h1 = false;
+        }
+        if (h0 && h1) {
+            int near = c0, far = c1;
+            float tfar = tmin1;
+            if (tmin1 < tmin0) { near = c1; far = c0; tfar = tmin0; }
+            const int2 e = make_int2(far, __float_as_int(tfar));
+            if (sp < kSmemStack) st.smem[sp * st.stride + st.tid] = e;
+            else if (sp < kStackMax) lstack[sp - kSmemStack] = e;
+            else { status |= ST_STACK_OVERFLOW; sp = kStackMax - 1; }
+            ++sp;
+            node = near;
+            continue;
+        }
+        if (h0) { node = c0; continue; }
+        if (h1) { node = c1; continue; }
+        bool found = false;
+        while (sp > 0) {
+            --sp;
+            const int2 e = sp < kSmemStack ? st.smem[sp * st.stride + st.tid] : lstack[sp - kSmemStack];
+            if (__int_as_float(e.y) <= t_best * kRobust) { node = e.x; found = true; break; }
+        }
+        if (!found) break;
+    }
+    if (TRI64 && best >= 0) t_best = (float)t_best64;
+    return best;
+}
+
+struct Cell { float lx, ly, z_min, z_top; int max_wraps; };
+
+// Trace one ray segment by segment through the periodic cell (Section 2.2,
+// last paragraph).  Returns the hit record; *wraps gets the lateral re-entries.
+// The re-entry point is carried in FP64 (a few operations per wrap) so a ray
+// that wraps many times does not accumulate FP32 rounding in its origin; each
+// cell query uses that point rounded to FP32.
+template <int FMT, bool COUNT, bool TRI64>
+__device__ __forceinline__ float4 trace_ray(const void* __restrict__ nodes, const float4* __restrict__ tris,
+                                            const float3 o32, const float3 d, int skip, const Cell& c, StackRef st,
+                                            int& wraps, unsigned& status, Counts* cnt)
+{
+    wraps = 0;
+    double ox = o32.x, oy = o32.y, oz = o32.z;
+    float3 o = o32;
+    for (;;) {
+        const RaySetup rs = setup_ray(o, d);
+        RaySetup64 r64;
+        if (TRI64) r64 = setup_ray64(o, d);
+        float t, u, v;
+        const int j = bvh_closest<FMT, COUNT, TRI64>(nodes, tris, rs, r64, skip, st, t, u, v, status, cnt);
+        if (j >= 0) return make_float4(t, u, v, __int_as_float(j));
+        double tx = INFINITY, ty = INFINITY, tz = INFINITY;
+        if (d.x > 0.f) tx = ((double)c.lx - ox) / d.x; else if (d.x < 0.f) tx = (0.0 - ox) / d.x;
+        if (d.y > 0.f) ty = ((double)c.ly - oy) / d.y; else if (d.y < 0.f) ty = (0.0 - oy) / d.y;
+        if (d.z > 0.f) tz = ((double)c.z_top - oz) / d.z; else if (d.z < 0.f) tz = ((double)c.z_min - oz) / d.z;
+        if (tz < tx && tz < ty)
+            return make_float4((float)tz, 0.f, 0.f, __int_as_float(d.z > 0.f ? HIT_ESCAPE : HIT_LOST));
+        if (++wraps > c.max_wraps) return make_float4((float)fmin(tx, ty), 0.f, 0.f, __int_as_float(HIT_LOST));
+        if (tx <= ty) {
+            oy = oy + tx * d.y;
+            oz = oz + tx * d.z;
+            ox = d.x > 0.f ? 0.0 : (double)c.lx;
+        } else {
+            ox = ox + ty * d.x;
+            oz = oz + ty * d.z;
+            oy = d.y > 0.f ? 0.0 : (double)c.ly;
+        }
+        o = make_float3((float)ox, (float)oy, (float)oz);
+        skip = -1;
+    }
+}
+
+template <int FMT, bool RECORD, bool COUNT>
+__global__ void __launch_bounds__(128)
+k_traverse(const void* __restrict__ nodes, const float4* __restrict__ tris, Cell cell,
+           const float4* __restrict__ oe, const float4* __restrict__ dt, float4* __restrict__ hits,
+           int* __restrict__ wraps_out, Control* __restrict__ ctl, int gen, unsigned cap,
+           Tally* __restrict__ tally)
+{
+    extern __shared__ int2 s_stack[];
+    const StackRef st{s_stack, (int)blockDim.x, (int)threadIdx.x};
+    const unsigned n = min(*((volatile unsigned*)&ctl->count[gen]), cap);
+    const int lane = threadIdx.x & 31;
+    unsigned long long my_wraps = 0;
+    unsigned status = 0;
+    Counts cnt;
+    for (;;) {
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(&ctl->next[gen], 32u);
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        if (base >= n) break;
+        const unsigned i = base + lane;
+        if (i < n) {
+            const float4 a = oe[i], b = dt[i];
+            int w;
+            const float4 h = trace_ray<FMT, COUNT, false>(nodes, tris, make_float3(a.x, a.y, a.z),
+                                                          make_float3(b.x, b.y, b.z), __float_as_int(b.w), cell,
+                                                          st, w, status, &cnt);
+            hits[i] = h;
+            my_wraps += (unsigned)w;
+            if (RECORD) wraps_out[i] = w;
+        }
+    }
+    for (int off = 16; off; off >>= 1) {
+        my_wraps += __shfl_xor_sync(0xFFFFFFFFu, my_wraps, off);
+        status |= __shfl_xor_sync(0xFFFFFFFFu, status, off);
+    }
+    if (COUNT) {
+        unsigned long long v = cnt.visits, t = cnt.tests;
+        for (int off = 16; off; off >>= 1) {
+            v += __shfl_xor_sync(0xFFFFFFFFu, v, off);
+            t += __shfl_xor_sync(0xFFFFFFFFu, t, off);
+        }
+        if (lane == 0) { atomicAdd(&tally->node_visits, v); atomicAdd(&tally->tri_tests, t); }
+    }
+    if (lane == 0) {
+        if (my_wraps) atomicAdd(&tally->wraps, my_wraps);
+        if (status) atomicOr(&tally->status, (unsigned long long)status);
+    }
+}
+
+// --------------------------------------------------------------------------
+// traverse, while-while form (Aila & Laine, HPG 2009): inner nodes and leaf
+// triangles run in separate loops so the lanes of a warp stay in the same
+// phase; the first leaf a lane meets is postponed until every active lane
+// has one.  A lane whose ray finishes takes a new ray from the generation's
+// queue (one atomic per warp refill) instead of idling until the whole tile
+// is done.  The FP64 re-entry point of each lane lives in shared memory.
+// With RETEST, hits closer than kEdgeEps (barycentric) to an edge or with
+// cos(incidence) below kGrazeCos are listed for the FP64 re-test kernel.
+// --------------------------------------------------------------------------
+constexpr int kEntrySentinel = 0x76543210;   // "stack empty" (never a node index)
+constexpr int kFetchThreshold = 20;          // default: refill when fewer lanes than this are active
+constexpr float kEdgeEps = 1e-5f;
+constexpr float kGrazeCos = 1e-3f;
+
+template <int FMT, bool RECORD, bool COUNT, bool RETEST, int SSTACK>
+__global__ void __launch_bounds__(128)
+k_traverse_ww(const void* __restrict__ nodes, const float4* __restrict__ tris, const float4* __restrict__ normals,
+              Cell cell, const float4* __restrict__ oe, const float4* __restrict__ dt, float4* __restrict__ hits,
+              int* __restrict__ wraps_out, Control* __restrict__ ctl, int gen, unsigned cap,
+              unsigned* __restrict__ retest_list, Tally* __restrict__ tally, int fetch_threshold)
+{
+    extern __shared__ int2 s_stack[];                                   // [SSTACK][blockDim]
+    const int B = blockDim.x, tid = threadIdx.x, lane = tid & 31;
+    double* s_o = reinterpret_cast<double*>(s_stack + SSTACK * B);       // [3][blockDim]
+    const unsigned lt = (1u << lane) - 1u;
+    const unsigned n = min(*((volatile unsigned*)&ctl->count[gen]), cap);
+    int2 lstack[kStackMax - SSTACK];
+
+    int ray = -1;
+    bool exhausted = false, drained = false;
+    float3 o = make_float3(0.f, 0.f, 0.f), d = make_float3(0.f, 0.f, 1.f);
+    RaySetup rs = setup_ray(o, d);
+    RaySetup64 r64;
+    float t_best = INFINITY, bu = 0.f, bv = 0.f;
+    double t_best64 = INFINITY;
+    int best = -1, best_orig = INT_MAX, node = kEntrySentinel, leaf = 0, sp = 0, skip = -1, wraps = 0, visits = 0;
+    unsigned status = 0;
+    unsigned long long my_wraps = 0;
+    Counts cnt;
+
+    auto push = [&](int node_ref, float tmin) {
+        const int2 e = make_int2(node_ref, __float_as_int(tmin));
+        if (sp < SSTACK) s_stack[sp * B + tid] = e;
+        else if (sp < kStackMax) lstack[sp - SSTACK] = e;
+        else { status |= ST_STACK_OVERFLOW; sp = kStackMax - 1; }
+        ++sp;
+    };
+    auto pop = [&]() -> int {
+        while (sp > 0) {
+            --sp;
+            const int2 e = sp < SSTACK ? s_stack[sp * B + tid] : lstack[sp - SSTACK];
+            if (__int_as_float(e.y) <= t_best * kRobust) return e.x;
+        }
+        return kEntrySentinel;
+    };
+    auto restart = [&]() {      // new cell traversal from the current origin
+        rs = setup_ray(o, d);
+        node = 0; leaf = 0; sp = 0; visits = 0;
+        t_best = INFINITY; best = -1; best_orig = INT_MAX; bu = bv = 0.f;
+    };
+
+    for (;;) {
+        const bool need = ray < 0 && !exhausted;
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, need);
+        if (m) {
+            const int leader = __ffs(m) - 1;
+            unsigned base = 0;
+            if (lane == leader) base = atomicAdd(&ctl->next[gen], (unsigned)__popc(m));
+            base = __shfl_sync(0xFFFFFFFFu, base, leader);
+            if (base + (unsigned)__popc(m) >= n) drained = true;
+            if (need) {
+                const unsigned idx = base + __popc(m & lt);
+                if (idx < n) {
+                    ray = (int)idx;
+                    const float4 a = oe[idx], b = dt[idx];
+                    o = make_float3(a.x, a.y, a.z);
+                    d = make_float3(b.x, b.y, b.z);
+                    skip = __float_as_int(b.w);
+                    s_o[tid] = a.x; s_o[B + tid] = a.y; s_o[2 * B + tid] = a.z;
+                    wraps = 0;
+                    restart();
+                } else {
+                    exhausted = true;
+                }
+            }
+        }
+        if (__all_sync(0xFFFFFFFFu, ray < 0)) break;
+        if (ray < 0) continue;
+
+        bool cell_done = false;
+        for (;;) {
+            while (node >= 0 && node != kEntrySentinel) {
+                if (++visits > kMaxVisits) { status |= ST_LOOP_LIMIT; node = kEntrySentinel; leaf = 0; sp = 0; break; }
+                if (COUNT) ++cnt.visits;
+                float tmin0, tmin1;
+                bool h0, h1;
+                int c0, c1;
+                node_children<FMT>(nodes, node, rs, t_best, tmin0, tmin1, h0, h1, c0, c1);
+                if (h0 && h1) {
+                    const bool first0 = tmin0 <= tmin1;
+                    push(first0 ? c1 : c0, first0 ? tmin1 : tmin0);
+                    node = first0 ? c0 : c1;
+                } else if (h0 || h1) {
+                    node = h0 ? c0 : c1;
+                } else {
+                    node = pop();
+                }
+                if (node < 0 && leaf == 0) { leaf = node; node = pop(); }
+                if (!__any_sync(__activemask(), leaf == 0)) break;
+            }
+            while (leaf < 0) {
+                test_leaf<COUNT, false>(tris, rs, r64, leaf, skip, t_best, t_best64, best, best_orig, bu, bv, &cnt);
+                leaf = 0;
+                if (node < 0) { leaf = node; node = pop(); }
+            }
+            if (node == kEntrySentinel) { cell_done = true; break; }
+            if (!drained && __popc(__activemask()) < fetch_threshold) break;
+        }
+        if (!cell_done) continue;
+
+        if (best >= 0) {
+            hits[ray] = make_float4(t_best, bu, bv, __int_as_float(best));
+            if (RETEST) {
+                bool flag = fminf(fminf(bu, bv), 1.f - bu - bv) < kEdgeEps;
+                if (!flag) {
+                    const float4 nr = ldg4(normals + best);
+                    flag = -(d.x * nr.x + d.y * nr.y + d.z * nr.z) < kGrazeCos;
+                }
+                if (flag) {
+                    const unsigned slot = atomicAdd(&ctl->n_retest[gen], 1u);
+                    if (slot < cap) retest_list[slot] = (unsigned)ray;
+                }
+            }
+        } else {
+            // no facet in this cell: leave through a face (FP64 re-entry point)
+            double ox = s_o[tid], oy = s_o[B + tid], oz = s_o[2 * B + tid];
+            double tx = INFINITY, ty = INFINITY, tz = INFINITY;
+            if (d.x > 0.f) tx = ((double)cell.lx - ox) / d.x; else if (d.x < 0.f) tx = (0.0 - ox) / d.x;
+            if (d.y > 0.f) ty = ((double)cell.ly - oy) / d.y; else if (d.y < 0.f) ty = (0.0 - oy) / d.y;
+            if (d.z > 0.f) tz = ((double)cell.z_top - oz) / d.z; else if (d.z < 0.f) tz = ((double)cell.z_min - oz) / d.z;
+            int code = 0;
+            float tout = 0.f;
+            if (tz < tx && tz < ty) {
+                code = d.z > 0.f ? HIT_ESCAPE : HIT_LOST;
+                tout = (float)tz;
+            } else if (++wraps > cell.max_wraps) {
+                code = HIT_LOST;
+                tout = (float)fmin(tx, ty);
+            }
+            if (code) {
+                hits[ray] = make_float4(tout, 0.f, 0.f, __int_as_float(code));
+            } else {
+                if (tx <= ty) {
+                    oy = oy + tx * d.y; oz = oz + tx * d.z; ox = d.x > 0.f ? 0.0 : (double)cell.lx;
+                } else {
+                    ox = ox + ty * d.x; oz = oz + ty * d.z; oy = d.y > 0.f ? 0.0 : (double)cell.ly;
+                }
+                s_o[tid] = ox; s_o[B + tid] = oy; s_o[2 * B + tid] = oz;
+                o = make_float3((float)ox, (float)oy, (float)oz);
+                skip = -1;
+                restart();
+                continue;
+            }
+        }
+        my_wraps += (unsigned)wraps;
+        if (RECORD) wraps_out[ray] = wraps;
+        ray = -1;
+    }
+    for (int off = 16; off; off >>= 1) {
+        my_wraps += __shfl_xor_sync(0xFFFFFFFFu, my_wraps, off);
+        status |= __shfl_xor_sync(0xFFFFFFFFu, status, off);
+    }
+    if (COUNT) {
+        unsigned long long v = cnt.visits, t = cnt.tests;
+        for (int off = 16; off; off >>= 1) {
+            v += __shfl_xor_sync(0xFFFFFFFFu, v, off);
+            t += __shfl_xor_sync(0xFFFFFFFFu, t, off);
+        }
+        if (lane == 0) { atomicAdd(&tally->node_visits, v); atomicAdd(&tally->tri_tests, t); }
+    }
+    if (lane == 0) {
+        if (my_wraps) atomicAdd(&tally->wraps, my_wraps);
+        if (status) atomicOr(&tally->status, (unsigned long long)status);
+    }
+}
+
+// FP64 re-test of the flagged rays of one generation: the whole ray is traced
+// again (same FP32 ray, same FP32 boxes, triangle tests in FP64) and its hit
+// record (and wrap count) replaced.
+template <int FMT, bool RECORD>
+__global__ void __launch_bounds__(128)
+k_retest(const void* __restrict__ nodes, const float4* __restrict__ tris, Cell cell, const float4* __restrict__ oe,
+         const float4* __restrict__ dt, float4* __restrict__ hits, int* __restrict__ wraps_out,
+         Control* __restrict__ ctl, int gen, unsigned cap, const unsigned* __restrict__ retest_list,
+         Tally* __restrict__ tally)
+{
+    extern __shared__ int2 s_stack[];
+    const StackRef st{s_stack, (int)blockDim.x, (int)threadIdx.x};
+    const unsigned n = min(*((volatile unsigned*)&ctl->n_retest[gen]), cap);
+    unsigned status = 0;
+    long long wdelta = 0;
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const unsigned i = retest_list[k];
+        const float4 a = oe[i], b = dt[i];
+        int w;
+        const float4 h = trace_ray<FMT, false, true>(nodes, tris, make_float3(a.x, a.y, a.z),
+                                                     make_float3(b.x, b.y, b.z), __float_as_int(b.w), cell, st, w,
+                                                     status, nullptr);
+        hits[i] = h;
+        if (RECORD) {
+            wdelta += (long long)w - (long long)wraps_out[i];
+            wraps_out[i] = w;
+        }
+    }
+    if (status) atomicOr(&tally->status, (unsigned long long)status);
+    if (RECORD && wdelta) atomicAdd(&tally->wraps, (unsigned long long)wdelta);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && n) atomicAdd(&tally->retested, (unsigned long long)n);
+}
+
+template <int FMT>
+__global__ void __launch_bounds__(128)
+k_trace_rays(const void* __restrict__ nodes, const float4* __restrict__ tris, const int* __restrict__ inv_order,
+             int n_tri, const float* __restrict__ o, const float* __restrict__ d, const int* __restrict__ skip,
+             int64_t n, rtmc_hit* __restrict__ hits, unsigned* __restrict__ status_out)
+{
+    extern __shared__ int2 s_stack[];
+    const StackRef st{s_stack, (int)blockDim.x, (int)threadIdx.x};
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float3 oo = make_float3(o[3 * i], o[3 * i + 1], o[3 * i + 2]);
+    const float3 dd = make_float3(d[3 * i], d[3 * i + 1], d[3 * i + 2]);
+    const int sk = (skip && skip[i] >= 0 && skip[i] < n_tri) ? inv_order[skip[i]] : -1;
+    unsigned status = 0;
+    float t, u, v;
+    RaySetup64 r64;
+    const int j = bvh_closest<FMT>(nodes, tris, setup_ray(oo, dd), r64, sk, st, t, u, v, status);
+    rtmc_hit h;
+    h.t = t; h.u = u; h.v = v;
+    h.tri = j >= 0 ? __float_as_int(__ldg(tris + 3ll * j).w) : -1;
+    hits[i] = h;
+    if (status) atomicOr(status_out, status);
+}
+
+}  // namespace
+
+template <int F, bool R, bool C, int SS>
+static cudaError_t ww_launch(const DeviceMesh& m, const Cell& cell, const Queues& q, int buf, int gen, int num_sms,
+                             const Tuning& tune, bool retest, const void* nodes, cudaStream_t s)
+{
+    const int bt = tune.block_threads;
+    int per_sm = tune.blocks_per_sm;
+    const int thr = tune.fetch_threshold > 0 ? tune.fetch_threshold : kFetchThreshold;
+    const size_t smem = (size_t)SS * bt * sizeof(int2) + 3 * (size_t)bt * sizeof(double);
+    if (retest) {
+        if (per_sm <= 0)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse_ww<F, R, C, true, SS>, bt, smem);
+        k_traverse_ww<F, R, C, true, SS><<<num_sms * (per_sm > 0 ? per_sm : 1), bt, smem, s>>>(
+            nodes, m.tris, m.normals, cell, q.oe[buf], q.dt[buf], q.hits, R ? q.wraps : nullptr, q.ctl, gen,
+            q.cap[buf], q.retest, q.tally, thr);
+    } else {
+        if (per_sm <= 0)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse_ww<F, R, C, false, SS>, bt, smem);
+        k_traverse_ww<F, R, C, false, SS><<<num_sms * (per_sm > 0 ? per_sm : 1), bt, smem, s>>>(
+            nodes, m.tris, m.normals, cell, q.oe[buf], q.dt[buf], q.hits, R ? q.wraps : nullptr, q.ctl, gen,
+            q.cap[buf], nullptr, q.tally, thr);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && retest) {
+        const int tb = 64;
+        const size_t rs = (size_t)kSmemStack * tb * sizeof(int2);
+        k_retest<F, R><<<num_sms, tb, rs, s>>>(nodes, m.tris, cell, q.oe[buf], q.dt[buf], q.hits,
+                                               R ? q.wraps : nullptr, q.ctl, gen, q.cap[buf], q.retest, q.tally);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+template <int F, bool R, bool C>
+static cudaError_t traverse_t(const DeviceMesh& m, const RunParams& p, const Queues& q, int buf, int gen,
+                              int num_sms, const Tuning& tune, bool retest, cudaStream_t s)
+{
+    const Cell cell{p.lx, p.ly, p.z_min, p.z_top, p.max_wraps};
+    const void* nodes = F == FMT_Q8 ? m.q8 : (const void*)m.nodes;
+    const int bt = tune.block_threads;
+    int per_sm = tune.blocks_per_sm;
+    if (tune.traversal == 1) {
+        const size_t smem = (size_t)kSmemStack * bt * sizeof(int2);
+        if (per_sm <= 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse<F, R, C>, bt, smem);
+        k_traverse<F, R, C><<<num_sms * (per_sm > 0 ? per_sm : 1), bt, smem, s>>>(
+            nodes, m.tris, cell, q.oe[buf], q.dt[buf], q.hits, R ? q.wraps : nullptr, q.ctl, gen, q.cap[buf],
+            q.tally);
+    } else {
+        const int depth = tune.stack_depth;
+        if (C || depth == 16) return ww_launch<F, R, C, 16>(m, cell, q, buf, gen, num_sms, tune, retest, nodes, s);
+        if (depth == 8) return ww_launch<F, R, false, 8>(m, cell, q, buf, gen, num_sms, tune, retest, nodes, s);
+        return ww_launch<F, R, false, 32>(m, cell, q, buf, gen, num_sms, tune, retest, nodes, s);
+    }
+    return cudaGetLastError();
+}
+
+template <int F>
+static cudaError_t traverse_f(const DeviceMesh& m, const RunParams& p, const Queues& q, int buf, int gen,
+                              int num_sms, const Tuning& tune, bool record, bool count, bool retest, cudaStream_t s)
+{
+    if (record) return count ? traverse_t<F, true, true>(m, p, q, buf, gen, num_sms, tune, retest, s)
+                             : traverse_t<F, true, false>(m, p, q, buf, gen, num_sms, tune, retest, s);
+    return count ? traverse_t<F, false, true>(m, p, q, buf, gen, num_sms, tune, retest, s)
+                 : traverse_t<F, false, false>(m, p, q, buf, gen, num_sms, tune, retest, s);
+}
+
+cudaError_t launch_traverse(const DeviceMesh& m, const RunParams& p, const Queues& q, int buf, int gen,
+                            int num_sms, const Tuning& tune, bool record, bool count, bool retest, cudaStream_t s)
+{
+    if (m.kind == FMT_Q8) return traverse_f<FMT_Q8>(m, p, q, buf, gen, num_sms, tune, record, count, retest, s);
+    return traverse_f<FMT_FP32>(m, p, q, buf, gen, num_sms, tune, record, count, retest, s);
+}
+
+cudaError_t launch_trace_rays(const DeviceMesh& m, const float* o, const float* d, const int* skip, int64_t n,
+                              rtmc_hit* hits, unsigned* status, cudaStream_t s)
+{
+    const int tb = 128;
+    const size_t smem = (size_t)kSmemStack * tb * sizeof(int2);
+    const int64_t gb = (n + tb - 1) / tb;
+    if (gb > 0 && m.kind == FMT_Q8)
+        k_trace_rays<FMT_Q8><<<(unsigned)gb, tb, smem, s>>>(m.q8, m.tris, m.inv_order, (int)m.n_tri, o, d, skip, n,
+                                                            hits, status);
+    else if (gb > 0)
+        k_trace_rays<FMT_FP32><<<(unsigned)gb, tb, smem, s>>>(m.nodes, m.tris, m.inv_order, (int)m.n_tri, o, d, skip,
+                                                              n, hits, status);
+    return cudaGetLastError();
+}
+
+}  // namespace rtmc

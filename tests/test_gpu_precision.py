@@ -123,3 +123,38 @@ def test_precision_config_sey_vs_plain_and_oracle(ctx):
         assert np.sum(dev != primary_hashes(o["records"], ids)) <= 1
         ctx.unload_mesh(m32)
         ctx.unload_mesh(mq)
+
+
+def test_large_config_tertiaries_sampled(ctx):
+    """Large config: 256^3 foam at porosity 0.7 (~8M triangles, Q8 BVH), tertiaries above
+    20 eV, 1e8 primaries at 500 eV x 9 angles, 128 / 36 bins -- the launch configuration of
+    `bench.py --config large`.  Invariants at full size; sampled primaries vs the oracle."""
+    import torch
+    from paper_1806_00205_gb300 import rtmc
+    mesh = I.grf_foam(256, 0.7)
+    assert 6e6 < mesh.n_tri < 1.2e7
+    em = rtmc.Emission(regen_min_ev=20.0, max_generation=2)
+    c2 = rtmc.Context(0)
+    try:
+        c2.load_see_tables(TABLE, em)
+        mid = c2.load_mesh(mesh.tri, mesh.box)
+        c2.build_bvh(mid, kind=rtmc.BVH_Q8)
+        n = 100_000_000
+        thetas = [10.0 * j for j in range(9)]
+        res, he, ha = c2.run(mid, [500.0], thetas, n, 1806, desc=rtmc.run_desc(n_ebins=128, n_abins=36))
+        assert he.shape == (9, 128) and ha.shape == (9, 36)
+        for r, h in zip(res, he):
+            assert r["rays"] == n + r["emitted"]
+            assert r["rays"] == r["escaped"] + r["absorbed_low"] + r["absorbed_other"] + r["emitters"] + r["lost"]
+            assert r["regenerated"] > 0 and r["lost"] <= 1e-6 * r["rays"]
+            assert int(h.sum()) == r["escaped"]
+        h = torch.zeros(n, dtype=torch.int64, device="cuda")
+        one, _, _ = c2.run(mid, [500.0], [40.0], n, 1806,
+                           desc=rtmc.run_desc(n_ebins=128, n_abins=36, prim_hash=h))
+        ids = np.sort(np.random.default_rng(8).choice(n, 40, replace=False)).astype(np.uint64)
+        o = O.run(mesh, TABLE, 500.0, 40.0, 0, seed=1806, prim_ids=ids, records=True, n_ebins=128, n_abins=36,
+                  emission=O.Emission(regen_min_ev=20.0, max_generation=2))
+        dev = h.cpu().numpy().view(np.uint64)[ids.astype(np.int64)]
+        assert np.sum(dev != primary_hashes(o["records"], ids)) <= 1
+    finally:
+        c2.close()
