@@ -305,7 +305,7 @@ def run_large(args):
 def run_ours(args):
     import torch
     import torch.distributed as dist
-    from paper_1806_00205_gb300 import autotune, rtmc
+    from paper_1806_00205_gb300 import autotune, rtmc, shard
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -323,7 +323,7 @@ def run_ours(args):
     ctx.load_see_tables(table)
     mid = ctx.load_mesh(mesh.tri, mesh.box)
     ctx.build_bvh(mid)
-    offset = rank * n_prim * len(energies)      # weak scaling: each rank its own primary ids
+    offset = shard.primary_offset(rank, n_prim)   # weak scaling: each rank its own primary ids
     if args.no_autotune:
         tuned = {}
     else:
