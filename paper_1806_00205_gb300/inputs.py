@@ -379,3 +379,40 @@ def batched_foams(n_foams: int = 16, p_lo: float = 0.30, p_hi: float = 0.90, g_l
     rng = np.random.Generator(np.random.Philox(seed))
     grids = grids[rng.permutation(n_foams)]
     return [(int(g), float(p), int(seed + k)) for k, (g, p) in enumerate(zip(grids, por))]
+
+
+def gibson_ashby_cage(v_f: float, cell: float = 1000.0, C: float = 28.0, res: int = 128) -> Mesh:
+    """Cubic open-cell cage on a flat substrate (the verification geometry of Section 3.1).
+
+    Ligament thickness t from the Gibson-Ashby relation v_f = C (t/l)^2 with the
+    paper's C = 28 and l = `cell` (nm).  The periodic cell (l x l, periodic in x
+    and y) holds square-section ligaments of side t centred on the cube edges:
+    a vertical ligament on the cell corner, and two horizontal ligaments (along
+    x and along y) on the top edges at z = l; the bottom edges lie in the solid
+    substrate (z < 0).  The solid is meshed by the periodic marching cubes on a
+    `res` samples-per-cell grid of the field max(substrate, ligaments), each
+    term the signed Chebyshev distance to a ligament's surface.
+    """
+    l = float(cell)
+    t = l * math.sqrt(v_f / C)
+    h = l / res
+    n_below, n_above = 2, int(math.ceil((0.5 * t) / h)) + 3
+    nz = n_below + res + n_above
+    x = np.arange(res) * h
+    z = (np.arange(nz) - n_below + 0.5) * h            # half-voxel shift: no sample on z = 0
+    dx = np.minimum(x, l - x)                            # periodic distance to the corner line x = 0
+    X = dx[:, None, None]
+    Y = dx[None, :, None]
+    Z = z[None, None, :]
+    f_sub = -Z + 0.0 * X + 0.0 * Y
+    f_vert = np.minimum(0.5 * t - np.maximum(X, Y), l + 0.5 * t - Z)
+    f_top_x = 0.5 * t - np.maximum(Y, np.abs(Z - l)) + 0.0 * X
+    f_top_y = 0.5 * t - np.maximum(X, np.abs(Z - l)) + 0.0 * Y
+    f = np.maximum(np.maximum(f_sub, f_vert), np.maximum(f_top_x, f_top_y))
+    thr = 1e-7 * h                                      # no sample exactly on the surface
+    tri = marching_cubes_periodic(f, thr, h, frac_clamp=1e-4)
+    tri[..., 2] += np.float32(z[0])
+    box = Box(l, l, float(z[0]), float(z[-1]))
+    m = Mesh(np.ascontiguousarray(tri), box, name=f"cage_vf{v_f:g}_l{l:g}")
+    m.porosity = 1.0 - (3 * (t / l) ** 2 - 2 * (t / l) ** 3)   # solid fraction of the ligament frame
+    return m

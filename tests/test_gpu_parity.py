@@ -306,3 +306,18 @@ def test_paper_scale_sampled_parity(ctx, paper):
     assert np.sum(dev != want) <= 1, np.sum(dev != want)
     # the sampled SEY agrees with the full-size GPU SEY within the sample's error
     assert abs(o["sey"] - r["sey"]) < 3 * math.hypot(o["sey_se"], r["sey_se"])
+
+
+def test_gibson_ashby_cage_records_match_oracle(ctx):
+    """Open-cell cage of Section 3.1 (v_f = 4 %, C = 28) on a substrate, 600 eV, normal incidence."""
+    mesh = I.gibson_ashby_cage(0.04)
+    mid = _mesh_id(ctx, mesh)
+    n = 30_000
+    g = ctx.run_records(mid, 600.0, 0.0, n, seed=13)
+    o = O.run(mesh, TABLE, 600.0, 0.0, n, seed=13, records=True)
+    st = compare_records(g["records"], o["records"])
+    assert st["frac_same"] >= 0.9999, {k: v for k, v in st.items() if k != "mismatch"}
+    assert g["lost"] == 0 and g["rays"] == n + g["emitted"]
+    # most primaries reach the substrate through the open cage, so the yield is near the flat value
+    flat = float(I.lin_joy_delta(600.0, 0.0))
+    assert 0.6 * flat < g["sey"] < 1.05 * flat

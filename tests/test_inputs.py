@@ -88,3 +88,20 @@ def test_grf_is_seeded():
     b = I.grf_field(8, 2.0, 5)
     c = I.grf_field(8, 2.0, 6)
     assert np.array_equal(a, b) and not np.array_equal(a, c)
+
+
+@pytest.mark.parametrize("v_f", [0.01, 0.04])
+def test_gibson_ashby_cage(v_f):
+    m = I.gibson_ashby_cage(v_f, res=96)
+    assert _is_closed(m)
+    t = 1000.0 * math.sqrt(v_f / 28.0)           # v_f = C (t/l)^2, C = 28 (Section 3.1)
+    # the vertical ligament's cross-section at mid height spans t (up to a voxel)
+    mid = m.tri[(np.abs(m.tri[..., 2] - 500.0) < 30.0).all(axis=1)]
+    xs = mid[..., 0].ravel()
+    near = np.minimum(xs, 1000.0 - xs)
+    assert abs(2 * near.max() - t) < 2 * 1000.0 / 96
+    # normals of the substrate point up, the top plane is above everything
+    flat = m.tri[(np.abs(m.tri[..., 2]) < 1e-3).all(axis=1)]
+    n = np.cross(flat[:, 1] - flat[:, 0], flat[:, 2] - flat[:, 0])
+    assert np.all(n[:, 2] > 0)
+    assert m.tri[..., 2].max() < m.box.z_top
