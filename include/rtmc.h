@@ -67,13 +67,26 @@ typedef struct {
 } rtmc_grid;
 
 /* Secondary emission (Section 2.2).  A primary always emits at its first hit;
-   a daughter of generation g re-emits when g < max_generation and
-   E >= regen_min_ev, else it is absorbed (absorbed_low below absorb_min_ev).
-   Daughter energies follow E/(E+phi)^4 on [0, e_cut_ev]; counts are
-   Poisson(delta) capped at k_max (<= 15). */
+   a daughter of generation g re-emits when g < max_generation (<= 6, the
+   depth a 32-bit ray path holds) and E >= regen_min_ev, else it is absorbed
+   (absorbed_low below absorb_min_ev).  Counts are capped at k_max (<= 15).
+   model RTMC_EMISSION_TABLE: count ~ Poisson(delta(E, alpha)) from the
+     loaded table; daughter energies follow E/(E+phi)^4 on [0, e_cut_ev];
+     directions cosine-law about the facet normal.
+   model RTMC_EMISSION_PAPER_FIT: the paper's own rules -- the yield gamma of
+     Eq. 6 (alpha in degrees) rounded stochastically (floor(gamma) + 1 with
+     probability gamma - floor(gamma)); the energy E_SEE of Eq. 7; daughters
+     in pairs sharing xi, the first with E_SEE sqrt(xi) at polar angle
+     asin(sqrt(xi)), the second with (1 - xi) E_SEE at pi/2 minus that angle;
+     an unpaired daughter with E_SEE at a cosine-law angle; uniform azimuths.
+     regen_min_ev plays E_c = phi + E_F.  The table is still loaded (its
+     grid is validated) but not read; phi_ev and e_cut_ev are unused. */
+#define RTMC_EMISSION_TABLE 0
+#define RTMC_EMISSION_PAPER_FIT 1
 typedef struct {
     double phi_ev, e_cut_ev, absorb_min_ev, regen_min_ev;
     int32_t max_generation, k_max;
+    int32_t model;                 /* RTMC_EMISSION_TABLE or RTMC_EMISSION_PAPER_FIT */
 } rtmc_emission;
 
 typedef struct {
@@ -99,6 +112,12 @@ typedef struct {
     int32_t no_graph;              /* rtmc_run_batch: 1 = launch eagerly, no CUDA graph */
     int32_t stack_depth;           /* shared-memory traversal stack entries: 8, 16 or 32 (0 -> 16) */
     int32_t fetch_threshold;       /* warp refills rays when fewer lanes than this are busy (0 -> 20) */
+    int32_t random_polar;          /* 1: random incidence -- polar angle from the cosine law
+                                      (sin^2 theta = u of a second Philox block, path 0) and
+                                      uniform azimuth; the item angle is ignored */
+    int32_t n_zbins;               /* penetration-depth bins over [0, z_top - z_min] below
+                                      z_top: every ray whose flight ends on a facet (0: off) */
+    uint64_t* hist_z;              /* host [n_items][n_zbins] when n_zbins > 0 */
     int32_t id_order;              /* 1: queue primaries in id order; 0: order them by a
                                       Morton-ordered 128 x 128 grid of entry points
                                       (coherent traversal; results do not depend on order) */
@@ -165,7 +184,11 @@ int rtmc_build_bvh(rtmc_ctx* ctx, int32_t mesh_id, int32_t bvh_kind);
    ie * n_theta + it.  Each item traces n_primaries primaries with seed `seed`
    (Philox4x32-10 streams keyed by seed and indexed by primary id, ray path and
    item).  Writes out[n_e * n_theta] and, when non-NULL, hist_e[item][n_ebins]
-   and hist_a[item][n_abins] (host memory).  desc may be NULL (defaults). */
+   and hist_a[item][n_abins] (host memory); with desc->n_zbins > 0 also
+   desc->hist_z[item][n_zbins], the penetration profile of Section 3.2: the
+   depth z_top - z of every point where a ray's flight ends on a facet (any
+   generation, re-emitting or absorbed), in n_zbins equal bins over
+   [0, z_top - z_min], clamped.  desc may be NULL (defaults). */
 int rtmc_run(rtmc_ctx* ctx, int32_t mesh_id, const double* energies_ev, int32_t n_e,
              const double* theta_deg, int32_t n_theta, int64_t n_primaries, uint64_t seed,
              const rtmc_run_desc* desc, rtmc_result* out, uint64_t* hist_e, uint64_t* hist_a);
@@ -178,7 +201,8 @@ int rtmc_run(rtmc_ctx* ctx, int32_t mesh_id, const double* energies_ev, int32_t 
    batch shape (desc->no_graph = 1 launches eagerly instead).  Item k uses the
    same random streams as rtmc_run with item_base = k, so its tallies are
    identical to that run's.  Requires max_generation == 1.  Writes
-   out[n_items]; hist_e / hist_a as in rtmc_run.  gpu_ms of every result is
+   out[n_items]; hist_e / hist_a / desc->hist_z as in rtmc_run, with
+   n_ebins + n_abins + n_zbins <= 512.  gpu_ms of every result is
    the device time of the whole batch, and node_visits / tri_tests / retested
    are batch totals (the traversal does not tell items apart); launches counts
    the batch's kernels; with no_graph and profile the ms_* fields hold the
@@ -247,7 +271,7 @@ int rtmc_philox(rtmc_ctx* ctx, const uint32_t* ctr, int64_t n, uint64_t key, uin
      n_primaries <= RTMC_NOALLOC_MAX_PRIMARIES per call (advance
        desc->primary_offset and call again for more primaries);
      the loaded emission parameters must have max_generation == 1;
-     n_ebins + n_abins <= 1024.
+     n_ebins + n_abins + n_zbins <= 1024.
    desc->profile is ignored; desc->prim_hash (device, n_primaries entries)
    and desc->count_visits work as in rtmc_run.
    The first call on a device looks up the array's device address
@@ -256,7 +280,8 @@ int rtmc_philox(rtmc_ctx* ctx, const uint32_t* ctr, int64_t n, uint64_t key, uin
    clears the counters it needs before it starts; calls whose GPU work
    overlaps (other host threads, other contexts or streams on the same
    device) race on the array and must be serialised by the caller.
-   Writes *out and, when non-NULL, hist_e[n_ebins] / hist_a[n_abins] (host). */
+   Writes *out and, when non-NULL, hist_e[n_ebins] / hist_a[n_abins] (host),
+   and desc->hist_z[n_zbins] when n_zbins > 0. */
 #define RTMC_NOALLOC_MAX_PRIMARIES 4096
 int rtmc_run_noalloc(rtmc_ctx* ctx, int32_t mesh_id, double energy_ev, double theta_deg,
                      uint32_t item, int64_t n_primaries, uint64_t seed,

@@ -26,7 +26,8 @@ class OrcPhysics(C.Structure):
     _fields_ = [("delta", C.POINTER(C.c_float)), ("n_e", C.c_int32), ("n_theta", C.c_int32),
                 ("e_lo_ev", C.c_double), ("e_hi_ev", C.c_double), ("theta_step_deg", C.c_double),
                 ("phi_ev", C.c_double), ("e_cut_ev", C.c_double), ("absorb_min_ev", C.c_double),
-                ("regen_min_ev", C.c_double), ("max_generation", C.c_int32), ("k_max", C.c_int32)]
+                ("regen_min_ev", C.c_double), ("max_generation", C.c_int32), ("k_max", C.c_int32),
+                ("model", C.c_int32)]
 
 
 class OrcRun(C.Structure):
@@ -35,7 +36,8 @@ class OrcRun(C.Structure):
                 ("primary_offset", C.c_uint64), ("prim_ids", C.POINTER(C.c_uint64)),
                 ("src_x0", C.c_double), ("src_x1", C.c_double), ("src_y0", C.c_double),
                 ("src_y1", C.c_double), ("n_ebins", C.c_int32), ("n_abins", C.c_int32),
-                ("hist_e_max_ev", C.c_double), ("max_wraps", C.c_int32), ("n_threads", C.c_int32)]
+                ("hist_e_max_ev", C.c_double), ("max_wraps", C.c_int32), ("n_threads", C.c_int32),
+                ("random_polar", C.c_int32), ("n_zbins", C.c_int32)]
 
 
 class OrcResult(C.Structure):
@@ -62,7 +64,7 @@ def lib():
         L.orc_run_rtmc.restype = C.c_int
         L.orc_run_rtmc.argtypes = [C.c_void_p, C.c_int64, C.POINTER(OrcBox), C.POINTER(OrcPhysics),
                                    C.POINTER(OrcRun), C.POINTER(OrcResult), C.c_void_p, C.c_void_p,
-                                   C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]
+                                   C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]
         for name in ("orc_closest_hit",):
             getattr(L, name).restype = None
             getattr(L, name).argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_int64,
@@ -85,6 +87,11 @@ def lib():
         L.orc_poisson.argtypes = [C.c_double, C.c_double, C.c_int32, C.POINTER(C.c_int)]
         L.orc_sample_energy.restype = C.c_double
         L.orc_sample_energy.argtypes = [C.POINTER(OrcPhysics), C.c_double]
+        for name in ("orc_gamma_fit", "orc_esee_fit"):
+            getattr(L, name).restype = C.c_double
+            getattr(L, name).argtypes = [C.c_double, C.c_double]
+        L.orc_round_stochastic.restype = C.c_int
+        L.orc_round_stochastic.argtypes = [C.c_double, C.c_double, C.c_int32, C.POINTER(C.c_int)]
         L.orc_cosine_dir.restype = None
         L.orc_cosine_dir.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_void_p]
         _lib = L
@@ -100,13 +107,24 @@ class Emission:
     regen_min_ev: float = float("inf")
     max_generation: int = 1
     k_max: int = 15
+    model: int = 0                  # 0: yield table; 1: the paper's fits (Eq. 6, Eq. 7)
+
+
+MODEL_TABLE, MODEL_PAPER_FIT = 0, 1
+
+
+def paper_emission(e_c_ev=10.0, max_generation=6):
+    """The paper's own emission rules: Eq. 6 yield rounded stochastically, Eq. 7
+    energies, the two-daughter split, re-emission above E_c = phi + E_F."""
+    return Emission(absorb_min_ev=e_c_ev, regen_min_ev=e_c_ev, max_generation=max_generation,
+                    model=MODEL_PAPER_FIT)
 
 
 def _physics(table, em: Emission):
     delta = np.ascontiguousarray(table.delta, dtype=np.float32)
     ph = OrcPhysics(delta.ctypes.data_as(C.POINTER(C.c_float)), table.n_e, table.n_theta,
                     table.e_lo_ev, table.e_hi_ev, table.theta_step_deg, em.phi_ev, em.e_cut_ev,
-                    em.absorb_min_ev, em.regen_min_ev, em.max_generation, em.k_max)
+                    em.absorb_min_ev, em.regen_min_ev, em.max_generation, em.k_max, em.model)
     return ph, delta
 
 
@@ -116,7 +134,8 @@ def _box(box):
 
 def run(mesh, table, energy_ev, theta_deg, n_primaries, seed, *, item=0, emission=None,
         primary_offset=0, prim_ids=None, window=None, random_azimuth=False, n_ebins=64,
-        n_abins=18, hist_e_max_ev=50.0, max_wraps=1024, n_threads=0, records=False):
+        n_abins=18, hist_e_max_ev=50.0, max_wraps=1024, n_threads=0, records=False,
+        random_polar=False, n_zbins=0):
     """One (energy, angle) RTMC run on the CPU.  Returns a dict of tallies."""
     L = lib()
     em = emission or Emission()
@@ -131,10 +150,11 @@ def run(mesh, table, energy_ev, theta_deg, n_primaries, seed, *, item=0, emissio
                int(n_primaries), int(primary_offset),
                ids_keep.ctypes.data_as(C.POINTER(C.c_uint64)) if ids_keep is not None else None,
                x0, x1, y0, y1, int(n_ebins), int(n_abins), float(hist_e_max_ev), int(max_wraps),
-               int(n_threads))
+               int(n_threads), int(bool(random_polar)), int(n_zbins))
     out = OrcResult()
     he = np.zeros(n_ebins, dtype=np.int64)
     ha = np.zeros(n_abins, dtype=np.int64)
+    hz = np.zeros(max(int(n_zbins), 1), dtype=np.int64)
     rec = None
     nrec = C.c_int64(0)
     if records:
@@ -142,7 +162,7 @@ def run(mesh, table, energy_ev, theta_deg, n_primaries, seed, *, item=0, emissio
         cap = min(cap, int(n_primaries) * 64 + 1024)
         rec = np.zeros(cap, dtype=RECORD_DTYPE)
     rc = L.orc_run_rtmc(tri.ctypes.data, tri.shape[0], C.byref(_box(mesh.box)), C.byref(ph),
-                        C.byref(r), C.byref(out), he.ctypes.data, ha.ctypes.data,
+                        C.byref(r), C.byref(out), he.ctypes.data, ha.ctypes.data, hz.ctypes.data,
                         rec.ctypes.data if rec is not None else None,
                         rec.size if rec is not None else 0, C.byref(nrec))
     if rc != 0:
@@ -150,6 +170,8 @@ def run(mesh, table, energy_ev, theta_deg, n_primaries, seed, *, item=0, emissio
     res = {name: getattr(out, name) for name, _ in OrcResult._fields_}
     res["hist_e"] = he
     res["hist_a"] = ha
+    if n_zbins:
+        res["hist_z"] = hz
     if rec is not None:
         rr = rec[:nrec.value]
         res["records"] = np.sort(rr, order=["prim", "gen", "path"])
@@ -220,3 +242,17 @@ def cosine_dir(n, u1, u2):
     d = np.zeros(3)
     lib().orc_cosine_dir(n.ctypes.data, float(u1), float(u2), d.ctypes.data)
     return d
+
+
+def gamma_fit(e_ev, alpha_deg):
+    return lib().orc_gamma_fit(float(e_ev), float(alpha_deg))
+
+
+def esee_fit(e_ev, alpha_deg):
+    return lib().orc_esee_fit(float(e_ev), float(alpha_deg))
+
+
+def round_stochastic(gamma, u, k_max=15):
+    cap = C.c_int(0)
+    k = lib().orc_round_stochastic(float(gamma), float(u), int(k_max), C.byref(cap))
+    return k, cap.value

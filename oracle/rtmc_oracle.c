@@ -27,12 +27,12 @@
  *  R5 Number of daughters: Poisson(delta(E, alpha)) by sequential inversion,
  *     capped at k_max; daughter energy from the pdf E/(E+phi)^4 on
  *     [0, E_cut]; direction cosine-law about the facet normal in the
- *     orthonormal basis of Duff et al. (JCGT 2017).  A primary always emits
- *     at its first hit; a daughter of generation g emits only when
- *     g < max_generation and E >= regen_min; otherwise it is absorbed
+ *     orthonormal basis of Duff et al. (JCGT 2017).
+ *  R6 A primary always emits at its first hit; a daughter of generation g
+ *     emits only when g < max_generation and E >= regen_min; otherwise it is absorbed
  *     (absorbed_low below absorb_min).  A daughter of any energy that
  *     reaches z_top moving up is emitted (Section 2.2, last paragraph).
- *  R6 Random streams: Philox4x32-10, key = (seed lo, seed hi), counter =
+ *  R7 Random streams: Philox4x32-10, key = (seed lo, seed hi), counter =
  *     (prim lo, prim hi, path, item).  Primary path = 1; daughter j of a ray
  *     with path p has path 16 p + j.  The four words w0..w3 of a ray's block
  *     map to uniforms u = ((w >> 9) + 0.5) 2^-23, a 24-bit odd multiple of
@@ -40,8 +40,40 @@
  *     in the source window, u2 -> azimuth when random, u3 -> its Poisson
  *     draw.  Daughter: u0 -> energy, u1, u2 -> direction, u3 -> its own
  *     Poisson draw if it re-emits.
- *  R7 delta(E, theta) is bilinear in (ln E, theta) on the table grid, with
+ *  R8 delta(E, theta) is bilinear in (ln E, theta) on the table grid, with
  *     E and theta clamped to the grid.
+ *  R14 Random primary incidence (Section 3.2, normal versus random
+ *     incidence) is the flux of an isotropic beam through the top plane:
+ *     the polar angle follows the cosine law, sin^2 theta = u0 of a second
+ *     Philox block (path 0, never a daughter path), and the azimuth is
+ *     uniform (u2 of the primary's block).  The item angle is then unused.
+ *  R15 The penetration profile (Section 3.2) tallies the depth z_top - z of
+ *     the point where each ray's flight ends on a facet, of any generation,
+ *     whether it re-emits or not: the electron itself stops there.  Bins
+ *     split [0, z_top - z_min] evenly, clamped at both ends.
+ *  R16 Paper-fit emission (model ORC_MODEL_PAPER_FIT), Section 2.2: the
+ *     angle in Eq. 6 and Eq. 7 is the local incidence angle in degrees, E in
+ *     eV, and sin(E) takes E as radians, as printed.  gamma < 0 counts as 0
+ *     and E_SEE < 0 as 0 eV.  The count is gamma rounded stochastically
+ *     (the footnote): floor(gamma) + 1 when u3 < gamma - floor(gamma).
+ *  R17 Daughters of one emission come in pairs (0,1), (2,3), ...: a pair
+ *     shares xi = u1 of its first daughter's block; the first takes
+ *     E_SEE sqrt(xi) at polar angle asin(sqrt(xi)), the second
+ *     (1 - xi) E_SEE at pi/2 minus that angle.  An unpaired daughter (a
+ *     single emission, or the last of an odd count) takes E_SEE at a
+ *     cosine-law angle (sin^2 = its own u1).  Every azimuth is uniform
+ *     (u2 of the daughter's own block) in the Duff et al. basis.
+ *  R18 E_c = phi + E_F is regen_min: a daughter below it still flies (and
+ *     escapes through z_top) but stops at the facet it hits, so on a flat
+ *     surface E[SEY] = gamma exactly (Section 3.1).  "Unbounded"
+ *     generations end at max_generation (at most 6, the depth the 32-bit
+ *     ray path holds); the fits shrink the energy each generation, so the
+ *     cap is rarely reached.
+ *
+ * PARITY UNPINNED: orc_esee_fit (Eq. 7).  The paper prints no value of
+ * E_SEE, so nothing outside this file fixes the formula's transcription; the
+ * tests pin how it is used (a single daughter carries E_SEE exactly, a pair
+ * splits it as Section 2.2 states) but not the formula itself.
  */
 #include "rtmc_oracle.h"
 
@@ -78,7 +110,7 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-/* The four uniforms of the ray (prim, path) in stream `item` (reading R6). */
+/* The four uniforms of the ray (prim, path) in stream `item` (reading R7). */
 static void ray_uniforms(uint64_t seed, uint64_t prim, uint32_t path, uint32_t item, double u[4])
 {
     uint32_t ctr[4] = { (uint32_t)prim, (uint32_t)(prim >> 32), path, item };
@@ -268,7 +300,7 @@ int orc_trace_ray(const float* tri, int64_t n_tri, const orc_box* box, const dou
 /* Sampling (Section 2.2)                                                    */
 /* ------------------------------------------------------------------------ */
 
-/* delta(E, alpha): bilinear in (ln E, angle) on the table grid (reading R7). */
+/* delta(E, alpha): bilinear in (ln E, angle) on the table grid (reading R8). */
 double orc_lookup_delta(const orc_physics* ph, double e_ev, double alpha_rad)
 {
     double x = log(e_ev / ph->e_lo_ev) / log(ph->e_hi_ev / ph->e_lo_ev) * (ph->n_e - 1);
@@ -326,6 +358,32 @@ double orc_sample_energy(const orc_physics* ph, double u)
     return 0.5 * (lo + hi);
 }
 
+/* Eq. 6 (Section 2.2): SEE yield of flat tungsten, E in eV, alpha in
+   degrees (reading R16). */
+double orc_gamma_fit(double e, double a)
+{
+    return 3.05 + 1.7949e-5 * a * a + 6.15e-7 * e * e
+           - (371.317 - exp(0.04826 * a)) / (87.602 + e)
+           - 1.974e-3 * e - 0.1097 * cos(0.1201 + 2.469 * a);
+}
+
+/* Eq. 7 (Section 2.2): energy of an emitted secondary, eV. */
+double orc_esee_fit(double e, double a)
+{
+    return 0.195 * e + 1.6e-4 * e * e + 0.148 * a * sin(e) + 3.44e-15 * e * pow(a, 7.0) - 6.54;
+}
+
+/* Section 2.2 footnote: a fractional yield is rounded up when u falls below
+   its fractional part, down otherwise; negative yields emit nothing. */
+int orc_round_stochastic(double gamma, double u, int32_t k_max, int* capped)
+{
+    if (gamma < 0.0) gamma = 0.0;
+    double fl = floor(gamma);
+    int k = (int)fl + (u < gamma - fl ? 1 : 0);
+    *capped = k > k_max;
+    return k > k_max ? k_max : k;
+}
+
 /* Cosine-law direction about the unit normal n: sin^2(theta') = u1,
    phi' = 2 pi u2, in the orthonormal basis of Duff et al. (JCGT 2017). */
 void orc_cosine_dir(const double n[3], double u1, double u2, double d[3])
@@ -353,7 +411,7 @@ typedef struct {
 
 typedef struct {
     orc_result r;
-    int64_t *he, *ha;
+    int64_t *he, *ha, *hz;
     orc_record* rec;
     int64_t nrec, caprec;
 } orc_local;
@@ -381,14 +439,23 @@ static void run_primary(const float* tri, int64_t n_tri, const orc_box* box,
     double u[4];
     ray_uniforms(run->seed, prim, 1u, run->item, u);
     double th = run->theta_deg * (ORC_PI / 180.0);
-    double ph_az = run->random_azimuth ? 2.0 * ORC_PI * u[2] : 0.0;
+    double sin_t = sin(th), cos_t = cos(th);
+    int random_az = run->random_azimuth;
+    if (run->random_polar) {                  /* reading R14: cosine-law incidence */
+        double v[4];
+        ray_uniforms(run->seed, prim, 0u, run->item, v);
+        sin_t = sqrt(v[0]);
+        cos_t = sqrt(1.0 - v[0]);
+        random_az = 1;
+    }
+    double ph_az = random_az ? 2.0 * ORC_PI * u[2] : 0.0;
     orc_ray r0;
     r0.o[0] = x0 + u[0] * (x1 - x0);
     r0.o[1] = y0 + u[1] * (y1 - y0);
     r0.o[2] = box->z_top;
-    r0.d[0] = sin(th) * cos(ph_az);
-    r0.d[1] = sin(th) * sin(ph_az);
-    r0.d[2] = -cos(th);
+    r0.d[0] = sin_t * cos(ph_az);
+    r0.d[1] = sin_t * sin(ph_az);
+    r0.d[2] = -cos_t;
     r0.e = run->energy_ev;
     r0.path = 1u;
     r0.gen = 0;
@@ -436,6 +503,16 @@ static void run_primary(const float* tri, int64_t n_tri, const orc_box* box,
             L->r.lost++;
         } else {
             rc.tri = (int32_t)j;
+            if (run->n_zbins > 0) {               /* reading R15: where the flight ends */
+                double v0[3], v1[3], v2[3];
+                vert(tri, j, 0, v0); vert(tri, j, 1, v1); vert(tri, j, 2, v2);
+                double z = (1.0 - uh - vh) * v0[2] + uh * v1[2] + vh * v2[2];
+                double dz = (box->z_top - box->z_min) / run->n_zbins;
+                int zb = (int)floor((box->z_top - z) / dz);
+                if (zb > run->n_zbins - 1) zb = run->n_zbins - 1;
+                if (zb < 0) zb = 0;
+                L->hz[zb]++;
+            }
             int emits = ray.gen == 0 ||
                         (ray.gen < ph->max_generation && ray.e >= ph->regen_min_ev);
             if (!emits) {
@@ -449,11 +526,18 @@ static void run_primary(const float* tri, int64_t n_tri, const orc_box* box,
                 facet_normal(tri, j, n);
                 double cosa = -dot3(ray.d, n);
                 double alpha = acos(fmin(1.0, cosa));          /* reading R3 */
-                double lam = orc_lookup_delta(ph, ray.e, alpha);
                 double ur[4];
                 ray_uniforms(run->seed, prim, ray.path, run->item, ur);
-                int capped;
-                int k = orc_poisson(lam, ur[3], ph->k_max, &capped);
+                int capped, k;
+                double esee = 0.0;
+                if (ph->model == ORC_MODEL_PAPER_FIT) {          /* readings R16-R18 */
+                    double a_deg = alpha * (180.0 / ORC_PI);
+                    k = orc_round_stochastic(orc_gamma_fit(ray.e, a_deg), ur[3], ph->k_max, &capped);
+                    esee = fmax(0.0, orc_esee_fit(ray.e, a_deg));
+                } else {
+                    double lam = orc_lookup_delta(ph, ray.e, alpha);
+                    k = orc_poisson(lam, ur[3], ph->k_max, &capped);
+                }
                 L->r.capped += capped;
                 L->r.emitted += k;
                 rc.k = k;
@@ -469,8 +553,22 @@ static void run_primary(const float* tri, int64_t n_tri, const orc_box* box,
                     dr.origin_tri = j;
                     double ud[4];
                     ray_uniforms(run->seed, prim, dr.path, run->item, ud);
-                    dr.e = orc_sample_energy(ph, ud[0]);
-                    orc_cosine_dir(n, ud[1], ud[2], dr.d);
+                    if (ph->model == ORC_MODEL_PAPER_FIT) {
+                        int first = jj & ~1;
+                        if (first + 1 < k) {                      /* one of a pair (R17) */
+                            double uf[4];
+                            ray_uniforms(run->seed, prim, ray.path * 16u + (uint32_t)first, run->item, uf);
+                            double xi = uf[1];
+                            if (jj == first) { dr.e = esee * sqrt(xi); orc_cosine_dir(n, xi, ud[2], dr.d); }
+                            else { dr.e = (1.0 - xi) * esee; orc_cosine_dir(n, 1.0 - xi, ud[2], dr.d); }
+                        } else {                                  /* unpaired */
+                            dr.e = esee;
+                            orc_cosine_dir(n, ud[1], ud[2], dr.d);
+                        }
+                    } else {
+                        dr.e = orc_sample_energy(ph, ud[0]);
+                        orc_cosine_dir(n, ud[1], ud[2], dr.d);
+                    }
                     memcpy(dr.o, p, sizeof p);
                     if (tail == cap) {
                         cap *= 2;
@@ -488,11 +586,12 @@ static void run_primary(const float* tri, int64_t n_tri, const orc_box* box,
 
 int orc_run_rtmc(const float* tri, int64_t n_tri, const orc_box* box,
                  const orc_physics* ph, const orc_run* run, orc_result* out,
-                 int64_t* hist_e, int64_t* hist_a,
+                 int64_t* hist_e, int64_t* hist_a, int64_t* hist_z,
                  orc_record* rec, int64_t rec_cap, int64_t* n_rec)
 {
     if (!tri || n_tri <= 0 || !box || !ph || !run || !out || run->n_primaries < 0 ||
-        run->n_ebins <= 0 || run->n_abins <= 0 || ph->n_e < 2 || ph->n_theta < 2)
+        run->n_ebins <= 0 || run->n_abins <= 0 || ph->n_e < 2 || ph->n_theta < 2 ||
+        run->n_zbins < 0 || (run->n_zbins > 0 && !hist_z))
         return -1;
     int64_t N = run->n_primaries;
     int64_t* kp = (int64_t*)calloc((size_t)(N > 0 ? N : 1), sizeof(int64_t));
@@ -506,6 +605,7 @@ int orc_run_rtmc(const float* tri, int64_t n_tri, const orc_box* box,
     for (int i = 0; i < nthr; ++i) {
         loc[i].he = (int64_t*)calloc((size_t)run->n_ebins, sizeof(int64_t));
         loc[i].ha = (int64_t*)calloc((size_t)run->n_abins, sizeof(int64_t));
+        loc[i].hz = (int64_t*)calloc((size_t)(run->n_zbins > 0 ? run->n_zbins : 1), sizeof(int64_t));
     }
     int want_rec = rec != NULL;
 
@@ -524,6 +624,7 @@ int orc_run_rtmc(const float* tri, int64_t n_tri, const orc_box* box,
     memset(out, 0, sizeof *out);
     memset(hist_e, 0, (size_t)run->n_ebins * sizeof(int64_t));
     memset(hist_a, 0, (size_t)run->n_abins * sizeof(int64_t));
+    if (run->n_zbins > 0) memset(hist_z, 0, (size_t)run->n_zbins * sizeof(int64_t));
     int64_t nr = 0;
     for (int i = 0; i < nthr; ++i) {
         orc_result* r = &loc[i].r;
@@ -534,10 +635,11 @@ int orc_run_rtmc(const float* tri, int64_t n_tri, const orc_box* box,
         out->lost += r->lost; out->wraps += r->wraps;
         for (int b = 0; b < run->n_ebins; ++b) hist_e[b] += loc[i].he[b];
         for (int b = 0; b < run->n_abins; ++b) hist_a[b] += loc[i].ha[b];
+        for (int b = 0; b < run->n_zbins; ++b) hist_z[b] += loc[i].hz[b];
         if (want_rec) {
             for (int64_t k = 0; k < loc[i].nrec && nr < rec_cap; ++k) rec[nr++] = loc[i].rec[k];
         }
-        free(loc[i].he); free(loc[i].ha); free(loc[i].rec);
+        free(loc[i].he); free(loc[i].ha); free(loc[i].hz); free(loc[i].rec);
     }
     if (n_rec) *n_rec = nr;
     /* per-primary sums in primary order: the same result for any thread count */

@@ -37,8 +37,14 @@ typedef struct {
     double absorb_min_ev;    /* below: absorbed_low on a facet hit (10 eV)  */
     double regen_min_ev;     /* daughters at/above may re-emit              */
     int32_t max_generation;  /* daughters of generation g < this re-emit    */
-    int32_t k_max;           /* Poisson count cap (15)                      */
+    int32_t k_max;           /* daughter count cap (15)                     */
+    int32_t model;           /* ORC_MODEL_TABLE or ORC_MODEL_PAPER_FIT      */
 } orc_physics;
+
+/* emission models: the yield table with Poisson counts and the truncated
+   spectrum, or the paper's own fits (Eq. 6, Eq. 7, stochastic rounding and
+   the two-daughter split of Section 2.2; readings R16-R18) */
+enum { ORC_MODEL_TABLE = 0, ORC_MODEL_PAPER_FIT = 1 };
 
 typedef struct {
     double energy_ev, theta_deg;
@@ -53,6 +59,8 @@ typedef struct {
     double hist_e_max_ev;
     int32_t max_wraps;
     int32_t n_threads;             /* 0 -> OpenMP default                    */
+    int32_t random_polar;          /* 1: cosine-law polar angle (reading R14) */
+    int32_t n_zbins;               /* penetration-depth bins (reading R15)    */
 } orc_run;
 
 typedef struct {
@@ -76,7 +84,7 @@ typedef struct {
 
 int orc_run_rtmc(const float* tri, int64_t n_tri, const orc_box* box,
                  const orc_physics* phys, const orc_run* run, orc_result* out,
-                 int64_t* hist_e, int64_t* hist_a,
+                 int64_t* hist_e, int64_t* hist_a, int64_t* hist_z,
                  orc_record* rec, int64_t rec_cap, int64_t* n_rec);
 
 /* Closest front-facing hit in one cell (no periodic walk); tri_id = -1 on a miss. */
@@ -100,6 +108,9 @@ double orc_lookup_delta(const orc_physics* phys, double e_ev, double alpha_rad);
 int orc_poisson(double lambda, double u, int32_t k_max, int* capped);
 double orc_sample_energy(const orc_physics* phys, double u);
 void orc_cosine_dir(const double n[3], double u1, double u2, double d[3]);
+double orc_gamma_fit(double e_ev, double alpha_deg);
+double orc_esee_fit(double e_ev, double alpha_deg);
+int orc_round_stochastic(double gamma, double u, int32_t k_max, int* capped);
 
 #ifdef __cplusplus
 }

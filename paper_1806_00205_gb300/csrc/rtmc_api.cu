@@ -87,6 +87,7 @@ RunParams make_params(const DeviceMesh& m, const rtmc_run_desc& d, uint64_t seed
     p.energy = (float)energy;
     p.theta_rad = (float)(theta_deg * kPi / 180.0);
     p.random_azimuth = d.random_azimuth;
+    p.random_polar = d.random_polar;
     const bool full = d.src_x0 == 0.0 && d.src_x1 == 0.0 && d.src_y0 == 0.0 && d.src_y1 == 0.0;
     p.src_x0 = full ? 0.f : (float)d.src_x0;
     p.src_x1 = full ? (float)m.box.lx : (float)d.src_x1;
@@ -101,6 +102,8 @@ RunParams make_params(const DeviceMesh& m, const rtmc_run_desc& d, uint64_t seed
     p.n_abins = d.n_abins;
     p.ebin_w = (float)(d.hist_e_max_ev / d.n_ebins);
     p.inv_abin = (float)(d.n_abins / (0.5 * kPi));
+    p.n_zbins = d.n_zbins;
+    p.inv_zbin = (float)(d.n_zbins / (m.box.z_top - m.box.z_min));
     p.prim_offset = d.primary_offset;
     return p;
 }
@@ -126,6 +129,7 @@ Emission make_emission(const rtmc_emission& em)
     e.regen_min = std::isinf(em.regen_min_ev) ? INFINITY : (float)em.regen_min_ev;
     e.max_generation = em.max_generation;
     e.k_max = em.k_max;
+    e.model = em.model;
     const double sn = em.phi_ev / (em.e_cut_ev + em.phi_ev);
     e.spec_norm = (float)(1.0 - 3.0 * sn * sn + 2.0 * sn * sn * sn);
     return e;
@@ -171,6 +175,7 @@ struct ItemOut {
     rtmc_result* res;
     uint64_t* hist_e;   // host, n_ebins or NULL
     uint64_t* hist_a;
+    uint64_t* hist_z;   // host, n_zbins or NULL
     rtmc_record* rec;   // host or NULL
     int64_t rec_cap;
     int64_t* n_rec;
@@ -228,7 +233,7 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
         if (ce == cudaSuccess) ce = scratch_reserve(ctx->ctl, sizeof(Control));
         if (ce == cudaSuccess && !d.id_order) ce = scratch_reserve(ctx->sort_counts, (size_t)kSortBucketsPerItem * 4);
         if (ce == cudaSuccess) ce = scratch_reserve(ctx->tally, sizeof(Tally));
-        if (ce == cudaSuccess) ce = scratch_reserve(ctx->hist, (size_t)(d.n_ebins + d.n_abins) * 8);
+        if (ce == cudaSuccess) ce = scratch_reserve(ctx->hist, (size_t)(d.n_ebins + d.n_abins + d.n_zbins) * 8);
         if (ce == cudaSuccess && record) ce = scratch_reserve(ctx->records, (size_t)std::max<int64_t>(o.rec_cap, 1) * sizeof(rtmc_record));
         if (ce != cudaSuccess) return ctx->fail(RTMC_ERR_OOM, std::string("run: scratch: ") + cudaGetErrorString(ce));
 
@@ -257,7 +262,7 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
         cudaEventCreate(&ev0);
         cudaEventCreate(&ev1);
         cudaMemsetAsync(q.tally, 0, sizeof(Tally), s);
-        cudaMemsetAsync(q.hist_e, 0, (size_t)(d.n_ebins + d.n_abins) * 8, s);
+        cudaMemsetAsync(q.hist_e, 0, (size_t)(d.n_ebins + d.n_abins + d.n_zbins) * 8, s);
         if (d.prim_hash) cudaMemsetAsync(d.prim_hash, 0, (size_t)n_prim * 8, s);
         // per-kernel timing (profile): one event pair per launch, kind 0..3
         std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> kev;
@@ -302,7 +307,7 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
         }
         cudaEventRecord(ev1, s);
         Tally t;
-        std::vector<unsigned long long> hist((size_t)(d.n_ebins + d.n_abins));
+        std::vector<unsigned long long> hist((size_t)(d.n_ebins + d.n_abins + d.n_zbins));
         if (ce == cudaSuccess) ce = cudaMemcpyAsync(&t, q.tally, sizeof t, cudaMemcpyDeviceToHost, s);
         if (ce == cudaSuccess)
             ce = cudaMemcpyAsync(hist.data(), q.hist_e, hist.size() * 8, cudaMemcpyDeviceToHost, s);
@@ -345,6 +350,7 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
         r.ms_finalize = kms[3];
         if (o.hist_e) for (int b = 0; b < d.n_ebins; ++b) o.hist_e[b] = hist[b];
         if (o.hist_a) for (int b = 0; b < d.n_abins; ++b) o.hist_a[b] = hist[d.n_ebins + b];
+        if (o.hist_z) for (int b = 0; b < d.n_zbins; ++b) o.hist_z[b] = hist[d.n_ebins + d.n_abins + b];
         if (record) {
             const int64_t nrec = (int64_t)std::min<unsigned long long>(t.rays_recorded, (unsigned long long)o.rec_cap);
             ce = cudaMemcpyAsync(o.rec, q.records, (size_t)nrec * sizeof(rtmc_record), cudaMemcpyDeviceToHost, s);
@@ -376,6 +382,8 @@ int rtmc::check_run_desc(rtmc_ctx* ctx, const rtmc_run_desc& d)
     if (d.block_threads != 0 && (d.block_threads % 32 != 0 || d.block_threads < 32 || d.block_threads > 128))
         return ctx->fail(RTMC_ERR_INVALID_ARG, "run: block_threads must be a multiple of 32 in [32, 128]");
     if (d.traversal < 0 || d.traversal > 2) return ctx->fail(RTMC_ERR_INVALID_ARG, "run: unknown traversal variant");
+    if (d.n_zbins < 0 || d.n_zbins > 4096 || (d.n_zbins > 0 && !d.hist_z))
+        return ctx->fail(RTMC_ERR_INVALID_ARG, "run: n_zbins in [0, 4096] and hist_z needed when n_zbins > 0");
     if (d.stack_depth != 0 && d.stack_depth != 8 && d.stack_depth != 16 && d.stack_depth != 32)
         return ctx->fail(RTMC_ERR_INVALID_ARG, "run: stack_depth must be 8, 16 or 32");
     if (d.fetch_threshold < 0 || d.fetch_threshold > 32)
@@ -492,7 +500,7 @@ int rtmc_load_see_tables(rtmc_ctx* ctx, const float* delta, const rtmc_grid* gri
         !(grid->e_lo_ev > 0.0) || !(grid->e_hi_ev > grid->e_lo_ev) || !(grid->theta_step_deg > 0.0))
         return ctx->fail(RTMC_ERR_INVALID_ARG, "load_see_tables: bad grid");
     if (em->k_max < 0 || em->k_max > 15 || em->max_generation < 1 || em->max_generation > 6 || !(em->phi_ev > 0.0) ||
-        !(em->e_cut_ev > 0.0))
+        !(em->e_cut_ev > 0.0) || (em->model != RTMC_EMISSION_TABLE && em->model != RTMC_EMISSION_PAPER_FIT))
         return ctx->fail(RTMC_ERR_INVALID_ARG, "load_see_tables: bad emission parameters");
     DeviceGuard g(ctx->device);
     const size_t bytes = (size_t)grid->n_e * grid->n_theta * sizeof(float);
@@ -545,7 +553,8 @@ int rtmc_run(rtmc_ctx* ctx, int32_t mesh_id, const double* energies_ev, int32_t 
         for (int it = 0; it < n_theta; ++it) {
             const int item = ie * n_theta + it;
             ItemOut o{&out[item], hist_e ? hist_e + (size_t)item * d.n_ebins : nullptr,
-                      hist_a ? hist_a + (size_t)item * d.n_abins : nullptr, nullptr, 0, nullptr};
+                      hist_a ? hist_a + (size_t)item * d.n_abins : nullptr,
+                      d.n_zbins ? d.hist_z + (size_t)item * d.n_zbins : nullptr, nullptr, 0, nullptr};
             rc = run_item(ctx, m, energies_ev[ie], theta_deg[it], d.item_base + (unsigned)item, n_primaries, seed,
                           d, o);
             if (rc) return rc;
@@ -565,7 +574,7 @@ int rtmc_run_records(rtmc_ctx* ctx, int32_t mesh_id, double energy_ev, double th
     if (!out || !rec || rec_cap <= 0 || !n_rec || !(energy_ev > 0.0) || !(theta_deg >= 0.0 && theta_deg < 90.0))
         return ctx->fail(RTMC_ERR_INVALID_ARG, "run_records: bad arguments");
     DeviceGuard g(ctx->device);
-    ItemOut o{out, nullptr, nullptr, rec, rec_cap, n_rec};
+    ItemOut o{out, nullptr, nullptr, d.n_zbins ? d.hist_z : nullptr, rec, rec_cap, n_rec};
     return run_item(ctx, ctx->meshes[mesh_id], energy_ev, theta_deg, item, n_primaries, seed, d, o);
 }
 

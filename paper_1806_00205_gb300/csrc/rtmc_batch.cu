@@ -73,7 +73,7 @@ cudaError_t record_batch(rtmc_ctx* ctx, const rtmc_batch& b, const rtmc_run_desc
                          KernelTimer& kt, int64_t& launches)
 {
     using namespace rtmc;
-    const int nbins = d.n_ebins + d.n_abins;
+    const int nbins = d.n_ebins + d.n_abins + d.n_zbins;
     cudaError_t ce = cudaMemsetAsync(d_tallies, 0, (size_t)(n_items + 1) * sizeof(Tally), s);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(d_hists, 0, (size_t)n_items * nbins * 8, s);
     const TableDesc tab = make_table(ctx);
@@ -148,8 +148,8 @@ extern "C" int rtmc_run_batch(rtmc_ctx* ctx, const rtmc_batch* batch, const rtmc
     if (ctx->emission.max_generation != 1)
         return ctx->fail(RTMC_ERR_INVALID_ARG, "run_batch: the batched form needs max_generation == 1");
     if (d.prim_hash) return ctx->fail(RTMC_ERR_INVALID_ARG, "run_batch: per-primary hashes are not supported");
-    if (d.n_ebins + d.n_abins > 512)
-        return ctx->fail(RTMC_ERR_INVALID_ARG, "run_batch: n_ebins + n_abins must be <= 512");
+    if (d.n_ebins + d.n_abins + d.n_zbins > 512)
+        return ctx->fail(RTMC_ERR_INVALID_ARG, "run_batch: n_ebins + n_abins + n_zbins must be <= 512");
     for (int i = 0; i < batch->n_meshes; ++i) {
         const int mid = batch->mesh_ids[i];
         if (mid < 0 || mid >= (int)ctx->meshes.size() || !ctx->meshes[mid].tri_in)
@@ -166,7 +166,7 @@ extern "C" int rtmc_run_batch(rtmc_ctx* ctx, const rtmc_batch* batch, const rtmc
     cudaStream_t s = ctx->stream;
     const int64_t per_mesh = (int64_t)batch->n_e * batch->n_theta;
     const int64_t n_items = per_mesh * batch->n_meshes;
-    const int nbins = d.n_ebins + d.n_abins;
+    const int nbins = d.n_ebins + d.n_abins + d.n_zbins;
 
     // item table (host -> device every call: energies and angles may change)
     std::vector<ItemDev> items((size_t)n_items);
@@ -255,11 +255,12 @@ extern "C" int rtmc_run_batch(rtmc_ctx* ctx, const rtmc_batch* batch, const rtmc
     std::string key;
     {
         char buf[512];
-        std::snprintf(buf, sizeof buf, "%d|%d|%d|%lld|%llu|%lld|%d|%d|%d|%d|%d|%d|%d|%d|%u|%.17g|%llu|%.17g|%.17g|%.17g|%.17g",
+        std::snprintf(buf, sizeof buf, "%d|%d|%d|%lld|%llu|%lld|%d|%d|%d|%d|%d|%d|%d|%d|%u|%.17g|%llu|%.17g|%.17g|%.17g|%.17g|z%d|rp%d",
                       batch->n_meshes, batch->n_e, batch->n_theta, (long long)batch->n_primaries,
                       (unsigned long long)batch->seed, (long long)chunk, d.n_ebins, d.n_abins, d.random_azimuth,
                       d.max_wraps, d.block_threads, d.blocks_per_sm, d.traversal * 10000 + d.stack_depth * 100 + d.fetch_threshold, d.fp64_retest, d.item_base,
-                      d.hist_e_max_ev, (unsigned long long)d.primary_offset, d.src_x0, d.src_x1, d.src_y0, d.src_y1);
+                      d.hist_e_max_ev, (unsigned long long)d.primary_offset, d.src_x0, d.src_x1, d.src_y0, d.src_y1,
+                      d.n_zbins, d.random_polar);
         key = buf;
         for (int i = 0; i < batch->n_meshes; ++i) {
             const DeviceMesh& m = ctx->meshes[batch->mesh_ids[i]];
@@ -342,6 +343,9 @@ extern "C" int rtmc_run_batch(rtmc_ctx* ctx, const rtmc_batch* batch, const rtmc
             for (int bb = 0; bb < d.n_ebins; ++bb) hist_e[k * d.n_ebins + bb] = h[(size_t)k * nbins + bb];
         if (hist_a)
             for (int bb = 0; bb < d.n_abins; ++bb) hist_a[k * d.n_abins + bb] = h[(size_t)k * nbins + d.n_ebins + bb];
+        if (d.n_zbins)
+            for (int bb = 0; bb < d.n_zbins; ++bb)
+                d.hist_z[k * d.n_zbins + bb] = h[(size_t)k * nbins + d.n_ebins + d.n_abins + bb];
     }
     return RTMC_OK;
 }

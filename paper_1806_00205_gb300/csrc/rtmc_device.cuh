@@ -78,6 +78,7 @@ struct Emission {
     float phi, e_cut, absorb_min, regen_min;
     int max_generation, k_max;
     float spec_norm;              // spectrum CDF at e_cut
+    int model;                    // RTMC_EMISSION_TABLE or RTMC_EMISSION_PAPER_FIT
 };
 
 struct TableDesc {

@@ -84,18 +84,21 @@ int build_lbvh(rtmc_ctx* ctx, DeviceMesh& m);
 
 // Wavefront launchers (rtmc_trace.cu).
 struct RunParams {
-    unsigned long long seed;
-    unsigned item;
-    float energy, theta_rad;
-    int random_azimuth;
-    float src_x0, src_x1, src_y0, src_y1;
-    float lx, ly, z_min, z_top;
-    int max_wraps;
-    int n_ebins, n_abins;
-    float ebin_w;                // eV per energy bin
-    float inv_abin;              // bins per radian of polar angle
-    unsigned long long prim_offset;
-    float sin_t, cos_t;          // incidence (single-item runs)
+    unsigned long long seed = 0;
+    unsigned item = 0;
+    float energy = 0.f, theta_rad = 0.f;
+    int random_azimuth = 0;
+    int random_polar = 0;        // 1: cosine-law polar angle of incidence (second Philox block, path 0)
+    float src_x0 = 0.f, src_x1 = 0.f, src_y0 = 0.f, src_y1 = 0.f;
+    float lx = 0.f, ly = 0.f, z_min = 0.f, z_top = 0.f;
+    int max_wraps = 1024;
+    int n_ebins = 0, n_abins = 0;
+    int n_zbins = 0;             // penetration-depth bins over [0, z_top - z_min] below z_top
+    float ebin_w = 1.f;          // eV per energy bin
+    float inv_abin = 0.f;        // bins per radian of polar angle
+    float inv_zbin = 0.f;        // bins per nm of depth
+    unsigned long long prim_offset = 0;
+    float sin_t = 0.f, cos_t = 1.f;   // incidence (single-item runs)
 };
 
 struct Queues {

@@ -8,7 +8,7 @@
 //   hits                         16 B x kMaxPrim x 15
 //   wraps                        4 B x kMaxPrim x 15   (per-primary hashing)
 //   per-primary escape counts    4 B x kMaxPrim
-//   Control, Tally, histograms   (n_ebins + n_abins <= kMaxBins) x 8 B
+//   Control, Tally, histograms   (n_ebins + n_abins + n_zbins <= kMaxBins) x 8 B
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -107,8 +107,11 @@ extern "C" int rtmc_run_noalloc(rtmc_ctx* ctx, int32_t mesh_id, double energy_ev
         d.n_abins = 18;
         d.hist_e_max_ev = 50.0;
     }
-    if (d.n_ebins <= 0 || d.n_abins <= 0 || d.n_ebins + d.n_abins > kMaxBins || !(d.hist_e_max_ev > 0.0))
-        return ctx->fail(RTMC_ERR_INVALID_ARG, "run_noalloc: histogram bins must satisfy n_ebins + n_abins <= 1024");
+    if (d.n_ebins <= 0 || d.n_abins <= 0 || d.n_zbins < 0 || d.n_ebins + d.n_abins + d.n_zbins > kMaxBins ||
+        !(d.hist_e_max_ev > 0.0) || (d.n_zbins > 0 && !d.hist_z))
+        return ctx->fail(RTMC_ERR_INVALID_ARG,
+                         "run_noalloc: histogram bins must satisfy n_ebins + n_abins + n_zbins <= 1024 "
+                         "(hist_z needed when n_zbins > 0)");
     if (d.max_wraps < 0 || d.max_wraps > (1 << 20))
         return ctx->fail(RTMC_ERR_INVALID_ARG, "run_noalloc: max_wraps out of range");
     if (d.block_threads != 0 && (d.block_threads % 32 != 0 || d.block_threads < 32 || d.block_threads > 128))
@@ -133,6 +136,7 @@ extern "C" int rtmc_run_noalloc(rtmc_ctx* ctx, int32_t mesh_id, double energy_ev
     p.energy = (float)energy_ev;
     p.theta_rad = (float)(theta_deg * kPi / 180.0);
     p.random_azimuth = d.random_azimuth;
+    p.random_polar = d.random_polar;
     const bool full = d.src_x0 == 0.0 && d.src_x1 == 0.0 && d.src_y0 == 0.0 && d.src_y1 == 0.0;
     p.src_x0 = full ? 0.f : (float)d.src_x0;
     p.src_x1 = full ? (float)m.box.lx : (float)d.src_x1;
@@ -147,6 +151,8 @@ extern "C" int rtmc_run_noalloc(rtmc_ctx* ctx, int32_t mesh_id, double energy_ev
     p.n_abins = d.n_abins;
     p.ebin_w = (float)(d.hist_e_max_ev / d.n_ebins);
     p.inv_abin = (float)(d.n_abins / (0.5 * kPi));
+    p.n_zbins = d.n_zbins;
+    p.inv_zbin = (float)(d.n_zbins / (m.box.z_top - m.box.z_min));
     p.prim_offset = d.primary_offset;
 
     TableDesc tab;
@@ -165,6 +171,7 @@ extern "C" int rtmc_run_noalloc(rtmc_ctx* ctx, int32_t mesh_id, double energy_ev
     e.max_generation = em.max_generation;
     e.k_max = em.k_max;
     e.spec_norm = (float)spectrum_cdf(em.e_cut_ev, em.phi_ev);
+    e.model = em.model;
 
     Queues q;
     for (int b = 0; b < 2; ++b) {
@@ -197,7 +204,7 @@ extern "C" int rtmc_run_noalloc(rtmc_ctx* ctx, int32_t mesh_id, double energy_ev
     // The array keeps the previous call's contents: clear everything that must start at zero.
     ce = cudaMemsetAsync(base + kCtl, 0, sizeof(Control), s);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(base + kTally, 0, sizeof(Tally), s);
-    if (ce == cudaSuccess) ce = cudaMemsetAsync(base + kHist, 0, 8 * (size_t)(d.n_ebins + d.n_abins), s);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(base + kHist, 0, 8 * (size_t)(d.n_ebins + d.n_abins + d.n_zbins), s);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(base + kKcount, 0, 4 * (size_t)kMaxPrim, s);
     if (ce == cudaSuccess && hashing) ce = cudaMemsetAsync(d.prim_hash, 0, 8 * (size_t)n_primaries, s);
     const unsigned n = (unsigned)n_primaries;
@@ -213,6 +220,9 @@ extern "C" int rtmc_run_noalloc(rtmc_ctx* ctx, int32_t mesh_id, double energy_ev
         ce = cudaMemcpyAsync(hist_e, base + kHist, 8 * (size_t)d.n_ebins, cudaMemcpyDeviceToHost, s);
     if (ce == cudaSuccess && hist_a)
         ce = cudaMemcpyAsync(hist_a, base + kHist + 8 * (size_t)d.n_ebins, 8 * (size_t)d.n_abins,
+                             cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess && d.n_zbins > 0)
+        ce = cudaMemcpyAsync(d.hist_z, base + kHist + 8 * (size_t)(d.n_ebins + d.n_abins), 8 * (size_t)d.n_zbins,
                              cudaMemcpyDeviceToHost, s);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
     if (ce != cudaSuccess) return ctx->fail(RTMC_ERR_CUDA, std::string("run_noalloc: ") + cudaGetErrorString(ce));

@@ -21,12 +21,33 @@ namespace rtmc {
 namespace {
 
 constexpr int kShadeThreads = 256;
+constexpr size_t kShadeDefaultSmem = 24 * 1024;   // dynamic bytes that fit beside the static arrays
 
 __device__ __forceinline__ float4 ldg4(const float4* p) { return __ldg(p); }
 
 // --------------------------------------------------------------------------
 // generate
 // --------------------------------------------------------------------------
+// Direction of a primary.  Fixed incidence: the item's polar angle, azimuth 0
+// or uniform (u2 of the primary's block).  Random incidence (Section 3.2):
+// the flux of an isotropic beam through the top plane, a cosine-law polar
+// angle with sin^2 theta = u0 of the path-0 block (no daughter uses path 0)
+// and a uniform azimuth.  u0 is an odd multiple of 2^-24, so 1 - u0 is exact.
+__device__ __forceinline__ float4 primary_dir(const RunParams& p, float sin_t, float cos_t, unsigned plo,
+                                              unsigned phi, unsigned pitem, unsigned wz)
+{
+    bool random_az = p.random_azimuth != 0;
+    if (p.random_polar) {
+        const float u = u01(ray_block(p.seed, plo, phi, 0u, pitem).x);
+        sin_t = sqrtf(u);
+        cos_t = sqrtf(1.f - u);
+        random_az = true;
+    }
+    float ca = 1.f, sa = 0.f;
+    if (random_az) sincospif(2.0f * u01(wz), &sa, &ca);
+    return make_float4(sin_t * ca, sin_t * sa, -cos_t, __int_as_float(-1));
+}
+
 __global__ void k_generate(RunParams p, float sin_t, float cos_t, unsigned long long first,
                            unsigned n, float4* __restrict__ oe, float4* __restrict__ dt,
                            uint4* __restrict__ id, Control* __restrict__ ctl)
@@ -39,10 +60,8 @@ __global__ void k_generate(RunParams p, float sin_t, float cos_t, unsigned long 
     const uint4 w = ray_block(p.seed, plo, phi, 1u, p.item);
     const float x = p.src_x0 + u01(w.x) * (p.src_x1 - p.src_x0);
     const float y = p.src_y0 + u01(w.y) * (p.src_y1 - p.src_y0);
-    float ca = 1.f, sa = 0.f;
-    if (p.random_azimuth) sincospif(2.0f * u01(w.z), &sa, &ca);
     oe[i] = make_float4(x, y, p.z_top, p.energy);
-    dt[i] = make_float4(sin_t * ca, sin_t * sa, -cos_t, __int_as_float(-1));
+    dt[i] = primary_dir(p, sin_t, cos_t, plo, phi, p.item, w.z);
     id[i] = make_uint4(plo, phi, 1u, 0u);
 }
 
@@ -62,10 +81,8 @@ __global__ void k_generate_items(RunParams p, ItemCtx ic, unsigned n, float4* __
     const uint4 w = ray_block(p.seed, (unsigned)prim, (unsigned)(prim >> 32), 1u, item.philox_item);
     const float x = p.src_x0 + u01(w.x) * (p.src_x1 - p.src_x0);
     const float y = p.src_y0 + u01(w.y) * (p.src_y1 - p.src_y0);
-    float ca = 1.f, sa = 0.f;
-    if (p.random_azimuth) sincospif(2.0f * u01(w.z), &sa, &ca);
     oe[i] = make_float4(x, y, p.z_top, item.energy);
-    dt[i] = make_float4(item.sin_t * ca, item.sin_t * sa, -item.cos_t, __int_as_float(-1));
+    dt[i] = primary_dir(p, item.sin_t, item.cos_t, (unsigned)prim, (unsigned)(prim >> 32), item.philox_item, w.z);
     id[i] = make_uint4(pl, it, 1u, 0u);
 }
 
@@ -116,10 +133,8 @@ __device__ __forceinline__ void primary_of(const RunParams& p, const ItemCtx& ic
     const float ux = u01(w.x), uy = u01(w.y);
     const float x = p.src_x0 + ux * (p.src_x1 - p.src_x0);
     const float y = p.src_y0 + uy * (p.src_y1 - p.src_y0);
-    float ca = 1.f, sa = 0.f;
-    if (p.random_azimuth) sincospif(2.0f * u01(w.z), &sa, &ca);
     oe = make_float4(x, y, p.z_top, energy);
-    dt = make_float4(sin_t * ca, sin_t * sa, -cos_t, __int_as_float(-1));
+    dt = primary_dir(p, sin_t, cos_t, (unsigned)prim, (unsigned)(prim >> 32), pitem, w.z);
     id = make_uint4(idxy.x, idxy.y, 1u, 0u);
     const unsigned cx = min((unsigned)(ux * (1 << kSortCellBits)), (1u << kSortCellBits) - 1);
     const unsigned cy = min((unsigned)(uy * (1 << kSortCellBits)), (1u << kSortCellBits) - 1);
@@ -225,6 +240,31 @@ __device__ __forceinline__ float sample_energy(const Emission& em, float u)
     return fminf(em.phi * (1.0f / s - 1.0f), em.e_cut);
 }
 
+// Section 2.2, Eq. 6: SEE yield of flat tungsten; e in eV, a (local incidence) in degrees.
+__device__ __forceinline__ float gamma_fit(float e, float a)
+{
+    return 3.05f + 1.7949e-5f * a * a + 6.15e-7f * e * e - (371.317f - expf(0.04826f * a)) / (87.602f + e) -
+           1.974e-3f * e - 0.1097f * cosf(0.1201f + 2.469f * a);
+}
+
+// Section 2.2, Eq. 7: energy (eV) of an emitted secondary; sin takes e as radians, as printed.
+__device__ __forceinline__ float esee_fit(float e, float a)
+{
+    const float a2 = a * a, a7 = a2 * a2 * a2 * a;
+    return 0.195f * e + 1.6e-4f * e * e + 0.148f * a * sinf(e) + 3.44e-15f * e * a7 - 6.54f;
+}
+
+// Section 2.2 footnote: round the fractional yield up when u falls below its
+// fractional part (g - floor(g) is exact in binary floating point).
+__device__ __forceinline__ int round_stochastic(float g, float u, int k_max, int& capped)
+{
+    g = fmaxf(g, 0.f);
+    const float fl = floorf(g);
+    const int k = (int)fl + (u < g - fl ? 1 : 0);
+    capped = k > k_max;
+    return min(k, k_max);
+}
+
 // Cosine-law direction about n in the basis of Duff et al. (JCGT 2017).
 __device__ __forceinline__ float3 cosine_dir(float3 n, float u1, float u2)
 {
@@ -300,7 +340,7 @@ k_shade(const float4* __restrict__ tris, const float4* __restrict__ normals, Tab
         unsigned long long* __restrict__ prim_hash, rtmc_record* __restrict__ records,
         unsigned long long rec_cap)
 {
-    extern __shared__ unsigned s_hist[];              // [ITEMS ? kChunkItems : 1][n_ebins + n_abins]
+    extern __shared__ unsigned s_hist[];              // [ITEMS ? kChunkItems : 1][n_ebins + n_abins + n_zbins]
     __shared__ unsigned s_excl[kShadeThreads + 1];
     __shared__ unsigned s_warp[kShadeThreads / 32];
     __shared__ float s_px[kShadeThreads], s_py[kShadeThreads], s_pz[kShadeThreads];
@@ -308,6 +348,7 @@ k_shade(const float4* __restrict__ tris, const float4* __restrict__ normals, Tab
     __shared__ uint4 s_id[kShadeThreads];             // child id: (x, y, parent path, gen + 1)
     __shared__ uint3 s_key[kShadeThreads];            // Philox: (prim lo, prim hi, item)
     __shared__ int s_tri[kShadeThreads];
+    __shared__ float s_esee[kShadeThreads];           // paper-fit model: E_SEE of the emission
     __shared__ unsigned s_base;
     __shared__ unsigned long long s_red[10][kShadeThreads / 32];
     __shared__ double s_dred[2][kShadeThreads / 32];
@@ -315,7 +356,8 @@ k_shade(const float4* __restrict__ tris, const float4* __restrict__ normals, Tab
     __shared__ double s_isum[kChunkItems][2];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nbins = p.n_ebins + p.n_abins;
+    const int nbins = p.n_ebins + p.n_abins + p.n_zbins;
+    const int zbase = p.n_ebins + p.n_abins;
     // multi-item chunks touching at most kChunkItems items accumulate per item in
     // shared memory; wider chunks (tiny items) send every ray to global atomics
     const bool shared_items = ITEMS && ic.n_items <= (unsigned)kChunkItems;
@@ -423,6 +465,16 @@ k_shade(const float4* __restrict__ tris, const float4* __restrict__ normals, Tab
             } else {
                 const float4 w0 = ldg4(tris + 3ll * tri);
                 orig = __float_as_int(w0.w);
+                const float bw = 1.f - h.y - h.z;
+                if (p.n_zbins > 0) {
+                    // penetration depth: the flight of every ray that meets a facet ends there
+                    const float z1 = ldg4(tris + 3ll * tri + 1).z, z2 = ldg4(tris + 3ll * tri + 2).z;
+                    const float pz = bw * w0.z + h.y * z1 + h.z * z2;
+                    const int z_bin = max(0, min((int)floorf((p.z_top - pz) * p.inv_zbin), p.n_zbins - 1));
+                    if (!ITEMS) atomicAdd(&s_hist[zbase + z_bin], 1u);
+                    else if (shared_items) atomicAdd(&s_hist[jslot * nbins + zbase + z_bin], 1u);
+                    else atomicAdd(&ic.hists[(size_t)slot * nbins + zbase + z_bin], 1ull);
+                }
                 const bool emits = g == 0 || ((int)g < em.max_generation && E >= em.regen_min);
                 if (!emits) {
                     if (E < em.absorb_min) { fate = RTMC_ABSORBED_LOW; r.low = 1; }
@@ -434,15 +486,19 @@ k_shade(const float4* __restrict__ tris, const float4* __restrict__ normals, Tab
                     const float4 nr = ldg4(normals + tri);
                     const float cosa = -(b.x * nr.x + b.y * nr.y + b.z * nr.z);
                     const float alpha = acosf(fminf(1.f, cosa));
-                    const float lam = lookup_delta(tab, E, alpha);
                     const uint4 w = ray_block(p.seed, (unsigned)prim, (unsigned)(prim >> 32), rid.z, pitem);
                     int capped;
-                    kk = poisson_inv(lam, u01(w.w), em.k_max, capped);
+                    if (em.model == RTMC_EMISSION_PAPER_FIT) {
+                        const float a_deg = alpha * 57.295779513082321f;
+                        kk = round_stochastic(gamma_fit(E, a_deg), u01(w.w), em.k_max, capped);
+                        s_esee[tid] = fmaxf(esee_fit(E, a_deg), 0.f);
+                    } else {
+                        kk = poisson_inv(lookup_delta(tab, E, alpha), u01(w.w), em.k_max, capped);
+                    }
                     r.capped = capped;
                     r.emitted = kk;
                     k = kk;
                     const float4 w1 = ldg4(tris + 3ll * tri + 1), w2 = ldg4(tris + 3ll * tri + 2);
-                    const float bw = 1.f - h.y - h.z;
                     s_px[tid] = bw * w0.x + h.y * w1.x + h.z * w2.x;
                     s_py[tid] = bw * w0.y + h.y * w1.y + h.z * w2.y;
                     s_pz[tid] = bw * w0.z + h.y * w1.z + h.z * w2.z;
@@ -534,8 +590,27 @@ k_shade(const float4* __restrict__ tris, const float4* __restrict__ normals, Tab
             const uint3 key = s_key[par];
             const unsigned path = pid.z * 16u + j;
             const uint4 w = ray_block(p.seed, key.x, key.y, path, key.z);
-            const float e = sample_energy(em, u01(w.x));
-            const float3 dd = cosine_dir(make_float3(s_nx[par], s_ny[par], s_nz[par]), u01(w.y), u01(w.z));
+            float e, sb2 = u01(w.y);                  // energy; sin^2 of the polar angle
+            if (em.model == RTMC_EMISSION_PAPER_FIT) {
+                // pairs (0,1), (2,3), ... share xi = u1 of the pair's first daughter;
+                // an unpaired daughter takes E_SEE at a cosine-law angle
+                const unsigned kpar = s_excl[par + 1] - s_excl[par];
+                const unsigned first = j & ~1u;
+                const float esee = s_esee[par];
+                e = esee;
+                if (first + 1 < kpar) {
+                    if (j & 1) {
+                        const float xi = u01(ray_block(p.seed, key.x, key.y, pid.z * 16u + first, key.z).y);
+                        e = (1.f - xi) * esee;        // cos^2(beta_1) E_SEE at beta_2 = pi/2 - beta_1
+                        sb2 = 1.f - xi;
+                    } else {
+                        e = esee * sqrtf(sb2);        // E_SEE sqrt(xi) at beta_1 = asin(sqrt(xi))
+                    }
+                }
+            } else {
+                e = sample_energy(em, u01(w.x));
+            }
+            const float3 dd = cosine_dir(make_float3(s_nx[par], s_ny[par], s_nz[par]), sb2, u01(w.z));
             const unsigned slot = base + s;
             if (slot < out.cap) {
                 out.oe[slot] = make_float4(s_px[par], s_py[par], s_pz[par], e);
@@ -710,9 +785,15 @@ cudaError_t launch_shade(const DeviceMesh& m, const RunParams& p, const TableDes
 {
     const int nb = 1 - buf;
     const ShadeOut out{q.oe[nb], q.dt[nb], q.id[nb], q.cap[nb]};
-    const size_t smem = (size_t)(p.n_ebins + p.n_abins) * sizeof(unsigned);
+    const size_t smem = (size_t)(p.n_ebins + p.n_abins + p.n_zbins) * sizeof(unsigned);
     const int blocks = num_sms * 4;
     const ItemCtx ic{};
+    if (smem > kShadeDefaultSmem) {
+        // up to 3 x 4096 bins: past the default dynamic shared-memory limit
+        cudaError_t e = cudaFuncSetAttribute(record ? k_shade<true, false> : k_shade<false, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
     if (record)
         k_shade<true, false><<<blocks, kShadeThreads, smem, s>>>(m.tris, m.normals, tab, em, p, ic, q.oe[buf],
                                                                  q.dt[buf], q.id[buf], q.hits, q.wraps, out, q.ctl,
@@ -771,7 +852,7 @@ cudaError_t launch_shade_items(const DeviceMesh& m, const RunParams& p, const Ta
 {
     const int nb = 1 - buf;
     const ShadeOut out{q.oe[nb], q.dt[nb], q.id[nb], q.cap[nb]};
-    const size_t smem = (size_t)kChunkItems * (p.n_ebins + p.n_abins) * sizeof(unsigned);
+    const size_t smem = (size_t)kChunkItems * (p.n_ebins + p.n_abins + p.n_zbins) * sizeof(unsigned);
     k_shade<false, true><<<num_sms * 4, kShadeThreads, smem, s>>>(m.tris, m.normals, tab, em, p, ic, q.oe[buf],
                                                                   q.dt[buf], q.id[buf], q.hits, q.wraps, out, q.ctl,
                                                                   gen, q.cap[buf], q.tally, nullptr, nullptr, q.kcount,

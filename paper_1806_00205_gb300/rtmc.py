@@ -48,7 +48,8 @@ class Grid(C.Structure):
 
 class EmissionC(C.Structure):
     _fields_ = [("phi_ev", C.c_double), ("e_cut_ev", C.c_double), ("absorb_min_ev", C.c_double),
-                ("regen_min_ev", C.c_double), ("max_generation", C.c_int32), ("k_max", C.c_int32)]
+                ("regen_min_ev", C.c_double), ("max_generation", C.c_int32), ("k_max", C.c_int32),
+                ("model", C.c_int32)]
 
 
 class RunDesc(C.Structure):
@@ -59,6 +60,7 @@ class RunDesc(C.Structure):
                 ("prim_hash", C.c_void_p), ("profile", C.c_int32), ("count_visits", C.c_int32),
                 ("traversal", C.c_int32), ("fp64_retest", C.c_int32), ("item_base", C.c_uint32),
                 ("no_graph", C.c_int32), ("stack_depth", C.c_int32), ("fetch_threshold", C.c_int32),
+                ("random_polar", C.c_int32), ("n_zbins", C.c_int32), ("hist_z", C.c_void_p),
                 ("id_order", C.c_int32)]
 
 
@@ -148,23 +150,58 @@ class Emission:
     regen_min_ev: float = float("inf")
     max_generation: int = 1
     k_max: int = 15
+    model: int = 0                  # EMISSION_TABLE or EMISSION_PAPER_FIT
+
+
+EMISSION_TABLE, EMISSION_PAPER_FIT = 0, 1
+
+
+def paper_emission(e_c_ev=10.0, max_generation=6):
+    """The paper's emission rules (Eq. 6 and Eq. 7, stochastic rounding, the
+    two-daughter split) with re-emission above E_c = phi + E_F."""
+    return Emission(absorb_min_ev=e_c_ev, regen_min_ev=e_c_ev, max_generation=max_generation,
+                    model=EMISSION_PAPER_FIT)
 
 
 def run_desc(n_ebins=64, n_abins=18, hist_e_max_ev=50.0, primary_offset=0, random_azimuth=False,
              max_wraps=1024, window=None, chunk=0, block_threads=0, blocks_per_sm=0, prim_hash=None,
              profile=False, count_visits=False, traversal=0, fp64_retest=False, item_base=0, no_graph=False,
-             stack_depth=0, fetch_threshold=0, id_order=False):
+             stack_depth=0, fetch_threshold=0, id_order=False, random_polar=False, n_zbins=0):
+    """Run descriptor.  ``random_polar`` draws each primary's polar angle from
+    the cosine law (the item angle is ignored); ``n_zbins`` > 0 adds the
+    penetration-depth histogram, returned as ``hist_z`` in each result dict
+    (the binding owns that buffer; ``hist_z`` is filled in per call)."""
     x0, x1, y0, y1 = window if window is not None else (0.0, 0.0, 0.0, 0.0)
-    return RunDesc(int(n_ebins), int(n_abins), float(hist_e_max_ev), int(primary_offset),
-                   int(bool(random_azimuth)), int(max_wraps), x0, x1, y0, y1, int(chunk), int(block_threads),
-                   int(blocks_per_sm), prim_hash.data_ptr() if prim_hash is not None else None,
-                   int(bool(profile)), int(bool(count_visits)), int(traversal), int(bool(fp64_retest)),
-                   int(item_base), int(bool(no_graph)), int(stack_depth), int(fetch_threshold),
-                   int(bool(id_order)))
+    return RunDesc(n_ebins=int(n_ebins), n_abins=int(n_abins), hist_e_max_ev=float(hist_e_max_ev),
+                   primary_offset=int(primary_offset), random_azimuth=int(bool(random_azimuth)),
+                   max_wraps=int(max_wraps), src_x0=x0, src_x1=x1, src_y0=y0, src_y1=y1, chunk=int(chunk),
+                   block_threads=int(block_threads), blocks_per_sm=int(blocks_per_sm),
+                   prim_hash=prim_hash.data_ptr() if prim_hash is not None else None,
+                   profile=int(bool(profile)), count_visits=int(bool(count_visits)), traversal=int(traversal),
+                   fp64_retest=int(bool(fp64_retest)), item_base=int(item_base), no_graph=int(bool(no_graph)),
+                   stack_depth=int(stack_depth), fetch_threshold=int(fetch_threshold),
+                   random_polar=int(bool(random_polar)), n_zbins=int(n_zbins), hist_z=None,
+                   id_order=int(bool(id_order)))
+
+
+def _with_hist_z(desc, n_items):
+    """A copy of ``desc`` whose hist_z points at a fresh [n_items, n_zbins] array."""
+    d = RunDesc.from_buffer_copy(desc)
+    hz = np.zeros((n_items, max(d.n_zbins, 0)), dtype=np.uint64)
+    d.hist_z = hz.ctypes.data if d.n_zbins > 0 else None
+    return d, hz
 
 
 def result_dict(r: Result):
     return {name: getattr(r, name) for name, _ in Result._fields_}
+
+
+def _results(out, hz, n_zbins):
+    res = [result_dict(r) for r in out]
+    if n_zbins > 0:
+        for k, r in enumerate(res):
+            r["hist_z"] = hz[k]
+    return res
 
 
 class Context:
@@ -221,7 +258,8 @@ class Context:
         em = emission or Emission()
         delta = np.ascontiguousarray(table.delta, dtype=np.float32)
         g = Grid(table.n_e, table.n_theta, table.e_lo_ev, table.e_hi_ev, table.theta_step_deg)
-        e = EmissionC(em.phi_ev, em.e_cut_ev, em.absorb_min_ev, em.regen_min_ev, em.max_generation, em.k_max)
+        e = EmissionC(em.phi_ev, em.e_cut_ev, em.absorb_min_ev, em.regen_min_ev, em.max_generation, em.k_max,
+                      em.model)
         self._check(self._L.rtmc_load_see_tables(self.h, _ptr(delta), C.byref(g), C.byref(e)))
 
     def build_bvh(self, mesh_id: int, kind: int = BVH_FP32, leaf: int = 0):
@@ -231,18 +269,18 @@ class Context:
         """All (energy, angle) items; returns (results list, hist_e [items, nE], hist_a [items, nA])."""
         e = np.ascontiguousarray(np.atleast_1d(energies), dtype=np.float64)
         t = np.ascontiguousarray(np.atleast_1d(thetas), dtype=np.float64)
-        d = desc or run_desc()
         n_items = e.size * t.size
+        d, hz = _with_hist_z(desc or run_desc(), n_items)
         out = (Result * n_items)()
         he = np.zeros((n_items, d.n_ebins), dtype=np.uint64)
         ha = np.zeros((n_items, d.n_abins), dtype=np.uint64)
         self._check(self._L.rtmc_run(self.h, int(mesh_id), e.ctypes.data_as(C.POINTER(C.c_double)), e.size,
                                      t.ctypes.data_as(C.POINTER(C.c_double)), t.size, int(n_primaries),
                                      int(seed), C.byref(d), out, _ptr(he), _ptr(ha)))
-        return [result_dict(r) for r in out], he, ha
+        return _results(out, hz, d.n_zbins), he, ha
 
     def run_records(self, mesh_id, energy, theta, n_primaries, seed, item=0, desc=None, rec_cap=None):
-        d = desc or run_desc()
+        d, hz = _with_hist_z(desc or run_desc(), 1)
         cap = int(rec_cap) if rec_cap else int(n_primaries) * 40 + 1024
         rec = np.zeros(cap, dtype=RECORD_DTYPE)
         res = Result()
@@ -251,6 +289,8 @@ class Context:
                                              int(n_primaries), int(seed), C.byref(d), C.byref(res), _ptr(rec),
                                              cap, C.byref(n)))
         out = result_dict(res)
+        if d.n_zbins > 0:
+            out["hist_z"] = hz[0]
         out["records"] = np.sort(rec[:n.value], order=["prim", "gen", "path"])
         return out
 
@@ -259,28 +299,28 @@ class Context:
         ids = np.ascontiguousarray(np.atleast_1d(mesh_ids), dtype=np.int32)
         e = np.ascontiguousarray(np.atleast_1d(energies), dtype=np.float64)
         t = np.ascontiguousarray(np.atleast_1d(thetas), dtype=np.float64)
-        d = desc or run_desc()
+        n_items = ids.size * e.size * t.size
+        d, hz = _with_hist_z(desc or run_desc(), n_items)
         b = Batch(ids.ctypes.data_as(C.POINTER(C.c_int32)), ids.size, e.ctypes.data_as(C.POINTER(C.c_double)),
                   e.size, t.ctypes.data_as(C.POINTER(C.c_double)), t.size, int(n_primaries), int(seed))
-        n_items = ids.size * e.size * t.size
         out = (Result * n_items)()
         he = np.zeros((n_items, d.n_ebins), dtype=np.uint64)
         ha = np.zeros((n_items, d.n_abins), dtype=np.uint64)
         self._check(self._L.rtmc_run_batch(self.h, C.byref(b), C.byref(d), out, _ptr(he), _ptr(ha)))
-        return [result_dict(r) for r in out], he, ha
+        return _results(out, hz, d.n_zbins), he, ha
 
     def run_noalloc(self, mesh_id, energy, theta, n_primaries, seed, item=0, desc=None):
         """One item through rtmc_run_noalloc (static device scratch, no allocation).
 
         Returns (result dict, hist_e, hist_a)."""
-        d = desc or run_desc()
+        d, hz = _with_hist_z(desc or run_desc(), 1)
         res = Result()
         he = np.zeros(d.n_ebins, dtype=np.uint64)
         ha = np.zeros(d.n_abins, dtype=np.uint64)
         self._check(self._L.rtmc_run_noalloc(self.h, int(mesh_id), float(energy), float(theta), int(item),
                                              int(n_primaries), int(seed), C.byref(d), C.byref(res), _ptr(he),
                                              _ptr(ha)))
-        return result_dict(res), he, ha
+        return _results([res], hz, d.n_zbins)[0], he, ha
 
     def trace_rays(self, mesh_id, o, d, skip=None):
         o = np.ascontiguousarray(o, dtype=np.float32)

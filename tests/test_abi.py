@@ -2,6 +2,7 @@
 declared entry point; host-only helpers behave as documented."""
 import os
 import re
+import ctypes as C
 import subprocess
 
 import numpy as np
@@ -69,3 +70,33 @@ def test_create_without_gpu_fails_cleanly(lib_path):
     from paper_1806_00205_gb300 import rtmc
     with pytest.raises(rtmc.RtmcError):
         rtmc.Context(0)
+
+
+def test_binding_struct_layouts_match_the_header(tmp_path):
+    """Every ctypes mirror has the C struct's size and field offsets (gcc, host only)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    from paper_1806_00205_gb300 import rtmc
+    pairs = [("rtmc_box", rtmc.Box), ("rtmc_grid", rtmc.Grid), ("rtmc_emission", rtmc.EmissionC),
+             ("rtmc_run_desc", rtmc.RunDesc), ("rtmc_batch", rtmc.Batch), ("rtmc_result", rtmc.Result),
+             ("rtmc_record", rtmc.Record)]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rtmc.h"', 'int main(void) {']
+    for cname, py in pairs:
+        lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ['return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        s, f, v = line.split()
+        got[(s, f)] = int(v)
+    for cname, py in pairs:
+        assert got[(cname, "sizeof")] == C.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)

@@ -45,6 +45,24 @@ def test_batch_items_equal_plain_runs(setup):
             assert np.array_equal(he[mi * per_mesh + j], phe[j]) and np.array_equal(ha[mi * per_mesh + j], pha[j])
 
 
+def test_batch_random_incidence_depth_profile_equals_plain_runs(setup):
+    ctx, ids, rtmc = setup
+    energies, thetas, n = [150.0, 900.0], [0.0], 25_000
+    desc = rtmc.run_desc(random_polar=True, n_zbins=48, chunk=30_000)
+    res, he, _ = ctx.run_batch(ids, energies, thetas, n, 31, desc=desc)
+    per_mesh = len(energies) * len(thetas)
+    for mi, mid in enumerate(ids):
+        plain, phe, _ = ctx.run(mid, energies, thetas, n, 31,
+                                desc=rtmc.run_desc(random_polar=True, n_zbins=48, item_base=mi * per_mesh))
+        for j in range(per_mesh):
+            b = res[mi * per_mesh + j]
+            for k in INT_KEYS:
+                assert b[k] == plain[j][k], (mi, j, k, b[k], plain[j][k])
+            assert np.array_equal(b["hist_z"], plain[j]["hist_z"])
+            assert b["hist_z"].sum() == b["emitters"] + b["absorbed_low"] + b["absorbed_other"]
+            assert np.array_equal(he[mi * per_mesh + j], phe[j])
+
+
 def test_batch_graph_replay_equals_eager(setup):
     ctx, ids, rtmc = setup
     args = (ids, [100.0, 700.0], [0.0, 60.0], 20_000, 5)

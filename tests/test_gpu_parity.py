@@ -321,3 +321,40 @@ def test_gibson_ashby_cage_records_match_oracle(ctx):
     # most primaries reach the substrate through the open cage, so the yield is near the flat value
     flat = float(I.lin_joy_delta(600.0, 0.0))
     assert 0.6 * flat < g["sey"] < 1.05 * flat
+
+
+def test_random_incidence_and_depth_profile_match_oracle(ctx, tiny):
+    """Cosine-law incidence and the penetration-depth tally, record by record."""
+    from paper_1806_00205_gb300 import rtmc
+    mesh, mid = tiny
+    n, nz = 20_000, 64
+    g = ctx.run_records(mid, 300.0, 0.0, n, seed=21, item=2,
+                        desc=rtmc.run_desc(random_polar=True, n_zbins=nz))
+    o = O.run(mesh, TABLE, 300.0, 0.0, n, seed=21, item=2, random_polar=True, n_zbins=nz, records=True)
+    st = compare_records(g["records"], o["records"])
+    assert st["frac_same"] >= 0.9999, {k: v for k, v in st.items() if k != "mismatch"}
+    hz, oz = g["hist_z"].astype(np.int64), o["hist_z"]
+    stops = g["emitters"] + g["absorbed_low"] + g["absorbed_other"]
+    assert hz.sum() == stops
+    # FP32 and FP64 hit points can fall on either side of a bin edge, rarely
+    assert np.abs(hz - oz).sum() <= max(4, int(2e-4 * stops)), (hz, oz)
+
+
+def test_depth_profile_normal_vs_random_incidence(ctx):
+    """Section 3.2 on a 4 % solid foam (Fig. pen, 100 eV): normal-incidence
+    electrons stop deeper than random-incidence ones."""
+    from paper_1806_00205_gb300 import rtmc
+    mesh = I.grf_foam(32, 0.96)
+    mid = _mesh_id(ctx, mesh)
+    box = mesh.box
+    nz, n = 64, 500_000
+    c = (np.arange(nz) + 0.5) * (box.z_top - box.z_min) / nz
+    depth = {}
+    for polar in (False, True):
+        r, _, _ = ctx.run(mid, [100.0], [0.0], n, 9, desc=rtmc.run_desc(random_polar=polar, n_zbins=nz))
+        hz = r[0]["hist_z"].astype(np.float64)
+        mean = (hz * c).sum() / hz.sum()
+        se = math.sqrt(((hz * c * c).sum() / hz.sum() - mean * mean) / hz.sum())
+        depth[polar] = (mean, se)
+    (dn, sn), (dr, sr) = depth[False], depth[True]
+    assert dn - dr > 5.0 * math.hypot(sn, sr), depth

@@ -341,3 +341,185 @@ def test_paper_yield_fit_peak():
     g = I.paper_delta(e, 0.0)
     assert abs(g.max() - 1.49) < 0.005
     assert 380 < e[np.argmax(g)] < 450
+
+
+# ------------------------------------------ random incidence and depth --
+
+def test_random_incidence_is_cosine_law():
+    """Reading R14: an isotropic beam crossing the top plane has cos^2(theta) uniform on (0, 1).
+
+    On a flat plane a primary that does not wrap hits after t = h / cos(theta);
+    a thin slab (h = 0.1 nm over a 160 nm cell) keeps wraps rare."""
+    h = 0.1
+    fp = I.flat_plane(160.0, height=h)
+    n = 20000
+    r = O.run(fp, TABLE, E47, 37.0, n, seed=77, random_polar=True, records=True)
+    rec = r["records"]
+    prim = rec[rec["gen"] == 0]
+    assert prim.size == n and np.all(prim["fate"] == O.EMITTER)
+    direct = prim[prim["wraps"] == 0]
+    assert direct.size > 0.99 * n
+    c2 = (h / direct["t"]) ** 2
+    assert stats.kstest(c2, "uniform").pvalue > 1e-3
+    # a mistaken law (cos theta uniform, or theta uniform) is far off: mean cos theta is 2/3 here
+    assert abs(np.mean(np.sqrt(c2)) - 2.0 / 3.0) < 0.01
+
+
+def test_random_incidence_flat_yield():
+    """Flat plane, cosine-law incidence: E[SEY] = int_0^{pi/2} delta(E, theta) sin(2 theta) d theta.
+
+    At a grid energy delta is linear in theta between the 5-degree nodes and
+    constant past 85 degrees (the table's last node)."""
+    fp = I.flat_plane(160.0)
+    r = O.run(fp, TABLE, E47, 0.0, 400000, seed=4242, random_polar=True)
+    th = np.radians(5.0 * np.arange(TABLE.delta.shape[1]))
+    row = TABLE.delta[47].astype(np.float64)
+    expect = integrate.quad(lambda a: np.interp(a, th, row) * math.sin(2.0 * a), 0.0, math.pi / 2,
+                            points=list(th[1:]), limit=200)[0]
+    assert r["lost"] == 0 and r["escaped"] == r["emitted"]
+    assert abs(r["sey"] - expect) < 3.0 * r["sey_se"], (r["sey"], expect, r["sey_se"])
+    # differs from normal incidence by far more than the error
+    assert r["sey"] - float(row[0]) > 10.0 * r["sey_se"]
+
+
+def test_depth_tally_flat_plane():
+    """Reading R15: every primary stops on the plane, 10 nm below z_top (box 170 nm deep, 16 bins)."""
+    fp = I.flat_plane(160.0)
+    n = 20000
+    for polar in (False, True):
+        r = O.run(fp, TABLE, E47, 30.0, n, seed=5, random_polar=polar, n_zbins=16)
+        hz = r["hist_z"]
+        assert hz[0] == n and hz.sum() == n == r["emitters"]
+
+
+def test_depth_tally_square_well_view_factors():
+    """Depth profile in a square well with absorbing walls.
+
+    Cosine-law emission from the uniformly lit a x a floor crosses the
+    coaxial square at height z with probability F(a/z) (parallel-squares view
+    factor), so the walls between heights z1 < z2 take F(a/z1) - F(a/z2) of
+    the daughters and the opening passes F(a/h).  Each primary stops on the
+    floor at depth z_top - 0."""
+    a, hw, nz = 100.0, 100.0, 40
+    well = I.square_well(a, hw)
+    box = well.box
+    n = 200000
+    r = O.run(well, TABLE, E47, 0.0, n, seed=8, window=I.opening_window(a), n_zbins=nz)
+    hz = r["hist_z"].astype(np.int64)
+    assert hz.sum() == r["emitters"] + r["absorbed_low"] + r["absorbed_other"]
+    dz = (box.z_top - box.z_min) / nz
+    floor_bin = int((box.z_top - 0.0) // dz)
+
+    def cross(z):                       # fraction of floor emission passing height z
+        return 1.0 if z <= 0.0 else view_factor_squares(a / z)
+
+    p = np.zeros(nz)
+    for b in range(nz):
+        z_hi = min(hw, box.z_top - b * dz)
+        z_lo = max(0.0, box.z_top - (b + 1) * dz)
+        if z_hi > z_lo:
+            p[b] = cross(z_lo) - cross(z_hi)
+    walls = hz.copy()
+    walls[floor_bin] -= n
+    assert walls[floor_bin] >= 0 and np.all(walls[p == 0.0] == 0)
+    nd = r["emitted"]
+    assert walls.sum() + r["escaped"] == nd
+    obs = np.append(walls[p > 0], r["escaped"])
+    exp = np.append(p[p > 0], cross(hw)) * nd
+    assert abs(exp.sum() - nd) < 1e-6 * nd
+    assert stats.chisquare(obs, exp).pvalue > 1e-3
+
+
+# ------------------------------------------------- paper-fit emission --
+
+PAPER = O.paper_emission()
+
+
+def test_paper_fit_peak_matches_printed_value():
+    """Section 3.1 prints a maximum flat-tungsten yield of about 1.49; Eq. 6 at
+    normal incidence (alpha in degrees, reading R16) peaks there near 416 eV."""
+    e = np.arange(100.0, 1500.0, 0.5)
+    g = np.array([O.gamma_fit(x, 0.0) for x in e])
+    assert abs(g.max() - 1.49) < 0.005
+    assert 380.0 < e[g.argmax()] < 450.0
+
+
+def test_stochastic_rounding_footnote_example():
+    """Section 2.2 footnote: gamma = 1.2 rounds down when xi >= 0.2, up otherwise."""
+    assert O.round_stochastic(1.2, 0.25) == (1, 0)
+    assert O.round_stochastic(1.2, 0.15) == (2, 0)
+    assert O.round_stochastic(-0.3, 0.01) == (0, 0)
+    assert O.round_stochastic(16.5, 0.9) == (15, 1)
+
+
+@pytest.mark.parametrize("energy,theta", [(416.0, 0.0), (150.0, 40.0), (1200.0, 75.0)])
+def test_paper_fit_flat_plane_yield_is_gamma(energy, theta):
+    """On a flat surface every daughter escapes, so E[SEY] = gamma(E, theta)
+    and the count variance is f (1 - f), f = frac(gamma) (not Poisson's gamma)."""
+    fp = I.flat_plane(160.0)
+    n = 200000
+    r = O.run(fp, TABLE, energy, theta, n, seed=3, emission=PAPER)
+    g = O.gamma_fit(energy, theta)
+    f = g - math.floor(g)
+    assert r["lost"] == 0 and r["escaped"] == r["emitted"] == r["sum_k"]
+    assert r["absorbed_low"] == 0 and r["absorbed_other"] == 0
+    assert abs(r["sey"] - g) < 3.5 * math.sqrt(f * (1 - f) / n) + 1e-9
+    var = r["sey_se"] ** 2 * n
+    assert abs(var - f * (1 - f)) < 0.02 * f * (1 - f) + 1e-6
+
+
+def test_paper_fit_pair_rule_on_flat_plane():
+    """Two daughters of one emission (Section 2.2): beta_2 = pi/2 - beta_1, so
+    cos^2(beta_1) + cos^2(beta_2) = 1, with E_1 = E_SEE sin(beta_1) and
+    E_2 = E_SEE cos^2(beta_1); a single daughter carries E_SEE.  On a thin flat
+    slab an escaping daughter that does not wrap travels t = h / cos(beta)."""
+    h = 0.1
+    fp = I.flat_plane(160.0, height=h)
+    energy, theta = 1200.0, 60.0                    # gamma about 1.5: one or two daughters
+    esee = O.esee_fit(energy, theta)
+    r = O.run(fp, TABLE, energy, theta, 20000, seed=19, emission=PAPER, records=True)
+    rec = r["records"]
+    d = rec[rec["gen"] == 1]
+    assert np.all(d["fate"] == O.ESCAPED)
+    k = np.bincount(d["prim"].astype(np.int64), minlength=20000)
+    pairs = np.flatnonzero(k == 2)
+    singles = np.flatnonzero(k == 1)
+    assert pairs.size > 4000 and singles.size > 4000
+    by_prim = {}
+    for row in d:
+        by_prim.setdefault(int(row["prim"]), {})[int(row["path"]) - 16] = row
+    checked = 0
+    for p in pairs[:3000]:
+        a, b = by_prim[p][0], by_prim[p][1]
+        if a["wraps"] or b["wraps"]:
+            continue
+        c1, c2 = h / a["t"], h / b["t"]
+        assert abs(c1 * c1 + c2 * c2 - 1.0) < 1e-6
+        s1 = math.sqrt(max(0.0, 1.0 - c1 * c1))
+        assert abs(a["energy"] - esee * s1) < 1e-6 * esee
+        assert abs(b["energy"] - esee * c1 * c1) < 1e-6 * esee
+        checked += 1
+    assert checked > 2500
+    one = np.array([by_prim[p][0]["energy"] for p in singles])
+    assert np.all(np.abs(one - esee) < 1e-9 * esee)
+    c2s = np.array([(h / by_prim[p][0]["t"]) ** 2 for p in singles if not by_prim[p][0]["wraps"]])
+    assert stats.kstest(c2s, "uniform").pvalue > 1e-3       # unpaired: cosine law
+
+
+def test_paper_fit_foam_generations_and_conservation():
+    """Unbounded generations above E_c on a 4 % solid foam: the energy falls
+    each generation, trees end well before the 6-generation path limit, and
+    every ray is accounted for."""
+    mesh = I.grf_foam(24, 0.96)
+    n = 6000
+    r = O.run(mesh, TABLE, 2000.0, 0.0, n, seed=4, emission=PAPER, records=True)
+    rec = r["records"]
+    assert r["rays"] == n + r["emitted"] == rec.size
+    assert r["rays"] == (r["escaped"] + r["absorbed_low"] + r["absorbed_other"] + r["emitters"] + r["lost"])
+    assert r["regenerated"] > 0 and rec["gen"].max() < 6
+    mean_e = [rec["energy"][rec["gen"] == g].mean() for g in range(rec["gen"].max() + 1)]
+    assert all(b < a for a, b in zip(mean_e, mean_e[1:])), mean_e
+    # a ray re-emits exactly when it is below the cap and at or above E_c
+    hit = rec[(rec["fate"] != O.ESCAPED) & (rec["fate"] != O.LOST)]
+    emit = hit["fate"] == O.EMITTER
+    assert np.array_equal(emit, (hit["gen"] == 0) | (hit["energy"] >= PAPER.regen_min_ev))

@@ -48,6 +48,17 @@ def test_noalloc_equals_run_on_two_calls(setup):
         assert got["rays"] > n
 
 
+def test_noalloc_random_incidence_depth_profile_equals_run(setup):
+    ctx, mid, rtmc = setup
+    n = 3000
+    desc = rtmc.run_desc(random_polar=True, n_zbins=100)
+    ref, _, _ = ctx.run(mid, [250.0], [0.0], n, 17, desc=desc)
+    got, _, _ = ctx.run_noalloc(mid, 250.0, 0.0, n, 17, desc=desc)
+    for k in INT_KEYS:
+        assert got[k] == ref[0][k], (k, got[k], ref[0][k])
+    assert np.array_equal(got["hist_z"], ref[0]["hist_z"]) and got["hist_z"].sum() > n
+
+
 def test_noalloc_hash_equals_run_hash(setup):
     import torch
     ctx, mid, rtmc = setup
