@@ -400,7 +400,11 @@ def run_ours(args):
     achieved = local_rays * b_ray / (trav_ms / 1e3) / 1e9
     pk, pk_kind = peaks()
     peak = float(pk.get("hbm_gbs", 6800.0))
-    traffic = measured_traffic()
+    rays_per_launch = local_rays / max(1, trav_launches)
+    traffic_per_ray = measured_traffic()
+    # DRAM bytes per traversal launch: the committed capture's bytes per ray (a
+    # smaller case of the same kernel) times the rays one launch of this run traces
+    traffic = traffic_per_ray * rays_per_launch if traffic_per_ray is not None else None
     l2_gbs = ctx.probe_bandwidth(32 << 20, 10)          # L2-resident streaming read (own probe)
     hbm_read_gbs = ctx.probe_bandwidth(4 << 30, 5)      # HBM streaming read (own probe)
 
@@ -462,6 +466,7 @@ def run_ours(args):
                          "peak_kind": f"{pk_kind} hbm_gbs", "bytes_per_ray": b_ray,
                          "node_visits_per_ray": visits, "tri_tests_per_ray": tests,
                          "traverse_ms_per_launch": trav_ms / max(1, trav_launches),
+                         "rays_per_launch": rays_per_launch, "traffic_bytes_per_ray": traffic_per_ray,
                          "l2_read_probe_gbs": l2_gbs, "frac_of_l2_read_probe": achieved / l2_gbs,
                          "hbm_read_probe_gbs": hbm_read_gbs},
             "e2e": {"value": e_rays / e_dt, "unit": "rays/s", "h2d_bytes_per_step": h2d,

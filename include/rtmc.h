@@ -46,6 +46,9 @@ extern "C" {
 #define RTMC_BVH_Q8   1     /* 32-byte nodes with 8-bit outward-rounded child boxes */
 /* bvh_kind = node format | RTMC_BVH_LEAF(n): leaves of up to n (1..8) triangles, default 4 */
 #define RTMC_BVH_LEAF(n) ((n) << 8)
+/* ... | RTMC_BVH_PLOC: build the hierarchy by locally-ordered clustering
+   (Meister & Bittner 2018) instead of the Karras split of the sorted codes */
+#define RTMC_BVH_PLOC (1 << 16)
 
 /* Ray fates (per-ray records) */
 #define RTMC_ESCAPED        0
@@ -177,7 +180,11 @@ int rtmc_load_see_tables(rtmc_ctx* ctx, const float* delta, const rtmc_grid* gri
    8 bits per coordinate in the node's own frame (origin + q 2^e, rounded
    outward).  `bvh_kind` is RTMC_BVH_FP32 or RTMC_BVH_Q8, optionally or-ed with
    RTMC_BVH_LEAF(n) to cap leaves at n triangles (subtrees with at most n
-   triangles become one leaf). */
+   triangles become one leaf).  With RTMC_BVH_PLOC the hierarchy comes from
+   locally-ordered clustering instead (Meister & Bittner 2018: mutually
+   nearest clusters by merged-box surface area within 16 positions of the
+   Morton order merge, round by round), rewritten into the same node layout;
+   it is deterministic and synchronises with the host once per round. */
 int rtmc_build_bvh(rtmc_ctx* ctx, int32_t mesh_id, int32_t bvh_kind);
 
 /* Run RTMC for every (energy, angle) pair: n_e * n_theta items, item

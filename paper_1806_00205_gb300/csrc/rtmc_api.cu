@@ -520,13 +520,14 @@ int rtmc_build_bvh(rtmc_ctx* ctx, int32_t mesh_id, int32_t bvh_kind)
     if (!ctx) return RTMC_ERR_INVALID_ARG;
     if (mesh_id < 0 || mesh_id >= (int)ctx->meshes.size() || !ctx->meshes[mesh_id].tri_in)
         return ctx->fail(RTMC_ERR_NOT_LOADED, "build_bvh: unknown mesh id");
-    const int format = bvh_kind & 0xFF, leaf = (bvh_kind >> 8) & 0xFF;
-    if ((format != RTMC_BVH_FP32 && format != RTMC_BVH_Q8) || (bvh_kind >> 16) != 0 || leaf > 8)
+    const int format = bvh_kind & 0xFF, leaf = (bvh_kind >> 8) & 0xFF, builder = bvh_kind >> 16;
+    if ((format != RTMC_BVH_FP32 && format != RTMC_BVH_Q8) || (builder != 0 && builder != 1) || leaf > 8)
         return ctx->fail(RTMC_ERR_INVALID_ARG, "build_bvh: unknown bvh kind or leaf size > 8");
     DeviceGuard g(ctx->device);
     DeviceMesh& m = ctx->meshes[mesh_id];
     m.kind = format;
     m.leaf_max = leaf ? leaf : 4;
+    m.ploc = builder == 1;
     return rtmc::build_lbvh(ctx, m);
 }
 

@@ -406,6 +406,237 @@ __global__ void k_depth(const int* __restrict__ parent, const int* __restrict__ 
     atomicMax(depth, d);
 }
 
+// ---- PLOC hierarchy (Meister & Bittner, "Parallel Locally-Ordered
+// Clustering for Bounding Volume Hierarchy Construction", TVCG 2018) --------
+// Clusters start as the Morton-sorted triangles.  Each round, every cluster
+// finds the neighbour within +-kPlocRadius positions whose union box has the
+// smallest surface area (ties: the lower position, which makes the choice a
+// total order on pairs, so the globally best pair is always mutual and every
+// round merges at least once); mutual pairs merge into a new node kept at the
+// lower position, and the surviving clusters are compacted in order.  Node
+// ids: leaves 0..n-1 (sorted positions), inner nodes n..2n-2 in creation
+// order, so the root is 2n-2.  The finished tree is rewritten into the Karras
+// layout the rest of the builder consumes (see k_ploc_emit).
+constexpr int kPlocRadius = 16;
+constexpr int kPlocBlock = 256;
+
+struct PlocState {
+    int count;      // clusters after the round
+    int created;    // inner nodes created so far
+};
+
+__device__ __forceinline__ float half_area(float3 lo, float3 hi)
+{
+    const float dx = hi.x - lo.x, dy = hi.y - lo.y, dz = hi.z - lo.z;
+    return dx * dy + dy * dz + dz * dx;
+}
+
+__global__ void k_ploc_init(const float* __restrict__ tri, const unsigned* __restrict__ sorted, int n,
+                            int* __restrict__ cl_node, float4* __restrict__ cl_lo, float4* __restrict__ cl_hi,
+                            int* __restrict__ cnt)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const Box3 b = tri_box(tri, sorted[i]);
+    cl_node[i] = i;
+    cl_lo[i] = make_float4(b.lo.x, b.lo.y, b.lo.z, 0.f);
+    cl_hi[i] = make_float4(b.hi.x, b.hi.y, b.hi.z, 0.f);
+    cnt[i] = 1;
+}
+
+__global__ void __launch_bounds__(kPlocBlock)
+k_ploc_nn(const float4* __restrict__ cl_lo, const float4* __restrict__ cl_hi, int c, int* __restrict__ nn)
+{
+    __shared__ float4 s_lo[kPlocBlock + 2 * kPlocRadius], s_hi[kPlocBlock + 2 * kPlocRadius];
+    const int b0 = blockIdx.x * kPlocBlock;
+    for (int t = threadIdx.x; t < kPlocBlock + 2 * kPlocRadius; t += kPlocBlock) {
+        const int g = b0 - kPlocRadius + t;
+        if (g >= 0 && g < c) { s_lo[t] = cl_lo[g]; s_hi[t] = cl_hi[g]; }
+    }
+    __syncthreads();
+    const int i = b0 + threadIdx.x;
+    if (i >= c) return;
+    const int li = threadIdx.x + kPlocRadius;
+    const float4 alo = s_lo[li], ahi = s_hi[li];
+    float best = INFINITY;
+    int bj = -1;
+    for (int dj = -kPlocRadius; dj <= kPlocRadius; ++dj) {
+        const int j = i + dj;
+        if (dj == 0 || j < 0 || j >= c) continue;
+        const float4 blo = s_lo[li + dj], bhi = s_hi[li + dj];
+        const float a = half_area(make_float3(fminf(alo.x, blo.x), fminf(alo.y, blo.y), fminf(alo.z, blo.z)),
+                                  make_float3(fmaxf(ahi.x, bhi.x), fmaxf(ahi.y, bhi.y), fmaxf(ahi.z, bhi.z)));
+        if (a < best) { best = a; bj = j; }       // increasing j: ties keep the lower position
+    }
+    nn[i] = bj;
+}
+
+// Per block: number of surviving clusters and of merges it starts.
+__device__ __forceinline__ void ploc_flags(const int* __restrict__ nn, int c, int i, bool& keep, bool& make)
+{
+    keep = false;
+    make = false;
+    if (i >= c) return;
+    const int j = nn[i];
+    const bool mutual = j >= 0 && nn[j] == i;
+    keep = !(mutual && j < i);        // the upper member of a mutual pair is absorbed
+    make = mutual && i < j;
+}
+
+__global__ void __launch_bounds__(kPlocBlock)
+k_ploc_count(const int* __restrict__ nn, int c, int2* __restrict__ block_counts)
+{
+    __shared__ int s_k[kPlocBlock / 32], s_m[kPlocBlock / 32];
+    const int i = blockIdx.x * kPlocBlock + threadIdx.x;
+    bool keep, make;
+    ploc_flags(nn, c, i, keep, make);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int k = __popc(__ballot_sync(0xFFFFFFFFu, keep)), m = __popc(__ballot_sync(0xFFFFFFFFu, make));
+    if (lane == 0) { s_k[w] = k; s_m[w] = m; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tk = 0, tm = 0;
+        for (int q = 0; q < kPlocBlock / 32; ++q) { tk += s_k[q]; tm += s_m[q]; }
+        block_counts[blockIdx.x] = make_int2(tk, tm);
+    }
+}
+
+// Exclusive scan of the per-block (keep, make) counts, one block; the totals
+// go to the state (new cluster count; inner nodes created).
+__global__ void k_ploc_scan(int2* __restrict__ block_counts, int n_blocks, PlocState* __restrict__ st)
+{
+    __shared__ int2 sums[1024];
+    const int per = (n_blocks + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int lo = threadIdx.x * per, hi = min(lo + per, n_blocks);
+    int2 s = make_int2(0, 0);
+    for (int b = lo; b < hi; ++b) { s.x += block_counts[b].x; s.y += block_counts[b].y; }
+    sums[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+        const int2 v = threadIdx.x >= (unsigned)off ? sums[threadIdx.x - off] : make_int2(0, 0);
+        __syncthreads();
+        sums[threadIdx.x].x += v.x;
+        sums[threadIdx.x].y += v.y;
+        __syncthreads();
+    }
+    int2 run = make_int2(sums[threadIdx.x].x - s.x, sums[threadIdx.x].y - s.y);
+    for (int b = lo; b < hi; ++b) {
+        const int2 v = block_counts[b];
+        block_counts[b] = run;
+        run.x += v.x;
+        run.y += v.y;
+    }
+    if (threadIdx.x == blockDim.x - 1) {
+        st->count = sums[threadIdx.x].x;
+        st->created += sums[threadIdx.x].y;
+    }
+}
+
+__global__ void __launch_bounds__(kPlocBlock)
+k_ploc_merge(const int* __restrict__ nn, int c, const int2* __restrict__ block_off, int first_id,
+             const int* __restrict__ cl_node, const float4* __restrict__ cl_lo, const float4* __restrict__ cl_hi,
+             int* __restrict__ out_node, float4* __restrict__ out_lo, float4* __restrict__ out_hi,
+             int2* __restrict__ kids, int* __restrict__ parent, int* __restrict__ cnt)
+{
+    __shared__ int s_k[kPlocBlock / 32], s_m[kPlocBlock / 32];
+    const int i = blockIdx.x * kPlocBlock + threadIdx.x;
+    bool keep, make;
+    ploc_flags(nn, c, i, keep, make);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned bk = __ballot_sync(0xFFFFFFFFu, keep), bm = __ballot_sync(0xFFFFFFFFu, make);
+    if (lane == 0) { s_k[w] = __popc(bk); s_m[w] = __popc(bm); }
+    __syncthreads();
+    int ok = block_off[blockIdx.x].x, om = block_off[blockIdx.x].y;
+    for (int q = 0; q < w; ++q) { ok += s_k[q]; om += s_m[q]; }
+    const unsigned lt = (1u << lane) - 1u;
+    ok += __popc(bk & lt);
+    om += __popc(bm & lt);
+    if (!keep) return;
+    if (make) {
+        const int j = nn[i];
+        const int a = cl_node[i], b = cl_node[j], id = first_id + om;
+        const float4 alo = cl_lo[i], ahi = cl_hi[i], blo = cl_lo[j], bhi = cl_hi[j];
+        kids[id] = make_int2(a, b);               // lower position on the left: leaves stay in Morton order
+        parent[a] = id;
+        parent[b] = id;
+        cnt[id] = cnt[a] + cnt[b];
+        out_node[ok] = id;
+        out_lo[ok] = make_float4(fminf(alo.x, blo.x), fminf(alo.y, blo.y), fminf(alo.z, blo.z), 0.f);
+        out_hi[ok] = make_float4(fmaxf(ahi.x, bhi.x), fmaxf(ahi.y, bhi.y), fmaxf(ahi.z, bhi.z), 0.f);
+    } else {
+        out_node[ok] = cl_node[i];
+        out_lo[ok] = cl_lo[i];
+        out_hi[ok] = cl_hi[i];
+    }
+}
+
+// First leaf position (depth-first, left to right) of every node: the sum of
+// the left-sibling counts along the path to the root.  The climb is bounded;
+// a longer path sets *bad.
+__global__ void k_ploc_first(const int2* __restrict__ kids, const int* __restrict__ parent,
+                             const int* __restrict__ cnt, int n_all, int root, int* __restrict__ first,
+                             int* __restrict__ bad)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n_all) return;
+    int lo = 0, x = v, steps = 0;
+    while (x != root) {
+        const int p = parent[x];
+        const int2 k = kids[p];
+        if (x == k.y) lo += cnt[k.x];
+        x = p;
+        if (++steps > 4096) { atomicExch(bad, 1); break; }
+    }
+    first[v] = lo;
+}
+
+// Rewrite into the Karras layout: leaves by depth-first position; an inner
+// node with leaf range [lo, hi] gets index hi if it is a left child, lo if it
+// is a right child, 0 if it is the root.  For any binary tree these indices
+// are distinct and fill [0, n-2], and the children of index g are g and g+1
+// (as leaves or inner nodes) -- the Karras (HPG 2012) numbering, which the
+// refit, the Q8 quantiser and the traversal rely on.
+__device__ __forceinline__ int karras_index(const int2* __restrict__ kids, const int* __restrict__ parent,
+                                            const int* __restrict__ cnt, const int* __restrict__ first,
+                                            int v, int root)
+{
+    if (v == root) return 0;
+    const int p = parent[v];
+    return kids[p].x == v ? first[v] + cnt[v] - 1 : first[v];
+}
+
+__global__ void k_ploc_emit(const int2* __restrict__ kids, const int* __restrict__ parent_all,
+                            const int* __restrict__ cnt, const int* __restrict__ first,
+                            const unsigned* __restrict__ sorted, int n, int root,
+                            int2* __restrict__ child, int2* __restrict__ range, int* __restrict__ parent,
+                            int* __restrict__ leaf_parent, unsigned* __restrict__ order)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) {                                   // leaf: its triangle at its depth-first position
+        order[first[v]] = sorted[v];
+        return;
+    }
+    if (v >= 2 * n - 1) return;
+    const int g = karras_index(kids, parent_all, cnt, first, v, root);
+    const int2 k = kids[v];
+    int ref[2];
+    const int cs[2] = {k.x, k.y};
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const int c = cs[s];
+        if (c < n) {
+            ref[s] = ~first[c];
+            leaf_parent[first[c]] = g;
+        } else {
+            ref[s] = karras_index(kids, parent_all, cnt, first, c, root);
+            parent[ref[s]] = g;
+        }
+    }
+    child[g] = make_int2(ref[0], ref[1]);
+    range[g] = make_int2(first[v], first[v] + cnt[v] - 1);
+    if (v == root) parent[0] = -1;
+}
+
 struct DevBuf {
     void* p = nullptr;
     ~DevBuf() { if (p) cudaFree(p); }
@@ -475,6 +706,66 @@ int build_lbvh(rtmc_ctx* ctx, DeviceMesh& m)
     }
     // after 4 passes the sorted data is back in (k0, v0)
     cudaMemsetAsync(depth.p, 0, 4, s);
+    const unsigned* order = vi;                  // leaf position -> triangle id
+    DevBuf ord;
+    if (n > 1 && m.ploc) {
+        const int n_all = 2 * n - 1;
+        const int max_blocks = (n + kPlocBlock - 1) / kPlocBlock;
+        DevBuf cn[2], clo[2], chi[2], nn, bc, kids, pall, cnt, first, st, bad;
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+            e = cn[b].alloc(4ull * n);
+            if (e == cudaSuccess) e = clo[b].alloc(16ull * n);
+            if (e == cudaSuccess) e = chi[b].alloc(16ull * n);
+        }
+        if (e == cudaSuccess) e = nn.alloc(4ull * n);
+        if (e == cudaSuccess) e = bc.alloc(8ull * max_blocks);
+        if (e == cudaSuccess) e = kids.alloc(8ull * n_all);
+        if (e == cudaSuccess) e = pall.alloc(4ull * n_all);
+        if (e == cudaSuccess) e = cnt.alloc(4ull * n_all);
+        if (e == cudaSuccess) e = first.alloc(4ull * n_all);
+        if (e == cudaSuccess) e = st.alloc(sizeof(PlocState));
+        if (e == cudaSuccess) e = bad.alloc(4);
+        if (e == cudaSuccess) e = ord.alloc(4ull * n);
+        if (e != cudaSuccess) return ctx->fail(RTMC_ERR_OOM, std::string("build_bvh (PLOC) scratch: ") + cudaGetErrorString(e));
+        k_ploc_init<<<gb, tb, 0, s>>>(m.tri_in, vi, n, cn[0].as<int>(), clo[0].as<float4>(), chi[0].as<float4>(),
+                                      cnt.as<int>());
+        cudaMemsetAsync(st.p, 0, sizeof(PlocState), s);
+        cudaMemsetAsync(bad.p, 0, 4, s);
+        int c = n, created = 0, cur = 0;
+        for (int round = 0; c > 1; ++round) {
+            if (round >= n) return ctx->fail(RTMC_ERR_DEVICE_CHECK, "build_bvh (PLOC): clustering made no progress");
+            const int nb = (c + kPlocBlock - 1) / kPlocBlock;
+            k_ploc_nn<<<nb, kPlocBlock, 0, s>>>(clo[cur].as<float4>(), chi[cur].as<float4>(), c, nn.as<int>());
+            k_ploc_count<<<nb, kPlocBlock, 0, s>>>(nn.as<int>(), c, bc.as<int2>());
+            k_ploc_scan<<<1, 1024, 0, s>>>(bc.as<int2>(), nb, st.as<PlocState>());
+            k_ploc_merge<<<nb, kPlocBlock, 0, s>>>(nn.as<int>(), c, bc.as<int2>(), n + created, cn[cur].as<int>(),
+                                                   clo[cur].as<float4>(), chi[cur].as<float4>(), cn[1 - cur].as<int>(),
+                                                   clo[1 - cur].as<float4>(), chi[1 - cur].as<float4>(),
+                                                   kids.as<int2>(), pall.as<int>(), cnt.as<int>());
+            PlocState h{};
+            e = cudaMemcpyAsync(&h, st.p, sizeof h, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return ctx->fail(RTMC_ERR_CUDA, std::string("build_bvh (PLOC): ") + cudaGetErrorString(e));
+            if (h.count >= c || h.created != n - h.count)
+                return ctx->fail(RTMC_ERR_DEVICE_CHECK, "build_bvh (PLOC): inconsistent cluster counts");
+            c = h.count;
+            created = h.created;
+            cur = 1 - cur;
+        }
+        const int root = n_all - 1;
+        const int ga = (n_all + tb - 1) / tb;
+        k_ploc_first<<<ga, tb, 0, s>>>(kids.as<int2>(), pall.as<int>(), cnt.as<int>(), n_all, root, first.as<int>(),
+                                       bad.as<int>());
+        k_ploc_emit<<<ga, tb, 0, s>>>(kids.as<int2>(), pall.as<int>(), cnt.as<int>(), first.as<int>(), vi, n, root,
+                                      child.as<int2>(), range.as<int2>(), parent.as<int>(), leafp.as<int>(),
+                                      ord.as<unsigned>());
+        int h_bad = 0;
+        e = cudaMemcpyAsync(&h_bad, bad.p, 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return ctx->fail(RTMC_ERR_CUDA, std::string("build_bvh (PLOC): ") + cudaGetErrorString(e));
+        if (h_bad) return ctx->fail(RTMC_ERR_DEVICE_CHECK, "build_bvh (PLOC): hierarchy too deep");
+        order = ord.as<unsigned>();
+    }
     if (n == 1) {
         k_single_leaf<<<1, 1, 0, s>>>(m.tri_in, m.nodes);
         if (m.kind == FMT_Q8) k_quantize_single<<<1, 1, 0, s>>>(m.tri_in, reinterpret_cast<uint4*>(m.q8));
@@ -483,16 +774,17 @@ int build_lbvh(rtmc_ctx* ctx, DeviceMesh& m)
     } else {
         cudaMemsetAsync(flag.p, 0, 4ull * n_nodes, s);
         const int gi = (n - 1 + tb - 1) / tb;
-        k_karras<<<gi, tb, 0, s>>>(ki, n, child.as<int2>(), range.as<int2>(), parent.as<int>(), leafp.as<int>());
-        k_refit<<<gb, tb, 0, s>>>(m.tri_in, vi, n, child.as<int2>(), range.as<int2>(), parent.as<int>(),
+        if (!m.ploc)
+            k_karras<<<gi, tb, 0, s>>>(ki, n, child.as<int2>(), range.as<int2>(), parent.as<int>(), leafp.as<int>());
+        k_refit<<<gb, tb, 0, s>>>(m.tri_in, order, n, child.as<int2>(), range.as<int2>(), parent.as<int>(),
                                   leafp.as<int>(), flag.as<unsigned>(), aabb.as<float4>(), m.nodes, m.leaf_max);
         k_depth<<<gb, tb, 0, s>>>(parent.as<int>(), leafp.as<int>(), n, depth.as<int>());
         if (m.kind == FMT_Q8)
-            k_quantize<<<gi, tb, 0, s>>>(m.tri_in, vi, n - 1, child.as<int2>(), range.as<int2>(), aabb.as<float4>(),
+            k_quantize<<<gi, tb, 0, s>>>(m.tri_in, order, n - 1, child.as<int2>(), range.as<int2>(), aabb.as<float4>(),
                                          m.leaf_max, reinterpret_cast<uint4*>(m.q8));
     }
     const int gp = (n + 1 + tb - 1) / tb;
-    k_pack<<<gp, tb, 0, s>>>(m.tri_in, vi, n, m.tris, m.normals, m.inv_order);
+    k_pack<<<gp, tb, 0, s>>>(m.tri_in, order, n, m.tris, m.normals, m.inv_order);
     int h_depth = 0;
     cudaMemcpyAsync(&h_depth, depth.p, 4, cudaMemcpyDeviceToHost, s);
     cudaEventRecord(ev1, s);

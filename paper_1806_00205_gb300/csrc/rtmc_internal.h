@@ -25,6 +25,7 @@ struct DeviceMesh {
     void* q8 = nullptr;            // n_nodes * 32 B quantised nodes (RTMC_BVH_Q8)
     int depth = 0;                 // hierarchy depth (root = 1)
     int leaf_max = 4;              // triangles per leaf (1..8)
+    bool ploc = false;             // hierarchy from locally-ordered clustering
     double build_ms = 0.0;
 };
 

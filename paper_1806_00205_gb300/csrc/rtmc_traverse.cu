@@ -340,7 +340,7 @@ constexpr float kEdgeEps = 1e-5f;
 constexpr float kGrazeCos = 1e-3f;
 
 template <int FMT, bool RECORD, bool COUNT, bool RETEST, int SSTACK>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 8)
 k_traverse_ww(const void* __restrict__ nodes, const float4* __restrict__ tris, const float4* __restrict__ normals,
               Cell cell, const float4* __restrict__ oe, const float4* __restrict__ dt, float4* __restrict__ hits,
               int* __restrict__ wraps_out, Control* __restrict__ ctl, int gen, unsigned cap,

@@ -29,6 +29,7 @@ EXPORTS = ["rtmc_create", "rtmc_destroy", "rtmc_last_error", "rtmc_load_mesh", "
            "rtmc_record_hash", "rtmc_run_noalloc", "rtmc_export_bvh", "rtmc_run_batch",
            "rtmc_probe_bandwidth"]
 NOALLOC_MAX_PRIMARIES = 4096
+BVH_PLOC = 1 << 16
 
 
 class RtmcError(RuntimeError):
@@ -262,8 +263,11 @@ class Context:
                       em.model)
         self._check(self._L.rtmc_load_see_tables(self.h, _ptr(delta), C.byref(g), C.byref(e)))
 
-    def build_bvh(self, mesh_id: int, kind: int = BVH_FP32, leaf: int = 0):
-        self._check(self._L.rtmc_build_bvh(self.h, int(mesh_id), int(kind) | (int(leaf) << 8)))
+    def build_bvh(self, mesh_id: int, kind: int = BVH_FP32, leaf: int = 0, ploc: bool = False):
+        """Build the mesh's BVH: node format `kind`, leaves of up to `leaf` triangles
+        (0: 4), hierarchy by Karras splits or (ploc=True) locally-ordered clustering."""
+        self._check(self._L.rtmc_build_bvh(self.h, int(mesh_id),
+                                           int(kind) | (int(leaf) << 8) | (BVH_PLOC if ploc else 0)))
 
     def run(self, mesh_id, energies, thetas, n_primaries, seed, desc: RunDesc | None = None):
         """All (energy, angle) items; returns (results list, hist_e [items, nE], hist_a [items, nA])."""

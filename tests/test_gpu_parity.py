@@ -82,15 +82,16 @@ def _rays_for(mesh, n, rng):
     return np.concatenate([o, o2]).astype(np.float32), np.concatenate([d, d2]).astype(np.float32)
 
 
-@pytest.mark.parametrize("kind,leaf", [(0, 4), (0, 1), (1, 4), (1, 8)])
+@pytest.mark.parametrize("kind,leaf,ploc", [(0, 4, False), (0, 1, False), (1, 4, False), (1, 8, False),
+                                             (0, 4, True), (1, 4, True), (0, 1, True), (1, 8, True)])
 @pytest.mark.parametrize("which", ["tiny", "flat", "well", "single", "foam8"])
-def test_bvh_closest_hit_matches_brute_force(ctx, which, kind, leaf):
+def test_bvh_closest_hit_matches_brute_force(ctx, which, kind, leaf, ploc):
     mesh = {"tiny": lambda: I.grf_foam(16, 0.5), "flat": lambda: I.flat_plane(),
             "well": lambda: I.square_well(100.0, 60.0),
             "single": lambda: I.Mesh(I.flat_plane().tri[:1], I.flat_plane().box),
             "foam8": lambda: I.grf_foam(8, 0.7, 1.5, 3)}[which]()
     mid = ctx.load_mesh(mesh.tri, mesh.box)
-    ctx.build_bvh(mid, kind=kind, leaf=leaf)
+    ctx.build_bvh(mid, kind=kind, leaf=leaf, ploc=ploc)
     rng = np.random.default_rng(42)
     o, d = _rays_for(mesh, 4000, rng)
     skip = rng.integers(-1, mesh.n_tri, o.shape[0]).astype(np.int32)
@@ -118,6 +119,20 @@ def test_bvh_closest_hit_matches_brute_force(ctx, which, kind, leaf):
 
 
 # ---------------------------------------------------------- full runs ------
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_ploc_hierarchy_records_match_oracle(ctx, kind):
+    """The clustering builder changes the tree, not the answer: records on the tiny foam."""
+    mesh = I.grf_foam(16, 0.5)
+    mid = ctx.load_mesh(mesh.tri, mesh.box)
+    ctx.build_bvh(mid, kind=kind, ploc=True)
+    n = 30_000
+    g = ctx.run_records(mid, 300.0, 0.0, n, seed=77)
+    o = O.run(mesh, TABLE, 300.0, 0.0, n, seed=77, records=True)
+    st = compare_records(g["records"], o["records"])
+    assert st["frac_same"] >= 0.9999, {k: v for k, v in st.items() if k != "mismatch"}
+    ctx.unload_mesh(mid)
+
 
 def test_tiny_config_records_match_oracle(ctx, tiny):
     """Tiny config: 16^3 foam, 1e5 primaries at 300 eV, normal incidence."""
