@@ -36,7 +36,7 @@ def merge_results(parts):
         out["sey_se"] = math.sqrt(var) if var > 0 else 0.0
     else:
         out["sey_se"] = 0.0
-    for h in ("hist_e", "hist_a"):
+    for h in ("hist_e", "hist_a", "hist_z"):
         if all(h in p for p in parts):
             acc = None
             for p in parts:

@@ -12,10 +12,11 @@ from paper_1806_00205_gb300 import shard
 def test_merge_results_adds_exactly():
     a = {k: 3 for k in shard.INT_KEYS}
     b = {k: 5 for k in shard.INT_KEYS}
-    a.update(e_sum=1.5, e2_sum=2.5, hist_e=[1, 2], hist_a=[0, 1])
-    b.update(e_sum=0.5, e2_sum=0.5, hist_e=[3, 4], hist_a=[2, 2])
+    a.update(e_sum=1.5, e2_sum=2.5, hist_e=[1, 2], hist_a=[0, 1], hist_z=[7, 0, 1])
+    b.update(e_sum=0.5, e2_sum=0.5, hist_e=[3, 4], hist_a=[2, 2], hist_z=[1, 1, 1])
     m = shard.merge_results([a, b])
     assert m["rays"] == 8 and m["sum_k"] == 8 and m["e_sum"] == 2.0 and m["hist_e"] == [4, 6]
+    assert m["hist_z"] == [8, 1, 2]
     assert m["sey"] == 1.0
     assert shard.primary_offset(3, 1000, 7) == 3007
 
