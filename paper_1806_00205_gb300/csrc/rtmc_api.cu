@@ -286,7 +286,7 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
                 ce = d.id_order ? launch_generate(p, q, 0, (unsigned long long)first, nc, s)
                                 : launch_generate_sorted(p, q, (unsigned long long)first, nc, s);
             tock(h);
-            ++launches;
+            launches += d.id_order ? 1 : 4;      // sorted: count, scan, scatter, write
             for (int g = 0; g <= em.max_generation && ce == cudaSuccess; ++g) {
                 const int buf = g & 1;
                 h = tick(1);
@@ -297,7 +297,7 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
                 if (ce == cudaSuccess)
                     ce = launch_shade(m, p, tab, e, q, buf, g, (unsigned long long)first, ctx->num_sms, record, s);
                 tock(h);
-                launches += 2;
+                launches += 2 + (d.fp64_retest ? 1 : 0);
                 ++trav_launches;
             }
             h = tick(3);

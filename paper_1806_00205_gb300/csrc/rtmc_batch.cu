@@ -101,7 +101,7 @@ cudaError_t record_batch(rtmc_ctx* ctx, const rtmc_batch& b, const rtmc_run_desc
             if (ce == cudaSuccess)
                 ce = sorted ? launch_generate_items_sorted(p, ic, qq, n, s) : launch_generate_items(p, ic, qq, n, s);
             kt.tock(h, s);
-            launches += 1;
+            launches += sorted ? 4 : 1;          // sorted: count, scan, scatter, write
             for (int g = 0; g <= ctx->emission.max_generation && ce == cudaSuccess; ++g) {
                 const int buf = g & 1;
                 h = kt.tick(1, s);

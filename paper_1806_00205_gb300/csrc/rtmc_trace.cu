@@ -178,24 +178,39 @@ __global__ void __launch_bounds__(1024) k_scan_counts(unsigned* __restrict__ c, 
     }
 }
 
+// Pass 2 places only the primary's 4-byte index (scattered); pass 3 then
+// writes the 48-byte queue entries in sorted order, coalesced, recomputing
+// each primary from its Philox stream.
 template <bool ITEMS>
-__global__ void k_generate_sorted(RunParams p, ItemCtx ic, unsigned long long first, unsigned n,
-                                  unsigned* __restrict__ cursor, float4* __restrict__ oe, float4* __restrict__ dt,
-                                  uint4* __restrict__ id, Control* __restrict__ ctl)
+__global__ void k_scatter_perm(RunParams p, ItemCtx ic, unsigned long long first, unsigned n,
+                               unsigned* __restrict__ cursor, unsigned* __restrict__ perm)
 {
     const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i == 0) ctl->count[0] = n;
     if (i >= n) return;
     float4 a, b;
     uint4 c;
     unsigned bucket;
     primary_of<ITEMS>(p, ic, first, i, a, b, c, bucket);
     const unsigned slot = atomicAdd(&cursor[bucket], 1u);
-    if (slot < n) {
-        oe[slot] = a;
-        dt[slot] = b;
-        id[slot] = c;
-    }
+    if (slot < n) perm[slot] = i;
+}
+
+template <bool ITEMS>
+__global__ void k_generate_sorted(RunParams p, ItemCtx ic, unsigned long long first, unsigned n,
+                                  const unsigned* __restrict__ perm, float4* __restrict__ oe, float4* __restrict__ dt,
+                                  uint4* __restrict__ id, Control* __restrict__ ctl)
+{
+    const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) ctl->count[0] = n;
+    if (i >= n) return;
+    const unsigned j = perm[i];
+    float4 a, b;
+    uint4 c;
+    unsigned bucket;
+    primary_of<ITEMS>(p, ic, first, j, a, b, c, bucket);
+    oe[i] = a;
+    dt[i] = b;
+    id[i] = c;
 }
 
 // --------------------------------------------------------------------------
@@ -818,8 +833,11 @@ static cudaError_t generate_sorted(const RunParams& p, const ItemCtx& ic, const 
     cudaError_t e = cudaMemsetAsync(q.sort_counts, 0, (size_t)buckets * 4, s);
     if (e == cudaSuccess && n) k_prim_count<ITEMS><<<gb, tb, 0, s>>>(p, ic, first, n, q.sort_counts);
     if (e == cudaSuccess) k_scan_counts<<<1, 1024, 0, s>>>(q.sort_counts, buckets);
+    // the hit records are idle until this chunk's first traversal: they hold the permutation
+    unsigned* perm = reinterpret_cast<unsigned*>(q.hits);
+    if (e == cudaSuccess && n) k_scatter_perm<ITEMS><<<gb, tb, 0, s>>>(p, ic, first, n, q.sort_counts, perm);
     if (e == cudaSuccess)
-        k_generate_sorted<ITEMS><<<gb, tb, 0, s>>>(p, ic, first, n, q.sort_counts, q.oe[0], q.dt[0], q.id[0], q.ctl);
+        k_generate_sorted<ITEMS><<<gb, tb, 0, s>>>(p, ic, first, n, perm, q.oe[0], q.dt[0], q.id[0], q.ctl);
     return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
