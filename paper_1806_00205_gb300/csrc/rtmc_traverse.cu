@@ -459,27 +459,50 @@ k_traverse_ww(const void* __restrict__ nodes, const float4* __restrict__ tris, c
                 }
             }
         } else {
-            // no facet in this cell: leave through a face (FP64 re-entry point)
+            // No facet in this cell: leave through a face.  The distances to the
+            // three faces ahead are estimated in FP32 from the FP64 offsets; they
+            // pick the face unless the two nearest lie within 1e-5 of each other,
+            // when the FP64 quotients decide (the reference rule: z first if
+            // strictly nearest, then x on a tie with y).  Only a wrap needs its
+            // distance in FP64, because it moves the FP64 re-entry point; an exit
+            // through z_top or z_min reports the FP32 estimate.  (FP64 division is
+            // slow on this GPU; most daughters leave a cell at least once.)
             double ox = s_o[tid], oy = s_o[B + tid], oz = s_o[2 * B + tid];
-            double tx = INFINITY, ty = INFINITY, tz = INFINITY;
-            if (d.x > 0.f) tx = ((double)cell.lx - ox) / d.x; else if (d.x < 0.f) tx = (0.0 - ox) / d.x;
-            if (d.y > 0.f) ty = ((double)cell.ly - oy) / d.y; else if (d.y < 0.f) ty = (0.0 - oy) / d.y;
-            if (d.z > 0.f) tz = ((double)cell.z_top - oz) / d.z; else if (d.z < 0.f) tz = ((double)cell.z_min - oz) / d.z;
+            const float fx = d.x != 0.f ? (float)(d.x > 0.f ? (double)cell.lx - ox : ox) * fabsf(rs.inv.x) : INFINITY;
+            const float fy = d.y != 0.f ? (float)(d.y > 0.f ? (double)cell.ly - oy : oy) * fabsf(rs.inv.y) : INFINITY;
+            const float fz = d.z != 0.f
+                                 ? (float)(d.z > 0.f ? (double)cell.z_top - oz : oz - (double)cell.z_min) * fabsf(rs.inv.z)
+                                 : INFINITY;
+            const float m1 = fminf(fx, fminf(fy, fz));
+            const float m2 = fmaxf(fminf(fx, fy), fminf(fmaxf(fx, fy), fz));   // second smallest
+            int face;                                                           // 0 x, 1 y, 2 z
+            if (m2 <= m1 * 1.00001f) {
+                double tx = INFINITY, ty = INFINITY, tz = INFINITY;
+                if (d.x > 0.f) tx = ((double)cell.lx - ox) / d.x; else if (d.x < 0.f) tx = (0.0 - ox) / d.x;
+                if (d.y > 0.f) ty = ((double)cell.ly - oy) / d.y; else if (d.y < 0.f) ty = (0.0 - oy) / d.y;
+                if (d.z > 0.f) tz = ((double)cell.z_top - oz) / d.z; else if (d.z < 0.f) tz = ((double)cell.z_min - oz) / d.z;
+                face = (tz < tx && tz < ty) ? 2 : (tx <= ty ? 0 : 1);
+            } else {
+                face = fz == m1 ? 2 : (fx == m1 ? 0 : 1);
+            }
             int code = 0;
             float tout = 0.f;
-            if (tz < tx && tz < ty) {
+            if (face == 2) {
                 code = d.z > 0.f ? HIT_ESCAPE : HIT_LOST;
-                tout = (float)tz;
+                tout = fz;
             } else if (++wraps > cell.max_wraps) {
                 code = HIT_LOST;
-                tout = (float)fmin(tx, ty);
+                tout = fminf(fx, fy);
             }
             if (code) {
                 hits[ray] = make_float4(tout, 0.f, 0.f, __int_as_float(code));
             } else {
-                if (tx <= ty) {
+                // the same FP64 quotient as above (and as the reference) for the face taken
+                if (face == 0) {
+                    const double tx = d.x > 0.f ? ((double)cell.lx - ox) / d.x : (0.0 - ox) / d.x;
                     oy = oy + tx * d.y; oz = oz + tx * d.z; ox = d.x > 0.f ? 0.0 : (double)cell.lx;
                 } else {
+                    const double ty = d.y > 0.f ? ((double)cell.ly - oy) / d.y : (0.0 - oy) / d.y;
                     ox = ox + ty * d.x; oz = oz + ty * d.z; oy = d.y > 0.f ? 0.0 : (double)cell.ly;
                 }
                 s_o[tid] = ox; s_o[B + tid] = oy; s_o[2 * B + tid] = oz;
