@@ -246,7 +246,9 @@ int rtmc_trace_rays(rtmc_ctx* ctx, int32_t mesh_id, const float* o, const float*
 /* Copy a built BVH to host memory for inspection: which = 0 FP32 nodes
    (n_nodes x 64 B), 1 Q8 nodes (n_nodes x 32 B, RTMC_BVH_Q8 meshes only),
    2 triangles in leaf order (n_tri x 48 B).  Layouts as in the library's
-   device code.  With out == NULL only *bytes_needed is written; otherwise
+   device code; a Q8 node holds per axis a shifted origin o' (float) and a
+   biased exponent byte b (scale s = 2^(b - 127)), and child bound q decodes
+   as fmaf(2^23 + q, s, o') in FP32.  With out == NULL only *bytes_needed is written; otherwise
    bytes must be at least that size. */
 int rtmc_export_bvh(rtmc_ctx* ctx, int32_t mesh_id, int32_t which, void* out, int64_t bytes,
                     int64_t* bytes_needed);

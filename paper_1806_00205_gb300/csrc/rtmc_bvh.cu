@@ -268,36 +268,50 @@ __global__ void k_single_leaf(const float* __restrict__ tri, float4* __restrict_
 }
 
 // ---- Q8 nodes: 8-bit child boxes, outward rounded -------------------------
-// The frame of node i is its own box: origin = box lo, per-axis scale 2^e with
-// fmaf(255, 2^e, origin) >= box hi.  A child bound decodes to fmaf(q, 2^e,
-// origin); lower bounds are rounded down and upper bounds up, checked with the
-// same FP32 decode the traversal uses, so a decoded child box always contains
+// The frame of node i is its own box.  Per axis it stores a power-of-two
+// scale s = 2^e (biased exponent e + 127 in one byte) and a shifted origin
+// o' = lo - 2^23 s rounded down.  A child bound q decodes with one FMA,
+// fmaf(M(q), s, o'), where M(q) = 2^23 + q is the float with bit pattern
+// 0x4B0000qq, so the traversal needs one byte permute and one FMA per bound.
+// Decode(0) <= lo by construction; e is the smallest exponent with
+// decode(255) >= hi.  Lower bounds are rounded down and upper bounds up,
+// checked with this same FP32 decode, so a decoded child box always contains
 // the exact one.
+__device__ __forceinline__ float q8_decode(unsigned q, float s, float o_shift)
+{
+    return fmaf(__int_as_float(0x4B000000 | (int)q), s, o_shift);
+}
+
+__device__ __forceinline__ float q8_shift(float lo, float s) { return __fsub_rd(lo, 8388608.0f * s); }
+
+// 2^23 s stays finite (coordinates up to about 2^100 fit a frame)
+constexpr int kQ8MaxExp = 100;
+
 __device__ int frame_exponent(float lo, float hi)
 {
     const float ext = hi - lo;
     int e = -126;
     if (ext > 0.f) {
         e = (int)ceilf(log2f(ext / 255.0f));
-        e = max(-126, min(e, 127));
+        e = max(-126, min(e, kQ8MaxExp));
     }
-    while (e < 127 && fmaf(255.0f, exp2_int(e), lo) < hi) ++e;
+    while (e < kQ8MaxExp && q8_decode(255u, exp2_int(e), q8_shift(lo, exp2_int(e))) < hi) ++e;
     return e;
 }
 
-__device__ unsigned quant_lo(float v, float o, float sc)
+__device__ unsigned quant_lo(float v, float o_shift, float sc)
 {
-    int q = (int)floorf((v - o) / sc);
+    int q = (int)floorf((v - q8_decode(0u, sc, o_shift)) / sc);
     q = max(0, min(q, 255));
-    while (q > 0 && fmaf((float)q, sc, o) > v) --q;
+    while (q > 0 && q8_decode((unsigned)q, sc, o_shift) > v) --q;
     return (unsigned)q;
 }
 
-__device__ unsigned quant_hi(float v, float o, float sc)
+__device__ unsigned quant_hi(float v, float o_shift, float sc)
 {
-    int q = (int)ceilf((v - o) / sc);
+    int q = (int)ceilf((v - q8_decode(0u, sc, o_shift)) / sc);
     q = max(0, min(q, 255));
-    while (q < 255 && fmaf((float)q, sc, o) < v) ++q;
+    while (q < 255 && q8_decode((unsigned)q, sc, o_shift) < v) ++q;
     return (unsigned)q;
 }
 
@@ -336,20 +350,21 @@ __global__ void k_quantize(const float* __restrict__ tri, const unsigned* __rest
     const float3 phi = make_float3(fmaxf(b[0].hi.x, b[1].hi.x), fmaxf(b[0].hi.y, b[1].hi.y), fmaxf(b[0].hi.z, b[1].hi.z));
     const int ex = frame_exponent(plo.x, phi.x), ey = frame_exponent(plo.y, phi.y), ez = frame_exponent(plo.z, phi.z);
     const float sx = exp2_int(ex), sy = exp2_int(ey), sz = exp2_int(ez);
+    const float ox = q8_shift(plo.x, sx), oy = q8_shift(plo.y, sy), oz = q8_shift(plo.z, sz);
     unsigned qb[12];
     for (int k = 0; k < 2; ++k) {
-        qb[6 * k + 0] = quant_lo(b[k].lo.x, plo.x, sx);
-        qb[6 * k + 1] = quant_lo(b[k].lo.y, plo.y, sy);
-        qb[6 * k + 2] = quant_lo(b[k].lo.z, plo.z, sz);
-        qb[6 * k + 3] = quant_hi(b[k].hi.x, plo.x, sx);
-        qb[6 * k + 4] = quant_hi(b[k].hi.y, plo.y, sy);
-        qb[6 * k + 5] = quant_hi(b[k].hi.z, plo.z, sz);
+        qb[6 * k + 0] = quant_lo(b[k].lo.x, ox, sx);
+        qb[6 * k + 1] = quant_lo(b[k].lo.y, oy, sy);
+        qb[6 * k + 2] = quant_lo(b[k].lo.z, oz, sz);
+        qb[6 * k + 3] = quant_hi(b[k].hi.x, ox, sx);
+        qb[6 * k + 4] = quant_hi(b[k].hi.y, oy, sy);
+        qb[6 * k + 5] = quant_hi(b[k].hi.z, oz, sz);
     }
     const unsigned meta = (leaf[0] ? 1u : 0u) | ((unsigned)(leaf[0] ? count[0] - 1 : 0) << 1) |
                           (leaf[1] ? 16u : 0u) | ((unsigned)(leaf[1] ? count[1] - 1 : 0) << 5);
-    const unsigned packed = (unsigned)(ex & 255) | ((unsigned)(ey & 255) << 8) | ((unsigned)(ez & 255) << 16) |
+    const unsigned packed = (unsigned)(ex + 127) | ((unsigned)(ey + 127) << 8) | ((unsigned)(ez + 127) << 16) |
                             (meta << 24);
-    q8[2ll * i] = make_uint4(__float_as_uint(plo.x), __float_as_uint(plo.y), __float_as_uint(plo.z), packed);
+    q8[2ll * i] = make_uint4(__float_as_uint(ox), __float_as_uint(oy), __float_as_uint(oz), packed);
     q8[2ll * i + 1] = make_uint4(qb[0] | qb[1] << 8 | qb[2] << 16 | qb[3] << 24,
                                  qb[4] | qb[5] << 8 | qb[6] << 16 | qb[7] << 24,
                                  qb[8] | qb[9] << 8 | qb[10] << 16 | qb[11] << 24, (unsigned)gamma);
@@ -362,9 +377,10 @@ __global__ void k_quantize_single(const float* __restrict__ tri, uint4* __restri
     const Box3 b = tri_box(tri, 0);
     const int ex = frame_exponent(b.lo.x, b.hi.x), ey = frame_exponent(b.lo.y, b.hi.y), ez = frame_exponent(b.lo.z, b.hi.z);
     const unsigned meta = 1u | 16u;
-    const unsigned packed = (unsigned)(ex & 255) | ((unsigned)(ey & 255) << 8) | ((unsigned)(ez & 255) << 16) |
+    const unsigned packed = (unsigned)(ex + 127) | ((unsigned)(ey + 127) << 8) | ((unsigned)(ez + 127) << 16) |
                             (meta << 24);
-    q8[0] = make_uint4(__float_as_uint(b.lo.x), __float_as_uint(b.lo.y), __float_as_uint(b.lo.z), packed);
+    q8[0] = make_uint4(__float_as_uint(q8_shift(b.lo.x, exp2_int(ex))), __float_as_uint(q8_shift(b.lo.y, exp2_int(ey))),
+                       __float_as_uint(q8_shift(b.lo.z, exp2_int(ez))), packed);
     q8[1] = make_uint4(0xFF000000u, 0x0000FFFFu, 0x00000000u, 0u);   // c0 = [0,255]^3, c1 = [0,0]^3
 }
 

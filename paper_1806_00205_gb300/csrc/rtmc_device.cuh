@@ -98,10 +98,10 @@ __host__ __device__ inline int leaf_ref(int first, int count) { return ~((first 
 // 2^e for e in [-126, 127] (a normal float built from its exponent field).
 __device__ __forceinline__ float exp2_int(int e) { return __int_as_float((e + 127) << 23); }
 
-// Byte k of w as a float (exact): 0x4B0000qq is 2^23 + q.
-__device__ __forceinline__ float byte_f(unsigned w, int k)
+// Byte q = byte k of w as the float 0x4B0000qq, i.e. 2^23 + q (exact).
+__device__ __forceinline__ float byte_m(unsigned w, int k)
 {
-    return __int_as_float(__byte_perm(w, 0x4B000000u, (unsigned)k | 0x7540u)) - 8388608.0f;
+    return __int_as_float(__byte_perm(w, 0x4B000000u, (unsigned)k | 0x7540u));
 }
 
 // --------------------------------------------------------------------------

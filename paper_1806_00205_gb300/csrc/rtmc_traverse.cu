@@ -74,18 +74,20 @@ __device__ __forceinline__ void node_children(const void* __restrict__ nodes, in
                                     __float_as_uint(f0.w));
         const uint4 w1 = make_uint4(__float_as_uint(f1.x), __float_as_uint(f1.y), __float_as_uint(f1.z),
                                     __float_as_uint(f1.w));
+        // shifted frame origin o', scales 2^e from biased exponent bytes; a bound
+        // decodes as fmaf(M(q), s, o') with M(q) the float 0x4B0000qq = 2^23 + q
         const float ox = __uint_as_float(w0.x), oy = __uint_as_float(w0.y), oz = __uint_as_float(w0.z);
         const unsigned pk = w0.w;
-        const float sx = exp2_int((int)(signed char)(pk & 255u));
-        const float sy = exp2_int((int)(signed char)((pk >> 8) & 255u));
-        const float sz = exp2_int((int)(signed char)((pk >> 16) & 255u));
+        const float sx = __uint_as_float((pk << 23) & 0x7F800000u);
+        const float sy = __uint_as_float((pk << 15) & 0x7F800000u);
+        const float sz = __uint_as_float((pk << 7) & 0x7F800000u);
         const unsigned meta = pk >> 24;
-        slab_box(fmaf(byte_f(w1.x, 0), sx, ox), fmaf(byte_f(w1.x, 3), sx, ox),
-                 fmaf(byte_f(w1.x, 1), sy, oy), fmaf(byte_f(w1.y, 0), sy, oy),
-                 fmaf(byte_f(w1.x, 2), sz, oz), fmaf(byte_f(w1.y, 1), sz, oz), r, t_best, tmin0, h0);
-        slab_box(fmaf(byte_f(w1.y, 2), sx, ox), fmaf(byte_f(w1.z, 1), sx, ox),
-                 fmaf(byte_f(w1.y, 3), sy, oy), fmaf(byte_f(w1.z, 2), sy, oy),
-                 fmaf(byte_f(w1.z, 0), sz, oz), fmaf(byte_f(w1.z, 3), sz, oz), r, t_best, tmin1, h1);
+        slab_box(fmaf(byte_m(w1.x, 0), sx, ox), fmaf(byte_m(w1.x, 3), sx, ox),
+                 fmaf(byte_m(w1.x, 1), sy, oy), fmaf(byte_m(w1.y, 0), sy, oy),
+                 fmaf(byte_m(w1.x, 2), sz, oz), fmaf(byte_m(w1.y, 1), sz, oz), r, t_best, tmin0, h0);
+        slab_box(fmaf(byte_m(w1.y, 2), sx, ox), fmaf(byte_m(w1.z, 1), sx, ox),
+                 fmaf(byte_m(w1.y, 3), sy, oy), fmaf(byte_m(w1.z, 2), sy, oy),
+                 fmaf(byte_m(w1.z, 0), sz, oz), fmaf(byte_m(w1.z, 3), sz, oz), r, t_best, tmin1, h1);
         const int g = (int)w1.w;
         c0 = (meta & 1u) ? leaf_ref(g - (int)((meta >> 1) & 7u), (int)((meta >> 1) & 7u) + 1) : g;
         c1 = (meta & 16u) ? leaf_ref(g + 1, (int)((meta >> 5) & 7u) + 1) : g + 1;

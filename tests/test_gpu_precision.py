@@ -25,21 +25,24 @@ def ctx():
 
 
 def _decode_q8(raw):
-    """Decode Q8 nodes (float32 arithmetic as on the device: origin + q 2^e, one rounding)."""
+    """Decode Q8 nodes as the device does: fmaf(2^23 + q, 2^(b-127), o'), one FP32 rounding.
+
+    (2^23 + q) 2^e and o' are both exact in float64 and close in magnitude, so
+    their float64 sum is exact and one cast to float32 is the FMA's rounding."""
     w = raw.view(np.uint32).reshape(-1, 8)
-    origin = w[:, 0:3].view(np.float32)
+    origin = w[:, 0:3].view(np.float32).astype(np.float64)
     pk = w[:, 3]
-    exps = np.stack([(pk >> (8 * k)) & 255 for k in range(3)], axis=1).astype(np.uint8).view(np.int8)
-    scale = np.ldexp(np.float32(1.0), exps.astype(np.int32)).astype(np.float32)
+    exps = np.stack([(pk >> (8 * k)) & 255 for k in range(3)], axis=1).astype(np.int32) - 127
+    scale = np.ldexp(1.0, exps)
     meta = (pk >> 24) & 255
-    qb = np.stack([(w[:, 4 + k // 4] >> (8 * (k % 4))) & 255 for k in range(12)], axis=1).astype(np.float32)
+    qb = np.stack([(w[:, 4 + k // 4] >> (8 * (k % 4))) & 255 for k in range(12)], axis=1).astype(np.float64)
     gamma = w[:, 7].view(np.int32)
     boxes = np.empty((w.shape[0], 2, 2, 3), dtype=np.float32)      # node, child, lo/hi, axis
     for c in range(2):
         for lh in range(2):
             for ax in range(3):
                 q = qb[:, 6 * c + 3 * lh + ax]
-                boxes[:, c, lh, ax] = origin[:, ax] + q * scale[:, ax]     # q * 2^e is exact
+                boxes[:, c, lh, ax] = ((8388608.0 + q) * scale[:, ax] + origin[:, ax]).astype(np.float32)
     cnt0 = ((meta >> 1) & 7).astype(np.int64)
     cnt1 = ((meta >> 5) & 7).astype(np.int64)
     g = gamma.astype(np.int64)
