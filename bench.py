@@ -38,10 +38,10 @@ GRID, POROSITY, CORR, SEED = 128, 0.6, 2.0, 1806
 NODE_BYTES, TRI_BYTES, RAY_BYTES = 64, 48, 48   # node fetch, triangle fetch, ray read + hit write
 
 
-def workload_name(n_tri, n_prim):
+def workload_name(n_tri, n_prim, energies=ENERGIES):
     return (f"plain RTMC, paper scale: {GRID}^3 periodic GRF foam (10 nm voxels, porosity {POROSITY}, "
-            f"corr {CORR:g} vox, seed {SEED}) -> {n_tri} FP32 triangles; {len(ENERGIES)} energies "
-            f"50-1000 eV x {n_prim:.0e} primaries, normal incidence")
+            f"corr {CORR:g} vox, seed {SEED}) -> {n_tri} FP32 triangles; {len(energies)} energies "
+            f"{energies[0]:g}-{energies[-1]:g} eV x {n_prim:.3g} primaries, normal incidence")
 
 
 class ClockSampler:
@@ -448,7 +448,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "primaries_per_s": prims / (ms / 1e3),
-            "config": {"workload": workload_name(mesh.n_tri, n_prim), "n_tri": mesh.n_tri,
+            "config": {"workload": workload_name(mesh.n_tri, n_prim, energies), "n_tri": mesh.n_tri,
                        "energies_ev": energies, "theta_deg": [0.0], "primaries_per_energy": n_prim,
                        "primaries_per_step": n_prim * len(energies) * world,
                        "engine": "rtmc_run_batch (multi-item queues), FP32 BVH nodes, autotuned",
