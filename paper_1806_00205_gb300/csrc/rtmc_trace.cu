@@ -20,7 +20,8 @@
 namespace rtmc {
 namespace {
 
-constexpr int kShadeThreads = 256;
+constexpr int kShadeThreads = 128;
+constexpr int kShadeBlocksPerSm = 1024 / kShadeThreads;   // resident blocks per SM at 64 registers
 constexpr size_t kShadeDefaultSmem = 24 * 1024;   // dynamic bytes that fit beside the static arrays
 
 __device__ __forceinline__ float4 ldg4(const float4* p) { return __ldg(p); }
@@ -345,7 +346,7 @@ __device__ __forceinline__ void acc_atomic(Tally* t, const Acc& a)
 // a warp whose rays share one item (the common case) adds one reduced value
 // per counter.  The block flushes to global memory once, at its end.
 template <bool RECORD, bool ITEMS>
-__global__ void __launch_bounds__(kShadeThreads)
+__global__ void __launch_bounds__(kShadeThreads, kShadeBlocksPerSm)
 k_shade(const float4* __restrict__ tris, const float4* __restrict__ normals, TableDesc tab, Emission em,
         RunParams p, ItemCtx ic, const float4* __restrict__ oe, const float4* __restrict__ dt,
         const uint4* __restrict__ id, const float4* __restrict__ hits, const int* __restrict__ wraps_in,
@@ -801,7 +802,7 @@ cudaError_t launch_shade(const DeviceMesh& m, const RunParams& p, const TableDes
     const int nb = 1 - buf;
     const ShadeOut out{q.oe[nb], q.dt[nb], q.id[nb], q.cap[nb]};
     const size_t smem = (size_t)(p.n_ebins + p.n_abins + p.n_zbins) * sizeof(unsigned);
-    const int blocks = num_sms * 4;
+    const int blocks = num_sms * kShadeBlocksPerSm;
     const ItemCtx ic{};
     if (smem > kShadeDefaultSmem) {
         // up to 3 x 4096 bins: past the default dynamic shared-memory limit
@@ -871,7 +872,7 @@ cudaError_t launch_shade_items(const DeviceMesh& m, const RunParams& p, const Ta
     const int nb = 1 - buf;
     const ShadeOut out{q.oe[nb], q.dt[nb], q.id[nb], q.cap[nb]};
     const size_t smem = (size_t)kChunkItems * (p.n_ebins + p.n_abins + p.n_zbins) * sizeof(unsigned);
-    k_shade<false, true><<<num_sms * 4, kShadeThreads, smem, s>>>(m.tris, m.normals, tab, em, p, ic, q.oe[buf],
+    k_shade<false, true><<<num_sms * kShadeBlocksPerSm, kShadeThreads, smem, s>>>(m.tris, m.normals, tab, em, p, ic, q.oe[buf],
                                                                   q.dt[buf], q.id[buf], q.hits, q.wraps, out, q.ctl,
                                                                   gen, q.cap[buf], q.tally, nullptr, nullptr, q.kcount,
                                                                   0ull, nullptr, nullptr, 0);
