@@ -44,6 +44,7 @@ extern "C" {
 
 #define RTMC_BVH_FP32 0     /* 64-byte nodes with FP32 child boxes */
 #define RTMC_BVH_Q8   1     /* 32-byte nodes with 8-bit outward-rounded child boxes */
+#define RTMC_BVH_W4   2     /* 128-byte 4-wide nodes with FP32 child boxes, collapsed from the binary hierarchy */
 /* bvh_kind = node format | RTMC_BVH_LEAF(n): leaves of up to n (1..8) triangles, default 4 */
 #define RTMC_BVH_LEAF(n) ((n) << 8)
 /* ... | RTMC_BVH_PLOC: build the hierarchy by locally-ordered clustering
@@ -184,7 +185,11 @@ int rtmc_load_see_tables(rtmc_ctx* ctx, const float* delta, const rtmc_grid* gri
    locally-ordered clustering instead (Meister & Bittner 2018: mutually
    nearest clusters by merged-box surface area within 16 positions of the
    Morton order merge, round by round), rewritten into the same node layout;
-   it is deterministic and synchronises with the host once per round. */
+   it is deterministic and synchronises with the host once per round.
+   RTMC_BVH_W4 builds the binary hierarchy and then collapses it into 4-wide
+   nodes (each opens the inner child of largest surface area until it holds
+   four children; leaves are those of the binary hierarchy), level by level,
+   one host synchronisation per level. */
 int rtmc_build_bvh(rtmc_ctx* ctx, int32_t mesh_id, int32_t bvh_kind);
 
 /* Run RTMC for every (energy, angle) pair: n_e * n_theta items, item
@@ -245,7 +250,10 @@ int rtmc_trace_rays(rtmc_ctx* ctx, int32_t mesh_id, const float* o, const float*
 
 /* Copy a built BVH to host memory for inspection: which = 0 FP32 nodes
    (n_nodes x 64 B), 1 Q8 nodes (n_nodes x 32 B, RTMC_BVH_Q8 meshes only),
-   2 triangles in leaf order (n_tri x 48 B).  Layouts as in the library's
+   2 triangles in leaf order (n_tri x 48 B), 3 4-wide nodes (RTMC_BVH_W4
+   meshes only, n_w4 x 128 B: rows lo.x, hi.x, lo.y, hi.y, lo.z, hi.z of the
+   four child boxes, then the four child refs; an empty slot has ref INT_MIN
+   and the box [+inf, +inf]^3).  Layouts as in the library's
    device code; a Q8 node holds per axis a shifted origin o' (float) and a
    biased exponent byte b (scale s = 2^(b - 127)), and child bound q decodes
    as fmaf(2^23 + q, s, o') in FP32.  With out == NULL only *bytes_needed is written; otherwise

@@ -653,6 +653,156 @@ __global__ void k_ploc_emit(const int2* __restrict__ kids, const int* __restrict
     if (v == root) parent[0] = -1;
 }
 
+// ---- 4-wide nodes, collapsed from the finished binary hierarchy ------------
+// Each 4-wide node stands for one binary inner node b: it starts from b's two
+// children and, while it has fewer than four, opens the inner child with the
+// largest box surface area (a child that collapses into a leaf stays closed).
+// Level by level: count the inner children of every node of the frontier,
+// scan, then write the nodes and the next frontier, so the numbering is
+// deterministic (root 0, then level order).
+constexpr int kW4Block = 256;
+
+__device__ __forceinline__ float box_area(float4 lo, float4 hi)
+{
+    const float dx = hi.x - lo.x, dy = hi.y - lo.y, dz = hi.z - lo.z;
+    return dx * dy + dy * dz + dz * dx;
+}
+
+__device__ __forceinline__ bool w4_open(int raw, const int2* __restrict__ range, int leaf_max)
+{
+    if (raw < 0) return false;
+    const int2 r = range[raw];
+    return r.y - r.x + 1 > leaf_max;
+}
+
+__device__ int w4_expand(int b, const int2* __restrict__ child, const int2* __restrict__ range,
+                         const float4* __restrict__ aabb, int leaf_max, int (&raw)[4])
+{
+    const int2 c = child[b];
+    raw[0] = c.x;
+    raw[1] = c.y;
+    raw[2] = raw[3] = -1;
+    int n = 2;
+    while (n < 4) {
+        int best = -1;
+        float ba = -1.f;
+        for (int k = 0; k < n; ++k) {
+            if (!w4_open(raw[k], range, leaf_max)) continue;
+            const float a = box_area(aabb[2ll * raw[k]], aabb[2ll * raw[k] + 1]);
+            if (a > ba) { ba = a; best = k; }
+        }
+        if (best < 0) break;
+        const int2 cc = child[raw[best]];
+        raw[best] = cc.x;
+        raw[n++] = cc.y;
+    }
+    return n;
+}
+
+__global__ void k_w4_count(const int2* __restrict__ front, int nf, const int2* __restrict__ child,
+                           const int2* __restrict__ range, const float4* __restrict__ aabb, int leaf_max,
+                           int* __restrict__ cnt)
+{
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    int raw[4];
+    const int n = w4_expand(front[f].x, child, range, aabb, leaf_max, raw);
+    int m = 0;
+    for (int k = 0; k < n; ++k) m += w4_open(raw[k], range, leaf_max) ? 1 : 0;
+    cnt[f] = m;
+}
+
+// Exclusive scan of cnt[0..n) into off, total to *tot (one block).
+__global__ void k_w4_scan(const int* __restrict__ cnt, int n, int* __restrict__ off, int* __restrict__ tot)
+{
+    __shared__ int sums[1024];
+    const int per = (n + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int lo = threadIdx.x * per, hi = min(lo + per, n);
+    int t = 0;
+    for (int i = lo; i < hi; ++i) t += cnt[i];
+    sums[threadIdx.x] = t;
+    __syncthreads();
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+        const int v = threadIdx.x >= (unsigned)o ? sums[threadIdx.x - o] : 0;
+        __syncthreads();
+        sums[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int run = sums[threadIdx.x] - t;
+    for (int i = lo; i < hi; ++i) { off[i] = run; run += cnt[i]; }
+    if (threadIdx.x == blockDim.x - 1) *tot = sums[threadIdx.x];
+}
+
+__device__ __forceinline__ void w4_store(float4* __restrict__ w4, int w, const Box3 (&b)[4], const int (&ref)[4])
+{
+    float4* nd = w4 + 8ll * w;
+    nd[0] = make_float4(b[0].lo.x, b[1].lo.x, b[2].lo.x, b[3].lo.x);
+    nd[1] = make_float4(b[0].hi.x, b[1].hi.x, b[2].hi.x, b[3].hi.x);
+    nd[2] = make_float4(b[0].lo.y, b[1].lo.y, b[2].lo.y, b[3].lo.y);
+    nd[3] = make_float4(b[0].hi.y, b[1].hi.y, b[2].hi.y, b[3].hi.y);
+    nd[4] = make_float4(b[0].lo.z, b[1].lo.z, b[2].lo.z, b[3].lo.z);
+    nd[5] = make_float4(b[0].hi.z, b[1].hi.z, b[2].hi.z, b[3].hi.z);
+    nd[6] = make_float4(__int_as_float(ref[0]), __int_as_float(ref[1]), __int_as_float(ref[2]),
+                        __int_as_float(ref[3]));
+    nd[7] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+__global__ void k_w4_emit(const int2* __restrict__ front, int nf, const int* __restrict__ off, int base,
+                          const int2* __restrict__ child, const int2* __restrict__ range,
+                          const float4* __restrict__ aabb, const float* __restrict__ tri,
+                          const unsigned* __restrict__ order, int leaf_max, float4* __restrict__ w4,
+                          int2* __restrict__ next)
+{
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    const int2 fw = front[f];
+    int raw[4];
+    const int n = w4_expand(fw.x, child, range, aabb, leaf_max, raw);
+    Box3 b[4];
+    int ref[4];
+    int j = 0;
+    for (int k = 0; k < 4; ++k) {
+        if (k >= n) {                                  // empty slot: a box no ray can hit
+            b[k].lo = b[k].hi = make_float3(INFINITY, INFINITY, INFINITY);
+            ref[k] = kEmptyChild;
+            continue;
+        }
+        const int r = raw[k];
+        if (r < 0) {                                   // single triangle at leaf position ~r
+            b[k] = tri_box(tri, order[~r]);
+            ref[k] = ~((~r) << 3);
+            continue;
+        }
+        const float4 lo = aabb[2ll * r], hi = aabb[2ll * r + 1];
+        b[k].lo = make_float3(lo.x, lo.y, lo.z);
+        b[k].hi = make_float3(hi.x, hi.y, hi.z);
+        const int2 rg = range[r];
+        const int c = rg.y - rg.x + 1;
+        if (c <= leaf_max) {
+            ref[k] = ~((rg.x << 3) | (c - 1));
+        } else {
+            const int slot = off[f] + j++;
+            ref[k] = base + slot;
+            next[slot] = make_int2(r, base + slot);
+        }
+    }
+    w4_store(w4, fw.y, b, ref);
+}
+
+// One-triangle mesh: the root holds the single leaf.
+__global__ void k_w4_single(const float* __restrict__ tri, float4* __restrict__ w4)
+{
+    Box3 b[4];
+    int ref[4];
+    b[0] = tri_box(tri, 0);
+    ref[0] = ~0;
+    for (int k = 1; k < 4; ++k) {
+        b[k].lo = b[k].hi = make_float3(INFINITY, INFINITY, INFINITY);
+        ref[k] = kEmptyChild;
+    }
+    w4_store(w4, 0, b, ref);
+}
+
 struct DevBuf {
     void* p = nullptr;
     ~DevBuf() { if (p) cudaFree(p); }
@@ -673,12 +823,16 @@ int build_lbvh(rtmc_ctx* ctx, DeviceMesh& m)
     if (m.normals) { cudaFree(m.normals); m.normals = nullptr; }
     if (m.inv_order) { cudaFree(m.inv_order); m.inv_order = nullptr; }
     if (m.q8) { cudaFree(m.q8); m.q8 = nullptr; }
+    if (m.w4) { cudaFree(m.w4); m.w4 = nullptr; }
+    m.n_w4 = 0;
+    m.depth_w4 = 0;
     m.built = false;
     const int64_t n_nodes = n > 1 ? n - 1 : 1;
     cudaError_t e = cudaMalloc(&m.nodes, n_nodes * 64);
     if (e == cudaSuccess) e = cudaMalloc(&m.tris, (size_t)(n + 1) * 48);
     if (e == cudaSuccess) e = cudaMalloc(&m.normals, (size_t)(n + 1) * 16);
     if (e == cudaSuccess && m.kind == FMT_Q8) e = cudaMalloc(&m.q8, n_nodes * 32);
+    if (e == cudaSuccess && m.kind == FMT_W4) e = cudaMalloc(&m.w4, n_nodes * 128);   // one per binary inner node at most
     if (e == cudaSuccess) e = cudaMalloc(&m.inv_order, (size_t)n * 4);
     if (e != cudaSuccess) return ctx->fail(RTMC_ERR_OOM, std::string("build_bvh: ") + cudaGetErrorString(e));
     m.n_nodes = n_nodes;
@@ -785,6 +939,11 @@ int build_lbvh(rtmc_ctx* ctx, DeviceMesh& m)
     if (n == 1) {
         k_single_leaf<<<1, 1, 0, s>>>(m.tri_in, m.nodes);
         if (m.kind == FMT_Q8) k_quantize_single<<<1, 1, 0, s>>>(m.tri_in, reinterpret_cast<uint4*>(m.q8));
+        if (m.kind == FMT_W4) {
+            k_w4_single<<<1, 1, 0, s>>>(m.tri_in, reinterpret_cast<float4*>(m.w4));
+            m.n_w4 = 1;
+            m.depth_w4 = 1;
+        }
         int one = 1;
         cudaMemcpyAsync(depth.p, &one, 4, cudaMemcpyHostToDevice, s);
     } else {
@@ -798,6 +957,40 @@ int build_lbvh(rtmc_ctx* ctx, DeviceMesh& m)
         if (m.kind == FMT_Q8)
             k_quantize<<<gi, tb, 0, s>>>(m.tri_in, order, n - 1, child.as<int2>(), range.as<int2>(), aabb.as<float4>(),
                                          m.leaf_max, reinterpret_cast<uint4*>(m.q8));
+        if (m.kind == FMT_W4) {
+            DevBuf fr[2], cnt, off, tot;
+            e = fr[0].alloc(8ull * n_nodes);
+            if (e == cudaSuccess) e = fr[1].alloc(8ull * n_nodes);
+            if (e == cudaSuccess) e = cnt.alloc(4ull * n_nodes);
+            if (e == cudaSuccess) e = off.alloc(4ull * n_nodes);
+            if (e == cudaSuccess) e = tot.alloc(4);
+            if (e != cudaSuccess)
+                return ctx->fail(RTMC_ERR_OOM, std::string("build_bvh (4-wide) scratch: ") + cudaGetErrorString(e));
+            const int2 root = make_int2(0, 0);
+            e = cudaMemcpyAsync(fr[0].p, &root, sizeof root, cudaMemcpyHostToDevice, s);
+            int nf = 1, base = 1, levels = 0, cur = 0;
+            while (nf > 0 && e == cudaSuccess) {
+                if (++levels > 1000) return ctx->fail(RTMC_ERR_DEVICE_CHECK, "build_bvh (4-wide): runaway collapse");
+                const int gf = (nf + kW4Block - 1) / kW4Block;
+                k_w4_count<<<gf, kW4Block, 0, s>>>(fr[cur].as<int2>(), nf, child.as<int2>(), range.as<int2>(),
+                                                   aabb.as<float4>(), m.leaf_max, cnt.as<int>());
+                k_w4_scan<<<1, 1024, 0, s>>>(cnt.as<int>(), nf, off.as<int>(), tot.as<int>());
+                k_w4_emit<<<gf, kW4Block, 0, s>>>(fr[cur].as<int2>(), nf, off.as<int>(), base, child.as<int2>(),
+                                                  range.as<int2>(), aabb.as<float4>(), m.tri_in, order, m.leaf_max,
+                                                  reinterpret_cast<float4*>(m.w4), fr[1 - cur].as<int2>());
+                int h_tot = 0;
+                e = cudaMemcpyAsync(&h_tot, tot.p, 4, cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                if (e == cudaSuccess && (h_tot < 0 || (int64_t)base + h_tot > n_nodes))
+                    return ctx->fail(RTMC_ERR_DEVICE_CHECK, "build_bvh (4-wide): node count out of range");
+                base += h_tot;
+                nf = h_tot;
+                cur = 1 - cur;
+            }
+            if (e != cudaSuccess) return ctx->fail(RTMC_ERR_CUDA, std::string("build_bvh (4-wide): ") + cudaGetErrorString(e));
+            m.n_w4 = base;
+            m.depth_w4 = levels;
+        }
     }
     const int gp = (n + 1 + tb - 1) / tb;
     k_pack<<<gp, tb, 0, s>>>(m.tri_in, order, n, m.tris, m.normals, m.inv_order);
@@ -815,6 +1008,8 @@ int build_lbvh(rtmc_ctx* ctx, DeviceMesh& m)
     m.build_ms = ms;
     if (h_depth >= kStackMax)
         return ctx->fail(RTMC_ERR_DEVICE_CHECK, "build_bvh: hierarchy deeper than the traversal stack");
+    if (m.kind == FMT_W4 && 3 * m.depth_w4 >= kStackMax)
+        return ctx->fail(RTMC_ERR_DEVICE_CHECK, "build_bvh: 4-wide hierarchy deeper than the traversal stack");
     m.built = true;
     return RTMC_OK;
 }

@@ -20,6 +20,7 @@
 //   hit (16 B): float4 (t, u, v, tri as int bits); tri >= 0 sorted triangle,
 //               HIT_ESCAPE or HIT_LOST.
 #pragma once
+#include <climits>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -27,7 +28,7 @@ namespace rtmc {
 
 constexpr int HIT_ESCAPE = -1;
 constexpr int HIT_LOST = -2;
-constexpr int kStackMax = 64;     // Karras hierarchies over 30-bit codes + index: depth <= 62
+constexpr int kStackMax = 128;    // binary: depth <= 62 (30-bit codes + index); 4-wide: 3 entries per level
 
 // device status word bits
 constexpr unsigned ST_STACK_OVERFLOW = 1u;
@@ -91,6 +92,8 @@ struct TableDesc {
 
 constexpr int FMT_FP32 = 0;
 constexpr int FMT_Q8 = 1;
+constexpr int FMT_W4 = 2;         // 4-wide nodes, FP32 child boxes (128 B)
+constexpr int kEmptyChild = INT_MIN;   // unused slot of a 4-wide node (its box is never hit)
 
 // Leaf reference used by both node formats: ~((first << 3) | (count - 1)).
 __host__ __device__ inline int leaf_ref(int first, int count) { return ~((first << 3) | (count - 1)); }

@@ -23,6 +23,9 @@ struct DeviceMesh {
     float4* normals = nullptr;     // n_tri float4
     int* inv_order = nullptr;      // original id -> leaf-order index
     void* q8 = nullptr;            // n_nodes * 32 B quantised nodes (RTMC_BVH_Q8)
+    void* w4 = nullptr;            // n_w4 * 128 B 4-wide nodes (RTMC_BVH_W4)
+    int64_t n_w4 = 0;
+    int depth_w4 = 0;              // levels of the 4-wide hierarchy
     int depth = 0;                 // hierarchy depth (root = 1)
     int leaf_max = 4;              // triangles per leaf (1..8)
     bool ploc = false;             // hierarchy from locally-ordered clustering

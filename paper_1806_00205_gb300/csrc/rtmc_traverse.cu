@@ -37,6 +37,12 @@ struct StackRef {
     int tid;
 };
 
+// Distance bound before any hit: finite, so that tmax = min(.., t_best) stays
+// finite and a box whose entry distance is +inf -- the empty slot of a 4-wide
+// node, [+inf, +inf]^3 -- is never hit.  Every real slab distance is far below
+// it (box coordinates are finite and |1/d| <= 1e30).
+constexpr float kNoHit = 1e37f;
+
 // Slab test of one box (Ize 2013 form: difference first, then the reciprocal,
 // tmax widened by 1 + 2 gamma_3 so the test is conservative).
 __device__ __forceinline__ void slab_box(float lox, float hix, float loy, float hiy, float loz, float hiz,
@@ -92,6 +98,40 @@ __device__ __forceinline__ void node_children(const void* __restrict__ nodes, in
         c0 = (meta & 1u) ? leaf_ref(g - (int)((meta >> 1) & 7u), (int)((meta >> 1) & 7u) + 1) : g;
         c1 = (meta & 16u) ? leaf_ref(g + 1, (int)((meta >> 5) & 7u) + 1) : g + 1;
     }
+}
+
+// 4-wide node (128 B): rows lo.x, hi.x, lo.y, hi.y, lo.z, hi.z of the four
+// child boxes, then the four child refs.  The hit children come back sorted by
+// entry distance (nearest first); *nh is their number.  An empty slot holds
+// the box [+inf, +inf]^3, which the slab test never hits.
+__device__ __forceinline__ void node4_children(const void* __restrict__ nodes, int node, const RaySetup& r,
+                                               float t_best, float (&tk)[4], int (&ck)[4], int& nh)
+{
+    const float4* np = reinterpret_cast<const float4*>(nodes) + 8ll * node;
+    float4 lx, hx, ly, hy, lz, hz, cr, pad;
+    ldg8(np, lx, hx);
+    ldg8(np + 2, ly, hy);
+    ldg8(np + 4, lz, hz);
+    ldg8(np + 6, cr, pad);
+    bool h0, h1, h2, h3;
+    slab_box(lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, r, t_best, tk[0], h0);
+    slab_box(lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, r, t_best, tk[1], h1);
+    slab_box(lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, r, t_best, tk[2], h2);
+    slab_box(lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, r, t_best, tk[3], h3);
+    ck[0] = __float_as_int(cr.x); ck[1] = __float_as_int(cr.y);
+    ck[2] = __float_as_int(cr.z); ck[3] = __float_as_int(cr.w);
+    if (!h0) tk[0] = INFINITY;
+    if (!h1) tk[1] = INFINITY;
+    if (!h2) tk[2] = INFINITY;
+    if (!h3) tk[3] = INFINITY;
+    nh = (int)h0 + (int)h1 + (int)h2 + (int)h3;
+    auto cswap = [&](int a, int b) {
+        if (tk[b] < tk[a]) {
+            const float t = tk[a]; tk[a] = tk[b]; tk[b] = t;
+            const int c = ck[a]; ck[a] = ck[b]; ck[b] = c;
+        }
+    };
+    cswap(0, 1); cswap(2, 3); cswap(0, 2); cswap(1, 3); cswap(1, 2);
 }
 
 struct Counts { unsigned visits = 0, tests = 0; };
@@ -191,10 +231,42 @@ __device__ __forceinline__ int bvh_closest(const void* __restrict__ nodes, const
     int node = 0;
     int best = -1, best_orig = INT_MAX;
     double t_best64 = INFINITY;
-    t_best = INFINITY;
+    t_best = kNoHit;
     bu = bv = 0.f;
+    auto push = [&](int ref, float tmin) {
+        const int2 e = make_int2(ref, __float_as_int(tmin));
+        if (sp < kSmemStack) st.smem[sp * st.stride + st.tid] = e;
+        else if (sp < kStackMax) lstack[sp - kSmemStack] = e;
+        else { status |= ST_STACK_OVERFLOW; sp = kStackMax - 1; }
+        ++sp;
+    };
+    auto pop = [&]() -> bool {
+        while (sp > 0) {
+            --sp;
+            const int2 e = sp < kSmemStack ? st.smem[sp * st.stride + st.tid] : lstack[sp - kSmemStack];
+            if (__int_as_float(e.y) <= t_best * kRobust) { node = e.x; return true; }
+        }
+        return false;
+    };
     for (int visits = 0;; ++visits) {
         if (visits >= kMaxVisits) { status |= ST_LOOP_LIMIT; break; }
+        if constexpr (FMT == FMT_W4) {
+            if (node < 0) {                                  // a leaf: test it now
+                test_leaf<COUNT, TRI64>(tris, r, r64, node, skip, t_best, t_best64, best, best_orig, bu, bv, cnt);
+                if (!pop()) break;
+                continue;
+            }
+            if (COUNT) ++cnt->visits;
+            float tk[4];
+            int ck[4], nh;
+            node4_children(nodes, node, r, t_best, tk, ck, nh);
+            if (nh > 3) push(ck[3], tk[3]);
+            if (nh > 2) push(ck[2], tk[2]);
+            if (nh > 1) push(ck[1], tk[1]);
+            if (nh > 0) node = ck[0];
+            else if (!pop()) break;
+            continue;
+        }
         if (COUNT) ++cnt->visits;
         float tmin0, tmin1;
         bool h0, h1;
@@ -360,7 +432,7 @@ k_traverse_ww(const void* __restrict__ nodes, const float4* __restrict__ tris, c
     float3 o = make_float3(0.f, 0.f, 0.f), d = make_float3(0.f, 0.f, 1.f);
     RaySetup rs = setup_ray(o, d);
     RaySetup64 r64;
-    float t_best = INFINITY, bu = 0.f, bv = 0.f;
+    float t_best = kNoHit, bu = 0.f, bv = 0.f;
     double t_best64 = INFINITY;
     int best = -1, best_orig = INT_MAX, node = kEntrySentinel, leaf = 0, sp = 0, skip = -1, wraps = 0, visits = 0;
     unsigned status = 0;
@@ -385,7 +457,7 @@ k_traverse_ww(const void* __restrict__ nodes, const float4* __restrict__ tris, c
     auto restart = [&]() {      // new cell traversal from the current origin
         rs = setup_ray(o, d);
         node = 0; leaf = 0; sp = 0; visits = 0;
-        t_best = INFINITY; best = -1; best_orig = INT_MAX; bu = bv = 0.f;
+        t_best = kNoHit; best = -1; best_orig = INT_MAX; bu = bv = 0.f;
     };
 
     for (;;) {
@@ -421,18 +493,28 @@ k_traverse_ww(const void* __restrict__ nodes, const float4* __restrict__ tris, c
             while (node >= 0 && node != kEntrySentinel) {
                 if (++visits > kMaxVisits) { status |= ST_LOOP_LIMIT; node = kEntrySentinel; leaf = 0; sp = 0; break; }
                 if (COUNT) ++cnt.visits;
-                float tmin0, tmin1;
-                bool h0, h1;
-                int c0, c1;
-                node_children<FMT>(nodes, node, rs, t_best, tmin0, tmin1, h0, h1, c0, c1);
-                if (h0 && h1) {
-                    const bool first0 = tmin0 <= tmin1;
-                    push(first0 ? c1 : c0, first0 ? tmin1 : tmin0);
-                    node = first0 ? c0 : c1;
-                } else if (h0 || h1) {
-                    node = h0 ? c0 : c1;
+                if constexpr (FMT == FMT_W4) {
+                    float tk[4];
+                    int ck[4], nh;
+                    node4_children(nodes, node, rs, t_best, tk, ck, nh);
+                    if (nh > 3) push(ck[3], tk[3]);           // farthest first: the nearest stays on top
+                    if (nh > 2) push(ck[2], tk[2]);
+                    if (nh > 1) push(ck[1], tk[1]);
+                    node = nh > 0 ? ck[0] : pop();
                 } else {
-                    node = pop();
+                    float tmin0, tmin1;
+                    bool h0, h1;
+                    int c0, c1;
+                    node_children<FMT>(nodes, node, rs, t_best, tmin0, tmin1, h0, h1, c0, c1);
+                    if (h0 && h1) {
+                        const bool first0 = tmin0 <= tmin1;
+                        push(first0 ? c1 : c0, first0 ? tmin1 : tmin0);
+                        node = first0 ? c0 : c1;
+                    } else if (h0 || h1) {
+                        node = h0 ? c0 : c1;
+                    } else {
+                        node = pop();
+                    }
                 }
                 if (node < 0 && leaf == 0) { leaf = node; node = pop(); }
                 if (!__any_sync(__activemask(), leaf == 0)) break;
@@ -587,7 +669,8 @@ k_trace_rays(const void* __restrict__ nodes, const float4* __restrict__ tris, co
     RaySetup64 r64;
     const int j = bvh_closest<FMT>(nodes, tris, setup_ray(oo, dd), r64, sk, st, t, u, v, status);
     rtmc_hit h;
-    h.t = t; h.u = u; h.v = v;
+    h.t = j >= 0 ? t : INFINITY;
+    h.u = u; h.v = v;
     h.tri = j >= 0 ? __float_as_int(__ldg(tris + 3ll * j).w) : -1;
     hits[i] = h;
     if (status) atomicOr(status_out, status);
@@ -632,7 +715,7 @@ static cudaError_t traverse_t(const DeviceMesh& m, const RunParams& p, const Que
                               int num_sms, const Tuning& tune, bool retest, cudaStream_t s)
 {
     const Cell cell{p.lx, p.ly, p.z_min, p.z_top, p.max_wraps};
-    const void* nodes = F == FMT_Q8 ? m.q8 : (const void*)m.nodes;
+    const void* nodes = F == FMT_Q8 ? m.q8 : (F == FMT_W4 ? m.w4 : (const void*)m.nodes);
     const int bt = tune.block_threads;
     int per_sm = tune.blocks_per_sm;
     if (tune.traversal == 1) {
@@ -664,6 +747,7 @@ cudaError_t launch_traverse(const DeviceMesh& m, const RunParams& p, const Queue
                             int num_sms, const Tuning& tune, bool record, bool count, bool retest, cudaStream_t s)
 {
     if (m.kind == FMT_Q8) return traverse_f<FMT_Q8>(m, p, q, buf, gen, num_sms, tune, record, count, retest, s);
+    if (m.kind == FMT_W4) return traverse_f<FMT_W4>(m, p, q, buf, gen, num_sms, tune, record, count, retest, s);
     return traverse_f<FMT_FP32>(m, p, q, buf, gen, num_sms, tune, record, count, retest, s);
 }
 
@@ -675,6 +759,9 @@ cudaError_t launch_trace_rays(const DeviceMesh& m, const float* o, const float* 
     const int64_t gb = (n + tb - 1) / tb;
     if (gb > 0 && m.kind == FMT_Q8)
         k_trace_rays<FMT_Q8><<<(unsigned)gb, tb, smem, s>>>(m.q8, m.tris, m.inv_order, (int)m.n_tri, o, d, skip, n,
+                                                            hits, status);
+    else if (gb > 0 && m.kind == FMT_W4)
+        k_trace_rays<FMT_W4><<<(unsigned)gb, tb, smem, s>>>(m.w4, m.tris, m.inv_order, (int)m.n_tri, o, d, skip, n,
                                                             hits, status);
     else if (gb > 0)
         k_trace_rays<FMT_FP32><<<(unsigned)gb, tb, smem, s>>>(m.nodes, m.tris, m.inv_order, (int)m.n_tri, o, d, skip,

@@ -21,6 +21,7 @@ ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NOT_LOADED", -5: "NOT_B
           -6: "CAPACITY", -7: "TIMEOUT", -8: "DEVICE_CHECK"}
 BVH_FP32 = 0
 BVH_Q8 = 1
+BVH_W4 = 2
 ESCAPED, EMITTER, ABSORBED_LOW, ABSORBED_OTHER, LOST = 0, 1, 2, 3, 4
 
 EXPORTS = ["rtmc_create", "rtmc_destroy", "rtmc_last_error", "rtmc_load_mesh", "rtmc_unload_mesh",
@@ -336,7 +337,7 @@ class Context:
         return hits
 
     def export_bvh(self, mesh_id, which):
-        """Raw bytes of a built BVH array (0 FP32 nodes, 1 Q8 nodes, 2 triangles)."""
+        """Raw bytes of a built BVH array (0 FP32 nodes, 1 Q8 nodes, 2 triangles, 3 4-wide nodes)."""
         need = C.c_int64()
         self._check(self._L.rtmc_export_bvh(self.h, int(mesh_id), int(which), None, 0, C.byref(need)))
         buf = np.zeros(need.value, dtype=np.uint8)
