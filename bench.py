@@ -35,7 +35,9 @@ METRIC = "traced rays/sec and primaries/sec at stated SEY error; % memory roofli
 ENERGIES = [50.0 * i for i in range(1, 21)]
 N_PRIM = 10_000_000
 GRID, POROSITY, CORR, SEED = 128, 0.6, 2.0, 1806
-NODE_BYTES, TRI_BYTES, RAY_BYTES = 64, 48, 48   # node fetch, triangle fetch, ray read + hit write
+TRI_BYTES, RAY_BYTES = 48, 48                   # triangle fetch, ray read + hit write
+NODE_BYTES = {0: 64, 1: 32, 2: 128}             # node fetch per visit: FP32 binary, Q8 binary, 4-wide FP32
+MAIN_KIND = 2                                   # the paper-config workload runs on 4-wide FP32 nodes
 
 
 def workload_name(n_tri, n_prim, energies=ENERGIES):
@@ -111,7 +113,7 @@ def measured_traffic():
         d = json.load(open(path))
     except (OSError, ValueError):
         return None
-    if d.get("kernel_sha") != kernel_sha():
+    if d.get("kernel_sha") != kernel_sha() or d.get("node_format") != MAIN_KIND:
         return None
     return d.get("dram_bytes_per_ray")
 
@@ -175,17 +177,16 @@ def run_forms(ctx, rtmc, autotune, n_prim):
     meshes = [I.grf_foam(g, p, CORR, sd) for g, p, sd in cfg]
     energies = [50.0 * i for i in range(1, 21)]
     thetas = [10.0 * j for j in range(9)]
-    ids32, idsq = [], []
+    ids32, idsq, idsw = [], [], []
     for m in meshes:
-        a = ctx.load_mesh(m.tri, m.box)
-        ctx.build_bvh(a, kind=rtmc.BVH_FP32)
-        ids32.append(a)
-        b = ctx.load_mesh(m.tri, m.box)
-        ctx.build_bvh(b, kind=rtmc.BVH_Q8)
-        idsq.append(b)
+        for ids, kind in ((ids32, rtmc.BVH_FP32), (idsq, rtmc.BVH_Q8), (idsw, rtmc.BVH_W4)):
+            a = ctx.load_mesh(m.tri, m.box)
+            ctx.build_bvh(a, kind=kind)
+            ids.append(a)
     ntri = [m.n_tri for m in meshes]
     pq = autotune.tune(ctx, idsq, ntri, energies, thetas, kind=1, cache_path=None, device_name="gb300")
     p32 = autotune.tune(ctx, ids32, ntri, energies, thetas, kind=0, cache_path=None, device_name="gb300")
+    pw = autotune.tune(ctx, idsw, ntri, energies, thetas, kind=2, cache_path=None, device_name="gb300")
     per_mesh = len(energies) * len(thetas)
 
     def plain():
@@ -201,6 +202,8 @@ def run_forms(ctx, rtmc, autotune, n_prim):
                                                           desc=rtmc.run_desc(**pq))[0]),
                      ("batched_fp32", lambda: ctx.run_batch(ids32, energies, thetas, n_prim, SEED,
                                                             desc=rtmc.run_desc(**p32))[0]),
+                     ("batched_w4", lambda: ctx.run_batch(idsw, energies, thetas, n_prim, SEED,
+                                                          desc=rtmc.run_desc(**pw))[0]),
                      ("plain_fp32", plain)):
         fn()
         torch.cuda.synchronize()
@@ -212,13 +215,13 @@ def run_forms(ctx, rtmc, autotune, n_prim):
         forms[name] = {"rays_per_s": rays / dt, "primaries_per_s": len(r) * n_prim / dt, "s": dt}
         results[name] = r
     d_sey = max(abs(a["sey"] - b["sey"]) for a, b in zip(results["batched_q8"], results["plain_fp32"]))
-    for mid in ids32 + idsq:
+    for mid in ids32 + idsq + idsw:
         ctx.unload_mesh(mid)
     return {"workload": f"16 GRF foams (grids 48^3..128^3, porosity 0.30..0.90, {min(ntri)}..{max(ntri)} "
                         f"triangles) x 20 energies (50..1000 eV) x 9 angles (0..80 deg) x {n_prim:.0e} primaries",
             "forms": forms, "max_abs_sey_diff_batched_q8_vs_plain_fp32": d_sey,
             "speedup_batched_q8_vs_plain_fp32": forms["plain_fp32"]["s"] / forms["batched_q8"]["s"],
-            "autotuned": {"batched_q8": pq, "batched_fp32": p32}}
+            "autotuned": {"batched_q8": pq, "batched_fp32": p32, "batched_w4": pw}}
 
 
 def run_large(args):
@@ -322,12 +325,12 @@ def run_ours(args):
     ctx = rtmc.Context(local, stream=stream)
     ctx.load_see_tables(table)
     mid = ctx.load_mesh(mesh.tri, mesh.box)
-    ctx.build_bvh(mid)
+    ctx.build_bvh(mid, kind=MAIN_KIND)
     offset = shard.primary_offset(rank, n_prim)   # weak scaling: each rank its own primary ids
     if args.no_autotune:
         tuned = {}
     else:
-        tuned = autotune.tune(ctx, [mid], [mesh.n_tri], energies, [0.0], kind=0, cache_path=None,
+        tuned = autotune.tune(ctx, [mid], [mesh.n_tri], energies, [0.0], kind=MAIN_KIND, cache_path=None,
                               device_name=torch.cuda.get_device_name(dev))
     desc = rtmc.run_desc(primary_offset=offset, profile=True, no_graph=True, **tuned)
 
@@ -395,7 +398,7 @@ def run_ours(args):
     c_rays = sum(r["rays"] for r in cres)
     visits = cres[0]["node_visits"] / c_rays
     tests = cres[0]["tri_tests"] / c_rays
-    b_ray = visits * NODE_BYTES + tests * TRI_BYTES + RAY_BYTES
+    b_ray = visits * NODE_BYTES[MAIN_KIND] + tests * TRI_BYTES + RAY_BYTES
     local_rays = sum(r["rays"] for r in results) * args.steps
     achieved = local_rays * b_ray / (trav_ms / 1e3) / 1e9
     pk, pk_kind = peaks()
@@ -418,7 +421,7 @@ def run_ours(args):
     e_rays = 0
     for _ in range(args.e2e_steps):
         m2 = ctx.load_mesh(tri_host, mesh.box)
-        ctx.build_bvh(m2)
+        ctx.build_bvh(m2, kind=MAIN_KIND)
         rr, _, _ = ctx.run_batch([m2], energies, [0.0], n_prim, SEED, desc=e2e_desc)
         ctx.unload_mesh(m2)
         e_rays += sum(r["rays"] for r in rr)
@@ -451,7 +454,7 @@ def run_ours(args):
             "config": {"workload": workload_name(mesh.n_tri, n_prim, energies), "n_tri": mesh.n_tri,
                        "energies_ev": energies, "theta_deg": [0.0], "primaries_per_energy": n_prim,
                        "primaries_per_step": n_prim * len(energies) * world,
-                       "engine": "rtmc_run_batch (multi-item queues), FP32 BVH nodes, autotuned",
+                       "engine": "rtmc_run_batch (multi-item queues), 4-wide FP32 BVH nodes, autotuned",
                        "autotuned": tuned,
                        "l2": "inputs larger than L2 (BVH nodes + triangles + normals "
                              f"{(mesh.n_tri - 1) * 64 / 1e6 + mesh.n_tri * 64 / 1e6:.0f} MB, ray queues > 1 GB)"},
@@ -461,7 +464,7 @@ def run_ours(args):
             "sey_se_max": max(r["sey_se"] for r in results),
             "sey_error": "GPU vs FP64 oracle: event records bit-exact on >= 99.99% of rays and SEY within "
                          "min(3 SE, 1e-3) (tests/test_gpu_parity.py); statistical SE per energy above",
-            "roofline": {"bound": "hbm", "kernel": "k_traverse_ww", "achieved": achieved, "peak": peak,
+            "roofline": {"bound": "hbm", "kernel": "k_traverse_ww (4-wide nodes)", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": f"{pk_kind} hbm_gbs", "bytes_per_ray": b_ray,
                          "node_visits_per_ray": visits, "tri_tests_per_ray": tests,
