@@ -100,6 +100,19 @@ __device__ __forceinline__ void node_children(const void* __restrict__ nodes, in
     }
 }
 
+// Slab test with the planes already ordered per axis (near first): the same
+// arithmetic and the same result as slab_box, without ordering each pair.
+__device__ __forceinline__ void slab_near_far(float nxp, float fxp, float nyp, float fyp, float nzp, float fzp,
+                                              const RaySetup& r, float t_best, float& tmin, bool& hit)
+{
+    const float nx = (nxp - r.o.x) * r.inv.x, fx = (fxp - r.o.x) * r.inv.x;
+    const float ny = (nyp - r.o.y) * r.inv.y, fy = (fyp - r.o.y) * r.inv.y;
+    const float nz = (nzp - r.o.z) * r.inv.z, fz = (fzp - r.o.z) * r.inv.z;
+    tmin = fmaxf(fmaxf(nx, ny), fmaxf(nz, 0.f));
+    const float tmax = fminf(fminf(fx, fy), fminf(fz, t_best));
+    hit = tmin <= tmax * kRobust;
+}
+
 // 4-wide node (128 B): rows lo.x, hi.x, lo.y, hi.y, lo.z, hi.z of the four
 // child boxes, then the four child refs.  The hit children come back sorted by
 // entry distance (nearest first); *nh is their number.  An empty slot holds
@@ -107,17 +120,22 @@ __device__ __forceinline__ void node_children(const void* __restrict__ nodes, in
 __device__ __forceinline__ void node4_children(const void* __restrict__ nodes, int node, const RaySetup& r,
                                                float t_best, float (&tk)[4], int (&ck)[4], int& nh)
 {
+    // Per axis the lane loads the near row first (lo when the direction is
+    // positive, hi when negative), so (near - o) * inv <= (far - o) * inv and no
+    // min / max is needed to order the two planes: the same values as the
+    // two-plane slab test, three more loads, 24 fewer ALU operations.
     const float4* np = reinterpret_cast<const float4*>(nodes) + 8ll * node;
-    float4 lx, hx, ly, hy, lz, hz, cr, pad;
-    ldg8(np, lx, hx);
-    ldg8(np + 2, ly, hy);
-    ldg8(np + 4, lz, hz);
-    ldg8(np + 6, cr, pad);
+    const int sx = (int)(__float_as_uint(r.inv.x) >> 31), sy = (int)(__float_as_uint(r.inv.y) >> 31),
+              sz = (int)(__float_as_uint(r.inv.z) >> 31);
+    const float4 nx = ldg4(np + sx), fx = ldg4(np + 1 - sx);
+    const float4 ny = ldg4(np + 2 + sy), fy = ldg4(np + 3 - sy);
+    const float4 nz = ldg4(np + 4 + sz), fz = ldg4(np + 5 - sz);
+    const float4 cr = ldg4(np + 6);
     bool h0, h1, h2, h3;
-    slab_box(lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, r, t_best, tk[0], h0);
-    slab_box(lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, r, t_best, tk[1], h1);
-    slab_box(lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, r, t_best, tk[2], h2);
-    slab_box(lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, r, t_best, tk[3], h3);
+    slab_near_far(nx.x, fx.x, ny.x, fy.x, nz.x, fz.x, r, t_best, tk[0], h0);
+    slab_near_far(nx.y, fx.y, ny.y, fy.y, nz.y, fz.y, r, t_best, tk[1], h1);
+    slab_near_far(nx.z, fx.z, ny.z, fy.z, nz.z, fz.z, r, t_best, tk[2], h2);
+    slab_near_far(nx.w, fx.w, ny.w, fy.w, nz.w, fz.w, r, t_best, tk[3], h3);
     ck[0] = __float_as_int(cr.x); ck[1] = __float_as_int(cr.y);
     ck[2] = __float_as_int(cr.z); ck[3] = __float_as_int(cr.w);
     if (!h0) tk[0] = INFINITY;
