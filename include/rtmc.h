@@ -252,8 +252,9 @@ int rtmc_trace_rays(rtmc_ctx* ctx, int32_t mesh_id, const float* o, const float*
    (n_nodes x 64 B), 1 Q8 nodes (n_nodes x 32 B, RTMC_BVH_Q8 meshes only),
    2 triangles in leaf order (n_tri x 48 B), 3 4-wide nodes (RTMC_BVH_W4
    meshes only, n_w4 x 128 B: rows lo.x, hi.x, lo.y, hi.y, lo.z, hi.z of the
-   four child boxes, then the four child refs; an empty slot has ref INT_MIN
-   and the box [+inf, +inf]^3).  Layouts as in the library's
+   four child boxes, each widened outward by M 2^-22 with M the largest
+   coordinate of the cell, then the four child refs; an empty slot has ref
+   INT_MIN and the box [+inf, +inf]^3).  Layouts as in the library's
    device code; a Q8 node holds per axis a shifted origin o' (float) and a
    biased exponent byte b (scale s = 2^(b - 127)), and child bound q decodes
    as fmaf(2^23 + q, s, o') in FP32.  With out == NULL only *bytes_needed is written; otherwise

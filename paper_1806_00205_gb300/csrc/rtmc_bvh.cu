@@ -12,6 +12,8 @@
 //   5. triangles and normals repacked in leaf order as 16-byte aligned float4.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstdio>
 
 #include "rtmc_internal.h"
@@ -747,10 +749,20 @@ __device__ __forceinline__ void w4_store(float4* __restrict__ w4, int w, const B
     nd[7] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
+// A box widened outward by m on every face, rounded outward (the 4-wide slab
+// test evaluates planes with one FMA and relies on this margin).
+__device__ __forceinline__ Box3 widen(const Box3& b, float m)
+{
+    Box3 w;
+    w.lo = make_float3(__fsub_rd(b.lo.x, m), __fsub_rd(b.lo.y, m), __fsub_rd(b.lo.z, m));
+    w.hi = make_float3(__fadd_ru(b.hi.x, m), __fadd_ru(b.hi.y, m), __fadd_ru(b.hi.z, m));
+    return w;
+}
+
 __global__ void k_w4_emit(const int2* __restrict__ front, int nf, const int* __restrict__ off, int base,
                           const int2* __restrict__ child, const int2* __restrict__ range,
                           const float4* __restrict__ aabb, const float* __restrict__ tri,
-                          const unsigned* __restrict__ order, int leaf_max, float4* __restrict__ w4,
+                          const unsigned* __restrict__ order, int leaf_max, float margin, float4* __restrict__ w4,
                           int2* __restrict__ next)
 {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
@@ -769,13 +781,14 @@ __global__ void k_w4_emit(const int2* __restrict__ front, int nf, const int* __r
         }
         const int r = raw[k];
         if (r < 0) {                                   // single triangle at leaf position ~r
-            b[k] = tri_box(tri, order[~r]);
+            b[k] = widen(tri_box(tri, order[~r]), margin);
             ref[k] = ~((~r) << 3);
             continue;
         }
         const float4 lo = aabb[2ll * r], hi = aabb[2ll * r + 1];
         b[k].lo = make_float3(lo.x, lo.y, lo.z);
         b[k].hi = make_float3(hi.x, hi.y, hi.z);
+        b[k] = widen(b[k], margin);
         const int2 rg = range[r];
         const int c = rg.y - rg.x + 1;
         if (c <= leaf_max) {
@@ -790,11 +803,11 @@ __global__ void k_w4_emit(const int2* __restrict__ front, int nf, const int* __r
 }
 
 // One-triangle mesh: the root holds the single leaf.
-__global__ void k_w4_single(const float* __restrict__ tri, float4* __restrict__ w4)
+__global__ void k_w4_single(const float* __restrict__ tri, float margin, float4* __restrict__ w4)
 {
     Box3 b[4];
     int ref[4];
-    b[0] = tri_box(tri, 0);
+    b[0] = widen(tri_box(tri, 0), margin);
     ref[0] = ~0;
     for (int k = 1; k < 4; ++k) {
         b[k].lo = b[k].hi = make_float3(INFINITY, INFINITY, INFINITY);
@@ -859,6 +872,12 @@ int build_lbvh(rtmc_ctx* ctx, DeviceMesh& m)
     if (e != cudaSuccess) return ctx->fail(RTMC_ERR_OOM, std::string("build_bvh scratch: ") + cudaGetErrorString(e));
 
     const rtmc_box& bx = m.box;
+    // outward margin of every 4-wide box: M 2^-22, M the largest coordinate a
+    // ray origin in the cell can have (the FMA slab test's o * inv rounding moves
+    // a plane by at most |o| 2^-24)
+    const double big = std::max(std::max(std::fabs(bx.lx), std::fabs(bx.ly)),
+                                std::max(std::fabs(bx.z_min), std::fabs(bx.z_top)));
+    const float w4_margin = (float)std::ldexp(big, -22);
     const float4 lo = make_float4(0.f, 0.f, (float)bx.z_min, 0.f);
     const float4 inv = make_float4((float)(1.0 / bx.lx), (float)(1.0 / bx.ly),
                                    (float)(1.0 / (bx.z_top - bx.z_min)), 0.f);
@@ -940,7 +959,7 @@ int build_lbvh(rtmc_ctx* ctx, DeviceMesh& m)
         k_single_leaf<<<1, 1, 0, s>>>(m.tri_in, m.nodes);
         if (m.kind == FMT_Q8) k_quantize_single<<<1, 1, 0, s>>>(m.tri_in, reinterpret_cast<uint4*>(m.q8));
         if (m.kind == FMT_W4) {
-            k_w4_single<<<1, 1, 0, s>>>(m.tri_in, reinterpret_cast<float4*>(m.w4));
+            k_w4_single<<<1, 1, 0, s>>>(m.tri_in, w4_margin, reinterpret_cast<float4*>(m.w4));
             m.n_w4 = 1;
             m.depth_w4 = 1;
         }
@@ -977,7 +996,7 @@ int build_lbvh(rtmc_ctx* ctx, DeviceMesh& m)
                 k_w4_scan<<<1, 1024, 0, s>>>(cnt.as<int>(), nf, off.as<int>(), tot.as<int>());
                 k_w4_emit<<<gf, kW4Block, 0, s>>>(fr[cur].as<int2>(), nf, off.as<int>(), base, child.as<int2>(),
                                                   range.as<int2>(), aabb.as<float4>(), m.tri_in, order, m.leaf_max,
-                                                  reinterpret_cast<float4*>(m.w4), fr[1 - cur].as<int2>());
+                                                  w4_margin, reinterpret_cast<float4*>(m.w4), fr[1 - cur].as<int2>());
                 int h_tot = 0;
                 e = cudaMemcpyAsync(&h_tot, tot.p, 4, cudaMemcpyDeviceToHost, s);
                 if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -100,14 +100,20 @@ __device__ __forceinline__ void node_children(const void* __restrict__ nodes, in
     }
 }
 
-// Slab test with the planes already ordered per axis (near first): the same
-// arithmetic and the same result as slab_box, without ordering each pair.
+// Slab test of a 4-wide child with the planes already ordered per axis (near
+// first), one FMA per plane: t = fmaf(plane, inv, -o * inv).  The product
+// plane * inv is exact inside the FMA; the rounding of o * inv moves a plane
+// by at most |o| 2^-24, and 4-wide boxes are stored widened outward by
+// M 2^-22 (M the largest cell coordinate), so the planes tested still enclose
+// the exact box.  The reciprocal and the FMA's own rounding are covered, as
+// in slab_box, by widening tmax by 1 + 2 gamma_3.  Rounding is monotonic, so
+// the near plane stays the nearer.
 __device__ __forceinline__ void slab_near_far(float nxp, float fxp, float nyp, float fyp, float nzp, float fzp,
-                                              const RaySetup& r, float t_best, float& tmin, bool& hit)
+                                              const RaySetup& r, float3 oi, float t_best, float& tmin, bool& hit)
 {
-    const float nx = (nxp - r.o.x) * r.inv.x, fx = (fxp - r.o.x) * r.inv.x;
-    const float ny = (nyp - r.o.y) * r.inv.y, fy = (fyp - r.o.y) * r.inv.y;
-    const float nz = (nzp - r.o.z) * r.inv.z, fz = (fzp - r.o.z) * r.inv.z;
+    const float nx = fmaf(nxp, r.inv.x, -oi.x), fx = fmaf(fxp, r.inv.x, -oi.x);
+    const float ny = fmaf(nyp, r.inv.y, -oi.y), fy = fmaf(fyp, r.inv.y, -oi.y);
+    const float nz = fmaf(nzp, r.inv.z, -oi.z), fz = fmaf(fzp, r.inv.z, -oi.z);
     tmin = fmaxf(fmaxf(nx, ny), fmaxf(nz, 0.f));
     const float tmax = fminf(fminf(fx, fy), fminf(fz, t_best));
     hit = tmin <= tmax * kRobust;
@@ -131,11 +137,12 @@ __device__ __forceinline__ void node4_children(const void* __restrict__ nodes, i
     const float4 ny = ldg4(np + 2 + sy), fy = ldg4(np + 3 - sy);
     const float4 nz = ldg4(np + 4 + sz), fz = ldg4(np + 5 - sz);
     const float4 cr = ldg4(np + 6);
+    const float3 oi = make_float3(r.o.x * r.inv.x, r.o.y * r.inv.y, r.o.z * r.inv.z);
     bool h0, h1, h2, h3;
-    slab_near_far(nx.x, fx.x, ny.x, fy.x, nz.x, fz.x, r, t_best, tk[0], h0);
-    slab_near_far(nx.y, fx.y, ny.y, fy.y, nz.y, fz.y, r, t_best, tk[1], h1);
-    slab_near_far(nx.z, fx.z, ny.z, fy.z, nz.z, fz.z, r, t_best, tk[2], h2);
-    slab_near_far(nx.w, fx.w, ny.w, fy.w, nz.w, fz.w, r, t_best, tk[3], h3);
+    slab_near_far(nx.x, fx.x, ny.x, fy.x, nz.x, fz.x, r, oi, t_best, tk[0], h0);
+    slab_near_far(nx.y, fx.y, ny.y, fy.y, nz.y, fz.y, r, oi, t_best, tk[1], h1);
+    slab_near_far(nx.z, fx.z, ny.z, fy.z, nz.z, fz.z, r, oi, t_best, tk[2], h2);
+    slab_near_far(nx.w, fx.w, ny.w, fy.w, nz.w, fz.w, r, oi, t_best, tk[3], h3);
     ck[0] = __float_as_int(cr.x); ck[1] = __float_as_int(cr.y);
     ck[2] = __float_as_int(cr.z); ck[3] = __float_as_int(cr.w);
     if (!h0) tk[0] = INFINITY;
