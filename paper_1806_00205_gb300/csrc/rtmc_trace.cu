@@ -312,14 +312,53 @@ struct ShadeOut {
 };
 
 // Per-ray contribution to the tallies.
+// Energy moments as unevaluated float pairs (hi + lo): FP64 is a small
+// fraction of the FP32 rate on this GPU, so per-ray and per-warp sums stay in
+// FP32 and become FP64 only where they enter an FP64 atomic.  E^2 splits
+// exactly (E E rounded plus its FMA remainder); a pair sum is Knuth's TwoSum of
+// the high parts with the error and the low parts carried in the low word
+// (relative error a few 2^-48, far below the FP64 moments' needs).  The
+// round-to-nearest intrinsics keep the compiler from contracting the steps.
+struct FF {
+    float hi = 0.f, lo = 0.f;
+};
+
+__device__ __forceinline__ FF ff_add(FF a, FF b)
+{
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bv = __fsub_rn(s, a.hi);
+    const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bv)), __fsub_rn(b.hi, bv));
+    const float lo = __fadd_rn(__fadd_rn(a.lo, b.lo), err);
+    FF r;
+    r.hi = __fadd_rn(s, lo);
+    r.lo = __fsub_rn(lo, __fsub_rn(r.hi, s));
+    return r;
+}
+
+__device__ __forceinline__ FF ff_warp_sum(FF v)
+{
+    for (int off = 16; off; off >>= 1) {
+        FF o;
+        o.hi = __shfl_xor_sync(0xFFFFFFFFu, v.hi, off);
+        o.lo = __shfl_xor_sync(0xFFFFFFFFu, v.lo, off);
+        v = ff_add(v, o);
+    }
+    return v;
+}
+
+__device__ __forceinline__ double ff_double(FF v) { return (double)v.hi + (double)v.lo; }
+__device__ __forceinline__ bool ff_nonzero(FF v) { return v.hi != 0.f || v.lo != 0.f; }
+
 struct Acc {
     unsigned rays = 0, esc = 0, lost = 0, low = 0, other = 0, emit = 0, regen = 0, emitted = 0, capped = 0;
     unsigned wraps = 0;               // multi-item chunks only (the traversal cannot tell items apart)
-    double es = 0.0, e2 = 0.0;
+    FF es, e2;                        // sum E, sum E^2
     __device__ void add(const Acc& a)
     {
         rays += a.rays; esc += a.esc; lost += a.lost; low += a.low; other += a.other; emit += a.emit;
-        regen += a.regen; emitted += a.emitted; capped += a.capped; wraps += a.wraps; es += a.es; e2 += a.e2;
+        regen += a.regen; emitted += a.emitted; capped += a.capped; wraps += a.wraps;
+        es = ff_add(es, a.es);
+        e2 = ff_add(e2, a.e2);
     }
 };
 
@@ -335,8 +374,8 @@ __device__ __forceinline__ void acc_atomic(Tally* t, const Acc& a)
     if (a.emitted) atomicAdd(&t->emitted, (unsigned long long)a.emitted);
     if (a.capped) atomicAdd(&t->capped, (unsigned long long)a.capped);
     if (a.wraps) atomicAdd(&t->wraps, (unsigned long long)a.wraps);
-    if (a.es != 0.0) atomicAdd(&t->e_sum, a.es);
-    if (a.e2 != 0.0) atomicAdd(&t->e2_sum, a.e2);
+    if (ff_nonzero(a.es)) atomicAdd(&t->e_sum, ff_double(a.es));
+    if (ff_nonzero(a.e2)) atomicAdd(&t->e2_sum, ff_double(a.e2));
 }
 
 // With ITEMS the queue holds rays of several items (ray id.y is the item
@@ -400,8 +439,8 @@ k_shade(const float4* __restrict__ tris, const float4* __restrict__ normals, Tab
             const unsigned v = warp_sum(cs[q]);
             if (lane == 0) s_red[q][warp] = v;
         }
-        const double es = warp_sum(acc.es), e2 = warp_sum(acc.e2);
-        if (lane == 0) { s_dred[0][warp] = es; s_dred[1][warp] = e2; }
+        const FF es = ff_warp_sum(acc.es), e2 = ff_warp_sum(acc.e2);
+        if (lane == 0) { s_dred[0][warp] = ff_double(es); s_dred[1][warp] = ff_double(e2); }
         __syncthreads();
         if (tid < 10) {
             unsigned long long v = 0;
@@ -473,8 +512,9 @@ k_shade(const float4* __restrict__ tris, const float4* __restrict__ normals, Tab
                 const unsigned long long ks = ITEMS ? (unsigned long long)rid.y * ic.n_per_item + rid.x - ic.g0
                                                     : prim - p.prim_offset - chunk_first;
                 atomicAdd(&kcount[ks], 1u);
-                r.es = (double)E;
-                r.e2 = (double)E * (double)E;
+                r.es.hi = E;
+                r.e2.hi = __fmul_rn(E, E);
+                r.e2.lo = __fmaf_rn(E, E, -r.e2.hi);     // exact remainder of E^2
             } else if (tri < 0) {
                 fate = RTMC_LOST;
                 r.lost = 1;
@@ -556,15 +596,23 @@ k_shade(const float4* __restrict__ tris, const float4* __restrict__ normals, Tab
                     const unsigned v = __reduce_add_sync(0xFFFFFFFFu, cs[c]);
                     if (lane == 0 && v) atomicAdd(&s_icnt[j0][c], v);
                 }
-                const double es = warp_sum(r.es), e2 = warp_sum(r.e2);
-                if (lane == 0 && es != 0.0) { atomicAdd(&s_isum[j0][0], es); atomicAdd(&s_isum[j0][1], e2); }
+                if (__any_sync(0xFFFFFFFFu, r.esc != 0u)) {
+                    const FF es = ff_warp_sum(r.es), e2 = ff_warp_sum(r.e2);
+                    if (lane == 0) {
+                        atomicAdd(&s_isum[j0][0], ff_double(es));
+                        atomicAdd(&s_isum[j0][1], ff_double(e2));
+                    }
+                }
             } else if (jslot >= 0) {
                 const unsigned cs[10] = {r.rays, r.esc, r.lost, r.low, r.other, r.emit, r.regen, r.emitted,
                                          r.capped, r.wraps};
 #pragma unroll
                 for (int c = 0; c < 10; ++c)
                     if (cs[c]) atomicAdd(&s_icnt[jslot][c], cs[c]);
-                if (r.es != 0.0) { atomicAdd(&s_isum[jslot][0], r.es); atomicAdd(&s_isum[jslot][1], r.e2); }
+                if (ff_nonzero(r.es)) {
+                    atomicAdd(&s_isum[jslot][0], ff_double(r.es));
+                    atomicAdd(&s_isum[jslot][1], ff_double(r.e2));
+                }
             }
         }
         // block exclusive prefix of the daughter counts (warp shuffles + warp totals)
