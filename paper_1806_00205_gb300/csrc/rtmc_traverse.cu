@@ -331,7 +331,11 @@ __device__ __forceinline__ int bvh_closest(const void* __restrict__ nodes, const
     return best;
 }
 
-struct Cell { float lx, ly, z_min, z_top; int max_wraps; };
+struct Cell {
+    float lx, ly, z_min, z_top;
+    int max_wraps;
+    float eps;      // 2^-20 M, M the largest cell coordinate: bound on FP32 face-distance errors
+};
 
 // Trace one ray segment by segment through the periodic cell (Section 2.2,
 // last paragraph).  Returns the hit record; *wraps gets the lateral re-entries.
@@ -569,23 +573,23 @@ k_traverse_ww(const void* __restrict__ nodes, const float4* __restrict__ tris, c
             }
         } else {
             // No facet in this cell: leave through a face.  The distances to the
-            // three faces ahead are estimated in FP32 from the FP64 offsets; they
-            // pick the face unless the two nearest lie within 1e-5 of each other,
-            // when the FP64 quotients decide (the reference rule: z first if
-            // strictly nearest, then x on a tie with y).  Only a wrap needs its
-            // distance in FP64, because it moves the FP64 re-entry point; an exit
-            // through z_top or z_min reports the FP32 estimate.  (FP64 division is
-            // slow on this GPU; most daughters leave a cell at least once.)
+            // three faces ahead are estimated in FP32 from the FP32 origin; they
+            // pick the face unless the two nearest lie closer than the estimates'
+            // error bound (2^-20 M per unit of |1/d|, plus 1e-5 relative), when
+            // the FP64 quotients decide (the reference rule: z first if strictly
+            // nearest, then x on a tie with y).  An exit through z_top or z_min
+            // reports its distance from the FP64 offset; a wrap divides in FP64,
+            // because it moves the FP64 re-entry point.  (FP64 is slow on this
+            // GPU; most daughters leave a cell at least once.)
             double ox = s_o[tid], oy = s_o[B + tid], oz = s_o[2 * B + tid];
-            const float fx = d.x != 0.f ? (float)(d.x > 0.f ? (double)cell.lx - ox : ox) * fabsf(rs.inv.x) : INFINITY;
-            const float fy = d.y != 0.f ? (float)(d.y > 0.f ? (double)cell.ly - oy : oy) * fabsf(rs.inv.y) : INFINITY;
-            const float fz = d.z != 0.f
-                                 ? (float)(d.z > 0.f ? (double)cell.z_top - oz : oz - (double)cell.z_min) * fabsf(rs.inv.z)
-                                 : INFINITY;
+            const float ax = fabsf(rs.inv.x), ay = fabsf(rs.inv.y), az = fabsf(rs.inv.z);
+            const float fx = d.x != 0.f ? (d.x > 0.f ? cell.lx - o.x : o.x) * ax : INFINITY;
+            const float fy = d.y != 0.f ? (d.y > 0.f ? cell.ly - o.y : o.y) * ay : INFINITY;
+            const float fz = d.z != 0.f ? (d.z > 0.f ? cell.z_top - o.z : o.z - cell.z_min) * az : INFINITY;
             const float m1 = fminf(fx, fminf(fy, fz));
             const float m2 = fmaxf(fminf(fx, fy), fminf(fmaxf(fx, fy), fz));   // second smallest
             int face;                                                           // 0 x, 1 y, 2 z
-            if (m2 <= m1 * 1.00001f) {
+            if (m2 - m1 <= 1e-5f * m2 + cell.eps * (ax + ay + az)) {
                 double tx = INFINITY, ty = INFINITY, tz = INFINITY;
                 if (d.x > 0.f) tx = ((double)cell.lx - ox) / d.x; else if (d.x < 0.f) tx = (0.0 - ox) / d.x;
                 if (d.y > 0.f) ty = ((double)cell.ly - oy) / d.y; else if (d.y < 0.f) ty = (0.0 - oy) / d.y;
@@ -598,7 +602,7 @@ k_traverse_ww(const void* __restrict__ nodes, const float4* __restrict__ tris, c
             float tout = 0.f;
             if (face == 2) {
                 code = d.z > 0.f ? HIT_ESCAPE : HIT_LOST;
-                tout = fz;
+                tout = (float)(d.z > 0.f ? (double)cell.z_top - oz : oz - (double)cell.z_min) * az;
             } else if (++wraps > cell.max_wraps) {
                 code = HIT_LOST;
                 tout = fminf(fx, fy);
@@ -739,7 +743,8 @@ template <int F, bool R, bool C>
 static cudaError_t traverse_t(const DeviceMesh& m, const RunParams& p, const Queues& q, int buf, int gen,
                               int num_sms, const Tuning& tune, bool retest, cudaStream_t s)
 {
-    const Cell cell{p.lx, p.ly, p.z_min, p.z_top, p.max_wraps};
+    const float big = fmaxf(fmaxf(fabsf(p.lx), fabsf(p.ly)), fmaxf(fabsf(p.z_min), fabsf(p.z_top)));
+    const Cell cell{p.lx, p.ly, p.z_min, p.z_top, p.max_wraps, ldexpf(big, -20)};
     const void* nodes = F == FMT_Q8 ? m.q8 : (F == FMT_W4 ? m.w4 : (const void*)m.nodes);
     const int bt = tune.block_threads;
     int per_sm = tune.blocks_per_sm;
