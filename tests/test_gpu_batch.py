@@ -22,7 +22,7 @@ def setup():
     ids = []
     for k, m in enumerate(meshes):
         mid = c.load_mesh(m.tri, m.box)
-        c.build_bvh(mid, kind=rtmc.BVH_Q8 if k == 1 else rtmc.BVH_FP32)
+        c.build_bvh(mid, kind=(rtmc.BVH_FP32, rtmc.BVH_Q8, rtmc.BVH_W4)[k])
         ids.append(mid)
     yield c, ids, rtmc
     c.close()
