@@ -159,5 +159,18 @@ def test_large_config_tertiaries_sampled(ctx):
                   emission=O.Emission(regen_min_ev=20.0, max_generation=2))
         dev = h.cpu().numpy().view(np.uint64)[ids.astype(np.int64)]
         assert np.sum(dev != primary_hashes(o["records"], ids)) <= 1
+        # 4-wide FP32 nodes on the same 9.9M-triangle mesh: the same tallies and the same
+        # per-primary event hashes as the Q8 hierarchy (first 1e7 primaries of the 40-degree item)
+        m4 = c2.load_mesh(mesh.tri, mesh.box)
+        c2.build_bvh(m4, kind=rtmc.BVH_W4)
+        n4 = 10_000_000
+        hq = torch.zeros(n4, dtype=torch.int64, device="cuda")
+        h4 = torch.zeros(n4, dtype=torch.int64, device="cuda")
+        rq, _, _ = c2.run(mid, [500.0], [40.0], n4, 1806, desc=rtmc.run_desc(n_ebins=128, n_abins=36, prim_hash=hq))
+        r4, _, _ = c2.run(m4, [500.0], [40.0], n4, 1806, desc=rtmc.run_desc(n_ebins=128, n_abins=36, prim_hash=h4))
+        for k in ("rays", "escaped", "emitted", "regenerated", "sum_k", "sum_k2", "wraps", "lost"):
+            assert rq[0][k] == r4[0][k], k
+        assert torch.equal(hq, h4)
+        assert torch.equal(hq, h[:n4])          # the prefix of the full 1e8 run
     finally:
         c2.close()
