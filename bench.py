@@ -305,6 +305,166 @@ def run_large(args):
     ctx.close()
 
 
+PREC_POROSITY = (0.4, 0.6, 0.8)
+PREC_E, PREC_THETA = [100.0, 300.0, 700.0], [0.0, 60.0]
+
+
+def precision_oracle_check(ctx, rtmc, O, mesh, table, mid, n_s):
+    """The first n_s primaries of every (E, theta) item, on the oracle and on the GPU
+    (same streams: item_base = item index).  Returns per-item (gpu, oracle) escape counts,
+    oracle rays and the oracle's seconds and threads."""
+    out, rays, secs = [], 0, 0.0
+    threads = os.cpu_count() or 1
+    for ie, e in enumerate(PREC_E):
+        for it, th in enumerate(PREC_THETA):
+            k = ie * len(PREC_THETA) + it
+            g, _, _ = ctx.run(mid, [e], [th], n_s, SEED, desc=rtmc.run_desc(fp64_retest=True, item_base=k))
+            t0 = time.perf_counter()
+            o = O.run(mesh, table, e, th, n_s, SEED, item=k, n_threads=threads)
+            secs += time.perf_counter() - t0
+            rays += o["rays"]
+            out.append((g[0]["escaped"], o["escaped"]))
+    return out, rays, secs, threads
+
+
+def run_precision(args):
+    """Precision config: 128^3 foams at porosity 0.4 / 0.6 / 0.8, 1e7 primaries at 100, 300
+    and 700 eV x incidence 0 and 60 deg.  Q8 nodes, FP32 watertight tests, FP64 re-test of
+    flagged hits, FP64 moments.  The same streams on FP32 nodes without re-test give the
+    plain SEY; the first primaries of every item go through the oracle as well."""
+    import torch
+    import oracle as O
+    from paper_1806_00205_gb300 import inputs as I
+    from paper_1806_00205_gb300 import rtmc
+    dev = torch.device("cuda", 0)
+    n_prim = args.primaries
+    table = I.see_table()
+    meshes = [I.grf_foam(GRID, p, CORR, SEED) for p in PREC_POROSITY]
+    stream = torch.cuda.Stream(device=dev)
+    ctx = rtmc.Context(0, stream=stream)
+    ctx.load_see_tables(table)
+    mq, m32 = [], []
+    for m in meshes:
+        for ids, kind in ((mq, rtmc.BVH_Q8), (m32, rtmc.BVH_FP32)):
+            a = ctx.load_mesh(m.tri, m.box)
+            ctx.build_bvh(a, kind=kind)
+            ids.append(a)
+    desc = rtmc.run_desc(fp64_retest=True, profile=True)
+    for _ in range(args.warmup):
+        for a in mq:
+            ctx.run(a, PREC_E, PREC_THETA, n_prim // 10, SEED, desc=desc)
+    clocks = ClockSampler(0)
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    rays = prims = launches = retested = trav_l = 0
+    trav_ms = 0.0
+    prec = []
+    for _ in range(args.steps):
+        prec = []
+        for a in mq:
+            res, _, _ = ctx.run(a, PREC_E, PREC_THETA, n_prim, SEED, desc=desc)
+            prec.append(res)
+            rays += sum(r["rays"] for r in res)
+            prims += sum(r["n_primaries"] for r in res)
+            launches += sum(r["launches"] for r in res)
+            retested += sum(r["retested"] for r in res)
+            trav_ms += sum(r["ms_traverse"] for r in res)
+            trav_l += sum(r["traverse_launches"] for r in res)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    return finish_precision(args, ctx, rtmc, O, I, meshes, table, mq, m32, prec, n_prim, dict(
+        rays=rays, prims=prims, launches=launches, retested=retested, trav_ms=trav_ms, trav_l=trav_l,
+        ms=ms, clk=clk, stream=stream))
+
+
+def finish_precision(args, ctx, rtmc, O, I, meshes, table, mq, m32, prec, n_prim, t):
+    import torch
+    dev = torch.device("cuda", 0)
+    stream = t["stream"]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    plain, plain_rays = [], 0
+    for a in m32:
+        res, _, _ = ctx.run(a, PREC_E, PREC_THETA, n_prim, SEED)
+        plain.append(res)
+        plain_rays += sum(r["rays"] for r in res)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    plain_ms = ev0.elapsed_time(ev1)
+    items, max_d = [], 0.0
+    for p, rq, rp in zip(PREC_POROSITY, prec, plain):
+        for k, (a, b) in enumerate(zip(rq, rp)):
+            d = abs(a["sey"] - b["sey"])
+            max_d = max(max_d, d)
+            items.append({"porosity": p, "energy_ev": PREC_E[k // len(PREC_THETA)],
+                          "theta_deg": PREC_THETA[k % len(PREC_THETA)], "sey": round(a["sey"], 6),
+                          "sey_se": round(a["sey_se"], 6), "sey_fp32_nodes": round(b["sey"], 6),
+                          "abs_diff_vs_fp32": d, "retested_frac": a["retested"] / a["rays"]})
+    cq, _, _ = ctx.run(mq[1], [300.0], [60.0], n_prim // 10, SEED,
+                       desc=rtmc.run_desc(fp64_retest=True, count_visits=True))
+    visits = cq[0]["node_visits"] / cq[0]["rays"]
+    tests = cq[0]["tri_tests"] / cq[0]["rays"]
+    b_ray = visits * NODE_BYTES[1] + tests * TRI_BYTES + RAY_BYTES
+    achieved = t["rays"] * b_ray / (t["trav_ms"] / 1e3) / 1e9
+    pk, pk_kind = peaks()
+    peak = float(pk.get("hbm_gbs", 6800.0))
+    ora, diffs, cpu = None, [], None
+    if not args.no_cpu:
+        n_s, o_rays, o_secs, thr, g_esc, o_esc = args.prec_oracle, 0, 0.0, 1, 0, 0
+        for m, a in zip(meshes, mq):
+            out, r, s, thr = precision_oracle_check(ctx, rtmc, O, m, table, a, n_s)
+            o_rays += r
+            o_secs += s
+            for g, o in out:
+                g_esc += g
+                o_esc += o
+                diffs.append(abs(g - o) / n_s)
+        ora = {"primaries_per_item": n_s, "items": len(diffs), "sey_gpu": g_esc / (n_s * len(diffs)),
+               "sey_oracle": o_esc / (n_s * len(diffs)), "max_abs_diff_per_item": max(diffs),
+               "note": "first primaries of every item, same random streams on both sides"}
+        cpu = {"value": o_rays / o_secs, "unit": "rays/s", "cores": thr, "kind": "oracle",
+               "sample": f"{n_s} primaries per (porosity, E, theta) item, 18 items, brute force over "
+                         f"all triangles per ray segment; {o_secs:.1f} s"}
+    hosts = [torch.from_numpy(m.tri.reshape(-1, 9)).pin_memory() for m in meshes]
+    torch.cuda.synchronize(dev)
+    e0 = time.perf_counter()
+    e_rays = 0
+    ctx.load_see_tables(table)
+    for h, m in zip(hosts, meshes):
+        a = ctx.load_mesh(h, m.box)
+        ctx.build_bvh(a, kind=rtmc.BVH_Q8)
+        rr, _, _ = ctx.run(a, PREC_E, PREC_THETA, n_prim, SEED, desc=rtmc.run_desc(fp64_retest=True))
+        e_rays += sum(r["rays"] for r in rr)
+        ctx.unload_mesh(a)
+    e_dt = time.perf_counter() - e0
+    ms, steps = t["ms"], args.steps
+    ntri = [m.n_tri for m in meshes]
+    line = {"metric": METRIC, "value": t["rays"] / (ms / 1e3), "unit": "rays/s", "n_gpus": 1, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "primaries_per_s": t["prims"] / (ms / 1e3),
+            "config": {"workload": f"precision: {GRID}^3 periodic GRF foams at porosity 0.4 / 0.6 / 0.8 -> "
+                                   f"{ntri} triangles, Q8 BVH, FP64 re-test of flagged hits; {n_prim:.0e} "
+                                   "primaries at 100 / 300 / 700 eV x incidence 0 / 60 deg",
+                       "n_tri": ntri, "l2": "inputs larger than L2 (three meshes, Q8 nodes + triangles)"},
+            "sey_error": {"max_abs_diff_vs_fp32_nodes": max_d, "oracle_sample": ora,
+                          "retested_frac": t["retested"] / t["rays"]},
+            "items": items, "plain_fp32_rays_per_s": plain_rays / (plain_ms / 1e3),
+            "roofline": {"bound": "hbm", "kernel": "k_traverse_ww (Q8)", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "peak_kind": f"{pk_kind} hbm_gbs", "bytes_per_ray": b_ray,
+                         "node_visits_per_ray": visits, "tri_tests_per_ray": tests},
+            "e2e": {"value": e_rays / e_dt, "unit": "rays/s",
+                    "h2d_bytes_per_step": sum(h.numel() * 4 for h in hosts) + table.delta.nbytes,
+                    "d2h_bytes_per_step": 18 * (rtmc.C.sizeof(rtmc.Result) + 8 * (64 + 18))},
+            "gpu_launches": t["launches"], "clocks": t["clk"], "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -500,13 +660,18 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the batched-config form comparison")
     ap.add_argument("--forms-primaries", type=int, default=1_000_000)
     ap.add_argument("--no-autotune", action="store_true", help="default launch parameters (profiling runs)")
-    ap.add_argument("--config", choices=("paper", "large"), default="paper",
-                    help="paper: 128^3 foam, 20 energies x 1e7 (default); large: 256^3 foam, tertiaries")
+    ap.add_argument("--config", choices=("paper", "large", "precision"), default="paper",
+                    help="paper: 128^3 foam, 20 energies x 1e7 (default); large: 256^3 foam, tertiaries; "
+                         "precision: 3 porosities, Q8 nodes + FP64 re-test, 3 energies x 2 angles")
+    ap.add_argument("--prec-oracle", type=int, default=64,
+                    help="precision config: primaries per item checked against the oracle")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
     elif args.config == "large":
         run_large(args)
+    elif args.config == "precision":
+        run_precision(args)
     else:
         run_ours(args)
 
