@@ -109,9 +109,11 @@ typedef struct {
     int32_t count_visits;          /* 1: count BVH node visits and triangle tests */
     int32_t traversal;             /* 0: default; 1: one ray per lane per 32-ray tile;
                                       2: while-while loop with per-lane ray refill */
-    int32_t fp64_retest;           /* 1: re-test hits within 1e-5 (barycentric) of an edge
-                                      or with cos(incidence) < 1e-3 using FP64 triangle
-                                      tests (while-while traversal only) */
+    int32_t fp64_retest;           /* 1: decide in FP64 every facet whose FP32 edge
+                                      functions lie within 1e-5 (relative to their sum)
+                                      of an edge, hit or miss, and take the distance of a
+                                      closest hit with cos(incidence) < 1e-3 from the FP64
+                                      test (while-while traversal only) */
     uint32_t item_base;            /* added to every item index (Philox counter word 3) */
     int32_t no_graph;              /* rtmc_run_batch: 1 = launch eagerly, no CUDA graph */
     int32_t stack_depth;           /* shared-memory traversal stack entries: 8, 16 or 32 (0 -> 16) */
@@ -138,7 +140,7 @@ typedef struct {
     int64_t node_visits, tri_tests;            /* with count_visits */
     double ms_generate, ms_traverse, ms_shade, ms_finalize;   /* with profile */
     int64_t traverse_launches;
-    int64_t retested;                          /* rays re-tested in FP64 */
+    int64_t retested;                          /* rays with a facet decided in FP64 */
 } rtmc_result;
 
 /* One traced ray: the integer event sequence used for parity checks. */

@@ -226,7 +226,6 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
         }
         if (ce == cudaSuccess) ce = scratch_reserve(ctx->hits, (size_t)capmax * 16);
         if (ce == cudaSuccess && need_wraps) ce = scratch_reserve(ctx->wraps, (size_t)capmax * 4);
-        if (ce == cudaSuccess && d.fp64_retest) ce = scratch_reserve(ctx->retest, (size_t)capmax * 4);
         const bool kc_new = ctx->kcount.bytes < (size_t)chunk * 4;
         if (ce == cudaSuccess) ce = scratch_reserve(ctx->kcount, (size_t)chunk * 4);
         if (ce == cudaSuccess && kc_new) ce = cudaMemsetAsync(ctx->kcount.ptr, 0, ctx->kcount.bytes, s);
@@ -248,7 +247,6 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
         q.hits = (float4*)ctx->hits.ptr;
         q.wraps = need_wraps ? (int*)ctx->wraps.ptr : nullptr;
         q.kcount = (unsigned*)ctx->kcount.ptr;
-        q.retest = d.fp64_retest ? (unsigned*)ctx->retest.ptr : nullptr;
         q.sort_counts = d.id_order ? nullptr : (unsigned*)ctx->sort_counts.ptr;
         q.ctl = (Control*)ctx->ctl.ptr;
         q.tally = (Tally*)ctx->tally.ptr;
@@ -297,7 +295,7 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
                 if (ce == cudaSuccess)
                     ce = launch_shade(m, p, tab, e, q, buf, g, (unsigned long long)first, ctx->num_sms, record, s);
                 tock(h);
-                launches += 2 + (d.fp64_retest ? 1 : 0);
+                launches += 2;
                 ++trav_launches;
             }
             h = tick(3);
@@ -440,7 +438,7 @@ void rtmc_destroy(rtmc_ctx* ctx)
     if (ctx->batch_graph) cudaGraphExecDestroy(ctx->batch_graph);
     rtmc::Scratch* all[] = {&ctx->q_oe[0], &ctx->q_oe[1], &ctx->q_dt[0], &ctx->q_dt[1], &ctx->q_id[0],
                             &ctx->q_id[1], &ctx->hits, &ctx->kcount, &ctx->ctl, &ctx->tally, &ctx->hist,
-                            &ctx->wraps, &ctx->records, &ctx->tmp, &ctx->retest, &ctx->items,
+                            &ctx->wraps, &ctx->records, &ctx->tmp, &ctx->items,
                             &ctx->sort_counts};
     for (auto* s : all) rtmc::scratch_free(*s);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);

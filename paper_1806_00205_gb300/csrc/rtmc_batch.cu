@@ -111,7 +111,7 @@ cudaError_t record_batch(rtmc_ctx* ctx, const rtmc_batch& b, const rtmc_run_desc
                 h = kt.tick(2, s);
                 if (ce == cudaSuccess) ce = launch_shade_items(m, p, tab, em, ic, qq, buf, g, ctx->num_sms, s);
                 kt.tock(h, s);
-                launches += 2 + (d.fp64_retest ? 1 : 0);
+                launches += 2;
             }
             h = kt.tick(3, s);
             if (ce == cudaSuccess) ce = launch_finalize_items(ic, qq, n, ctx->num_sms, s);
@@ -192,10 +192,10 @@ extern "C" int rtmc_run_batch(rtmc_ctx* ctx, const rtmc_batch* batch, const rtmc
     const int64_t cap0 = chunk, cap1 = chunk * kmax;
     if (cap1 > 0xFFFFFFF0ll) return ctx->fail(RTMC_ERR_CAPACITY, "run_batch: chunk too large");
     cudaError_t ce = cudaSuccess;
-    const void* before[15] = {ctx->q_oe[0].ptr, ctx->q_oe[1].ptr, ctx->q_dt[0].ptr, ctx->q_dt[1].ptr,
+    const void* before[14] = {ctx->q_oe[0].ptr, ctx->q_oe[1].ptr, ctx->q_dt[0].ptr, ctx->q_dt[1].ptr,
                               ctx->q_id[0].ptr, ctx->q_id[1].ptr, ctx->hits.ptr, ctx->kcount.ptr,
                               ctx->ctl.ptr, ctx->tally.ptr, ctx->hist.ptr, ctx->items.ptr, ctx->wraps.ptr,
-                              ctx->retest.ptr, ctx->sort_counts.ptr};
+                              ctx->sort_counts.ptr};
     for (int bb = 0; bb < 2 && ce == cudaSuccess; ++bb) {
         const int64_t c = bb ? cap1 : cap0;
         ce = scratch_reserve(ctx->q_oe[bb], (size_t)c * 16);
@@ -211,14 +211,13 @@ extern "C" int rtmc_run_batch(rtmc_ctx* ctx, const rtmc_batch* batch, const rtmc
     if (ce == cudaSuccess) ce = scratch_reserve(ctx->wraps, (size_t)cap1 * 4);
     if (ce == cudaSuccess) ce = scratch_reserve(ctx->hist, (size_t)n_items * nbins * 8);
     if (ce == cudaSuccess) ce = scratch_reserve(ctx->items, (size_t)n_items * sizeof(ItemDev));
-    if (ce == cudaSuccess && d.fp64_retest) ce = scratch_reserve(ctx->retest, (size_t)cap1 * 4);
     if (ce == cudaSuccess && !d.id_order)
         ce = scratch_reserve(ctx->sort_counts, (size_t)kChunkItems * kSortBucketsPerItem * 4);
     if (ce != cudaSuccess) return ctx->fail(RTMC_ERR_OOM, std::string("run_batch: scratch: ") + cudaGetErrorString(ce));
-    const void* after[15] = {ctx->q_oe[0].ptr, ctx->q_oe[1].ptr, ctx->q_dt[0].ptr, ctx->q_dt[1].ptr,
+    const void* after[14] = {ctx->q_oe[0].ptr, ctx->q_oe[1].ptr, ctx->q_dt[0].ptr, ctx->q_dt[1].ptr,
                              ctx->q_id[0].ptr, ctx->q_id[1].ptr, ctx->hits.ptr, ctx->kcount.ptr,
                              ctx->ctl.ptr, ctx->tally.ptr, ctx->hist.ptr, ctx->items.ptr, ctx->wraps.ptr,
-                             ctx->retest.ptr, ctx->sort_counts.ptr};
+                             ctx->sort_counts.ptr};
     const bool moved = std::memcmp(before, after, sizeof before) != 0;
 
     Queues q;
@@ -232,7 +231,6 @@ extern "C" int rtmc_run_batch(rtmc_ctx* ctx, const rtmc_batch* batch, const rtmc
     q.hits = (float4*)ctx->hits.ptr;
     q.wraps = (int*)ctx->wraps.ptr;
     q.kcount = (unsigned*)ctx->kcount.ptr;
-    q.retest = d.fp64_retest ? (unsigned*)ctx->retest.ptr : nullptr;
     q.sort_counts = d.id_order ? nullptr : (unsigned*)ctx->sort_counts.ptr;
     q.ctl = (Control*)ctx->ctl.ptr;
     q.tally = (Tally*)ctx->tally.ptr;

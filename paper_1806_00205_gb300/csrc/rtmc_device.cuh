@@ -50,7 +50,6 @@ struct Tally {                    // one (energy, angle) item, device resident
 struct Control {                  // per chunk
     unsigned int count[8];        // rays in queue of generation g
     unsigned int next[8];         // persistent-traversal work counter per generation
-    unsigned int n_retest[8];     // rays flagged for the FP64 re-test per generation
 };
 
 // One (energy, angle) item of a batched launch.

@@ -59,7 +59,7 @@ struct rtmc_ctx {
     rtmc_emission emission{};
     bool table_loaded = false;
     // run buffers
-    rtmc::Scratch q_oe[2], q_dt[2], q_id[2], hits, kcount, ctl, tally, hist, wraps, records, tmp, retest;
+    rtmc::Scratch q_oe[2], q_dt[2], q_id[2], hits, kcount, ctl, tally, hist, wraps, records, tmp;
     rtmc::Scratch items;                      // batched item table
     rtmc::Scratch sort_counts;                // spatial sort of primaries
     cudaGraphExec_t batch_graph = nullptr;    // captured batch launch sequence
@@ -112,7 +112,6 @@ struct Queues {
     float4* hits;
     int* wraps;                  // record mode only
     unsigned* kcount;
-    unsigned* retest;            // flagged ray indices (FP64 re-test), capacity max(cap)
     unsigned* sort_counts;       // spatial sort of primaries: per-bucket counts / cursors
     Control* ctl;
     Tally* tally;

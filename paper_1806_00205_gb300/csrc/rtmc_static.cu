@@ -187,7 +187,6 @@ extern "C" int rtmc_run_noalloc(rtmc_ctx* ctx, int32_t mesh_id, double energy_ev
     const bool hashing = d.prim_hash != nullptr;
     q.wraps = hashing ? reinterpret_cast<int*>(base + kWraps) : nullptr;
     q.kcount = reinterpret_cast<unsigned*>(base + kKcount);
-    q.retest = nullptr;
     q.sort_counts = nullptr;   // primaries stay in id order here (no sort scratch)
     q.ctl = reinterpret_cast<Control*>(base + kCtl);
     q.tally = reinterpret_cast<Tally*>(base + kTally);

@@ -245,13 +245,14 @@ __device__ __forceinline__ void test_leaf(const float4* __restrict__ tris, const
 
 // Closest front-facing triangle (leaf order index) with t > 0, skipping
 // `skip`: one ray per lane, leaves tested as soon as their box is hit.
-template <int FMT, bool COUNT = false, bool TRI64 = false>
+// SMEM: stack entries per ray held in shared memory (the rest in local memory).
+template <int FMT, bool COUNT = false, bool TRI64 = false, int SMEM = kSmemStack>
 __device__ __forceinline__ int bvh_closest(const void* __restrict__ nodes, const float4* __restrict__ tris,
                                            const RaySetup& r, const RaySetup64& r64, int skip, StackRef st,
                                            float& t_best, float& bu, float& bv, unsigned& status,
                                            Counts* cnt = nullptr)
 {
-    int2 lstack[kStackMax - kSmemStack];
+    int2 lstack[kStackMax - SMEM];
     int sp = 0;
     int node = 0;
     int best = -1, best_orig = INT_MAX;
@@ -260,15 +261,15 @@ __device__ __forceinline__ int bvh_closest(const void* __restrict__ nodes, const
     bu = bv = 0.f;
     auto push = [&](int ref, float tmin) {
         const int2 e = make_int2(ref, __float_as_int(tmin));
-        if (sp < kSmemStack) st.smem[sp * st.stride + st.tid] = e;
-        else if (sp < kStackMax) lstack[sp - kSmemStack] = e;
+        if (sp < SMEM) st.smem[sp * st.stride + st.tid] = e;
+        else if (sp < kStackMax) lstack[sp - SMEM] = e;
         else { status |= ST_STACK_OVERFLOW; sp = kStackMax - 1; }
         ++sp;
     };
     auto pop = [&]() -> bool {
         while (sp > 0) {
             --sp;
-            const int2 e = sp < kSmemStack ? st.smem[sp * st.stride + st.tid] : lstack[sp - kSmemStack];
+            const int2 e = sp < SMEM ? st.smem[sp * st.stride + st.tid] : lstack[sp - SMEM];
             if (__int_as_float(e.y) <= t_best * kRobust) { node = e.x; return true; }
         }
         return false;
@@ -310,8 +311,8 @@ __device__ __forceinline__ int bvh_closest(const void* __restrict__ nodes, const
             float tfar = tmin1;
             if (tmin1 < tmin0) { near = c1; far = c0; tfar = tmin0; }
             const int2 e = make_int2(far, __float_as_int(tfar));
-            if (sp < kSmemStack) st.smem[sp * st.stride + st.tid] = e;
-            else if (sp < kStackMax) lstack[sp - kSmemStack] = e;
+            if (sp < SMEM) st.smem[sp * st.stride + st.tid] = e;
+            else if (sp < kStackMax) lstack[sp - SMEM] = e;
             else { status |= ST_STACK_OVERFLOW; sp = kStackMax - 1; }
             ++sp;
             node = near;
@@ -322,7 +323,7 @@ __device__ __forceinline__ int bvh_closest(const void* __restrict__ nodes, const
         bool found = false;
         while (sp > 0) {
             --sp;
-            const int2 e = sp < kSmemStack ? st.smem[sp * st.stride + st.tid] : lstack[sp - kSmemStack];
+            const int2 e = sp < SMEM ? st.smem[sp * st.stride + st.tid] : lstack[sp - SMEM];
             if (__int_as_float(e.y) <= t_best * kRobust) { node = e.x; found = true; break; }
         }
         if (!found) break;
@@ -342,7 +343,7 @@ struct Cell {
 // The re-entry point is carried in FP64 (a few operations per wrap) so a ray
 // that wraps many times does not accumulate FP32 rounding in its origin; each
 // cell query uses that point rounded to FP32.
-template <int FMT, bool COUNT, bool TRI64>
+template <int FMT, bool COUNT, bool TRI64, int SMEM = kSmemStack>
 __device__ __forceinline__ float4 trace_ray(const void* __restrict__ nodes, const float4* __restrict__ tris,
                                             const float3 o32, const float3 d, int skip, const Cell& c, StackRef st,
                                             int& wraps, unsigned& status, Counts* cnt)
@@ -355,7 +356,7 @@ __device__ __forceinline__ float4 trace_ray(const void* __restrict__ nodes, cons
         RaySetup64 r64;
         if (TRI64) r64 = setup_ray64(o, d);
         float t, u, v;
-        const int j = bvh_closest<FMT, COUNT, TRI64>(nodes, tris, rs, r64, skip, st, t, u, v, status, cnt);
+        const int j = bvh_closest<FMT, COUNT, TRI64, SMEM>(nodes, tris, rs, r64, skip, st, t, u, v, status, cnt);
         if (j >= 0) return make_float4(t, u, v, __int_as_float(j));
         double tx = INFINITY, ty = INFINITY, tz = INFINITY;
         if (d.x > 0.f) tx = ((double)c.lx - ox) / d.x; else if (d.x < 0.f) tx = (0.0 - ox) / d.x;
@@ -427,6 +428,57 @@ k_traverse(const void* __restrict__ nodes, const float4* __restrict__ tris, Cell
     }
 }
 
+// Re-test form of the FP32 watertight test: besides a new closest hit (1) or
+// none (0) it answers 2 when the facet's smallest edge function lies within
+// edge_eps (relative to |U| + |V| + |W|) of zero -- a hit or a miss too close
+// to an edge for FP32 to decide -- and leaves that facet to the FP64 test.
+// With edge_eps = 0 every facet gets the plain FP32 decision.
+__device__ __forceinline__ int intersect_tri_rt(const RaySetup& r, float4 w0, float4 w1, float4 w2, float edge_eps,
+                                                float& t_best, int& best_orig, float& bu, float& bv)
+{
+    const float3 A = f3(w0) - r.o, B = f3(w1) - r.o, C = f3(w2) - r.o;
+    const float ax = dot3(A, r.mx), ay = dot3(A, r.my);
+    const float bx = dot3(B, r.mx), by = dot3(B, r.my);
+    const float cx = dot3(C, r.mx), cy = dot3(C, r.my);
+    const float U = cx * by - cy * bx, V = ax * cy - ay * cx, W = bx * ay - by * ax;
+    const float m = fminf(fminf(U, V), W);
+    const float e = edge_eps * (fabsf(U) + fabsf(V) + fabsf(W));
+    if (m < -e) return 0;                          // clearly outside or back-facing
+    if (m <= e && edge_eps > 0.f) return 2;        // near an edge: FP64 decides
+    const float det = U + V + W;
+    if (det == 0.f) return 0;
+    const float az = dot3(A, r.mz), bz = dot3(B, r.mz), cz = dot3(C, r.mz);
+    const float T = U * az + V * bz + W * cz;
+    if (T <= 0.f) return 0;
+    const float t = T / det;
+    const int orig = __float_as_int(w0.w);
+    if (t < t_best || (t == t_best && orig < best_orig)) {
+        t_best = t;
+        best_orig = orig;
+        bu = V / det;
+        bv = W / det;
+        return 1;
+    }
+    return 0;
+}
+
+// FP64 test of one facet against the best hit so far (state in and out by
+// value).  Out of line, so its double-precision registers never press on the
+// traversal loop that calls it for the rare ambiguous facet.
+struct Hit64 {
+    double t;             // best distance so far
+    float u, v;
+    int orig;             // original index of the best facet
+    bool won;             // this facet is the new best
+};
+
+__device__ __noinline__ Hit64 facet_fp64(float3 o, float3 d, float4 w0, float4 w1, float4 w2, Hit64 cur)
+{
+    const RaySetup64 r64 = setup_ray64(o, d);
+    cur.won = intersect_tri64(r64, w0, w1, w2, cur.t, cur.orig, cur.u, cur.v);
+    return cur;
+}
+
 // --------------------------------------------------------------------------
 // traverse, while-while form (Aila & Laine, HPG 2009): inner nodes and leaf
 // triangles run in separate loops so the lanes of a warp stay in the same
@@ -434,24 +486,37 @@ k_traverse(const void* __restrict__ nodes, const float4* __restrict__ tris, Cell
 // has one.  A lane whose ray finishes takes a new ray from the generation's
 // queue (one atomic per warp refill) instead of idling until the whole tile
 // is done.  The FP64 re-entry point of each lane lives in shared memory.
-// With RETEST, hits closer than kEdgeEps (barycentric) to an edge or with
-// cos(incidence) below kGrazeCos are listed for the FP64 re-test kernel.
+// With RETEST, a facet whose FP32 edge functions cannot decide it (within
+// kEdgeEps of an edge, hit or miss) is set aside -- up to kAmbMax per cell
+// traversal, in the lane's shared-memory list -- and decided by the FP64 test
+// once the cell's traversal ends; a closest hit meeting its facet with
+// cos(incidence) below kGrazeCos gets its distance from the FP64 test too.
+// Setting a facet aside only weakens the culling meanwhile, so none is
+// missed.  The FP64 work is per ambiguous facet, in the same launch, and its
+// call stays out of the inner loops (a call there costs registers on every
+// iteration).  Ambiguous facets beyond kAmbMax in one cell (expected about
+// once in 1e17 cells at the measured rate of 1e-4 per test) keep the FP32
+// decision.
 // --------------------------------------------------------------------------
 constexpr int kEntrySentinel = 0x76543210;   // "stack empty" (never a node index)
 constexpr int kFetchThreshold = 20;          // default: refill when fewer lanes than this are active
 constexpr float kEdgeEps = 1e-5f;
 constexpr float kGrazeCos = 1e-3f;
+constexpr int kAmbMax = 4;
 
 template <int FMT, bool RECORD, bool COUNT, bool RETEST, int SSTACK>
 __global__ void __launch_bounds__(128, 8)
 k_traverse_ww(const void* __restrict__ nodes, const float4* __restrict__ tris, const float4* __restrict__ normals,
               Cell cell, const float4* __restrict__ oe, const float4* __restrict__ dt, float4* __restrict__ hits,
               int* __restrict__ wraps_out, Control* __restrict__ ctl, int gen, unsigned cap,
-              unsigned* __restrict__ retest_list, Tally* __restrict__ tally, int fetch_threshold)
+              Tally* __restrict__ tally, int fetch_threshold)
 {
     extern __shared__ int2 s_stack[];                                   // [SSTACK][blockDim]
     const int B = blockDim.x, tid = threadIdx.x, lane = tid & 31;
     double* s_o = reinterpret_cast<double*>(s_stack + SSTACK * B);       // [3][blockDim]
+    double* s_t64 = s_o + 3 * B;                                         // RETEST: [blockDim]
+    int* s_b64 = reinterpret_cast<int*>(s_t64 + B);                      // RETEST: [blockDim]
+    int* s_amb = s_b64 + B;                                              // RETEST: [kAmbMax][blockDim]
     const unsigned lt = (1u << lane) - 1u;
     const unsigned n = min(*((volatile unsigned*)&ctl->count[gen]), cap);
     int2 lstack[kStackMax - SSTACK];
@@ -460,12 +525,14 @@ k_traverse_ww(const void* __restrict__ nodes, const float4* __restrict__ tris, c
     bool exhausted = false, drained = false;
     float3 o = make_float3(0.f, 0.f, 0.f), d = make_float3(0.f, 0.f, 1.f);
     RaySetup rs = setup_ray(o, d);
-    RaySetup64 r64;
     float t_best = kNoHit, bu = 0.f, bv = 0.f;
     double t_best64 = INFINITY;
     int best = -1, best_orig = INT_MAX, node = kEntrySentinel, leaf = 0, sp = 0, skip = -1, wraps = 0, visits = 0;
     unsigned status = 0;
     unsigned long long my_wraps = 0;
+    unsigned my_retested = 0;
+    bool used64 = false;                 // RETEST: the current ray had a facet decided in FP64
+    int namb = 0;                        // RETEST: facets set aside for FP64 in this cell
     Counts cnt;
 
     auto push = [&](int node_ref, float tmin) {
@@ -487,6 +554,7 @@ k_traverse_ww(const void* __restrict__ nodes, const float4* __restrict__ tris, c
         rs = setup_ray(o, d);
         node = 0; leaf = 0; sp = 0; visits = 0;
         t_best = kNoHit; best = -1; best_orig = INT_MAX; bu = bv = 0.f;
+        if (RETEST) { s_b64[tid] = -1; namb = 0; }   // s_t64: FP64 distance of facet s_b64 (if the best)
     };
 
     for (;;) {
@@ -549,7 +617,24 @@ k_traverse_ww(const void* __restrict__ nodes, const float4* __restrict__ tris, c
                 if (!__any_sync(__activemask(), leaf == 0)) break;
             }
             while (leaf < 0) {
-                test_leaf<COUNT, false>(tris, rs, r64, leaf, skip, t_best, t_best64, best, best_orig, bu, bv, &cnt);
+                if (RETEST) {
+                    const int v = ~leaf;
+                    const int first = v >> 3, count = (v & 7) + 1;
+                    for (int k = 0; k < count; ++k) {
+                        const int j = first + k;
+                        if (j == skip) continue;
+                        if (COUNT) ++cnt.tests;
+                        const float4* tp = tris + 3ll * j;
+                        const float4 w0 = ldg4(tp), w1 = ldg4(tp + 1), w2 = ldg4(tp + 2);
+                        const int r = intersect_tri_rt(rs, w0, w1, w2, namb < kAmbMax ? kEdgeEps : 0.f, t_best,
+                                                       best_orig, bu, bv);
+                        if (r == 1) best = j;
+                        else if (r == 2) s_amb[(namb++) * B + tid] = j;
+                    }
+                } else {
+                    test_leaf<COUNT, false>(tris, rs, RaySetup64{}, leaf, skip, t_best, t_best64, best, best_orig,
+                                            bu, bv, &cnt);
+                }
                 leaf = 0;
                 if (node < 0) { leaf = node; node = pop(); }
             }
@@ -558,19 +643,35 @@ k_traverse_ww(const void* __restrict__ nodes, const float4* __restrict__ tris, c
         }
         if (!cell_done) continue;
 
-        if (best >= 0) {
-            hits[ray] = make_float4(t_best, bu, bv, __int_as_float(best));
-            if (RETEST) {
-                bool flag = fminf(fminf(bu, bv), 1.f - bu - bv) < kEdgeEps;
-                if (!flag) {
-                    const float4 nr = ldg4(normals + best);
-                    flag = -(d.x * nr.x + d.y * nr.y + d.z * nr.z) < kGrazeCos;
-                }
-                if (flag) {
-                    const unsigned slot = atomicAdd(&ctl->n_retest[gen], 1u);
-                    if (slot < cap) retest_list[slot] = (unsigned)ray;
+        if (RETEST && namb > 0) {        // the facets set aside, against the FP32 best, in FP64
+            for (int k = 0; k < namb; ++k) {
+                const int j = s_amb[k * B + tid];
+                const float4* tp = tris + 3ll * j;
+                const double ref = (best >= 0 && s_b64[tid] == best) ? s_t64[tid] : (double)t_best;
+                const Hit64 h = facet_fp64(o, d, ldg4(tp), ldg4(tp + 1), ldg4(tp + 2),
+                                           Hit64{ref, bu, bv, best_orig, false});
+                if (h.won) {
+                    best = j; best_orig = h.orig; bu = h.u; bv = h.v;
+                    t_best = (float)h.t;
+                    s_t64[tid] = h.t; s_b64[tid] = j;
                 }
             }
+            namb = 0;
+            used64 = true;
+        }
+
+        if (best >= 0) {
+            if (RETEST && s_b64[tid] != best) {
+                const float4 nr = ldg4(normals + best);
+                if (-(d.x * nr.x + d.y * nr.y + d.z * nr.z) < kGrazeCos) {   // grazing: distance in FP64
+                    const float4* tp = tris + 3ll * best;
+                    const Hit64 h = facet_fp64(o, d, ldg4(tp), ldg4(tp + 1), ldg4(tp + 2),
+                                               Hit64{INFINITY, bu, bv, INT_MAX, false});
+                    if (h.won) { t_best = (float)h.t; bu = h.u; bv = h.v; }
+                    used64 = true;
+                }
+            }
+            hits[ray] = make_float4(t_best, bu, bv, __int_as_float(best));
         } else {
             // No facet in this cell: leave through a face.  The distances to the
             // three faces ahead are estimated in FP32 from the FP32 origin; they
@@ -627,11 +728,13 @@ k_traverse_ww(const void* __restrict__ nodes, const float4* __restrict__ tris, c
         }
         my_wraps += (unsigned)wraps;
         if (RECORD) wraps_out[ray] = wraps;
+        if (RETEST) { my_retested += used64 ? 1u : 0u; used64 = false; }
         ray = -1;
     }
     for (int off = 16; off; off >>= 1) {
         my_wraps += __shfl_xor_sync(0xFFFFFFFFu, my_wraps, off);
         status |= __shfl_xor_sync(0xFFFFFFFFu, status, off);
+        if (RETEST) my_retested += __shfl_xor_sync(0xFFFFFFFFu, my_retested, off);
     }
     if (COUNT) {
         unsigned long long v = cnt.visits, t = cnt.tests;
@@ -644,40 +747,8 @@ k_traverse_ww(const void* __restrict__ nodes, const float4* __restrict__ tris, c
     if (lane == 0) {
         if (my_wraps) atomicAdd(&tally->wraps, my_wraps);
         if (status) atomicOr(&tally->status, (unsigned long long)status);
+        if (RETEST && my_retested) atomicAdd(&tally->retested, (unsigned long long)my_retested);
     }
-}
-
-// FP64 re-test of the flagged rays of one generation: the whole ray is traced
-// again (same FP32 ray, same FP32 boxes, triangle tests in FP64) and its hit
-// record (and wrap count) replaced.
-template <int FMT, bool RECORD>
-__global__ void __launch_bounds__(128)
-k_retest(const void* __restrict__ nodes, const float4* __restrict__ tris, Cell cell, const float4* __restrict__ oe,
-         const float4* __restrict__ dt, float4* __restrict__ hits, int* __restrict__ wraps_out,
-         Control* __restrict__ ctl, int gen, unsigned cap, const unsigned* __restrict__ retest_list,
-         Tally* __restrict__ tally)
-{
-    extern __shared__ int2 s_stack[];
-    const StackRef st{s_stack, (int)blockDim.x, (int)threadIdx.x};
-    const unsigned n = min(*((volatile unsigned*)&ctl->n_retest[gen]), cap);
-    unsigned status = 0;
-    long long wdelta = 0;
-    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const unsigned i = retest_list[k];
-        const float4 a = oe[i], b = dt[i];
-        int w;
-        const float4 h = trace_ray<FMT, false, true>(nodes, tris, make_float3(a.x, a.y, a.z),
-                                                     make_float3(b.x, b.y, b.z), __float_as_int(b.w), cell, st, w,
-                                                     status, nullptr);
-        hits[i] = h;
-        if (RECORD) {
-            wdelta += (long long)w - (long long)wraps_out[i];
-            wraps_out[i] = w;
-        }
-    }
-    if (status) atomicOr(&tally->status, (unsigned long long)status);
-    if (RECORD && wdelta) atomicAdd(&tally->wraps, (unsigned long long)wdelta);
-    if (blockIdx.x == 0 && threadIdx.x == 0 && n) atomicAdd(&tally->retested, (unsigned long long)n);
 }
 
 template <int FMT>
@@ -716,27 +787,20 @@ static cudaError_t ww_launch(const DeviceMesh& m, const Cell& cell, const Queues
     const int thr = tune.fetch_threshold > 0 ? tune.fetch_threshold : kFetchThreshold;
     const size_t smem = (size_t)SS * bt * sizeof(int2) + 3 * (size_t)bt * sizeof(double);
     if (retest) {
+        const size_t smem_rt = smem + (size_t)bt * (sizeof(double) + (1 + kAmbMax) * sizeof(int));
         if (per_sm <= 0)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse_ww<F, R, C, true, SS>, bt, smem);
-        k_traverse_ww<F, R, C, true, SS><<<num_sms * (per_sm > 0 ? per_sm : 1), bt, smem, s>>>(
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse_ww<F, R, C, true, SS>, bt, smem_rt);
+        k_traverse_ww<F, R, C, true, SS><<<num_sms * (per_sm > 0 ? per_sm : 1), bt, smem_rt, s>>>(
             nodes, m.tris, m.normals, cell, q.oe[buf], q.dt[buf], q.hits, R ? q.wraps : nullptr, q.ctl, gen,
-            q.cap[buf], q.retest, q.tally, thr);
+            q.cap[buf], q.tally, thr);
     } else {
         if (per_sm <= 0)
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse_ww<F, R, C, false, SS>, bt, smem);
         k_traverse_ww<F, R, C, false, SS><<<num_sms * (per_sm > 0 ? per_sm : 1), bt, smem, s>>>(
             nodes, m.tris, m.normals, cell, q.oe[buf], q.dt[buf], q.hits, R ? q.wraps : nullptr, q.ctl, gen,
-            q.cap[buf], nullptr, q.tally, thr);
+            q.cap[buf], q.tally, thr);
     }
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess && retest) {
-        const int tb = 64;
-        const size_t rs = (size_t)kSmemStack * tb * sizeof(int2);
-        k_retest<F, R><<<num_sms, tb, rs, s>>>(nodes, m.tris, cell, q.oe[buf], q.dt[buf], q.hits,
-                                               R ? q.wraps : nullptr, q.ctl, gen, q.cap[buf], q.retest, q.tally);
-        e = cudaGetLastError();
-    }
-    return e;
+    return cudaGetLastError();
 }
 
 template <int F, bool R, bool C>

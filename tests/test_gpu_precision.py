@@ -100,6 +100,27 @@ def test_precision_form_records_match_oracle(ctx, kind, retest):
         assert g["retested"] == 0
 
 
+@pytest.mark.parametrize("kind", [0, 1, 2])
+def test_fp64_retest_brings_records_closer_to_oracle(ctx, kind):
+    """The FP64 decisions replace FP32 ones only where FP32 cannot decide (a facet within
+    1e-5 of an edge, a grazing hit): the re-test run never has more per-ray record
+    mismatches against the FP64 oracle than the FP32 run on the same streams."""
+    from paper_1806_00205_gb300 import rtmc
+    mesh = I.grf_foam(16, 0.5)
+    mid = ctx.load_mesh(mesh.tri, mesh.box)
+    ctx.build_bvh(mid, kind=kind)
+    n = 100_000
+    plain = ctx.run_records(mid, 300.0, 60.0, n, seed=1806)
+    rt = ctx.run_records(mid, 300.0, 60.0, n, seed=1806, desc=rtmc.run_desc(fp64_retest=True))
+    ctx.unload_mesh(mid)
+    o = O.run(mesh, TABLE, 300.0, 60.0, n, seed=1806, records=True)
+    sp, sr = compare_records(plain["records"], o["records"]), compare_records(rt["records"], o["records"])
+    miss_p, miss_r = sp["n_oracle"] - sp["n_same"], sr["n_oracle"] - sr["n_same"]
+    assert 0 < rt["retested"] <= 1e-3 * rt["rays"]
+    assert miss_r <= miss_p, (miss_r, miss_p)
+    assert sr["frac_same"] >= 0.9999
+
+
 def test_precision_config_sey_vs_plain_and_oracle(ctx):
     """Precision config: 128^3 foams at porosity 0.4 / 0.6 / 0.8, E in {100, 300, 700} eV,
     incidence 0 and 60 deg.  Q8 nodes + FP64 re-test against FP32 nodes (same streams),
