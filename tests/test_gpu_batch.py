@@ -63,6 +63,28 @@ def test_batch_random_incidence_depth_profile_equals_plain_runs(setup):
             assert np.array_equal(he[mi * per_mesh + j], phe[j])
 
 
+def test_batch_fp64_retest_equals_plain_runs(setup):
+    """The FP64 re-test decides each ambiguous facet against the best hit of its cell, so a
+    ray's result does not depend on the launch: batched items equal plain runs with the
+    re-test on, on binary FP32, Q8 and 4-wide meshes, and the batch's re-test count (a
+    batch total) is the sum of the plain runs'."""
+    ctx, ids, rtmc = setup
+    energies, thetas, n = [120.0, 600.0], [0.0, 70.0], 40_000
+    res, he, _ = ctx.run_batch(ids, energies, thetas, n, 13, desc=rtmc.run_desc(fp64_retest=True, chunk=70_000))
+    per_mesh = len(energies) * len(thetas)
+    total = 0
+    for mi, mid in enumerate(ids):
+        plain, phe, _ = ctx.run(mid, energies, thetas, n, 13,
+                                desc=rtmc.run_desc(fp64_retest=True, item_base=mi * per_mesh))
+        total += sum(r["retested"] for r in plain)
+        for j in range(per_mesh):
+            b = res[mi * per_mesh + j]
+            for k in INT_KEYS:
+                assert b[k] == plain[j][k], (mi, j, k, b[k], plain[j][k])
+            assert np.array_equal(he[mi * per_mesh + j], phe[j])
+    assert res[0]["retested"] == total > 0
+
+
 def test_batch_graph_replay_equals_eager(setup):
     ctx, ids, rtmc = setup
     args = (ids, [100.0, 700.0], [0.0, 60.0], 20_000, 5)
