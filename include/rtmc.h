@@ -292,8 +292,9 @@ int rtmc_philox(rtmc_ctx* ctx, const uint32_t* ctr, int64_t n, uint64_t key, uin
        desc->primary_offset and call again for more primaries);
      the loaded emission parameters must have max_generation == 1;
      n_ebins + n_abins + n_zbins <= 1024.
-   desc->profile is ignored; desc->prim_hash (device, n_primaries entries)
-   and desc->count_visits work as in rtmc_run.
+   desc->profile is ignored; desc->prim_hash (device, n_primaries entries),
+   desc->count_visits and desc->fp64_retest work as in rtmc_run (the FP64
+   re-test runs inside the traversal kernel and needs no scratch).
    The first call on a device looks up the array's device address
    (cudaGetSymbolAddress) with that device current; make that first call
    before any stream capture.  Every call on a device uses the same array and

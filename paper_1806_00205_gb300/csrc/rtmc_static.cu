@@ -209,7 +209,8 @@ extern "C" int rtmc_run_noalloc(rtmc_ctx* ctx, int32_t mesh_id, double energy_ev
     const unsigned n = (unsigned)n_primaries;
     if (ce == cudaSuccess) ce = launch_generate(p, q, 0, 0ull, n, s);
     for (int g = 0; g <= 1 && ce == cudaSuccess; ++g) {
-        ce = launch_traverse(m, p, q, g, g, ctx->num_sms, tune, hashing, d.count_visits != 0, false, s);
+        ce = launch_traverse(m, p, q, g, g, ctx->num_sms, tune, hashing, d.count_visits != 0, d.fp64_retest != 0,
+                             s);
         if (ce == cudaSuccess) ce = launch_shade(m, p, tab, e, q, g, g, 0ull, ctx->num_sms, false, s);
     }
     if (ce == cudaSuccess) ce = launch_finalize(q, n, s);
@@ -248,6 +249,7 @@ extern "C" int rtmc_run_noalloc(rtmc_ctx* ctx, int32_t mesh_id, double energy_ev
     r.e2_sum = t.e2_sum;
     r.node_visits = (int64_t)t.node_visits;
     r.tri_tests = (int64_t)t.tri_tests;
+    r.retested = (int64_t)t.retested;
     r.launches = 6;
     r.traverse_launches = 2;
     if (n_primaries > 0) r.sey = (double)r.sum_k / (double)n_primaries;

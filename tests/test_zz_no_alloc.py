@@ -70,6 +70,23 @@ def test_noalloc_hash_equals_run_hash(setup):
     assert torch.equal(h_ref, h_got)
 
 
+def test_noalloc_fp64_retest_equals_run(setup):
+    """The FP64 re-test needs no scratch, so the scratch-free entry runs it too: the same
+    tallies, histograms and re-test counts as rtmc_run, call by call."""
+    ctx, mid, rtmc = setup
+    n = rtmc.NOALLOC_MAX_PRIMARIES
+    total = 0
+    for c in range(10):
+        desc = rtmc.run_desc(fp64_retest=True, primary_offset=c * n)
+        ref, he, ha = ctx.run(mid, [300.0], [60.0], n, 23, desc=desc)
+        got, ge, ga = ctx.run_noalloc(mid, 300.0, 60.0, n, 23, desc=desc)
+        for k in INT_KEYS + ("retested",):
+            assert got[k] == ref[0][k], (c, k, got[k], ref[0][k])
+        assert np.array_equal(ge, he[0]) and np.array_equal(ga, ha[0])
+        total += got["retested"]
+    assert total > 0
+
+
 def test_noalloc_rejects_sizes_beyond_the_limit(setup):
     ctx, mid, rtmc = setup
     with pytest.raises(rtmc.RtmcError) as e:
