@@ -250,11 +250,12 @@ def run_large(args):
     clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    rays = prims = launches = 0
+    rays = prims = launches = col_rays = 0
     trav_ms, trav_l = 0.0, 0
     for _ in range(args.steps):
         res, he, ha = ctx.run(mid, [500.0], thetas, n_prim, SEED, desc=desc)
         rays += sum(r["rays"] for r in res)
+        col_rays += sum(r["column_rays"] for r in res)
         prims += sum(r["n_primaries"] for r in res)
         launches += sum(r["launches"] for r in res)
         trav_ms += sum(r["ms_traverse"] for r in res)
@@ -265,10 +266,11 @@ def run_large(args):
     ms = ev0.elapsed_time(ev1)
     cres, _, _ = ctx.run(mid, [500.0], thetas[:1], n_prim // 10, SEED,
                          desc=rtmc.run_desc(n_ebins=128, n_abins=36, count_visits=True))
-    visits = cres[0]["node_visits"] / cres[0]["rays"]
-    tests = cres[0]["tri_tests"] / cres[0]["rays"]
+    h_rays = cres[0]["rays"] - cres[0]["column_rays"]          # the hierarchy's rays (counters cover these)
+    visits = cres[0]["node_visits"] / h_rays
+    tests = cres[0]["tri_tests"] / h_rays
     b_ray = visits * 32 + tests * TRI_BYTES + RAY_BYTES
-    achieved = rays / args.steps * args.steps * b_ray / (trav_ms / 1e3) / 1e9
+    achieved = (rays - col_rays) * b_ray / (trav_ms / 1e3) / 1e9
     pk, pk_kind = peaks()
     peak = float(pk.get("hbm_gbs", 6800.0))
     tri_host = torch.from_numpy(mesh.tri.reshape(-1, 9)).pin_memory()
@@ -358,7 +360,7 @@ def run_precision(args):
     clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    rays = prims = launches = retested = trav_l = 0
+    rays = prims = launches = retested = trav_l = col_rays = 0
     trav_ms = 0.0
     prec = []
     for _ in range(args.steps):
@@ -370,6 +372,7 @@ def run_precision(args):
             prims += sum(r["n_primaries"] for r in res)
             launches += sum(r["launches"] for r in res)
             retested += sum(r["retested"] for r in res)
+            col_rays += sum(r["column_rays"] for r in res)
             trav_ms += sum(r["ms_traverse"] for r in res)
             trav_l += sum(r["traverse_launches"] for r in res)
     ev1.record(stream)
@@ -378,7 +381,7 @@ def run_precision(args):
     ms = ev0.elapsed_time(ev1)
     return finish_precision(args, ctx, rtmc, O, I, meshes, table, mq, m32, prec, n_prim, dict(
         rays=rays, prims=prims, launches=launches, retested=retested, trav_ms=trav_ms, trav_l=trav_l,
-        ms=ms, clk=clk, stream=stream))
+        ms=ms, clk=clk, stream=stream, col_rays=col_rays))
 
 
 def finish_precision(args, ctx, rtmc, O, I, meshes, table, mq, m32, prec, n_prim, t):
@@ -409,7 +412,7 @@ def finish_precision(args, ctx, rtmc, O, I, meshes, table, mq, m32, prec, n_prim
     visits = cq[0]["node_visits"] / cq[0]["rays"]
     tests = cq[0]["tri_tests"] / cq[0]["rays"]
     b_ray = visits * NODE_BYTES[1] + tests * TRI_BYTES + RAY_BYTES
-    achieved = t["rays"] * b_ray / (t["trav_ms"] / 1e3) / 1e9
+    achieved = (t["rays"] - t["col_rays"]) * b_ray / (t["trav_ms"] / 1e3) / 1e9   # the hierarchy's rays
     pk, pk_kind = peaks()
     peak = float(pk.get("hbm_gbs", 6800.0))
     ora, diffs, cpu = None, [], None
@@ -509,8 +512,8 @@ def run_ours(args):
     clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    rays = prims = launches = trav_launches = 0
-    trav_ms = 0.0
+    rays = prims = launches = trav_launches = col_rays = 0
+    trav_ms = col_ms = 0.0
     results = None
     for _ in range(args.steps):
         results, _, _ = step()
@@ -519,6 +522,8 @@ def run_ours(args):
         launches += results[0]["launches"]
         trav_launches += results[0]["traverse_launches"]
         trav_ms += results[0]["ms_traverse"]
+        col_ms += results[0]["ms_column"]           # generation 0 through the column grid
+        col_rays += results[0]["column_rays"]
     ev1.record(stream)
     barrier()
     clk = clocks.stop()
@@ -555,11 +560,12 @@ def run_ours(args):
     # node-visit counts of the same workload (counting variant, untimed) -> algorithmic bytes
     cres, _, _ = ctx.run_batch([mid], energies, [0.0], n_prim, SEED,
                                desc=rtmc.run_desc(primary_offset=offset, count_visits=True, no_graph=True, **tuned))
-    c_rays = sum(r["rays"] for r in cres)
+    # the counters cover the hierarchy's rays only (not those of the column grid)
+    c_rays = sum(r["rays"] for r in cres) - cres[0]["column_rays"]
     visits = cres[0]["node_visits"] / c_rays
     tests = cres[0]["tri_tests"] / c_rays
     b_ray = visits * NODE_BYTES[MAIN_KIND] + tests * TRI_BYTES + RAY_BYTES
-    local_rays = sum(r["rays"] for r in results) * args.steps
+    local_rays = sum(r["rays"] for r in results) * args.steps - col_rays
     achieved = local_rays * b_ray / (trav_ms / 1e3) / 1e9
     pk, pk_kind = peaks()
     peak = float(pk.get("hbm_gbs", 6800.0))
@@ -632,6 +638,9 @@ def run_ours(args):
                          "rays_per_launch": rays_per_launch, "traffic_bytes_per_ray": traffic_per_ray,
                          "l2_read_probe_gbs": l2_gbs, "frac_of_l2_read_probe": achieved / l2_gbs,
                          "hbm_read_probe_gbs": hbm_read_gbs},
+            "column_kernel": {"kernel": "k_trace_columns (generation 0, normal incidence)",
+                              "ms_per_step": col_ms / args.steps, "rays_per_step": col_rays / args.steps,
+                              "rays_per_s": col_rays / (col_ms / 1e3) if col_ms > 0 else None},
             "e2e": {"value": e_rays / e_dt, "unit": "rays/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,

@@ -107,8 +107,10 @@ typedef struct {
                                       sum of record hashes (see rtmc_record_hash) */
     int32_t profile;               /* 1: time every kernel launch with CUDA events */
     int32_t count_visits;          /* 1: count BVH node visits and triangle tests */
-    int32_t traversal;             /* 0: default; 1: one ray per lane per 32-ray tile;
-                                      2: while-while loop with per-lane ray refill */
+    int32_t traversal;             /* 0: default (2, and the column grid for generation 0
+                                      at normal incidence, see rtmc_build_bvh); 1: one ray
+                                      per lane per 32-ray tile; 2: while-while loop with
+                                      per-lane ray refill, the hierarchy for every ray */
     int32_t fp64_retest;           /* 1: decide in FP64 every facet whose FP32 edge
                                       functions lie within 1e-5 (relative to their sum)
                                       of an edge, hit or miss, and take the distance of a
@@ -139,8 +141,11 @@ typedef struct {
     int64_t launches;                          /* kernels launched for this item */
     int64_t node_visits, tri_tests;            /* with count_visits */
     double ms_generate, ms_traverse, ms_shade, ms_finalize;   /* with profile */
-    int64_t traverse_launches;
+    int64_t traverse_launches;                 /* hierarchy traversal launches */
     int64_t retested;                          /* rays with a facet decided in FP64 */
+    double ms_column;                          /* with profile: the column-grid launches */
+    int64_t column_rays;                       /* rays traced through the column grid (not
+                                                  counted in node_visits / tri_tests) */
 } rtmc_result;
 
 /* One traced ray: the integer event sequence used for parity checks. */
@@ -191,7 +196,15 @@ int rtmc_load_see_tables(rtmc_ctx* ctx, const float* delta, const rtmc_grid* gri
    RTMC_BVH_W4 builds the binary hierarchy and then collapses it into 4-wide
    nodes (each opens the inner child of largest surface area until it holds
    four children; leaves are those of the binary hierarchy), level by level,
-   one host synchronisation per level. */
+   one host synchronisation per level.
+   Every kind also gets a column grid for rays parallel to z (generation 0 at
+   normal incidence): about n_tri / 21 pixels over [0, lx) x [0, ly), each
+   listing the facets whose xy box meets it, sorted by top z (descending, then
+   index).  Such a ray tests its pixel's facets in that order and stops when
+   no facet further down the list can be closer than its best hit; the facet
+   tests are the hierarchy's, so every hit record is the same.  A mesh the grid
+   does not suit (a facet over more than 64 pixels, a pixel with more than 2048
+   facets, more than 2^24 facets, or no device memory for it) gets none. */
 int rtmc_build_bvh(rtmc_ctx* ctx, int32_t mesh_id, int32_t bvh_kind);
 
 /* Run RTMC for every (energy, angle) pair: n_e * n_theta items, item

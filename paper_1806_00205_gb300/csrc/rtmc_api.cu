@@ -156,6 +156,7 @@ void fill_result(rtmc_result& r, const Tally& t, int64_t n_prim)
     r.node_visits = (int64_t)t.node_visits;
     r.tri_tests = (int64_t)t.tri_tests;
     r.retested = (int64_t)t.retested;
+    r.column_rays = (int64_t)t.col_rays;
     if (n_prim > 0) r.sey = (double)r.sum_k / (double)n_prim;
     if (n_prim > 1) {
         const double var = ((double)r.sum_k2 / (double)n_prim - r.sey * r.sey) / (double)(n_prim - 1);
@@ -193,6 +194,8 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
 
     const RunParams p = make_params(m, d, seed, item, energy, theta_deg);
     const TableDesc tab = make_table(ctx);
+    // generation 0 at normal incidence runs parallel to z: the column grid
+    const bool columns = m.col_ok && d.traversal == 0 && theta_deg == 0.0 && !d.random_polar;
     const Emission e = make_emission(em);
 
     // Queue capacities: generation g holds at most k_max^g rays per primary.
@@ -262,7 +265,7 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
         cudaMemsetAsync(q.tally, 0, sizeof(Tally), s);
         cudaMemsetAsync(q.hist_e, 0, (size_t)(d.n_ebins + d.n_abins + d.n_zbins) * 8, s);
         if (d.prim_hash) cudaMemsetAsync(d.prim_hash, 0, (size_t)n_prim * 8, s);
-        // per-kernel timing (profile): one event pair per launch, kind 0..3
+        // per-kernel timing (profile): one event pair per launch, kind 0..4 (4: column grid)
         std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> kev;
         auto tick = [&](int kind) -> int {
             if (!d.profile) return -1;
@@ -287,16 +290,18 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
             launches += d.id_order ? 1 : 4;      // sorted: count, scan, scatter, write
             for (int g = 0; g <= em.max_generation && ce == cudaSuccess; ++g) {
                 const int buf = g & 1;
-                h = tick(1);
-                ce = launch_traverse(m, p, q, buf, g, ctx->num_sms, tune, need_wraps, d.count_visits != 0,
-                                     d.fp64_retest != 0, s);
+                const bool col = columns && g == 0;
+                h = tick(col ? 4 : 1);
+                ce = col ? launch_columns(m, p, q, buf, g, ctx->num_sms, need_wraps, d.fp64_retest != 0, s)
+                         : launch_traverse(m, p, q, buf, g, ctx->num_sms, tune, need_wraps, d.count_visits != 0,
+                                           d.fp64_retest != 0, s);
                 tock(h);
                 h = tick(2);
                 if (ce == cudaSuccess)
                     ce = launch_shade(m, p, tab, e, q, buf, g, (unsigned long long)first, ctx->num_sms, record, s);
                 tock(h);
                 launches += 2;
-                ++trav_launches;
+                if (!col) ++trav_launches;
             }
             h = tick(3);
             if (ce == cudaSuccess) ce = launch_finalize(q, nc, s);
@@ -314,7 +319,7 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
         if (ce == cudaSuccess) cudaEventElapsedTime(&ms, ev0, ev1);
         cudaEventDestroy(ev0);
         cudaEventDestroy(ev1);
-        double kms[4] = {0.0, 0.0, 0.0, 0.0};
+        double kms[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
         for (auto& k : kev) {
             float x = 0.f;
             if (ce == cudaSuccess && cudaEventElapsedTime(&x, k.second.first, k.second.second) == cudaSuccess)
@@ -332,8 +337,8 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
             cudaMemsetAsync(ctx->kcount.ptr, 0, ctx->kcount.bytes, s);
             continue;
         }
-        if (status_all & (ST_STACK_OVERFLOW | ST_LOOP_LIMIT))
-            return ctx->fail(RTMC_ERR_DEVICE_CHECK, "run: traversal stack overflow or iteration bound");
+        if (status_all & (ST_STACK_OVERFLOW | ST_LOOP_LIMIT | ST_COLUMN))
+            return ctx->fail(RTMC_ERR_DEVICE_CHECK, "run: traversal stack overflow, iteration bound or a non-vertical ray in the column grid");
         if (record && (status_all & ST_RECORD_OVERFLOW))
             return ctx->fail(RTMC_ERR_CAPACITY, "run_records: record buffer too small");
 
@@ -346,6 +351,7 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
         r.ms_traverse = kms[1];
         r.ms_shade = kms[2];
         r.ms_finalize = kms[3];
+        r.ms_column = kms[4];
         if (o.hist_e) for (int b = 0; b < d.n_ebins; ++b) o.hist_e[b] = hist[b];
         if (o.hist_a) for (int b = 0; b < d.n_abins; ++b) o.hist_a[b] = hist[d.n_ebins + b];
         if (o.hist_z) for (int b = 0; b < d.n_zbins; ++b) o.hist_z[b] = hist[d.n_ebins + d.n_abins + b];
@@ -433,6 +439,7 @@ void rtmc_destroy(rtmc_ctx* ctx)
         cudaFree(m.inv_order);
         cudaFree(m.q8);
         cudaFree(m.w4);
+        rtmc::free_columns(m);
     }
     cudaFree(ctx->delta);
     if (ctx->batch_graph) cudaGraphExecDestroy(ctx->batch_graph);
@@ -489,6 +496,7 @@ int rtmc_unload_mesh(rtmc_ctx* ctx, int32_t mesh_id)
     cudaFree(m.inv_order);
     cudaFree(m.q8);
     cudaFree(m.w4);
+    rtmc::free_columns(m);
     m = DeviceMesh();
     return RTMC_OK;
 }

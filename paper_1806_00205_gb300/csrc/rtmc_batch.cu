@@ -38,7 +38,7 @@ struct DeviceGuard {
 };
 
 // Per-kernel CUDA-event timing of an eager batch (kind 0 generate, 1
-// traverse, 2 shade, 3 finalize).
+// traverse, 2 shade, 3 finalize, 4 column grid).
 struct KernelTimer {
     bool on = false;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
@@ -53,7 +53,7 @@ struct KernelTimer {
         return (int)ev.size() - 1;
     }
     void tock(int h, cudaStream_t s) { if (h >= 0) cudaEventRecord(ev[h].second.second, s); }
-    void collect(double ms[4], int64_t& trav_launches)
+    void collect(double ms[5], int64_t& trav_launches)
     {
         for (auto& k : ev) {
             float x = 0.f;
@@ -79,8 +79,12 @@ cudaError_t record_batch(rtmc_ctx* ctx, const rtmc_batch& b, const rtmc_run_desc
     const TableDesc tab = make_table(ctx);
     const Emission em = make_emission(ctx->emission);
     const int64_t per_mesh = (int64_t)b.n_e * b.n_theta;
+    // generation 0 runs parallel to z when every item is at normal incidence
+    bool vertical = d.traversal == 0 && !d.random_polar;
+    for (int it = 0; it < b.n_theta; ++it) vertical = vertical && b.theta_deg[it] == 0.0;
     for (int mi = 0; mi < b.n_meshes && ce == cudaSuccess; ++mi) {
         const DeviceMesh& m = ctx->meshes[b.mesh_ids[mi]];
+        const bool columns = vertical && m.col_ok;
         const RunParams p = make_params(m, d, b.seed, 0u, 1.0, 0.0);
         ItemCtx ic;
         ic.items = d_items + mi * per_mesh;
@@ -104,9 +108,11 @@ cudaError_t record_batch(rtmc_ctx* ctx, const rtmc_batch& b, const rtmc_run_desc
             launches += sorted ? 4 : 1;          // sorted: count, scan, scatter, write
             for (int g = 0; g <= ctx->emission.max_generation && ce == cudaSuccess; ++g) {
                 const int buf = g & 1;
-                h = kt.tick(1, s);
-                ce = launch_traverse(m, p, qq, buf, g, ctx->num_sms, tune, true, d.count_visits != 0,
-                                     d.fp64_retest != 0, s);
+                const bool col = columns && g == 0;
+                h = kt.tick(col ? 4 : 1, s);
+                ce = col ? launch_columns(m, p, qq, buf, g, ctx->num_sms, true, d.fp64_retest != 0, s)
+                         : launch_traverse(m, p, qq, buf, g, ctx->num_sms, tune, true, d.count_visits != 0,
+                                           d.fp64_retest != 0, s);
                 kt.tock(h, s);
                 h = kt.tick(2, s);
                 if (ce == cudaSuccess) ce = launch_shade_items(m, p, tab, em, ic, qq, buf, g, ctx->num_sms, s);
@@ -315,14 +321,14 @@ extern "C" int rtmc_run_batch(rtmc_ctx* ctx, const rtmc_batch* batch, const rtmc
     if (ce == cudaSuccess) cudaEventElapsedTime(&ms, ev0, ev1);
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);
-    double kms[4] = {0.0, 0.0, 0.0, 0.0};
+    double kms[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     int64_t trav_launches = 0;
     kt.collect(kms, trav_launches);
     if (ce != cudaSuccess) return ctx->fail(RTMC_ERR_CUDA, std::string("run_batch: ") + cudaGetErrorString(ce));
     unsigned long long status = 0;
     for (const Tally& x : t) status |= x.status;
     if (status & ST_QUEUE_OVERFLOW) return ctx->fail(RTMC_ERR_CAPACITY, "run_batch: daughter queue overflow");
-    if (status & (ST_STACK_OVERFLOW | ST_LOOP_LIMIT))
+    if (status & (ST_STACK_OVERFLOW | ST_LOOP_LIMIT | ST_COLUMN))
         return ctx->fail(RTMC_ERR_DEVICE_CHECK, "run_batch: traversal stack overflow or iteration bound");
     const Tally& all = t[(size_t)n_items];
     for (int64_t k = 0; k < n_items; ++k) {
@@ -331,12 +337,14 @@ extern "C" int rtmc_run_batch(rtmc_ctx* ctx, const rtmc_batch* batch, const rtmc
         out[k].node_visits = (int64_t)all.node_visits;     // traversal counters: batch totals
         out[k].tri_tests = (int64_t)all.tri_tests;
         out[k].retested = (int64_t)all.retested;
+        out[k].column_rays = (int64_t)all.col_rays;
         out[k].launches = launches;
         out[k].traverse_launches = trav_launches;
         out[k].ms_generate = kms[0];
         out[k].ms_traverse = kms[1];
         out[k].ms_shade = kms[2];
         out[k].ms_finalize = kms[3];
+        out[k].ms_column = kms[4];
         if (hist_e)
             for (int bb = 0; bb < d.n_ebins; ++bb) hist_e[k * d.n_ebins + bb] = h[(size_t)k * nbins + bb];
         if (hist_a)

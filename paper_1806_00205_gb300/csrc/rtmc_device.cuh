@@ -35,6 +35,7 @@ constexpr unsigned ST_STACK_OVERFLOW = 1u;
 constexpr unsigned ST_QUEUE_OVERFLOW = 2u;
 constexpr unsigned ST_RECORD_OVERFLOW = 4u;
 constexpr unsigned ST_LOOP_LIMIT = 8u;     // a traversal exceeded its iteration bound
+constexpr unsigned ST_COLUMN = 16u;        // the column kernel got a ray not parallel to z
 constexpr int kMaxVisits = 1 << 22;        // node visits per ray segment before giving up
 
 struct Tally {                    // one (energy, angle) item, device resident
@@ -44,7 +45,8 @@ struct Tally {                    // one (energy, angle) item, device resident
     unsigned long long rays_recorded;
     unsigned long long status;    // ST_* bits raised by any kernel of the item
     unsigned long long node_visits, tri_tests;   // counting variant of traverse only
-    unsigned long long retested;                 // rays re-tested in FP64
+    unsigned long long retested;                 // rays with a facet decided in FP64
+    unsigned long long col_rays;                 // rays traced through the column grid
 };
 
 struct Control {                  // per chunk

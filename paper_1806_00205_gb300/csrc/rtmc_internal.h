@@ -30,6 +30,17 @@ struct DeviceMesh {
     int leaf_max = 4;              // triangles per leaf (1..8)
     bool ploc = false;             // hierarchy from locally-ordered clustering
     double build_ms = 0.0;
+    // Column grid for rays parallel to z (generation 0 at normal incidence):
+    // col_gx x col_gy pixels over [0, lx) x [0, ly); pixel p lists the facets
+    // whose xy box (widened by col_margin) meets it, as (leaf-order index, top z
+    // bits) pairs col_ent[col_off[p] .. col_off[p + 1]) sorted by top z
+    // descending, then index ascending.
+    bool col_ok = false;
+    int col_gx = 0, col_gy = 0;
+    float col_inv_wx = 0.f, col_inv_wy = 0.f;
+    unsigned* col_off = nullptr;   // col_gx * col_gy + 1
+    uint2* col_ent = nullptr;
+    int64_t col_entries = 0;
 };
 
 // Growable device scratch owned by the context.
@@ -144,6 +155,12 @@ cudaError_t launch_generate_items_sorted(const RunParams& p, const ItemCtx& ic, 
 cudaError_t launch_shade_items(const DeviceMesh& m, const RunParams& p, const TableDesc& tab, const Emission& em,
                                const ItemCtx& ic, const Queues& q, int buf, int gen, int num_sms, cudaStream_t s);
 cudaError_t launch_finalize_items(const ItemCtx& ic, const Queues& q, unsigned n, int num_sms, cudaStream_t s);
+// Generation `gen` of rays parallel to z (all of them) through the column grid
+// instead of the hierarchy: the same facet tests, so the same hit records.
+cudaError_t launch_columns(const DeviceMesh& m, const RunParams& p, const Queues& q, int buf, int gen,
+                           int num_sms, bool record, bool retest, cudaStream_t s);
+int build_columns(rtmc_ctx* ctx, DeviceMesh& m);
+void free_columns(DeviceMesh& m);
 cudaError_t launch_trace_rays(const DeviceMesh& m, const float* o, const float* d, const int* skip,
                               int64_t n, rtmc_hit* hits, unsigned* status, cudaStream_t s);
 cudaError_t launch_read_probe(const void* buf, size_t bytes, int passes, int num_sms, float* sink, cudaStream_t s);

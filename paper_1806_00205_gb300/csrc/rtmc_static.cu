@@ -208,9 +208,12 @@ extern "C" int rtmc_run_noalloc(rtmc_ctx* ctx, int32_t mesh_id, double energy_ev
     if (ce == cudaSuccess && hashing) ce = cudaMemsetAsync(d.prim_hash, 0, 8 * (size_t)n_primaries, s);
     const unsigned n = (unsigned)n_primaries;
     if (ce == cudaSuccess) ce = launch_generate(p, q, 0, 0ull, n, s);
+    const bool columns = m.col_ok && d.traversal == 0 && theta_deg == 0.0 && !d.random_polar;
     for (int g = 0; g <= 1 && ce == cudaSuccess; ++g) {
-        ce = launch_traverse(m, p, q, g, g, ctx->num_sms, tune, hashing, d.count_visits != 0, d.fp64_retest != 0,
-                             s);
+        ce = columns && g == 0
+                 ? launch_columns(m, p, q, g, g, ctx->num_sms, hashing, d.fp64_retest != 0, s)
+                 : launch_traverse(m, p, q, g, g, ctx->num_sms, tune, hashing, d.count_visits != 0,
+                                   d.fp64_retest != 0, s);
         if (ce == cudaSuccess) ce = launch_shade(m, p, tab, e, q, g, g, 0ull, ctx->num_sms, false, s);
     }
     if (ce == cudaSuccess) ce = launch_finalize(q, n, s);
@@ -227,7 +230,7 @@ extern "C" int rtmc_run_noalloc(rtmc_ctx* ctx, int32_t mesh_id, double energy_ev
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
     if (ce != cudaSuccess) return ctx->fail(RTMC_ERR_CUDA, std::string("run_noalloc: ") + cudaGetErrorString(ce));
     if (t.status & ST_QUEUE_OVERFLOW) return ctx->fail(RTMC_ERR_CAPACITY, "run_noalloc: daughter queue overflow");
-    if (t.status & (ST_STACK_OVERFLOW | ST_LOOP_LIMIT))
+    if (t.status & (ST_STACK_OVERFLOW | ST_LOOP_LIMIT | ST_COLUMN))
         return ctx->fail(RTMC_ERR_DEVICE_CHECK, "run_noalloc: traversal stack overflow or iteration bound");
 
     rtmc_result& r = *out;
@@ -250,8 +253,9 @@ extern "C" int rtmc_run_noalloc(rtmc_ctx* ctx, int32_t mesh_id, double energy_ev
     r.node_visits = (int64_t)t.node_visits;
     r.tri_tests = (int64_t)t.tri_tests;
     r.retested = (int64_t)t.retested;
+    r.column_rays = (int64_t)t.col_rays;
     r.launches = 6;
-    r.traverse_launches = 2;
+    r.traverse_launches = columns ? 1 : 2;
     if (n_primaries > 0) r.sey = (double)r.sum_k / (double)n_primaries;
     if (n_primaries > 1) {
         const double var = ((double)r.sum_k2 / (double)n_primaries - r.sey * r.sey) / (double)(n_primaries - 1);

@@ -751,6 +751,118 @@ k_traverse_ww(const void* __restrict__ nodes, const float4* __restrict__ tris, c
     }
 }
 
+// --------------------------------------------------------------------------
+// a generation of rays parallel to z through the column grid
+// --------------------------------------------------------------------------
+// A ray with direction (0, 0, d_z) meets a facet only inside the facet's xy
+// box and, going down, at or below the facet's top z.  It tests the facets
+// listed for its pixel in order of decreasing top z and stops when even the
+// next top z lies farther than the best hit (margins 1 + 2^-12 relative and
+// 2^-16 M absolute, M the largest cell coordinate, far above the rounding of
+// a facet distance), so no facet it skips could have won.  The facet tests,
+// the FP64 re-test and the tie rule are those of the hierarchy's traversal,
+// so the hit record is the same; a ray that meets no facet leaves through
+// z_min (z_top going up) as in the hierarchy's cell exit.  It never wraps.
+constexpr float kColRel = 1.000244140625f;     // 1 + 2^-12
+
+template <bool RECORD, bool RETEST>
+__global__ void __launch_bounds__(128)
+k_trace_columns(const unsigned* __restrict__ col_off, const uint2* __restrict__ col_ent, int gx, int gy, float iwx,
+                float iwy, const float4* __restrict__ tris, const float4* __restrict__ normals, Cell cell,
+                const float4* __restrict__ oe, const float4* __restrict__ dt, float4* __restrict__ hits,
+                int* __restrict__ wraps_out, Control* __restrict__ ctl, int gen, unsigned cap,
+                Tally* __restrict__ tally)
+{
+    const unsigned n = min(*((volatile unsigned*)&ctl->count[gen]), cap);
+    const float eps_abs = cell.eps * 16.f;
+    unsigned status = 0, my_rays = 0, my_retested = 0;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float4 a = oe[i], b = dt[i];
+        const float3 o = make_float3(a.x, a.y, a.z), d = make_float3(b.x, b.y, b.z);
+        const int skip = __float_as_int(b.w);
+        ++my_rays;
+        if (RECORD) wraps_out[i] = 0;
+        if (d.x != 0.f || d.y != 0.f || !(d.z != 0.f)) {      // not a column ray: the caller chose wrongly
+            status |= ST_COLUMN;
+            hits[i] = make_float4(0.f, 0.f, 0.f, __int_as_float(HIT_LOST));
+            continue;
+        }
+        const RaySetup rs = setup_ray(o, d);
+        const float az = fabsf(rs.inv.z);
+        const int px = min(max((int)floorf(o.x * iwx), 0), gx - 1);
+        const int py = min(max((int)floorf(o.y * iwy), 0), gy - 1);
+        const unsigned e0 = col_off[py * gx + px], e1 = col_off[py * gx + px + 1];
+        float t_best = kNoHit, bu = 0.f, bv = 0.f;
+        int best = -1, best_orig = INT_MAX;
+        int amb[kAmbMax];
+        int namb = 0;
+        uint2 nx = e0 < e1 ? col_ent[e0] : make_uint2(0u, 0u);
+        for (unsigned e = e0; e < e1; ++e) {
+            const uint2 en = nx;
+            if (e + 1 < e1) nx = col_ent[e + 1];        // the next entry loads while this facet is tested
+            if (d.z < 0.f && (o.z - __uint_as_float(en.y)) * az > t_best * kColRel + eps_abs) break;
+            const int j = (int)en.x;
+            if (j == skip) continue;
+            const float4* tp = tris + 3ll * j;
+            if (RETEST) {
+                const int r = intersect_tri_rt(rs, ldg4(tp), ldg4(tp + 1), ldg4(tp + 2),
+                                               namb < kAmbMax ? kEdgeEps : 0.f, t_best, best_orig, bu, bv);
+                if (r == 1) best = j;
+                else if (r == 2) amb[namb++] = j;
+            } else {
+                if (intersect_tri(rs, ldg4(tp), ldg4(tp + 1), ldg4(tp + 2), t_best, best_orig, bu, bv)) best = j;
+            }
+        }
+        bool used64 = false;
+        int b64 = -1;
+        double t64 = 0.0;
+        if (RETEST && namb > 0) {                 // the facets set aside, against the FP32 best, in FP64
+            for (int k = 0; k < namb; ++k) {
+                const int j = amb[k];
+                const float4* tp = tris + 3ll * j;
+                const double ref = (best >= 0 && b64 == best) ? t64 : (double)t_best;
+                const Hit64 h = facet_fp64(o, d, ldg4(tp), ldg4(tp + 1), ldg4(tp + 2),
+                                           Hit64{ref, bu, bv, best_orig, false});
+                if (h.won) {
+                    best = j; best_orig = h.orig; bu = h.u; bv = h.v;
+                    t_best = (float)h.t;
+                    t64 = h.t; b64 = j;
+                }
+            }
+            used64 = true;
+        }
+        if (best >= 0) {
+            if (RETEST && b64 != best) {
+                const float4 nr = ldg4(normals + best);
+                if (-(d.x * nr.x + d.y * nr.y + d.z * nr.z) < kGrazeCos) {   // grazing: distance in FP64
+                    const float4* tp = tris + 3ll * best;
+                    const Hit64 h = facet_fp64(o, d, ldg4(tp), ldg4(tp + 1), ldg4(tp + 2),
+                                               Hit64{INFINITY, bu, bv, INT_MAX, false});
+                    if (h.won) { t_best = (float)h.t; bu = h.u; bv = h.v; }
+                    used64 = true;
+                }
+            }
+            hits[i] = make_float4(t_best, bu, bv, __int_as_float(best));
+        } else {
+            const double oz = (double)o.z;
+            const float tout = (float)(d.z > 0.f ? (double)cell.z_top - oz : oz - (double)cell.z_min) * az;
+            hits[i] = make_float4(tout, 0.f, 0.f, __int_as_float(d.z > 0.f ? HIT_ESCAPE : HIT_LOST));
+        }
+        if (RETEST && used64) ++my_retested;
+    }
+    const int lane = threadIdx.x & 31;
+    for (int off = 16; off; off >>= 1) {
+        my_rays += __shfl_xor_sync(0xFFFFFFFFu, my_rays, off);
+        status |= __shfl_xor_sync(0xFFFFFFFFu, status, off);
+        if (RETEST) my_retested += __shfl_xor_sync(0xFFFFFFFFu, my_retested, off);
+    }
+    if (lane == 0) {
+        if (my_rays) atomicAdd(&tally->col_rays, (unsigned long long)my_rays);
+        if (status) atomicOr(&tally->status, (unsigned long long)status);
+        if (RETEST && my_retested) atomicAdd(&tally->retested, (unsigned long long)my_retested);
+    }
+}
+
 template <int FMT>
 __global__ void __launch_bounds__(128)
 k_trace_rays(const void* __restrict__ nodes, const float4* __restrict__ tris, const int* __restrict__ inv_order,
@@ -843,6 +955,30 @@ cudaError_t launch_traverse(const DeviceMesh& m, const RunParams& p, const Queue
     if (m.kind == FMT_Q8) return traverse_f<FMT_Q8>(m, p, q, buf, gen, num_sms, tune, record, count, retest, s);
     if (m.kind == FMT_W4) return traverse_f<FMT_W4>(m, p, q, buf, gen, num_sms, tune, record, count, retest, s);
     return traverse_f<FMT_FP32>(m, p, q, buf, gen, num_sms, tune, record, count, retest, s);
+}
+
+cudaError_t launch_columns(const DeviceMesh& m, const RunParams& p, const Queues& q, int buf, int gen,
+                           int num_sms, bool record, bool retest, cudaStream_t s)
+{
+    if (!m.col_ok) return cudaErrorInvalidValue;
+    const float big = fmaxf(fmaxf(fabsf(p.lx), fabsf(p.ly)), fmaxf(fabsf(p.z_min), fabsf(p.z_top)));
+    const Cell cell{p.lx, p.ly, p.z_min, p.z_top, p.max_wraps, ldexpf(big, -20)};
+    const int tb = 128;
+    int per_sm = 0;
+    if (record) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, retest ? k_trace_columns<true, true>
+                                                                              : k_trace_columns<true, false>, tb, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, retest ? k_trace_columns<false, true>
+                                                                       : k_trace_columns<false, false>, tb, 0);
+    const unsigned gb = (unsigned)num_sms * (unsigned)(per_sm > 0 ? per_sm : 1);   // one wave, grid-stride
+    int* wr = record ? q.wraps : nullptr;
+#define RTMC_COLUMNS(R, T)                                                                                      \
+    k_trace_columns<R, T><<<gb, tb, 0, s>>>(m.col_off, m.col_ent, m.col_gx, m.col_gy, m.col_inv_wx, m.col_inv_wy, \
+                                            m.tris, m.normals, cell, q.oe[buf], q.dt[buf], q.hits, wr, q.ctl, gen, \
+                                            q.cap[buf], q.tally)
+    if (record) { if (retest) RTMC_COLUMNS(true, true); else RTMC_COLUMNS(true, false); }
+    else { if (retest) RTMC_COLUMNS(false, true); else RTMC_COLUMNS(false, false); }
+#undef RTMC_COLUMNS
+    return cudaGetLastError();
 }
 
 cudaError_t launch_trace_rays(const DeviceMesh& m, const float* o, const float* d, const int* skip, int64_t n,

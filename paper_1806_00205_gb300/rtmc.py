@@ -80,7 +80,8 @@ class Result(C.Structure):
         (n, C.c_double) for n in ("e_sum", "e2_sum", "sey", "sey_se", "gpu_ms")] + [
         (n, C.c_int64) for n in ("launches", "node_visits", "tri_tests")] + [
         (n, C.c_double) for n in ("ms_generate", "ms_traverse", "ms_shade", "ms_finalize")] + [
-        ("traverse_launches", C.c_int64), ("retested", C.c_int64)]
+        ("traverse_launches", C.c_int64), ("retested", C.c_int64), ("ms_column", C.c_double),
+        ("column_rays", C.c_int64)]
 
 
 class Record(C.Structure):

@@ -67,7 +67,9 @@ def test_batch_fp64_retest_equals_plain_runs(setup):
     """The FP64 re-test decides each ambiguous facet against the best hit of its cell, so a
     ray's result does not depend on the launch: batched items equal plain runs with the
     re-test on, on binary FP32, Q8 and 4-wide meshes, and the batch's re-test count (a
-    batch total) is the sum of the plain runs'."""
+    batch total) is the sum of the plain runs'.  A batch with an oblique angle traces
+    every generation through the hierarchy, so the plain runs do too (traversal 2): the
+    count depends on which facets a path tests."""
     ctx, ids, rtmc = setup
     energies, thetas, n = [120.0, 600.0], [0.0, 70.0], 40_000
     res, he, _ = ctx.run_batch(ids, energies, thetas, n, 13, desc=rtmc.run_desc(fp64_retest=True, chunk=70_000))
@@ -75,7 +77,7 @@ def test_batch_fp64_retest_equals_plain_runs(setup):
     total = 0
     for mi, mid in enumerate(ids):
         plain, phe, _ = ctx.run(mid, energies, thetas, n, 13,
-                                desc=rtmc.run_desc(fp64_retest=True, item_base=mi * per_mesh))
+                                desc=rtmc.run_desc(fp64_retest=True, item_base=mi * per_mesh, traversal=2))
         total += sum(r["retested"] for r in plain)
         for j in range(per_mesh):
             b = res[mi * per_mesh + j]
