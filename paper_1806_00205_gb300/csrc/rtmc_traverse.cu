@@ -796,22 +796,34 @@ k_trace_columns(const unsigned* __restrict__ col_off, const uint2* __restrict__ 
         int best = -1, best_orig = INT_MAX;
         int amb[kAmbMax];
         int namb = 0;
-        uint2 nx = e0 < e1 ? col_ent[e0] : make_uint2(0u, 0u);
-        for (unsigned e = e0; e < e1; ++e) {
-            const uint2 en = nx;
-            if (e + 1 < e1) nx = col_ent[e + 1];        // the next entry loads while this facet is tested
-            if (d.z < 0.f && (o.z - __uint_as_float(en.y)) * az > t_best * kColRel + eps_abs) break;
-            const int j = (int)en.x;
-            if (j == skip) continue;
+        // Two entries per pass: both stop checks use the best distance before the
+        // pass, which can only test a facet more (never skip one that could win),
+        // and both facets' loads are in flight together.
+        auto test = [&](int j) {
+            if (j == skip) return;
             const float4* tp = tris + 3ll * j;
+            const float4 w0 = ldg4(tp), w1 = ldg4(tp + 1), w2 = ldg4(tp + 2);
             if (RETEST) {
-                const int r = intersect_tri_rt(rs, ldg4(tp), ldg4(tp + 1), ldg4(tp + 2),
-                                               namb < kAmbMax ? kEdgeEps : 0.f, t_best, best_orig, bu, bv);
+                const int r = intersect_tri_rt(rs, w0, w1, w2, namb < kAmbMax ? kEdgeEps : 0.f, t_best, best_orig,
+                                               bu, bv);
                 if (r == 1) best = j;
                 else if (r == 2) amb[namb++] = j;
             } else {
-                if (intersect_tri(rs, ldg4(tp), ldg4(tp + 1), ldg4(tp + 2), t_best, best_orig, bu, bv)) best = j;
+                if (intersect_tri(rs, w0, w1, w2, t_best, best_orig, bu, bv)) best = j;
             }
+        };
+        uint2 nx0 = e0 < e1 ? col_ent[e0] : make_uint2(0u, 0u);
+        uint2 nx1 = e0 + 1 < e1 ? col_ent[e0 + 1] : make_uint2(0u, 0u);
+        for (unsigned e = e0; e < e1; e += 2) {
+            const uint2 ea = nx0, eb = nx1;
+            if (e + 2 < e1) nx0 = col_ent[e + 2];        // the next pair loads while these facets are tested
+            if (e + 3 < e1) nx1 = col_ent[e + 3];
+            const float lim = t_best * kColRel + eps_abs;
+            if (d.z < 0.f && (o.z - __uint_as_float(ea.y)) * az > lim) break;
+            const bool second = e + 1 < e1 && !(d.z < 0.f && (o.z - __uint_as_float(eb.y)) * az > lim);
+            test((int)ea.x);
+            if (!second) break;
+            test((int)eb.x);
         }
         bool used64 = false;
         int b64 = -1;
