@@ -266,11 +266,16 @@ extern "C" int rtmc_run_batch(rtmc_ctx* ctx, const rtmc_batch* batch, const rtmc
                       d.hist_e_max_ev, (unsigned long long)d.primary_offset, d.src_x0, d.src_x1, d.src_y0, d.src_y1,
                       d.n_zbins, d.random_polar);
         key = buf;
-        for (int i = 0; i < batch->n_meshes; ++i) {
+        for (int i = 0; i < batch->n_meshes; ++i) {      // every mesh array a recorded launch reads
             const DeviceMesh& m = ctx->meshes[batch->mesh_ids[i]];
-            std::snprintf(buf, sizeof buf, "|%d:%p:%p:%d", batch->mesh_ids[i], (const void*)m.nodes, m.q8, m.kind);
+            std::snprintf(buf, sizeof buf, "|%d:%p:%p:%p:%p:%p:%p:%p:%d:%d", batch->mesh_ids[i],
+                          (const void*)m.nodes, m.q8, m.w4, (const void*)m.tris, (const void*)m.normals,
+                          (const void*)m.col_off, (const void*)m.col_ent, m.kind, (int)m.col_ok);
             key += buf;
         }
+        bool vertical = true;                             // the column grid is recorded for generation 0
+        for (int it = 0; it < batch->n_theta; ++it) vertical = vertical && batch->theta_deg[it] == 0.0;
+        key += vertical ? "|v1" : "|v0";
         std::snprintf(buf, sizeof buf, "|cv%d|io%d|%p", d.count_visits, d.id_order, (const void*)ctx->delta);
         key += buf;
     }

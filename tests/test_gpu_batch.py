@@ -109,3 +109,20 @@ def test_batch_rejects_what_it_cannot_do(setup):
         ctx.run_batch([12345], [300.0], [0.0], 10, 1)
     with pytest.raises(rtmc.RtmcError):
         ctx.run_batch(ids, [300.0], [95.0], 10, 1)
+
+
+def test_batch_graph_follows_angles_and_rebuilds(setup):
+    """A cached batch graph is recorded again when the angles change the kernels it holds
+    (the column grid at normal incidence, the hierarchy otherwise) or a mesh is rebuilt."""
+    ctx, ids, rtmc = setup
+    mid, n = ids[2], 20_000
+    a, _, _ = ctx.run_batch([mid], [300.0], [0.0], n, 9)       # records the column grid
+    b, _, _ = ctx.run_batch([mid], [300.0], [35.0], n, 9)      # same shape, oblique
+    pb, _, _ = ctx.run(mid, [300.0], [35.0], n, 9)
+    assert a[0]["column_rays"] == n and b[0]["column_rays"] == 0
+    for k in INT_KEYS:
+        assert b[0][k] == pb[0][k], k
+    ctx.build_bvh(mid, kind=rtmc.BVH_W4)                         # new device arrays
+    c, _, _ = ctx.run_batch([mid], [300.0], [0.0], n, 9)
+    for k in INT_KEYS:
+        assert c[0][k] == a[0][k], k
