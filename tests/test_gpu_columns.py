@@ -97,3 +97,27 @@ def test_column_grid_records_match_oracle(ctx):
     o = O.run(mesh, TABLE, 300.0, 0.0, n, seed=1806, records=True)
     st = compare_records(g["records"], o["records"])
     assert st["frac_same"] >= 0.9999, {k: v for k, v in st.items() if k != "mismatch"}
+
+
+@pytest.mark.parametrize("model", ["tertiaries", "paper_fit"])
+def test_column_grid_under_deeper_trees(model):
+    """Generation 0 through the grid feeds trees of several generations (tertiaries above
+    20 eV; the paper-fit emission, up to 6 generations): the hierarchy's tallies."""
+    import torch
+    from paper_1806_00205_gb300 import rtmc
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    em = rtmc.Emission(regen_min_ev=20.0, max_generation=2) if model == "tertiaries" else rtmc.paper_emission()
+    mesh = I.grf_foam(32, 0.7, seed=11)
+    with rtmc.Context(0) as c:
+        c.load_see_tables(TABLE, em)
+        mid = c.load_mesh(mesh.tri, mesh.box)
+        c.build_bvh(mid, kind=rtmc.BVH_W4)
+        n = 100_000
+        a, ha, _ = c.run(mid, [500.0, 1500.0], [0.0], n, 44)
+        b, hb, _ = c.run(mid, [500.0, 1500.0], [0.0], n, 44, desc=rtmc.run_desc(traversal=2))
+    for x, y in zip(a, b):
+        assert x["column_rays"] == n and x["regenerated"] > 0
+        for k in INT_KEYS[:-1] + ("regenerated",):
+            assert x[k] == y[k], k
+    assert np.array_equal(ha, hb)
