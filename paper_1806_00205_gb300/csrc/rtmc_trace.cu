@@ -622,7 +622,9 @@ k_shade(const float4* __restrict__ tris, const float4* __restrict__ normals, Tab
             if (lane >= off) incl += v;
         }
         if (lane == 31) s_warp[warp] = incl;
-        __syncthreads();
+        // the barrier also tells whether the tile has any daughter: one without
+        // (every tile of the last generation) skips the scan and the expansion
+        if (!__syncthreads_or(k != 0u)) continue;
         if (warp == 0) {
             unsigned v = lane < kShadeThreads / 32 ? s_warp[lane] : 0u;
             for (int off = 1; off < 32; off <<= 1) {
