@@ -198,13 +198,14 @@ int rtmc_load_see_tables(rtmc_ctx* ctx, const float* delta, const rtmc_grid* gri
    four children; leaves are those of the binary hierarchy), level by level,
    one host synchronisation per level.
    Every kind also gets a column grid for rays parallel to z (generation 0 at
-   normal incidence): about n_tri / 21 pixels over [0, lx) x [0, ly), each
+   normal incidence): about n_tri / 5 pixels over [0, lx) x [0, ly), each
    listing the facets whose xy box meets it, sorted by top z (descending, then
    index).  Such a ray tests its pixel's facets in that order and stops when
    no facet further down the list can be closer than its best hit; the facet
-   tests are the hierarchy's, so every hit record is the same.  A mesh the grid
-   does not suit (a facet over more than 64 pixels, a pixel with more than 2048
-   facets, more than 2^24 facets, or no device memory for it) gets none. */
+   tests are the hierarchy's, so every hit record is the same.  A facet over
+   more than 64 pixels makes the build retry with a quarter of the pixels (up
+   to four times); a mesh the grid still does not suit (a pixel with more than
+   2048 facets, more than 2^24 facets, or no device memory for it) gets none. */
 int rtmc_build_bvh(rtmc_ctx* ctx, int32_t mesh_id, int32_t bvh_kind);
 
 /* Run RTMC for every (energy, angle) pair: n_e * n_theta items, item

@@ -1140,11 +1140,13 @@ void free_columns(DeviceMesh& m)
     m.col_entries = 0;
 }
 
-// The column grid over the leaf-order facets.  About 21 facets per pixel
-// (5 nm pixels on a 128^3 foam of 10 nm voxels: 7.5e6 entries, ~5 facet
-// tests per vertical ray).  A mesh the grid does not suit (a facet over more
-// than kColMaxSpan pixels, a pixel with more than kColSortMax facets, more
-// than 2^24 facets) gets none, and its vertical rays take the hierarchy.
+// The column grid over the leaf-order facets.  About 5 facets per pixel (2.4 nm
+// pixels on a 128^3 foam of 10 nm voxels; finer pixels cut the facet tests per
+// vertical ray, 5 -> 2.4 nm took a fifth off the column kernel).  A facet over
+// more than kColMaxSpan pixels makes the build retry with a quarter of the
+// pixels; a pixel with more than kColSortMax facets, more than 2^24 facets or
+// no room on the device leave the mesh without a grid, and its vertical rays
+// take the hierarchy.
 int build_columns(rtmc_ctx* ctx, DeviceMesh& m)
 {
     free_columns(m);
@@ -1152,53 +1154,60 @@ int build_columns(rtmc_ctx* ctx, DeviceMesh& m)
     const double lx = m.box.lx, ly = m.box.ly;
     if (n <= 0 || n > (1 << 24) || !(lx > 0.0) || !(ly > 0.0)) return RTMC_OK;
     cudaStream_t s = ctx->stream;
-    const double pix = std::max(1.0, (double)n / 21.0);
-    const int gx = std::min(2048, std::max(1, (int)std::lround(std::sqrt(pix * lx / ly))));
-    const int gy = std::min(2048, std::max(1, (int)std::lround(pix / gx)));
-    const int np = gx * gy;
-    const float iwx = (float)(gx / lx), iwy = (float)(gy / ly);
-    DevBuf cnt, tot, bad;
-    cudaError_t e = cnt.alloc(4ull * np);
-    if (e == cudaSuccess) e = tot.alloc(4);
-    if (e == cudaSuccess) e = bad.alloc(4);
-    if (e == cudaSuccess) e = cudaMalloc(&m.col_off, 4ull * (np + 1));
-    if (e == cudaSuccess) e = cudaMemsetAsync(cnt.p, 0, 4ull * np, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(bad.p, 0, 4, s);
-    const int tb = 256, gb = (n + tb - 1) / tb;
-    if (e == cudaSuccess) {
-        k_col_count<<<gb, tb, 0, s>>>(m.tris, n, gx, gy, iwx, iwy, cnt.as<int>(), bad.as<int>());
-        k_w4_scan<<<1, 1024, 0, s>>>(cnt.as<int>(), np, reinterpret_cast<int*>(m.col_off), tot.as<int>());
-        e = cudaGetLastError();
-    }
-    int h_tot = 0, h_bad = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(m.col_off + np, tot.p, 4, cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_tot, tot.p, 4, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_bad, bad.p, 4, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e == cudaSuccess && !h_bad && h_tot > 0) {
-        e = cudaMalloc(&m.col_ent, 8ull * h_tot);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(cnt.p, m.col_off, 4ull * np, cudaMemcpyDeviceToDevice, s);
+    double pix = std::max(1.0, (double)n / 5.0);
+    for (int attempt = 0; attempt < 5; ++attempt, pix = std::max(1.0, pix / 4.0)) {
+        free_columns(m);
+        const int gx = std::min(2048, std::max(1, (int)std::lround(std::sqrt(pix * lx / ly))));
+        const int gy = std::min(2048, std::max(1, (int)std::lround(pix / gx)));
+        const int np = gx * gy;
+        const float iwx = (float)(gx / lx), iwy = (float)(gy / ly);
+        DevBuf cnt, tot, bad;
+        cudaError_t e = cnt.alloc(4ull * np);
+        if (e == cudaSuccess) e = tot.alloc(4);
+        if (e == cudaSuccess) e = bad.alloc(4);
+        if (e == cudaSuccess) e = cudaMalloc(&m.col_off, 4ull * (np + 1));
+        if (e == cudaSuccess) e = cudaMemsetAsync(cnt.p, 0, 4ull * np, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(bad.p, 0, 4, s);
+        const int tb = 256, gb = (n + tb - 1) / tb;
         if (e == cudaSuccess) {
-            k_col_fill<<<gb, tb, 0, s>>>(m.tris, n, gx, gy, iwx, iwy, cnt.as<int>(), m.col_ent);
-            k_col_sort<<<np, 128, 0, s>>>(reinterpret_cast<const int*>(m.col_off), m.col_ent, bad.as<int>());
+            k_col_count<<<gb, tb, 0, s>>>(m.tris, n, gx, gy, iwx, iwy, cnt.as<int>(), bad.as<int>());
+            k_w4_scan<<<1, 1024, 0, s>>>(cnt.as<int>(), np, reinterpret_cast<int*>(m.col_off), tot.as<int>());
             e = cudaGetLastError();
         }
+        int h_tot = 0, h_bad = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(m.col_off + np, tot.p, 4, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&h_tot, tot.p, 4, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(&h_bad, bad.p, 4, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    }
-    if (e == cudaErrorMemoryAllocation) {          // no room: the hierarchy serves every ray
-        cudaGetLastError();
-        free_columns(m);
+        if (e == cudaSuccess && (h_bad & 1)) continue;          // a facet too wide for these pixels
+        if (e == cudaSuccess && h_tot > 0) {
+            e = cudaMalloc(&m.col_ent, 8ull * h_tot);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(cnt.p, m.col_off, 4ull * np, cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess) {
+                k_col_fill<<<gb, tb, 0, s>>>(m.tris, n, gx, gy, iwx, iwy, cnt.as<int>(), m.col_ent);
+                k_col_sort<<<np, 128, 0, s>>>(reinterpret_cast<const int*>(m.col_off), m.col_ent, bad.as<int>());
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&h_bad, bad.p, 4, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        }
+        if (e == cudaErrorMemoryAllocation) {      // no room: the hierarchy serves every ray
+            cudaGetLastError();
+            free_columns(m);
+            return RTMC_OK;
+        }
+        if (e != cudaSuccess)
+            return ctx->fail(RTMC_ERR_CUDA, std::string("build_bvh: column grid: ") + cudaGetErrorString(e));
+        if (h_bad || h_tot <= 0) { free_columns(m); return RTMC_OK; }
+        m.col_gx = gx;
+        m.col_gy = gy;
+        m.col_inv_wx = iwx;
+        m.col_inv_wy = iwy;
+        m.col_entries = h_tot;
+        m.col_ok = true;
         return RTMC_OK;
     }
-    if (e != cudaSuccess) return ctx->fail(RTMC_ERR_CUDA, std::string("build_bvh: column grid: ") + cudaGetErrorString(e));
-    if (h_bad || h_tot <= 0) { free_columns(m); return RTMC_OK; }
-    m.col_gx = gx;
-    m.col_gy = gy;
-    m.col_inv_wx = iwx;
-    m.col_inv_wy = iwy;
-    m.col_entries = h_tot;
-    m.col_ok = true;
+    free_columns(m);
     return RTMC_OK;
 }
 

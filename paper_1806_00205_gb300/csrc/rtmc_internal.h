@@ -30,7 +30,7 @@ struct DeviceMesh {
     int leaf_max = 4;              // triangles per leaf (1..8)
     bool ploc = false;             // hierarchy from locally-ordered clustering
     double build_ms = 0.0;
-    // Column grid for rays parallel to z (generation 0 at normal incidence):
+    // Column grid for rays parallel to z (generation 0 at normal incidence),
     // col_gx x col_gy pixels over [0, lx) x [0, ly); pixel p lists the facets
     // whose xy box (widened by col_margin) meets it, as (leaf-order index, top z
     // bits) pairs col_ent[col_off[p] .. col_off[p + 1]) sorted by top z
