@@ -121,3 +121,24 @@ def test_column_grid_under_deeper_trees(model):
         for k in INT_KEYS[:-1] + ("regenerated",):
             assert x[k] == y[k], k
     assert np.array_equal(ha, hb)
+
+
+def test_column_grid_retries_coarser_for_a_wide_facet(ctx):
+    """A facet as wide as the cell spans more pixels than the grid allows at first: the build
+    retries with coarser pixels, and the vertical rays still give the hierarchy's tallies."""
+    from paper_1806_00205_gb300 import rtmc
+    mesh = I.grf_foam(16, 0.5, seed=9)
+    b = mesh.box
+    z = b.z_min + 0.25 * (b.z_top - b.z_min) * 0.01
+    big = np.array([[0.0, 0.0, z, b.lx, 0.0, z, 0.0, b.ly, z]], dtype=np.float32)   # faces up, under the foam
+    tri = np.concatenate([mesh.tri.reshape(-1, 9).astype(np.float32), big])
+    mid = ctx.load_mesh(tri, b)
+    ctx.build_bvh(mid, kind=rtmc.BVH_W4)
+    n = 50_000
+    a, ha, _ = ctx.run(mid, [300.0], [0.0], n, 5)
+    c, hc, _ = ctx.run(mid, [300.0], [0.0], n, 5, desc=rtmc.run_desc(traversal=2))
+    ctx.unload_mesh(mid)
+    assert a[0]["column_rays"] == n and c[0]["column_rays"] == 0
+    for k in INT_KEYS[:-1]:
+        assert a[0][k] == c[0][k], k
+    assert np.array_equal(ha, hc)
