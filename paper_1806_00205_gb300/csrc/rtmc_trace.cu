@@ -155,14 +155,27 @@ __global__ void k_prim_count(RunParams p, ItemCtx ic, unsigned long long first, 
     atomicAdd(&counts[bucket], 1u);
 }
 
-// Exclusive scan of `m` counts in place (one block of 1024 threads).
+// Exclusive scan of `m` counts in place (one block of 1024 threads).  A thread
+// owns a contiguous segment; when the segments are whole multiples of four
+// counts (m = items x 16384) they move as 16-byte vectors, several loads in
+// flight per thread instead of one dependent load per count.
 __global__ void __launch_bounds__(1024) k_scan_counts(unsigned* __restrict__ c, unsigned m)
 {
     __shared__ unsigned sums[1024];
     const unsigned per = (m + blockDim.x - 1) / blockDim.x;
     const unsigned lo = threadIdx.x * per, hi = min(lo + per, m);
+    const bool vec = (per & 3u) == 0u && (m & 3u) == 0u;
     unsigned t = 0;
-    for (unsigned i = lo; i < hi; ++i) t += c[i];
+    if (vec) {
+        const uint4* c4 = reinterpret_cast<const uint4*>(c);
+#pragma unroll 4
+        for (unsigned i = lo / 4; i < hi / 4; ++i) {
+            const uint4 v = c4[i];
+            t += v.x + v.y + v.z + v.w;
+        }
+    } else {
+        for (unsigned i = lo; i < hi; ++i) t += c[i];
+    }
     sums[threadIdx.x] = t;
     __syncthreads();
     for (unsigned off = 1; off < blockDim.x; off <<= 1) {
@@ -172,10 +185,24 @@ __global__ void __launch_bounds__(1024) k_scan_counts(unsigned* __restrict__ c, 
         __syncthreads();
     }
     unsigned run = sums[threadIdx.x] - t;
-    for (unsigned i = lo; i < hi; ++i) {
-        const unsigned v = c[i];
-        c[i] = run;
-        run += v;
+    if (vec) {
+        uint4* c4 = reinterpret_cast<uint4*>(c);
+#pragma unroll 4
+        for (unsigned i = lo / 4; i < hi / 4; ++i) {
+            const uint4 v = c4[i];
+            uint4 o;
+            o.x = run; run += v.x;
+            o.y = run; run += v.y;
+            o.z = run; run += v.z;
+            o.w = run; run += v.w;
+            c4[i] = o;
+        }
+    } else {
+        for (unsigned i = lo; i < hi; ++i) {
+            const unsigned v = c[i];
+            c[i] = run;
+            run += v;
+        }
     }
 }
 
