@@ -36,7 +36,9 @@ ENERGIES = [50.0 * i for i in range(1, 21)]
 N_PRIM = 10_000_000
 GRID, POROSITY, CORR, SEED = 128, 0.6, 2.0, 1806
 TRI_BYTES, RAY_BYTES = 48, 48                   # triangle fetch, ray read + hit write
-NODE_BYTES = {0: 64, 1: 32, 2: 128}             # node fetch per visit: FP32 binary, Q8 binary, 4-wide FP32
+NODE_BYTES = {0: 64, 1: 32, 2: 128, 3: 64}      # node fetch per visit: FP32 binary, Q8 binary, 4-wide FP32, 4-wide Q8
+PREC_NODES = {"q4": 3, "q8": 1}                 # precision config: 8-bit node formats
+PREC_NODE_NAME = {3: "4-wide Q8", 1: "Q8"}
 MAIN_KIND = 2                                   # the paper-config workload runs on 4-wide FP32 nodes
 
 
@@ -331,7 +333,8 @@ def precision_oracle_check(ctx, rtmc, O, mesh, table, mid, n_s):
 
 def run_precision(args):
     """Precision config: 128^3 foams at porosity 0.4 / 0.6 / 0.8, 1e7 primaries at 100, 300
-    and 700 eV x incidence 0 and 60 deg.  Q8 nodes, FP32 watertight tests, FP64 re-test of
+    and 700 eV x incidence 0 and 60 deg.  8-bit quantised nodes (4-wide 64-byte by default,
+    binary 32-byte with --prec-nodes q8), FP32 watertight tests, FP64 re-test of
     flagged hits, FP64 moments.  The same streams on FP32 nodes without re-test give the
     plain SEY; the first primaries of every item go through the oracle as well."""
     import torch
@@ -346,8 +349,9 @@ def run_precision(args):
     ctx = rtmc.Context(0, stream=stream)
     ctx.load_see_tables(table)
     mq, m32 = [], []
+    qkind = PREC_NODES[args.prec_nodes]
     for m in meshes:
-        for ids, kind in ((mq, rtmc.BVH_Q8), (m32, rtmc.BVH_FP32)):
+        for ids, kind in ((mq, qkind), (m32, rtmc.BVH_FP32)):
             a = ctx.load_mesh(m.tri, m.box)
             ctx.build_bvh(a, kind=kind)
             ids.append(a)
@@ -411,7 +415,8 @@ def finish_precision(args, ctx, rtmc, O, I, meshes, table, mq, m32, prec, n_prim
                        desc=rtmc.run_desc(fp64_retest=True, count_visits=True))
     visits = cq[0]["node_visits"] / cq[0]["rays"]
     tests = cq[0]["tri_tests"] / cq[0]["rays"]
-    b_ray = visits * NODE_BYTES[1] + tests * TRI_BYTES + RAY_BYTES
+    qkind = PREC_NODES[args.prec_nodes]
+    b_ray = visits * NODE_BYTES[qkind] + tests * TRI_BYTES + RAY_BYTES
     achieved = (t["rays"] - t["col_rays"]) * b_ray / (t["trav_ms"] / 1e3) / 1e9   # the hierarchy's rays
     pk, pk_kind = peaks()
     peak = float(pk.get("hbm_gbs", 6800.0))
@@ -439,7 +444,7 @@ def finish_precision(args, ctx, rtmc, O, I, meshes, table, mq, m32, prec, n_prim
     ctx.load_see_tables(table)
     for h, m in zip(hosts, meshes):
         a = ctx.load_mesh(h, m.box)
-        ctx.build_bvh(a, kind=rtmc.BVH_Q8)
+        ctx.build_bvh(a, kind=qkind)
         rr, _, _ = ctx.run(a, PREC_E, PREC_THETA, n_prim, SEED, desc=rtmc.run_desc(fp64_retest=True))
         e_rays += sum(r["rays"] for r in rr)
         ctx.unload_mesh(a)
@@ -450,13 +455,15 @@ def finish_precision(args, ctx, rtmc, O, I, meshes, table, mq, m32, prec, n_prim
             "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "primaries_per_s": t["prims"] / (ms / 1e3),
             "config": {"workload": f"precision: {GRID}^3 periodic GRF foams at porosity 0.4 / 0.6 / 0.8 -> "
-                                   f"{ntri} triangles, Q8 BVH, FP64 re-test of flagged hits; {n_prim:.0e} "
+                                   f"{ntri} triangles, {PREC_NODE_NAME[qkind]} BVH, FP64 re-test of flagged "
+                                   f"hits; {n_prim:.0e} "
                                    "primaries at 100 / 300 / 700 eV x incidence 0 / 60 deg",
-                       "n_tri": ntri, "l2": "inputs larger than L2 (three meshes, Q8 nodes + triangles)"},
+                       "n_tri": ntri, "l2": "inputs larger than L2 (three meshes, 8-bit nodes + triangles)"},
             "sey_error": {"max_abs_diff_vs_fp32_nodes": max_d, "oracle_sample": ora,
                           "retested_frac": t["retested"] / t["rays"]},
             "items": items, "plain_fp32_rays_per_s": plain_rays / (plain_ms / 1e3),
-            "roofline": {"bound": "hbm", "kernel": "k_traverse_ww (Q8)", "achieved": achieved, "peak": peak,
+            "roofline": {"bound": "hbm", "kernel": f"k_traverse_ww ({PREC_NODE_NAME[qkind]})", "achieved": achieved,
+                         "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                          "peak_kind": f"{pk_kind} hbm_gbs", "bytes_per_ray": b_ray,
                          "node_visits_per_ray": visits, "tri_tests_per_ray": tests},
@@ -671,7 +678,9 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="default launch parameters (profiling runs)")
     ap.add_argument("--config", choices=("paper", "large", "precision"), default="paper",
                     help="paper: 128^3 foam, 20 energies x 1e7 (default); large: 256^3 foam, tertiaries; "
-                         "precision: 3 porosities, Q8 nodes + FP64 re-test, 3 energies x 2 angles")
+                         "precision: 3 porosities, 8-bit nodes + FP64 re-test, 3 energies x 2 angles")
+    ap.add_argument("--prec-nodes", choices=tuple(PREC_NODES), default="q4",
+                    help="precision config: 8-bit node format (q4: 4-wide 64-byte nodes, q8: binary 32-byte)")
     ap.add_argument("--prec-oracle", type=int, default=64,
                     help="precision config: primaries per item checked against the oracle")
     args = ap.parse_args()

@@ -45,6 +45,7 @@ extern "C" {
 #define RTMC_BVH_FP32 0     /* 64-byte nodes with FP32 child boxes */
 #define RTMC_BVH_Q8   1     /* 32-byte nodes with 8-bit outward-rounded child boxes */
 #define RTMC_BVH_W4   2     /* 128-byte 4-wide nodes with FP32 child boxes, collapsed from the binary hierarchy */
+#define RTMC_BVH_Q4   3     /* 64-byte 4-wide nodes with 8-bit outward-rounded child boxes (the RTMC_BVH_W4 hierarchy, quantised) */
 /* bvh_kind = node format | RTMC_BVH_LEAF(n): leaves of up to n (1..8) triangles, default 4 */
 #define RTMC_BVH_LEAF(n) ((n) << 8)
 /* ... | RTMC_BVH_PLOC: build the hierarchy by locally-ordered clustering
@@ -196,7 +197,12 @@ int rtmc_load_see_tables(rtmc_ctx* ctx, const float* delta, const rtmc_grid* gri
    RTMC_BVH_W4 builds the binary hierarchy and then collapses it into 4-wide
    nodes (each opens the inner child of largest surface area until it holds
    four children; leaves are those of the binary hierarchy), level by level,
-   one host synchronisation per level.
+   one host synchronisation per level.  RTMC_BVH_Q4 builds that 4-wide
+   hierarchy and quantises every node to 64 bytes: per axis a quantum
+   s = 2^e and a frame origin, and per child and plane one byte, rounded
+   outward by at least s + M 2^-21 (M the largest cell coordinate) so that the
+   traversal may evaluate each plane with one FMA.  RTMC_ERR_INVALID_ARG if a
+   node would need a quantum above 2^40 (coordinates beyond about 2^47).
    Every kind also gets a column grid for rays parallel to z (generation 0 at
    normal incidence): about n_tri / 5 pixels over [0, lx) x [0, ly), each
    listing the facets whose xy box meets it, sorted by top z (descending, then
@@ -270,7 +276,11 @@ int rtmc_trace_rays(rtmc_ctx* ctx, int32_t mesh_id, const float* o, const float*
    meshes only, n_w4 x 128 B: rows lo.x, hi.x, lo.y, hi.y, lo.z, hi.z of the
    four child boxes, each widened outward by M 2^-22 with M the largest
    coordinate of the cell, then the four child refs; an empty slot has ref
-   INT_MIN and the box [+inf, +inf]^3).  Layouts as in the library's
+   INT_MIN and the box [+inf, +inf]^3), 4 quantised 4-wide nodes
+   (RTMC_BVH_Q4 meshes only, n_w4 x 64 B: floats o'.x, o'.y, o'.z, s.x | s.y,
+   s.z, then six words lo.x, hi.x, lo.y, hi.y, lo.z, hi.z whose byte c is
+   child c's code q, then the four child refs; a plane is o' + (2^23 + q) s,
+   an empty slot has codes lo 255, hi 0 and ref INT_MIN).  Layouts as in the library's
    device code; a Q8 node holds per axis a shifted origin o' (float) and a
    biased exponent byte b (scale s = 2^(b - 127)), and child bound q decodes
    as fmaf(2^23 + q, s, o') in FP32.  With out == NULL only *bytes_needed is written; otherwise

@@ -439,6 +439,7 @@ void rtmc_destroy(rtmc_ctx* ctx)
         cudaFree(m.inv_order);
         cudaFree(m.q8);
         cudaFree(m.w4);
+        cudaFree(m.q4);
         rtmc::free_columns(m);
     }
     cudaFree(ctx->delta);
@@ -496,6 +497,7 @@ int rtmc_unload_mesh(rtmc_ctx* ctx, int32_t mesh_id)
     cudaFree(m.inv_order);
     cudaFree(m.q8);
     cudaFree(m.w4);
+    cudaFree(m.q4);
     rtmc::free_columns(m);
     m = DeviceMesh();
     return RTMC_OK;
@@ -529,7 +531,8 @@ int rtmc_build_bvh(rtmc_ctx* ctx, int32_t mesh_id, int32_t bvh_kind)
     if (mesh_id < 0 || mesh_id >= (int)ctx->meshes.size() || !ctx->meshes[mesh_id].tri_in)
         return ctx->fail(RTMC_ERR_NOT_LOADED, "build_bvh: unknown mesh id");
     const int format = bvh_kind & 0xFF, leaf = (bvh_kind >> 8) & 0xFF, builder = bvh_kind >> 16;
-    if ((format != RTMC_BVH_FP32 && format != RTMC_BVH_Q8 && format != RTMC_BVH_W4) || (builder != 0 && builder != 1) ||
+    if ((format != RTMC_BVH_FP32 && format != RTMC_BVH_Q8 && format != RTMC_BVH_W4 && format != RTMC_BVH_Q4) ||
+        (builder != 0 && builder != 1) ||
         leaf > 8)
         return ctx->fail(RTMC_ERR_INVALID_ARG, "build_bvh: unknown bvh kind or leaf size > 8");
     DeviceGuard g(ctx->device);
@@ -639,6 +642,7 @@ int rtmc_export_bvh(rtmc_ctx* ctx, int32_t mesh_id, int32_t which, void* out, in
     else if (which == 1 && m.q8) { src = m.q8; need = m.n_nodes * 32; }
     else if (which == 2) { src = m.tris; need = m.n_tri * 48; }
     else if (which == 3 && m.w4) { src = m.w4; need = m.n_w4 * 128; }
+    else if (which == 4 && m.q4) { src = m.q4; need = m.n_w4 * 64; }
     else return ctx->fail(RTMC_ERR_INVALID_ARG, "export_bvh: unknown array or not built in this format");
     if (bytes_needed) *bytes_needed = need;
     if (!out) return RTMC_OK;

@@ -268,8 +268,8 @@ extern "C" int rtmc_run_batch(rtmc_ctx* ctx, const rtmc_batch* batch, const rtmc
         key = buf;
         for (int i = 0; i < batch->n_meshes; ++i) {      // every mesh array a recorded launch reads
             const DeviceMesh& m = ctx->meshes[batch->mesh_ids[i]];
-            std::snprintf(buf, sizeof buf, "|%d:%p:%p:%p:%p:%p:%p:%p:%d:%d", batch->mesh_ids[i],
-                          (const void*)m.nodes, m.q8, m.w4, (const void*)m.tris, (const void*)m.normals,
+            std::snprintf(buf, sizeof buf, "|%d:%p:%p:%p:%p:%p:%p:%p:%p:%d:%d", batch->mesh_ids[i],
+                          (const void*)m.nodes, m.q8, m.w4, m.q4, (const void*)m.tris, (const void*)m.normals,
                           (const void*)m.col_off, (const void*)m.col_ent, m.kind, (int)m.col_ok);
             key += buf;
         }

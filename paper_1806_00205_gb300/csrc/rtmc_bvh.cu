@@ -816,6 +816,74 @@ __global__ void k_w4_single(const float* __restrict__ tri, float margin, float4*
     w4_store(w4, 0, b, ref);
 }
 
+// ---- 4-wide nodes quantised to 8 bits ---------------------------------------
+// Per axis a quantum s = 2^e and an integer frame start m (origin m s); child
+// plane codes q in [0, 255] stand for (m + q) s.  The traversal evaluates a
+// plane as fmaf(2^23 + q, s / d, (o' - o) / d) with o' = (m - 2^23) s: the
+// rounding of o' - o and of its quotient moves a plane by at most
+// |o' - o| 2^-23 <= s + M 2^-22 (|o'| < 2^23 s + M, |o| <= M), so every code
+// is rounded outward by k = 1 + ceil(M 2^-21 / s) quanta beyond the FP32
+// 4-wide box.  All of it is exact in FP64: s is a power of two, |m| < 2^23.
+// Returns false when no quantum up to 2^kQ4MaxExp fits (coordinates too large).
+__device__ bool q4_axis(const float4& lo_row, const float4& hi_row, const bool (&real)[4], double big,
+                        float& o_shift, float& scale, unsigned& w_lo, unsigned& w_hi)
+{
+    const float lo[4] = {lo_row.x, lo_row.y, lo_row.z, lo_row.w};
+    const float hi[4] = {hi_row.x, hi_row.y, hi_row.z, hi_row.w};
+    double L = INFINITY, H = -INFINITY;
+    for (int c = 0; c < 4; ++c)
+        if (real[c]) { L = fmin(L, (double)lo[c]); H = fmax(H, (double)hi[c]); }
+    const double span = fmax(H - L, 0.0), mag = fmax(fabs(L), fabs(H));
+    int e = -126;
+    if (span > 0.0) e = max(e, ilogb(span / 250.0));
+    if (mag > 0.0) e = max(e, ilogb(mag) - 22);
+    for (; e <= kQ4MaxExp; ++e) {
+        const double sc = ldexp(1.0, e);
+        const double k = 1.0 + ceil(big * 0x1p-21 / sc);
+        const double m = floor(L / sc) - k;
+        if (!(fabs(m) < 0x1p23) || ceil((H - m * sc) / sc) + k > 255.0) continue;
+        w_lo = w_hi = 0u;
+        for (int c = 0; c < 4; ++c) {
+            unsigned ql = 255u, qh = 0u;                 // empty slot: lo above hi
+            if (real[c]) {
+                ql = (unsigned)(floor(((double)lo[c] - m * sc) / sc) - k);
+                qh = (unsigned)(ceil(((double)hi[c] - m * sc) / sc) + k);
+            }
+            w_lo |= ql << (8 * c);
+            w_hi |= qh << (8 * c);
+        }
+        o_shift = (float)((m - 0x1p23) * sc);
+        scale = (float)sc;
+        return true;
+    }
+    return false;
+}
+
+__global__ void k_q4_quantize(const float4* __restrict__ w4, int n, double big, uint4* __restrict__ q4,
+                              int* __restrict__ bad)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4* nd = w4 + 8ll * i;
+    const float4 cr = nd[6];
+    const int ref[4] = {__float_as_int(cr.x), __float_as_int(cr.y), __float_as_int(cr.z), __float_as_int(cr.w)};
+    const bool real[4] = {ref[0] != kEmptyChild, ref[1] != kEmptyChild, ref[2] != kEmptyChild,
+                          ref[3] != kEmptyChild};
+    float o[3], sc[3];
+    unsigned wl[3], wh[3];
+    bool ok = true;
+    for (int a = 0; a < 3; ++a) ok = q4_axis(nd[2 * a], nd[2 * a + 1], real, big, o[a], sc[a], wl[a], wh[a]) && ok;
+    if (!ok) {
+        atomicExch(bad, 1);
+        for (int a = 0; a < 3; ++a) { o[a] = 0.f; sc[a] = 1.f; wl[a] = 0u; wh[a] = 0xFFFFFFFFu; }
+    }
+    q4[4ll * i + 0] = make_uint4(__float_as_uint(o[0]), __float_as_uint(o[1]), __float_as_uint(o[2]),
+                                 __float_as_uint(sc[0]));
+    q4[4ll * i + 1] = make_uint4(__float_as_uint(sc[1]), __float_as_uint(sc[2]), wl[0], wh[0]);
+    q4[4ll * i + 2] = make_uint4(wl[1], wh[1], wl[2], wh[2]);
+    q4[4ll * i + 3] = make_uint4((unsigned)ref[0], (unsigned)ref[1], (unsigned)ref[2], (unsigned)ref[3]);
+}
+
 // ---- column grid -----------------------------------------------------------
 // A ray parallel to z meets only facets whose xy box contains its xy point, and
 // none above its first hit: per pixel of an xy grid the facets whose box meets
@@ -930,6 +998,7 @@ int build_lbvh(rtmc_ctx* ctx, DeviceMesh& m)
     if (m.inv_order) { cudaFree(m.inv_order); m.inv_order = nullptr; }
     if (m.q8) { cudaFree(m.q8); m.q8 = nullptr; }
     if (m.w4) { cudaFree(m.w4); m.w4 = nullptr; }
+    if (m.q4) { cudaFree(m.q4); m.q4 = nullptr; }
     m.n_w4 = 0;
     m.depth_w4 = 0;
     m.built = false;
@@ -939,7 +1008,9 @@ int build_lbvh(rtmc_ctx* ctx, DeviceMesh& m)
     if (e == cudaSuccess) e = cudaMalloc(&m.tris, (size_t)(n + 1) * 48);
     if (e == cudaSuccess) e = cudaMalloc(&m.normals, (size_t)(n + 1) * 16);
     if (e == cudaSuccess && m.kind == FMT_Q8) e = cudaMalloc(&m.q8, n_nodes * 32);
-    if (e == cudaSuccess && m.kind == FMT_W4) e = cudaMalloc(&m.w4, n_nodes * 128);   // one per binary inner node at most
+    const bool wide = m.kind == FMT_W4 || m.kind == FMT_Q4;
+    if (e == cudaSuccess && wide) e = cudaMalloc(&m.w4, n_nodes * 128);   // one per binary inner node at most
+    if (e == cudaSuccess && m.kind == FMT_Q4) e = cudaMalloc(&m.q4, n_nodes * 64);
     if (e == cudaSuccess) e = cudaMalloc(&m.inv_order, (size_t)n * 4);
     if (e != cudaSuccess) return ctx->fail(RTMC_ERR_OOM, std::string("build_bvh: ") + cudaGetErrorString(e));
     m.n_nodes = n_nodes;
@@ -1052,7 +1123,7 @@ int build_lbvh(rtmc_ctx* ctx, DeviceMesh& m)
     if (n == 1) {
         k_single_leaf<<<1, 1, 0, s>>>(m.tri_in, m.nodes);
         if (m.kind == FMT_Q8) k_quantize_single<<<1, 1, 0, s>>>(m.tri_in, reinterpret_cast<uint4*>(m.q8));
-        if (m.kind == FMT_W4) {
+        if (wide) {
             k_w4_single<<<1, 1, 0, s>>>(m.tri_in, w4_margin, reinterpret_cast<float4*>(m.w4));
             m.n_w4 = 1;
             m.depth_w4 = 1;
@@ -1070,7 +1141,7 @@ int build_lbvh(rtmc_ctx* ctx, DeviceMesh& m)
         if (m.kind == FMT_Q8)
             k_quantize<<<gi, tb, 0, s>>>(m.tri_in, order, n - 1, child.as<int2>(), range.as<int2>(), aabb.as<float4>(),
                                          m.leaf_max, reinterpret_cast<uint4*>(m.q8));
-        if (m.kind == FMT_W4) {
+        if (wide) {
             DevBuf fr[2], cnt, off, tot;
             e = fr[0].alloc(8ull * n_nodes);
             if (e == cudaSuccess) e = fr[1].alloc(8ull * n_nodes);
@@ -1105,6 +1176,17 @@ int build_lbvh(rtmc_ctx* ctx, DeviceMesh& m)
             m.depth_w4 = levels;
         }
     }
+    DevBuf qbad;
+    int h_qbad = 0;
+    if (m.kind == FMT_Q4) {
+        e = qbad.alloc(4);
+        if (e == cudaSuccess) e = cudaMemsetAsync(qbad.p, 0, 4, s);
+        if (e != cudaSuccess) return ctx->fail(RTMC_ERR_OOM, std::string("build_bvh (Q4): ") + cudaGetErrorString(e));
+        k_q4_quantize<<<(unsigned)((m.n_w4 + tb - 1) / tb), tb, 0, s>>>(reinterpret_cast<const float4*>(m.w4),
+                                                                       (int)m.n_w4, big, reinterpret_cast<uint4*>(m.q4),
+                                                                       qbad.as<int>());
+        cudaMemcpyAsync(&h_qbad, qbad.p, 4, cudaMemcpyDeviceToHost, s);
+    }
     const int gp = (n + 1 + tb - 1) / tb;
     k_pack<<<gp, tb, 0, s>>>(m.tri_in, order, n, m.tris, m.normals, m.inv_order);
     int h_depth = 0;
@@ -1121,7 +1203,8 @@ int build_lbvh(rtmc_ctx* ctx, DeviceMesh& m)
     m.build_ms = ms;
     if (h_depth >= kStackMax)
         return ctx->fail(RTMC_ERR_DEVICE_CHECK, "build_bvh: hierarchy deeper than the traversal stack");
-    if (m.kind == FMT_W4 && 3 * m.depth_w4 >= kStackMax)
+    if (h_qbad) return ctx->fail(RTMC_ERR_INVALID_ARG, "build_bvh (Q4): coordinates too large for 8-bit 4-wide nodes");
+    if (wide && 3 * m.depth_w4 >= kStackMax)
         return ctx->fail(RTMC_ERR_DEVICE_CHECK, "build_bvh: 4-wide hierarchy deeper than the traversal stack");
     const int rc = build_columns(ctx, m);
     if (rc != RTMC_OK) return rc;

@@ -94,6 +94,12 @@ struct TableDesc {
 constexpr int FMT_FP32 = 0;
 constexpr int FMT_Q8 = 1;
 constexpr int FMT_W4 = 2;         // 4-wide nodes, FP32 child boxes (128 B)
+constexpr int FMT_Q4 = 3;         // 4-wide nodes, 8-bit child boxes (64 B)
+// A 4-wide 8-bit node keeps its shifted frame origin (|o'| about 2^23 quanta)
+// finite after the slab test multiplies it by 1/d: the quantum stays below
+// 2^kQ4MaxExp and the traversal clamps |1/d| to 2^kQ4MaxInvExp.
+constexpr int kQ4MaxExp = 40;
+constexpr int kQ4MaxInvExp = 64;
 constexpr int kEmptyChild = INT_MIN;   // unused slot of a 4-wide node (its box is never hit)
 
 // Leaf reference used by both node formats: ~((first << 3) | (count - 1)).

@@ -23,7 +23,8 @@ struct DeviceMesh {
     float4* normals = nullptr;     // n_tri float4
     int* inv_order = nullptr;      // original id -> leaf-order index
     void* q8 = nullptr;            // n_nodes * 32 B quantised nodes (RTMC_BVH_Q8)
-    void* w4 = nullptr;            // n_w4 * 128 B 4-wide nodes (RTMC_BVH_W4)
+    void* w4 = nullptr;            // n_w4 * 128 B 4-wide nodes (RTMC_BVH_W4, RTMC_BVH_Q4)
+    void* q4 = nullptr;            // n_w4 * 64 B quantised 4-wide nodes (RTMC_BVH_Q4)
     int64_t n_w4 = 0;
     int depth_w4 = 0;              // levels of the 4-wide hierarchy
     int depth = 0;                 // hierarchy depth (root = 1)

@@ -120,31 +120,72 @@ __device__ __forceinline__ void slab_near_far(float nxp, float fxp, float nyp, f
 }
 
 // 4-wide node (128 B): rows lo.x, hi.x, lo.y, hi.y, lo.z, hi.z of the four
-// child boxes, then the four child refs.  The hit children come back sorted by
+// child boxes, then the four child refs.  The 8-bit form (64 B) holds per
+// axis a shifted origin o' and a quantum s, then the same six rows as one
+// code byte per child, then the refs.  The hit children come back sorted by
 // entry distance (nearest first); *nh is their number.  An empty slot holds
-// the box [+inf, +inf]^3, which the slab test never hits.
+// the box [+inf, +inf]^3 (FP32) or the ref kEmptyChild (8-bit), never hit.
+template <int FMT>
 __device__ __forceinline__ void node4_children(const void* __restrict__ nodes, int node, const RaySetup& r,
                                                float t_best, float (&tk)[4], int (&ck)[4], int& nh)
 {
-    // Per axis the lane loads the near row first (lo when the direction is
-    // positive, hi when negative), so (near - o) * inv <= (far - o) * inv and no
-    // min / max is needed to order the two planes: the same values as the
-    // two-plane slab test, three more loads, 24 fewer ALU operations.
-    const float4* np = reinterpret_cast<const float4*>(nodes) + 8ll * node;
-    const int sx = (int)(__float_as_uint(r.inv.x) >> 31), sy = (int)(__float_as_uint(r.inv.y) >> 31),
-              sz = (int)(__float_as_uint(r.inv.z) >> 31);
-    const float4 nx = ldg4(np + sx), fx = ldg4(np + 1 - sx);
-    const float4 ny = ldg4(np + 2 + sy), fy = ldg4(np + 3 - sy);
-    const float4 nz = ldg4(np + 4 + sz), fz = ldg4(np + 5 - sz);
-    const float4 cr = ldg4(np + 6);
-    const float3 oi = make_float3(r.o.x * r.inv.x, r.o.y * r.inv.y, r.o.z * r.inv.z);
     bool h0, h1, h2, h3;
-    slab_near_far(nx.x, fx.x, ny.x, fy.x, nz.x, fz.x, r, oi, t_best, tk[0], h0);
-    slab_near_far(nx.y, fx.y, ny.y, fy.y, nz.y, fz.y, r, oi, t_best, tk[1], h1);
-    slab_near_far(nx.z, fx.z, ny.z, fy.z, nz.z, fz.z, r, oi, t_best, tk[2], h2);
-    slab_near_far(nx.w, fx.w, ny.w, fy.w, nz.w, fz.w, r, oi, t_best, tk[3], h3);
-    ck[0] = __float_as_int(cr.x); ck[1] = __float_as_int(cr.y);
-    ck[2] = __float_as_int(cr.z); ck[3] = __float_as_int(cr.w);
+    if constexpr (FMT == FMT_Q4) {
+        // Plane (m + q) s evaluated as fmaf(2^23 + q, s / d, (o' - o) / d): one
+        // FMA per plane on the code byte made a float by __byte_perm.  The
+        // codes are rounded outward far enough to cover the rounding of
+        // (o' - o) / d (see the quantiser); the near row of each axis is
+        // chosen by the sign of the direction, as for FP32 nodes.
+        const float4* np = reinterpret_cast<const float4*>(nodes) + 4ll * node;
+        float4 a, b, c, cr;
+        ldg8(np, a, b);                          // o'.xyz, s.x | s.y, s.z, row lo.x, row hi.x
+        ldg8(np + 2, c, cr);                     // rows lo.y, hi.y, lo.z, hi.z | refs
+        const float kx = a.w * r.inv.x, ky = b.x * r.inv.y, kz = b.y * r.inv.z;
+        const float ox = (a.x - r.o.x) * r.inv.x, oy = (a.y - r.o.y) * r.inv.y, oz = (a.z - r.o.z) * r.inv.z;
+        const unsigned lx = __float_as_uint(b.z), hx = __float_as_uint(b.w);
+        const unsigned ly = __float_as_uint(c.x), hy = __float_as_uint(c.y);
+        const unsigned lz = __float_as_uint(c.z), hz = __float_as_uint(c.w);
+        const bool gx = r.inv.x < 0.f, gy = r.inv.y < 0.f, gz = r.inv.z < 0.f;
+        const unsigned nxw = gx ? hx : lx, fxw = gx ? lx : hx;
+        const unsigned nyw = gy ? hy : ly, fyw = gy ? ly : hy;
+        const unsigned nzw = gz ? hz : lz, fzw = gz ? lz : hz;
+        ck[0] = __float_as_int(cr.x); ck[1] = __float_as_int(cr.y);
+        ck[2] = __float_as_int(cr.z); ck[3] = __float_as_int(cr.w);
+        auto child = [&](int j, float& tmin, bool& hit) {
+            const float tnx = fmaf(byte_m(nxw, j), kx, ox), tfx = fmaf(byte_m(fxw, j), kx, ox);
+            const float tny = fmaf(byte_m(nyw, j), ky, oy), tfy = fmaf(byte_m(fyw, j), ky, oy);
+            const float tnz = fmaf(byte_m(nzw, j), kz, oz), tfz = fmaf(byte_m(fzw, j), kz, oz);
+            tmin = fmaxf(fmaxf(tnx, tny), fmaxf(tnz, 0.f));
+            const float tmax = fminf(fminf(tfx, tfy), fminf(tfz, t_best));
+            hit = tmin <= tmax * kRobust;
+        };
+        child(0, tk[0], h0);
+        child(1, tk[1], h1);
+        child(2, tk[2], h2);
+        child(3, tk[3], h3);
+        h1 = h1 && ck[1] != kEmptyChild;
+        h2 = h2 && ck[2] != kEmptyChild;
+        h3 = h3 && ck[3] != kEmptyChild;
+    } else {
+        // Per axis the lane loads the near row first (lo when the direction is
+        // positive, hi when negative), so (near - o) * inv <= (far - o) * inv and no
+        // min / max is needed to order the two planes: the same values as the
+        // two-plane slab test, three more loads, 24 fewer ALU operations.
+        const float4* np = reinterpret_cast<const float4*>(nodes) + 8ll * node;
+        const int sx = (int)(__float_as_uint(r.inv.x) >> 31), sy = (int)(__float_as_uint(r.inv.y) >> 31),
+                  sz = (int)(__float_as_uint(r.inv.z) >> 31);
+        const float4 nx = ldg4(np + sx), fx = ldg4(np + 1 - sx);
+        const float4 ny = ldg4(np + 2 + sy), fy = ldg4(np + 3 - sy);
+        const float4 nz = ldg4(np + 4 + sz), fz = ldg4(np + 5 - sz);
+        const float4 cr = ldg4(np + 6);
+        const float3 oi = make_float3(r.o.x * r.inv.x, r.o.y * r.inv.y, r.o.z * r.inv.z);
+        slab_near_far(nx.x, fx.x, ny.x, fy.x, nz.x, fz.x, r, oi, t_best, tk[0], h0);
+        slab_near_far(nx.y, fx.y, ny.y, fy.y, nz.y, fz.y, r, oi, t_best, tk[1], h1);
+        slab_near_far(nx.z, fx.z, ny.z, fy.z, nz.z, fz.z, r, oi, t_best, tk[2], h2);
+        slab_near_far(nx.w, fx.w, ny.w, fy.w, nz.w, fz.w, r, oi, t_best, tk[3], h3);
+        ck[0] = __float_as_int(cr.x); ck[1] = __float_as_int(cr.y);
+        ck[2] = __float_as_int(cr.z); ck[3] = __float_as_int(cr.w);
+    }
     if (!h0) tk[0] = INFINITY;
     if (!h1) tk[1] = INFINITY;
     if (!h2) tk[2] = INFINITY;
@@ -157,6 +198,19 @@ __device__ __forceinline__ void node4_children(const void* __restrict__ nodes, i
         }
     };
     cswap(0, 1); cswap(2, 3); cswap(0, 2); cswap(1, 3); cswap(1, 2);
+}
+
+// The 8-bit 4-wide nodes multiply their shifted origin by 1/d: |1/d| is
+// clamped to 2^kQ4MaxInvExp there so the product stays finite.  Only a
+// direction component below 2^-64 in magnitude (in practice an exact zero,
+// whose 1/d the ray set-up makes 1e30) changes, and for it any magnitude this
+// large keeps each slab either all-pass or all-miss.
+__device__ __forceinline__ RaySetup q4_setup(RaySetup r)
+{
+    const float lim = 0x1p64f;
+    r.inv = make_float3(fminf(fmaxf(r.inv.x, -lim), lim), fminf(fmaxf(r.inv.y, -lim), lim),
+                        fminf(fmaxf(r.inv.z, -lim), lim));
+    return r;
 }
 
 struct Counts { unsigned visits = 0, tests = 0; };
@@ -276,7 +330,7 @@ __device__ __forceinline__ int bvh_closest(const void* __restrict__ nodes, const
     };
     for (int visits = 0;; ++visits) {
         if (visits >= kMaxVisits) { status |= ST_LOOP_LIMIT; break; }
-        if constexpr (FMT == FMT_W4) {
+        if constexpr (FMT == FMT_W4 || FMT == FMT_Q4) {
             if (node < 0) {                                  // a leaf: test it now
                 test_leaf<COUNT, TRI64>(tris, r, r64, node, skip, t_best, t_best64, best, best_orig, bu, bv, cnt);
                 if (!pop()) break;
@@ -285,7 +339,7 @@ __device__ __forceinline__ int bvh_closest(const void* __restrict__ nodes, const
             if (COUNT) ++cnt->visits;
             float tk[4];
             int ck[4], nh;
-            node4_children(nodes, node, r, t_best, tk, ck, nh);
+            node4_children<FMT>(nodes, node, FMT == FMT_Q4 ? q4_setup(r) : r, t_best, tk, ck, nh);
             if (nh > 3) push(ck[3], tk[3]);
             if (nh > 2) push(ck[2], tk[2]);
             if (nh > 1) push(ck[1], tk[1]);
@@ -552,6 +606,7 @@ k_traverse_ww(const void* __restrict__ nodes, const float4* __restrict__ tris, c
     };
     auto restart = [&]() {      // new cell traversal from the current origin
         rs = setup_ray(o, d);
+        if constexpr (FMT == FMT_Q4) rs = q4_setup(rs);   // the cell exit reads only finite 1/d
         node = 0; leaf = 0; sp = 0; visits = 0;
         t_best = kNoHit; best = -1; best_orig = INT_MAX; bu = bv = 0.f;
         if (RETEST) { s_b64[tid] = -1; namb = 0; }   // s_t64: FP64 distance of facet s_b64 (if the best)
@@ -590,10 +645,10 @@ k_traverse_ww(const void* __restrict__ nodes, const float4* __restrict__ tris, c
             while (node >= 0 && node != kEntrySentinel) {
                 if (++visits > kMaxVisits) { status |= ST_LOOP_LIMIT; node = kEntrySentinel; leaf = 0; sp = 0; break; }
                 if (COUNT) ++cnt.visits;
-                if constexpr (FMT == FMT_W4) {
+                if constexpr (FMT == FMT_W4 || FMT == FMT_Q4) {
                     float tk[4];
                     int ck[4], nh;
-                    node4_children(nodes, node, rs, t_best, tk, ck, nh);
+                    node4_children<FMT>(nodes, node, rs, t_best, tk, ck, nh);
                     if (nh > 3) push(ck[3], tk[3]);           // farthest first: the nearest stays on top
                     if (nh > 2) push(ck[2], tk[2]);
                     if (nh > 1) push(ck[1], tk[1]);
@@ -933,7 +988,7 @@ static cudaError_t traverse_t(const DeviceMesh& m, const RunParams& p, const Que
 {
     const float big = fmaxf(fmaxf(fabsf(p.lx), fabsf(p.ly)), fmaxf(fabsf(p.z_min), fabsf(p.z_top)));
     const Cell cell{p.lx, p.ly, p.z_min, p.z_top, p.max_wraps, ldexpf(big, -20)};
-    const void* nodes = F == FMT_Q8 ? m.q8 : (F == FMT_W4 ? m.w4 : (const void*)m.nodes);
+    const void* nodes = F == FMT_Q8 ? m.q8 : (F == FMT_W4 ? m.w4 : (F == FMT_Q4 ? m.q4 : (const void*)m.nodes));
     const int bt = tune.block_threads;
     int per_sm = tune.blocks_per_sm;
     if (tune.traversal == 1) {
@@ -966,6 +1021,7 @@ cudaError_t launch_traverse(const DeviceMesh& m, const RunParams& p, const Queue
 {
     if (m.kind == FMT_Q8) return traverse_f<FMT_Q8>(m, p, q, buf, gen, num_sms, tune, record, count, retest, s);
     if (m.kind == FMT_W4) return traverse_f<FMT_W4>(m, p, q, buf, gen, num_sms, tune, record, count, retest, s);
+    if (m.kind == FMT_Q4) return traverse_f<FMT_Q4>(m, p, q, buf, gen, num_sms, tune, record, count, retest, s);
     return traverse_f<FMT_FP32>(m, p, q, buf, gen, num_sms, tune, record, count, retest, s);
 }
 
@@ -1004,6 +1060,9 @@ cudaError_t launch_trace_rays(const DeviceMesh& m, const float* o, const float* 
                                                             hits, status);
     else if (gb > 0 && m.kind == FMT_W4)
         k_trace_rays<FMT_W4><<<(unsigned)gb, tb, smem, s>>>(m.w4, m.tris, m.inv_order, (int)m.n_tri, o, d, skip, n,
+                                                            hits, status);
+    else if (gb > 0 && m.kind == FMT_Q4)
+        k_trace_rays<FMT_Q4><<<(unsigned)gb, tb, smem, s>>>(m.q4, m.tris, m.inv_order, (int)m.n_tri, o, d, skip, n,
                                                             hits, status);
     else if (gb > 0)
         k_trace_rays<FMT_FP32><<<(unsigned)gb, tb, smem, s>>>(m.nodes, m.tris, m.inv_order, (int)m.n_tri, o, d, skip,

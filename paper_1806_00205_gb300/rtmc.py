@@ -22,6 +22,7 @@ ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NOT_LOADED", -5: "NOT_B
 BVH_FP32 = 0
 BVH_Q8 = 1
 BVH_W4 = 2
+BVH_Q4 = 3
 ESCAPED, EMITTER, ABSORBED_LOW, ABSORBED_OTHER, LOST = 0, 1, 2, 3, 4
 
 EXPORTS = ["rtmc_create", "rtmc_destroy", "rtmc_last_error", "rtmc_load_mesh", "rtmc_unload_mesh",
@@ -338,7 +339,8 @@ class Context:
         return hits
 
     def export_bvh(self, mesh_id, which):
-        """Raw bytes of a built BVH array (0 FP32 nodes, 1 Q8 nodes, 2 triangles, 3 4-wide nodes)."""
+        """Raw bytes of a built BVH array (0 FP32 nodes, 1 Q8 nodes, 2 triangles, 3 4-wide nodes,
+        4 quantised 4-wide nodes)."""
         need = C.c_int64()
         self._check(self._L.rtmc_export_bvh(self.h, int(mesh_id), int(which), None, 0, C.byref(need)))
         buf = np.zeros(need.value, dtype=np.uint8)

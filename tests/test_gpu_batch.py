@@ -18,11 +18,12 @@ def setup():
     from paper_1806_00205_gb300 import rtmc
     c = rtmc.Context(0)
     c.load_see_tables(TABLE)
-    meshes = [I.grf_foam(16, 0.5), I.grf_foam(24, 0.8, seed=3), I.grf_foam(12, 0.35, seed=4)]
+    meshes = [I.grf_foam(16, 0.5), I.grf_foam(24, 0.8, seed=3), I.grf_foam(12, 0.35, seed=4),
+              I.grf_foam(16, 0.6, seed=5)]
     ids = []
     for k, m in enumerate(meshes):
         mid = c.load_mesh(m.tri, m.box)
-        c.build_bvh(mid, kind=(rtmc.BVH_FP32, rtmc.BVH_Q8, rtmc.BVH_W4)[k])
+        c.build_bvh(mid, kind=(rtmc.BVH_FP32, rtmc.BVH_Q8, rtmc.BVH_W4, rtmc.BVH_Q4)[k])
         ids.append(mid)
     yield c, ids, rtmc
     c.close()

@@ -84,7 +84,8 @@ def _rays_for(mesh, n, rng):
 
 @pytest.mark.parametrize("kind,leaf,ploc", [(0, 4, False), (0, 1, False), (1, 4, False), (1, 8, False),
                                              (0, 4, True), (1, 4, True), (0, 1, True), (1, 8, True),
-                                             (2, 4, False), (2, 1, False), (2, 8, True)])
+                                             (2, 4, False), (2, 1, False), (2, 8, True),
+                                             (3, 4, False), (3, 1, False), (3, 8, True)])
 @pytest.mark.parametrize("which", ["tiny", "flat", "well", "single", "foam8"])
 def test_bvh_closest_hit_matches_brute_force(ctx, which, kind, leaf, ploc):
     mesh = {"tiny": lambda: I.grf_foam(16, 0.5), "flat": lambda: I.flat_plane(),
@@ -121,12 +122,13 @@ def test_bvh_closest_hit_matches_brute_force(ctx, which, kind, leaf, ploc):
 
 # ---------------------------------------------------------- full runs ------
 
-def test_four_wide_nodes_records_match_oracle(ctx):
-    """4-wide nodes change the traversal, not the answer: records on the tiny foam."""
+@pytest.mark.parametrize("kind", [2, 3])
+def test_four_wide_nodes_records_match_oracle(ctx, kind):
+    """4-wide nodes (FP32 or 8-bit boxes) change the traversal, not the answer: records on the tiny foam."""
     from paper_1806_00205_gb300 import rtmc
     mesh = I.grf_foam(16, 0.5)
     mid = ctx.load_mesh(mesh.tri, mesh.box)
-    ctx.build_bvh(mid, kind=rtmc.BVH_W4)
+    ctx.build_bvh(mid, kind=kind)
     n = 30_000
     g = ctx.run_records(mid, 300.0, 0.0, n, seed=78)
     o = O.run(mesh, TABLE, 300.0, 0.0, n, seed=78, records=True)
@@ -354,6 +356,16 @@ def test_paper_scale_sampled_parity(ctx, paper):
         assert r4[0][k] == r[k], k
     assert np.array_equal(he4, he) and np.array_equal(ha4, ha)
     assert torch.equal(h4, h)
+    # and so do the 8-bit 4-wide nodes of the precision form
+    q4 = ctx.load_mesh(mesh.tri, mesh.box)
+    ctx.build_bvh(q4, kind=rtmc.BVH_Q4)
+    hq = torch.zeros(n, dtype=torch.int64, device="cuda")
+    rq, heq, haq = ctx.run(q4, [500.0], [0.0], n, seed=1806, desc=rtmc.run_desc(prim_hash=hq))
+    ctx.unload_mesh(q4)
+    for k in ("rays", "escaped", "emitted", "sum_k", "sum_k2", "wraps", "lost", "absorbed_low", "absorbed_other"):
+        assert rq[0][k] == r[k], k
+    assert np.array_equal(heq, he) and np.array_equal(haq, ha)
+    assert torch.equal(hq, h)
 
 
 def test_gibson_ashby_cage_records_match_oracle(ctx):

@@ -1,4 +1,4 @@
-"""Precision form: 8-bit quantised 32-byte nodes and the FP64 re-test (GB300)."""
+"""Precision form: 8-bit quantised nodes (binary 32-byte, 4-wide 64-byte) and the FP64 re-test (GB300)."""
 import math
 
 import numpy as np
@@ -81,7 +81,51 @@ def test_q8_boxes_contain_fp32_boxes(ctx, n, p, leaf):
     assert np.median(grow) < 0.05
 
 
-@pytest.mark.parametrize("kind,retest", [(1, False), (1, True), (0, True)])
+def _decode_q4(raw):
+    """Quantised 4-wide nodes: the exact planes o' + (2^23 + q) s (float64 holds them exactly:
+    (m + q) s with |m + q| < 2^24 and s a power of two), the codes, the quanta and the refs."""
+    w = raw.view(np.uint32).reshape(-1, 16)
+    f = raw.view(np.float32).reshape(-1, 16)[:, :6].astype(np.float64)
+    ax = [0, 0, 1, 1, 2, 2]                                   # rows lo.x hi.x lo.y hi.y lo.z hi.z
+    q = np.stack([(w[:, 6:12] >> (8 * c)) & 255 for c in range(4)], axis=2).astype(np.float64)
+    planes = f[:, ax, None] + (8388608.0 + q) * f[:, [3 + a for a in ax], None]
+    return planes, q, f[:, 3:6], w[:, 12:16].view(np.int32)
+
+
+@pytest.mark.parametrize("n,p,leaf", [(16, 0.5, 4), (48, 0.3, 1), (128, 0.6, 4)])
+def test_q4_planes_enclose_four_wide_boxes(ctx, n, p, leaf):
+    """Exhaustive: every quantised 4-wide child plane lies outside its FP32 4-wide plane by at
+    least one quantum plus M 2^-22, the rounding the one-FMA evaluation may add; empty slots
+    keep lo code 255 above hi code 0; the child refs are those of the FP32 4-wide nodes."""
+    from paper_1806_00205_gb300 import rtmc
+    mesh = I.grf_foam(n, p)
+    mid = ctx.load_mesh(mesh.tri, mesh.box)
+    ctx.build_bvh(mid, kind=rtmc.BVH_Q4, leaf=leaf)
+    planes, q, s, refs = _decode_q4(ctx.export_bvh(mid, 4))
+    w4 = ctx.export_bvh(mid, 3)
+    ctx.unload_mesh(mid)
+    rows = w4.view(np.float32).reshape(-1, 32)[:, :24].reshape(-1, 6, 4).astype(np.float64)
+    wrefs = w4.view(np.int32).reshape(-1, 32)[:, 24:28]
+    assert np.array_equal(refs, wrefs)
+    box = mesh.box
+    big = max(abs(box.lx), abs(box.ly), abs(box.z_min), abs(box.z_top))
+    real = refs != np.iinfo(np.int32).min                      # node, child
+    rows = np.where(real[:, None, :], rows, 0.0)               # empty slots: +inf boxes, not compared
+    need = s[:, [0, 0, 1, 1, 2, 2], None] + big * 2.0 ** -22   # node, row, 1
+    lo_ok = planes[:, 0::2] <= rows[:, 0::2] - need[:, 0::2]
+    hi_ok = planes[:, 1::2] >= rows[:, 1::2] + need[:, 1::2]
+    assert np.all(lo_ok | ~real[:, None, :]) and np.all(hi_ok | ~real[:, None, :])
+    empty = ~real[:, None, :]
+    assert np.all((q[:, 0::2] == 255) | ~empty) and np.all((q[:, 1::2] == 0) | ~empty)
+    assert real[:, :2].all()
+    # the quantised boxes stay tight: a few quanta per side against the child's extent
+    ext = np.maximum(rows[:, 1::2] - rows[:, 0::2], 1e-6)
+    grow = ((planes[:, 1::2] - planes[:, 0::2]) - (rows[:, 1::2] - rows[:, 0::2])) / ext
+    assert np.median(grow[np.broadcast_to(real[:, None, :], grow.shape)]) < 0.25
+    assert np.all(np.isfinite(planes[np.broadcast_to(np.repeat(real[:, None, :], 6, axis=1), planes.shape)]))
+
+
+@pytest.mark.parametrize("kind,retest", [(1, False), (1, True), (0, True), (3, False), (3, True)])
 def test_precision_form_records_match_oracle(ctx, kind, retest):
     from paper_1806_00205_gb300 import rtmc
     mesh = I.grf_foam(16, 0.5)
@@ -100,7 +144,7 @@ def test_precision_form_records_match_oracle(ctx, kind, retest):
         assert g["retested"] == 0
 
 
-@pytest.mark.parametrize("kind", [0, 1, 2])
+@pytest.mark.parametrize("kind", [0, 1, 2, 3])
 def test_fp64_retest_brings_records_closer_to_oracle(ctx, kind):
     """The FP64 decisions replace FP32 ones only where FP32 cannot decide (a facet within
     1e-5 of an edge, a grazing hit): the re-test run never has more per-ray record
