@@ -68,12 +68,6 @@ rtmc_run_desc default_desc()
     return d;
 }
 
-double spectrum_cdf(double e, double phi)
-{
-    const double s = phi / (e + phi);
-    return 1.0 - 3.0 * s * s + 2.0 * s * s * s;
-}
-
 }  // namespace
 
 namespace rtmc {
