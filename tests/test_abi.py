@@ -45,6 +45,20 @@ def test_binding_loads_and_lists_exports(lib_path):
         assert hasattr(L, s)
 
 
+def test_binding_constants_match_the_header():
+    """The binding's node formats, error codes, fates and limits are the header's #define values."""
+    from paper_1806_00205_gb300 import rtmc
+    src = open(os.path.join(ROOT, "include", "rtmc.h")).read()
+    defs = {k: v for k, v in re.findall(r"#define\s+RTMC_(\w+)\s+\(?(-?\d+(?:\s*<<\s*\d+)?)\)?", src)}
+    val = {k: eval(v) for k, v in defs.items()}          # integer literals and one shift, nothing else
+    for name in ("BVH_FP32", "BVH_Q8", "BVH_W4", "BVH_Q4", "BVH_PLOC", "ESCAPED", "EMITTER", "ABSORBED_LOW",
+                 "ABSORBED_OTHER", "LOST", "NOALLOC_MAX_PRIMARIES"):
+        assert getattr(rtmc, name) == val[name], name
+    assert rtmc.OK == val["OK"]
+    for code, name in rtmc.ERRORS.items():
+        assert val["ERR_" + name] == code, name
+
+
 def test_record_hash_matches_documented_formula(lib_path):
     from paper_1806_00205_gb300 import rtmc
     from tests.parity import record_hashes
