@@ -70,10 +70,9 @@
  *     ray path holds); the fits shrink the energy each generation, so the
  *     cap is rarely reached.
  *
- * PARITY UNPINNED: orc_esee_fit (Eq. 7).  The paper prints no value of
- * E_SEE, so nothing outside this file fixes the formula's transcription; the
- * tests pin how it is used (a single daughter carries E_SEE exactly, a pair
- * splits it as Section 2.2 states) but not the formula itself.
+ * Eq. 6 and Eq. 7 are pinned by a table of their printed terms worked out
+ * one by one at sixteen (E, alpha) points (alpha != 0, sin E < 0, a negative
+ * E_SEE), and Eq. 6's maximum by the 1.49 that Section 3.2 quotes for flat W.
  */
 #include "rtmc_oracle.h"
 

@@ -29,7 +29,7 @@ import numpy as np
 
 __all__ = [
     "Box", "Mesh", "SeeTable", "grf_field", "marching_cubes_periodic",
-    "grf_foam", "flat_plane", "square_well", "see_table", "paper_delta",
+    "grf_foam", "flat_plane", "square_well", "see_table",
 ]
 
 
@@ -106,19 +106,6 @@ def see_table(n_e=64, n_theta=18, e_lo_ev=1.0, e_hi_ev=2000.0, theta_step_deg=5.
     d = lin_joy_delta(e[:, None], th[None, :], delta_max, e_max_ev)
     return SeeTable(np.ascontiguousarray(d.astype(np.float32)), float(e_lo_ev),
                     float(e_hi_ev), float(theta_step_deg))
-
-
-def paper_delta(e_ev, alpha):
-    """The paper's flat-tungsten yield fit gamma(E, alpha) (Eq. 6, "seey").
-
-    Used only as tabulated input data.  The paper does not state the unit of
-    alpha; it is passed through unchanged.
-    """
-    e = np.asarray(e_ev, dtype=np.float64)
-    a = np.asarray(alpha, dtype=np.float64)
-    return (3.05 + 1.7949e-5 * a * a + 6.15e-7 * e * e
-            - (371.317 - np.exp(0.04826 * a)) / (87.602 + e)
-            - 1.974e-3 * e - 0.1097 * np.cos(0.1201 + 2.469 * a))
 
 
 # ----------------------------------------------------------------------------

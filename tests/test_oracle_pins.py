@@ -335,14 +335,6 @@ def test_primary_ids_replay_the_same_trees():
     assert sub.tobytes() == want.tobytes()
 
 
-def test_paper_yield_fit_peak():
-    """Eq. 6 at normal incidence peaks near 1.49 (Section 3.2 quotes 1.49 for flat W)."""
-    e = np.linspace(50, 1000, 95001)
-    g = I.paper_delta(e, 0.0)
-    assert abs(g.max() - 1.49) < 0.005
-    assert 380 < e[np.argmax(g)] < 450
-
-
 # ------------------------------------------ random incidence and depth --
 
 def test_random_incidence_is_cosine_law():
@@ -436,7 +428,7 @@ PAPER = O.paper_emission()
 
 
 def test_paper_fit_peak_matches_printed_value():
-    """Section 3.1 prints a maximum flat-tungsten yield of about 1.49; Eq. 6 at
+    """Section 3.2 quotes a maximum flat-tungsten yield of about 1.49; Eq. 6 at
     normal incidence (alpha in degrees, reading R16) peaks there near 416 eV."""
     e = np.arange(100.0, 1500.0, 0.5)
     g = np.array([O.gamma_fit(x, 0.0) for x in e])
@@ -450,6 +442,35 @@ def test_stochastic_rounding_footnote_example():
     assert O.round_stochastic(1.2, 0.15) == (2, 0)
     assert O.round_stochastic(-0.3, 0.01) == (0, 0)
     assert O.round_stochastic(16.5, 0.9) == (15, 1)
+
+
+def _paper_fit_rows():
+    rows = []
+    with open(os.path.join(HERE, "golden", "paper_fits.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                w = line.split()
+                rows.append((w[0], [float(x) for x in w[1:]]))
+    return rows
+
+
+@pytest.mark.parametrize("which,cols", _paper_fit_rows())
+def test_paper_fits_match_term_by_term_table(which, cols):
+    """Eq. 6 and Eq. 7 (Section 2.2) at points where every term matters.
+
+    tests/golden/paper_fits.txt lists each printed term of the two equations
+    worked out on its own (alpha != 0, the alpha^7 term, sin(E) < 0, a negative
+    E_SEE), so a dropped term, a wrong sign or a mistyped coefficient in the
+    oracle's transcription changes the value by far more than the tolerance."""
+    e, a = cols[0], cols[1]
+    if which == "gamma":
+        terms, total = [cols[i - 1] for i in (3, 4, 5, 7, 8, 11)], cols[11]
+        got = O.gamma_fit(e, a)
+    else:
+        terms, total = [cols[i - 1] for i in (3, 4, 6, 8, 9)], cols[9]
+        got = O.esee_fit(e, a)
+    assert math.isclose(math.fsum(terms), total, rel_tol=0, abs_tol=1e-12 * max(1.0, abs(total)))
+    assert math.isclose(got, total, rel_tol=0, abs_tol=1e-11 * max(1.0, abs(total))), (which, e, a, got, total)
 
 
 @pytest.mark.parametrize("energy,theta", [(416.0, 0.0), (150.0, 40.0), (1200.0, 75.0)])
