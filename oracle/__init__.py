@@ -49,8 +49,9 @@ class OrcResult(C.Structure):
 
 RECORD_DTYPE = np.dtype([("prim", "<u8"), ("path", "<u4"), ("gen", "<i4"), ("fate", "<i4"),
                          ("tri", "<i4"), ("k", "<i4"), ("e_bin", "<i4"), ("a_bin", "<i4"),
-                         ("wraps", "<i4"), ("t", "<f8"), ("energy", "<f8")])
-assert RECORD_DTYPE.itemsize == 56
+                         ("wraps", "<i4"), ("t", "<f8"), ("energy", "<f8"), ("cos_in", "<f8"),
+                         ("flight", "<f8")])
+assert RECORD_DTYPE.itemsize == 72
 
 ESCAPED, EMITTER, ABSORBED_LOW, ABSORBED_OTHER, LOST = 0, 1, 2, 3, 4
 

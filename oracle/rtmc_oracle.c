@@ -252,14 +252,17 @@ void orc_closest_hit_mt(const float* tri, int64_t n_tri, const double o[3], cons
 
 /* Periodic cell walk (reading R4).  Returns ORC_EMITTER for "hit a facet",
    ORC_ESCAPED or ORC_LOST. */
-int orc_trace_ray(const float* tri, int64_t n_tri, const orc_box* box, const double o_in[3],
-                  const double d[3], int64_t origin_tri, int32_t max_wraps,
-                  int64_t* tri_id, double* t, double* u, double* v, int32_t* wraps,
-                  double o_last[3])
+/* The periodic walk; *flight gets the length of the whole path (every
+   segment, the last one included), used only to state error bounds. */
+static int walk_ray(const float* tri, int64_t n_tri, const orc_box* box, const double o_in[3],
+                    const double d[3], int64_t origin_tri, int32_t max_wraps,
+                    int64_t* tri_id, double* t, double* u, double* v, int32_t* wraps,
+                    double o_last[3], double* flight)
 {
     double o[3] = { o_in[0], o_in[1], o_in[2] };
     int64_t excl = origin_tri;
     int32_t nw = 0;
+    double run_len = 0.0;
     for (;;) {
         double th, uh, vh;
         int64_t j;
@@ -267,6 +270,7 @@ int orc_trace_ray(const float* tri, int64_t n_tri, const orc_box* box, const dou
         if (j >= 0) {
             *tri_id = j; *t = th; *u = uh; *v = vh; *wraps = nw;
             memcpy(o_last, o, sizeof o);
+            *flight = run_len + th;
             return ORC_EMITTER;
         }
         /* no facet in this cell: find the face the ray leaves through */
@@ -281,9 +285,11 @@ int orc_trace_ray(const float* tri, int64_t n_tri, const orc_box* box, const dou
         memcpy(o_last, o, sizeof o);
         if (tz < tx && tz < ty) {
             *t = tz;
+            *flight = run_len + tz;
             return d[2] > 0.0 ? ORC_ESCAPED : ORC_LOST;  /* top: emission; bottom: leak */
         }
-        if (++nw > max_wraps) { *t = fmin(tx, ty); *wraps = nw; return ORC_LOST; }
+        if (++nw > max_wraps) { *t = fmin(tx, ty); *wraps = nw; *flight = run_len + *t; return ORC_LOST; }
+        run_len += fmin(tx, ty);
         if (tx <= ty) {
             o[1] = o[1] + tx * d[1]; o[2] = o[2] + tx * d[2];
             o[0] = d[0] > 0.0 ? 0.0 : box->lx;      /* re-enter on the opposite face */
@@ -293,6 +299,15 @@ int orc_trace_ray(const float* tri, int64_t n_tri, const orc_box* box, const dou
         }
         excl = -1;
     }
+}
+
+int orc_trace_ray(const float* tri, int64_t n_tri, const orc_box* box, const double o_in[3],
+                  const double d[3], int64_t origin_tri, int32_t max_wraps,
+                  int64_t* tri_id, double* t, double* u, double* v, int32_t* wraps,
+                  double o_last[3])
+{
+    double flight;
+    return walk_ray(tri, n_tri, box, o_in, d, origin_tri, max_wraps, tri_id, t, u, v, wraps, o_last, &flight);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -474,12 +489,12 @@ static void run_primary(const float* tri, int64_t n_tri, const orc_box* box,
         rc.prim = prim; rc.path = ray.path; rc.gen = ray.gen; rc.tri = -1;
         rc.k = 0; rc.e_bin = -1; rc.a_bin = -1; rc.energy = ray.e;
 
-        int64_t j; double t, uh, vh, olast[3];
+        int64_t j; double t, uh, vh, olast[3], flight;
         int32_t nw;
-        int fate = orc_trace_ray(tri, n_tri, box, ray.o, ray.d, ray.origin_tri, run->max_wraps,
-                                 &j, &t, &uh, &vh, &nw, olast);
+        int fate = walk_ray(tri, n_tri, box, ray.o, ray.d, ray.origin_tri, run->max_wraps,
+                            &j, &t, &uh, &vh, &nw, olast, &flight);
         L->r.wraps += nw;
-        rc.wraps = nw; rc.t = t;
+        rc.wraps = nw; rc.t = t; rc.flight = flight;
 
         if (fate == ORC_ESCAPED && ray.gen > 0) {
             /* emission event: reached z_max moving up */
@@ -495,6 +510,7 @@ static void run_primary(const float* tri, int64_t n_tri, const orc_box* box,
             if (ab < 0) ab = 0;
             L->he[eb]++; L->ha[ab]++;
             rc.e_bin = eb; rc.a_bin = ab;
+            rc.cos_in = ray.d[2];
             es += ray.e; e2 += ray.e * ray.e;
         } else if (fate == ORC_ESCAPED || fate == ORC_LOST) {
             /* a primary that never meets the surface, a leak, or too many wraps */
@@ -502,6 +518,11 @@ static void run_primary(const float* tri, int64_t n_tri, const orc_box* box,
             L->r.lost++;
         } else {
             rc.tri = (int32_t)j;
+            {
+                double nf[3];
+                facet_normal(tri, j, nf);
+                rc.cos_in = -dot3(ray.d, nf);
+            }
             if (run->n_zbins > 0) {               /* reading R15: where the flight ends */
                 double v0[3], v1[3], v2[3];
                 vert(tri, j, 0, v0); vert(tri, j, 1, v1); vert(tri, j, 2, v2);

@@ -80,7 +80,9 @@ typedef struct {
     int32_t gen, fate, tri, k, e_bin, a_bin, wraps;
     double t;        /* length parameter of the final segment (hit or exit) */
     double energy;   /* ray energy, eV                                      */
-} orc_record;        /* 56 bytes */
+    double cos_in;   /* -d.n at a facet hit, d_z at an escape, 0 if lost    */
+    double flight;   /* path length over every segment (wraps included)     */
+} orc_record;        /* 72 bytes */
 
 int orc_run_rtmc(const float* tri, int64_t n_tri, const orc_box* box,
                  const orc_physics* phys, const orc_run* run, orc_result* out,

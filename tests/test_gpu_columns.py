@@ -86,7 +86,7 @@ def test_column_grid_only_at_normal_incidence(ctx):
 def test_column_grid_records_match_oracle(ctx):
     """Per-ray records of the tiny config through the column grid against the FP64 oracle."""
     import oracle as O
-    from tests.parity import compare_records
+    from tests.parity import check_moments, compare_records
     mesh = I.grf_foam(16, 0.5)
     mid = ctx.load_mesh(mesh.tri, mesh.box)
     ctx.build_bvh(mid)
@@ -95,8 +95,10 @@ def test_column_grid_records_match_oracle(ctx):
     ctx.unload_mesh(mid)
     assert g["column_rays"] == n
     o = O.run(mesh, TABLE, 300.0, 0.0, n, seed=1806, records=True)
-    st = compare_records(g["records"], o["records"])
+    st = compare_records(g["records"], o["records"], mesh=mesh)
     assert st["frac_same"] >= 0.9999, {k: v for k, v in st.items() if k != "mismatch"}
+    assert st["t_bound_violations"] == 0, (st["t_bound_ratio_max"], st["t_bound_worst"])
+    check_moments(g, o, st)
 
 
 @pytest.mark.parametrize("model", ["tertiaries", "paper_fit"])

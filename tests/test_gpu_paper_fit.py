@@ -8,7 +8,7 @@ import pytest
 
 import oracle as O
 from paper_1806_00205_gb300 import inputs as I
-from tests.parity import compare_records
+from tests.parity import check_moments, compare_records, paper_fit_energy_gain
 
 pytestmark = pytest.mark.gpu
 TABLE = I.see_table()
@@ -41,8 +41,10 @@ def test_paper_fit_records_match_oracle(pctx, energy, theta):
     n = 20_000
     g = ctx.run_records(mid, energy, theta, n, seed=23, desc=rtmc.run_desc(n_zbins=32))
     o = O.run(mesh, TABLE, energy, theta, n, seed=23, emission=O.paper_emission(), records=True, n_zbins=32)
-    st = compare_records(g["records"], o["records"])
+    st = compare_records(g["records"], o["records"], mesh=mesh, energy_gain=paper_fit_energy_gain)
     assert st["frac_same"] >= 0.9999, {k: v for k, v in st.items() if k != "mismatch"}
+    assert st["t_bound_violations"] == 0, (st["t_bound_ratio_max"], st["t_bound_worst"])
+    check_moments(g, o, st)
     assert g["regenerated"] > 0 and g["rays"] == n + g["emitted"]
     assert abs(int(g["rays"]) - int(o["rays"])) <= max(3, 1e-4 * o["rays"])
     assert np.abs(g["hist_z"].astype(np.int64) - o["hist_z"]).sum() <= max(6, int(3e-4 * o["rays"]))

@@ -6,7 +6,7 @@ import pytest
 
 import oracle as O
 from paper_1806_00205_gb300 import inputs as I
-from tests.parity import compare_records, primary_hashes
+from tests.parity import check_moments, compare_records, primary_hashes
 
 pytestmark = pytest.mark.gpu
 TABLE = I.see_table()
@@ -135,9 +135,11 @@ def test_precision_form_records_match_oracle(ctx, kind, retest):
     g = ctx.run_records(mid, 300.0, 0.0, n, seed=1806, desc=rtmc.run_desc(fp64_retest=retest))
     ctx.unload_mesh(mid)
     o = O.run(mesh, TABLE, 300.0, 0.0, n, seed=1806, records=True)
-    st = compare_records(g["records"], o["records"])
+    st = compare_records(g["records"], o["records"], mesh=mesh)
     assert st["frac_same"] >= 0.9999, {k: v for k, v in st.items() if k != "mismatch"}
     assert st["t_rel_p999"] <= 1e-5
+    assert st["t_bound_violations"] == 0, (st["t_bound_ratio_max"], st["t_bound_worst"])
+    check_moments(g, o, st)
     if retest:
         assert 0 < g["retested"] <= 1e-3 * g["rays"]
     else:

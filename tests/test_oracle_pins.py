@@ -145,6 +145,27 @@ def test_periodic_walk_counts_wraps():
     assert r["fate"] == O.LOST and r["wraps"] == 9
 
 
+def test_record_incidence_cosine_and_flight_length():
+    """The records' error-bound fields on a flat plane in closed form: a primary
+    at polar angle theta meets the plane with -d.n = cos(theta) after a flight of
+    z_top / cos(theta), wraps included; an escaping daughter records d_z and a
+    flight of z_top / d_z from its start on the plane."""
+    fp = I.flat_plane(160.0, height=400.0)      # tall slab: steep primaries wrap several times
+    for theta in (0.0, 37.0, 75.0):
+        r = O.run(fp, TABLE, E47, theta, 3000, seed=31, records=True)
+        rec = r["records"]
+        prim, dau = rec[rec["gen"] == 0], rec[rec["gen"] == 1]
+        c = math.cos(math.radians(theta))
+        assert np.allclose(prim["cos_in"], c, rtol=0, atol=1e-12)
+        assert np.allclose(prim["flight"], 400.0 / c, rtol=1e-12, atol=0)
+        if theta == 75.0:
+            assert prim["wraps"].max() >= 5
+        esc = dau[dau["fate"] == O.ESCAPED]
+        assert esc.size > 1000
+        assert np.allclose(esc["flight"] * esc["cos_in"], 400.0, rtol=1e-9, atol=0)
+        assert np.all((esc["cos_in"] > 0) & (esc["cos_in"] <= 1))
+
+
 # ---------------------------------------------------------------- sampling --
 
 def test_delta_lookup_grid_nodes_and_bilinearity():
