@@ -130,6 +130,20 @@ typedef struct {
     int32_t id_order;              /* 1: queue primaries in id order; 0: order them by a
                                       Morton-ordered 128 x 128 grid of entry points
                                       (coherent traversal; results do not depend on order) */
+    int32_t max_visits;            /* failure-detection bound: inner-node visits one cell
+                                      traversal may make before its ray is abandoned and
+                                      the call fails with RTMC_ERR_DEVICE_CHECK.  The
+                                      library always applies the tree's own bound (its
+                                      inner-node count + 1: a correct traversal visits each
+                                      inner node at most once); a value > 0 lowers it */
+    double queue_factor;           /* daughter-queue capacity of a chunk's first attempt,
+                                      in rays per primary (0: twice the largest expected
+                                      yield of the loaded emission, at least 2, at most
+                                      k_max); if any chunk's daughters overflow their queue,
+                                      the item (rtmc_run) or the batch (rtmc_run_batch) is
+                                      run again from the start with twice the capacity, up
+                                      to six times, then the call fails with
+                                      RTMC_ERR_CAPACITY */
 } rtmc_run_desc;
 
 typedef struct {
@@ -147,6 +161,8 @@ typedef struct {
     double ms_column;                          /* with profile: the column-grid launches */
     int64_t column_rays;                       /* rays traced through the column grid (not
                                                   counted in node_visits / tri_tests) */
+    int64_t queue_retries;                     /* times the item (or batch) was run again
+                                                  after a daughter-queue overflow */
 } rtmc_result;
 
 /* One traced ray: the integer event sequence used for parity checks. */
@@ -234,7 +250,12 @@ int rtmc_run(rtmc_ctx* ctx, int32_t mesh_id, const double* energies_ev, int32_t 
    is captured once into a CUDA graph and replayed on later calls with the same
    batch shape (desc->no_graph = 1 launches eagerly instead).  Item k uses the
    same random streams as rtmc_run with item_base = k, so its tallies are
-   identical to that run's.  Requires max_generation == 1.  Writes
+   identical to that run's.  Every generation the loaded emission allows
+   (max_generation <= 6) is traced, one traversal and one shade launch per
+   generation and chunk; a generation with no rays ends its launches at once.
+   Queues are sized as in rtmc_run (desc->queue_factor); if a chunk overflows,
+   the whole batch is recorded again with twice the capacity and run again
+   (up to six times; queue_retries counts the repeats).  Writes
    out[n_items]; hist_e / hist_a / desc->hist_z as in rtmc_run, with
    n_ebins + n_abins + n_zbins <= 512.  gpu_ms of every result is
    the device time of the whole batch, and node_visits / tri_tests / retested
@@ -316,12 +337,18 @@ int rtmc_philox(rtmc_ctx* ctx, const uint32_t* ctr, int64_t n, uint64_t key, uin
        desc->primary_offset and call again for more primaries);
      the loaded emission parameters must have max_generation == 1;
      n_ebins + n_abins + n_zbins <= 1024.
-   desc->profile is ignored; desc->prim_hash (device, n_primaries entries),
-   desc->count_visits and desc->fp64_retest work as in rtmc_run (the FP64
-   re-test runs inside the traversal kernel and needs no scratch).
-   The first call on a device looks up the array's device address
-   (cudaGetSymbolAddress) with that device current; make that first call
-   before any stream capture.  Every call on a device uses the same array and
+   desc is checked as rtmc_run checks it.  desc->profile, desc->chunk and
+   desc->queue_factor are ignored (the static queues hold k_max daughters per
+   primary); desc->prim_hash (device, n_primaries entries), desc->count_visits,
+   desc->fp64_retest (it runs inside the traversal kernel and needs no
+   scratch) and the traversal controls (traversal, stack_depth,
+   fetch_threshold, block_threads, blocks_per_sm, max_visits) work as in
+   rtmc_run.
+   The first call in a context looks up the array's device address
+   (cudaGetSymbolAddress) with the context's device current and keeps it in
+   the context; make that first call before any stream capture.  A device
+   reset ends the context's use, as for every other entry point: destroy the
+   context and create a new one.  Every call on a device uses the same array and
    clears the counters it needs before it starts; calls whose GPU work
    overlaps (other host threads, other contexts or streams on the same
    device) race on the array and must be serialised by the caller.

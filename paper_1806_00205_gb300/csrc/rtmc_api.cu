@@ -129,6 +129,36 @@ Emission make_emission(const rtmc_emission& em)
     return e;
 }
 
+// Eq. 6 (Section 2.2) on the host, alpha in degrees: only to size queues.
+static double paper_yield(double e, double a)
+{
+    return 3.05 + 1.7949e-5 * a * a + 6.15e-7 * e * e - (371.317 - std::exp(0.04826 * a)) / (87.602 + e) -
+           1.974e-3 * e - 0.1097 * std::cos(0.1201 + 2.469 * a);
+}
+
+QueueFactors queue_factors(const rtmc_ctx* ctx, const rtmc_run_desc& d, double e_max_ev)
+{
+    const rtmc_emission& em = ctx->emission;
+    double y = ctx->yield_max;
+    if (em.model == RTMC_EMISSION_PAPER_FIT) {        // daughters never exceed the primary energy by much
+        y = 0.0;
+        const double top = std::max(e_max_ev, 10.0) * 1.05;
+        for (int i = 0; i <= 256; ++i)
+            for (int a = 0; a <= 90; ++a) y = std::max(y, paper_yield(top * i / 256.0, (double)a));
+    }
+    y = std::max(y, 1.0);
+    const double kmax = std::max(1, em.k_max);
+    QueueFactors q;
+    double yg = 1.0;
+    for (int g = 1; g <= em.max_generation; ++g) {
+        yg *= y;
+        const double need = g == 1 ? std::min(kmax, std::max(2.0, 2.0 * y)) : std::min(16.0, 2.0 * yg);
+        q.f[g & 1] = std::max(q.f[g & 1], need);
+    }
+    if (d.queue_factor > 0.0) q.f[1] = d.queue_factor;
+    return q;
+}
+
 void fill_result(rtmc_result& r, const Tally& t, int64_t n_prim)
 {
     std::memset(&r, 0, sizeof r);
@@ -192,25 +222,20 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
     const bool columns = m.col_ok && d.traversal == 0 && theta_deg == 0.0 && !d.random_polar;
     const Emission e = make_emission(em);
 
-    // Queue capacities: generation g holds at most k_max^g rays per primary.
-    // Buffer 0 holds even generations, buffer 1 odd ones; deep trees use a
-    // bounded multiplier and grow it if the device reports an overflow.
-    const int kmax = std::max(1, em.k_max);
+    // Queue capacities: buffer 0 holds even generations, buffer 1 odd ones,
+    // sized from the expected yield (queue_factors); a chunk whose daughters
+    // overflow is run again with doubled capacities.
     int64_t chunk = d.chunk > 0 ? d.chunk : ((int64_t)1 << 22);
     if (em.max_generation >= 2 && d.chunk <= 0) chunk = (int64_t)1 << 20;
     chunk = std::min<int64_t>(chunk, std::max<int64_t>(n_prim, 1));
-    int64_t mult[2] = {1, kmax};
-    if (em.max_generation >= 2) mult[0] = std::min<int64_t>((int64_t)kmax * kmax, 64);
-    if (em.max_generation >= 3) mult[1] = std::min<int64_t>((int64_t)kmax * kmax * kmax, 64);
-    Tuning tune;
-    if (d.block_threads > 0) tune.block_threads = d.block_threads;
-    tune.blocks_per_sm = d.blocks_per_sm;
-    tune.traversal = d.traversal;
-    if (d.stack_depth > 0) tune.stack_depth = d.stack_depth;
-    tune.fetch_threshold = d.fetch_threshold;
+    const QueueFactors qf = queue_factors(ctx, d, energy);
+    double mult[2] = {qf.f[0], qf.f[1]};
+    const Tuning tune = tuning_from(d);
+    int64_t retries = 0;
 
     for (int attempt = 0;; ++attempt) {
-        const int64_t cap0 = chunk * mult[0], cap1 = chunk * mult[1];
+        const int64_t cap0 = (int64_t)std::ceil((double)chunk * mult[0]) + 256;
+        const int64_t cap1 = (int64_t)std::ceil((double)chunk * mult[1]) + 256;
         if (cap0 > 0xFFFFFFF0ll || cap1 > 0xFFFFFFF0ll)
             return ctx->fail(RTMC_ERR_CAPACITY, "run: queue capacity exceeds 2^32 rays; lower chunk");
         const int64_t capmax = std::max(cap0, cap1);
@@ -324,9 +349,9 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
         if (ce != cudaSuccess) return cuda_fail(ctx, ce, "run");
         const unsigned long long status_all = t.status;
         if (status_all & ST_QUEUE_OVERFLOW) {
-            if (attempt >= 6) return ctx->fail(RTMC_ERR_CAPACITY, "run: daughter queue overflow");
+            if (attempt >= 6) return ctx->fail(RTMC_ERR_CAPACITY, "run: daughter queue overflow after six retries");
             mult[0] *= 2; mult[1] *= 2;
-            chunk = std::max<int64_t>(chunk / 2, 1024);
+            ++retries;
             // the per-primary counts of the aborted chunk must start from zero again
             cudaMemsetAsync(ctx->kcount.ptr, 0, ctx->kcount.bytes, s);
             continue;
@@ -338,6 +363,7 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
 
         rtmc_result& r = *o.res;
         rtmc::fill_result(r, t, n_prim);
+        r.queue_retries = retries;
         r.gpu_ms = ms;
         r.launches = launches;
         r.traverse_launches = trav_launches;
@@ -391,6 +417,9 @@ int rtmc::check_run_desc(rtmc_ctx* ctx, const rtmc_run_desc& d)
     if (d.chunk < 0 || d.chunk > ((int64_t)1 << 28)) return ctx->fail(RTMC_ERR_INVALID_ARG, "run: chunk out of range");
     if (d.max_wraps < 0 || d.max_wraps > (1 << 20)) return ctx->fail(RTMC_ERR_INVALID_ARG, "run: max_wraps out of range");
     if (d.blocks_per_sm < 0 || d.blocks_per_sm > 64) return ctx->fail(RTMC_ERR_INVALID_ARG, "run: blocks_per_sm out of range");
+    if (d.max_visits < 0) return ctx->fail(RTMC_ERR_INVALID_ARG, "run: max_visits must be >= 0");
+    if (!(d.queue_factor >= 0.0 && d.queue_factor <= 64.0))
+        return ctx->fail(RTMC_ERR_INVALID_ARG, "run: queue_factor must be in [0, 64]");
     return RTMC_OK;
 }
 
@@ -513,6 +542,14 @@ int rtmc_load_see_tables(rtmc_ctx* ctx, const float* delta, const rtmc_grid* gri
     if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->delta, delta, bytes, cudaMemcpyDefault, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "load_see_tables");
+    {   // the largest tabulated yield sizes the daughter queues
+        std::vector<float> h((size_t)grid->n_e * grid->n_theta);
+        e = cudaMemcpy(h.data(), ctx->delta, bytes, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "load_see_tables");
+        double y = 0.0;
+        for (float v : h) if (std::isfinite(v)) y = std::max(y, (double)v);
+        ctx->yield_max = y;
+    }
     ctx->grid = *grid;
     ctx->emission = *em;
     ctx->table_loaded = true;

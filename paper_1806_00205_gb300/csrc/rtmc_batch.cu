@@ -151,8 +151,6 @@ extern "C" int rtmc_run_batch(rtmc_ctx* ctx, const rtmc_batch* batch, const rtmc
     int rc = check_run_desc(ctx, d);
     if (rc) return rc;
     if (!ctx->table_loaded) return ctx->fail(RTMC_ERR_NOT_LOADED, "run_batch: load_see_tables first");
-    if (ctx->emission.max_generation != 1)
-        return ctx->fail(RTMC_ERR_INVALID_ARG, "run_batch: the batched form needs max_generation == 1");
     if (d.prim_hash) return ctx->fail(RTMC_ERR_INVALID_ARG, "run_batch: per-primary hashes are not supported");
     if (d.n_ebins + d.n_abins + d.n_zbins > 512)
         return ctx->fail(RTMC_ERR_INVALID_ARG, "run_batch: n_ebins + n_abins + n_zbins must be <= 512");
@@ -191,12 +189,27 @@ extern "C" int rtmc_run_batch(rtmc_ctx* ctx, const rtmc_batch* batch, const rtmc
                 x.pad = 0;
             }
 
-    // scratch: queues for one chunk (worst case k_max daughters per primary)
-    const int kmax = std::max(1, ctx->emission.k_max);
+    // scratch: queues for one chunk, sized from the expected yield as in rtmc_run;
+    // an overflow records the batch again with doubled capacities
     int64_t chunk = d.chunk > 0 ? d.chunk : ((int64_t)1 << 23);
     chunk = std::min<int64_t>(chunk, std::max<int64_t>(per_mesh * batch->n_primaries, 1));
-    const int64_t cap0 = chunk, cap1 = chunk * kmax;
-    if (cap1 > 0xFFFFFFF0ll) return ctx->fail(RTMC_ERR_CAPACITY, "run_batch: chunk too large");
+    double e_max = 0.0;
+    for (int i = 0; i < batch->n_e; ++i) e_max = std::max(e_max, batch->energies_ev[i]);
+    const QueueFactors qf = queue_factors(ctx, d, e_max);
+    double mult[2] = {qf.f[0], qf.f[1]};
+    const Tuning tune = tuning_from(d);
+    int64_t retries = 0;
+    std::vector<Tally> t((size_t)n_items + 1);
+    std::vector<unsigned long long> h((size_t)n_items * nbins);
+    float ms = 0.f;
+    double kms[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    int64_t launches = 0, trav_launches = 0;
+    for (int attempt = 0;; ++attempt) {
+    const int64_t cap0 = (int64_t)std::ceil((double)chunk * mult[0]) + 256;
+    const int64_t cap1 = (int64_t)std::ceil((double)chunk * mult[1]) + 256;
+    if (cap0 > 0xFFFFFFF0ll || cap1 > 0xFFFFFFF0ll)
+        return ctx->fail(RTMC_ERR_CAPACITY, "run_batch: queue capacity exceeds 2^32 rays; lower chunk");
+    const int64_t capmax = std::max(cap0, cap1);
     cudaError_t ce = cudaSuccess;
     const void* before[14] = {ctx->q_oe[0].ptr, ctx->q_oe[1].ptr, ctx->q_dt[0].ptr, ctx->q_dt[1].ptr,
                               ctx->q_id[0].ptr, ctx->q_id[1].ptr, ctx->hits.ptr, ctx->kcount.ptr,
@@ -208,13 +221,13 @@ extern "C" int rtmc_run_batch(rtmc_ctx* ctx, const rtmc_batch* batch, const rtmc
         if (ce == cudaSuccess) ce = scratch_reserve(ctx->q_dt[bb], (size_t)c * 16);
         if (ce == cudaSuccess) ce = scratch_reserve(ctx->q_id[bb], (size_t)c * 16);
     }
-    if (ce == cudaSuccess) ce = scratch_reserve(ctx->hits, (size_t)cap1 * 16);
+    if (ce == cudaSuccess) ce = scratch_reserve(ctx->hits, (size_t)capmax * 16);
     const bool kc_new = ctx->kcount.bytes < (size_t)chunk * 4;
     if (ce == cudaSuccess) ce = scratch_reserve(ctx->kcount, (size_t)chunk * 4);
-    if (ce == cudaSuccess && kc_new) ce = cudaMemsetAsync(ctx->kcount.ptr, 0, ctx->kcount.bytes, s);
+    if (ce == cudaSuccess && (kc_new || attempt > 0)) ce = cudaMemsetAsync(ctx->kcount.ptr, 0, ctx->kcount.bytes, s);
     if (ce == cudaSuccess) ce = scratch_reserve(ctx->ctl, sizeof(Control));
     if (ce == cudaSuccess) ce = scratch_reserve(ctx->tally, (size_t)(n_items + 1) * sizeof(Tally));
-    if (ce == cudaSuccess) ce = scratch_reserve(ctx->wraps, (size_t)cap1 * 4);
+    if (ce == cudaSuccess) ce = scratch_reserve(ctx->wraps, (size_t)capmax * 4);
     if (ce == cudaSuccess) ce = scratch_reserve(ctx->hist, (size_t)n_items * nbins * 8);
     if (ce == cudaSuccess) ce = scratch_reserve(ctx->items, (size_t)n_items * sizeof(ItemDev));
     if (ce == cudaSuccess && !d.id_order)
@@ -245,12 +258,6 @@ extern "C" int rtmc_run_batch(rtmc_ctx* ctx, const rtmc_batch* batch, const rtmc
     q.prim_hash = nullptr;
     q.records = nullptr;
     q.rec_cap = 0;
-    Tuning tune;
-    if (d.block_threads > 0) tune.block_threads = d.block_threads;
-    tune.blocks_per_sm = d.blocks_per_sm;
-    tune.traversal = d.traversal;
-    if (d.stack_depth > 0) tune.stack_depth = d.stack_depth;
-    tune.fetch_threshold = d.fetch_threshold;
 
     ce = cudaMemcpyAsync(ctx->items.ptr, items.data(), items.size() * sizeof(ItemDev), cudaMemcpyHostToDevice, s);
     if (ce != cudaSuccess) return ctx->fail(RTMC_ERR_CUDA, std::string("run_batch: ") + cudaGetErrorString(ce));
@@ -259,12 +266,13 @@ extern "C" int rtmc_run_batch(rtmc_ctx* ctx, const rtmc_batch* batch, const rtmc
     std::string key;
     {
         char buf[512];
-        std::snprintf(buf, sizeof buf, "%d|%d|%d|%lld|%llu|%lld|%d|%d|%d|%d|%d|%d|%d|%d|%u|%.17g|%llu|%.17g|%.17g|%.17g|%.17g|z%d|rp%d",
+        std::snprintf(buf, sizeof buf, "%d|%d|%d|%lld|%llu|%lld|%d|%d|%d|%d|%d|%d|%d|%d|%u|%.17g|%llu|%.17g|%.17g|%.17g|%.17g|z%d|rp%d|c%lld:%lld|mv%d|g%d",
                       batch->n_meshes, batch->n_e, batch->n_theta, (long long)batch->n_primaries,
                       (unsigned long long)batch->seed, (long long)chunk, d.n_ebins, d.n_abins, d.random_azimuth,
                       d.max_wraps, d.block_threads, d.blocks_per_sm, d.traversal * 10000 + d.stack_depth * 100 + d.fetch_threshold, d.fp64_retest, d.item_base,
                       d.hist_e_max_ev, (unsigned long long)d.primary_offset, d.src_x0, d.src_x1, d.src_y0, d.src_y1,
-                      d.n_zbins, d.random_polar);
+                      d.n_zbins, d.random_polar, (long long)cap0, (long long)cap1, d.max_visits,
+                      ctx->emission.max_generation);
         key = buf;
         for (int i = 0; i < batch->n_meshes; ++i) {      // every mesh array a recorded launch reads
             const DeviceMesh& m = ctx->meshes[batch->mesh_ids[i]];
@@ -290,7 +298,7 @@ extern "C" int rtmc_run_batch(rtmc_ctx* ctx, const rtmc_batch* batch, const rtmc
     cudaEventCreate(&ev1);
     KernelTimer kt;
     kt.on = d.no_graph && d.profile;
-    int64_t launches = 0;
+    launches = 0;
     cudaEventRecord(ev0, s);
     if (d.no_graph) {
         ce = record_batch(ctx, *batch, d, q, (ItemDev*)ctx->items.ptr, (Tally*)ctx->tally.ptr,
@@ -317,24 +325,29 @@ extern "C" int rtmc_run_batch(rtmc_ctx* ctx, const rtmc_batch* batch, const rtmc
         launches = ctx->batch_launches;
     }
     cudaEventRecord(ev1, s);
-    std::vector<Tally> t((size_t)n_items + 1);
-    std::vector<unsigned long long> h((size_t)n_items * nbins);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(t.data(), ctx->tally.ptr, t.size() * sizeof(Tally), cudaMemcpyDeviceToHost, s);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(h.data(), ctx->hist.ptr, h.size() * 8, cudaMemcpyDeviceToHost, s);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
-    float ms = 0.f;
     if (ce == cudaSuccess) cudaEventElapsedTime(&ms, ev0, ev1);
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);
-    double kms[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    int64_t trav_launches = 0;
+    trav_launches = 0;
+    for (double& x : kms) x = 0.0;
     kt.collect(kms, trav_launches);
     if (ce != cudaSuccess) return ctx->fail(RTMC_ERR_CUDA, std::string("run_batch: ") + cudaGetErrorString(ce));
     unsigned long long status = 0;
     for (const Tally& x : t) status |= x.status;
-    if (status & ST_QUEUE_OVERFLOW) return ctx->fail(RTMC_ERR_CAPACITY, "run_batch: daughter queue overflow");
+    if (status & ST_QUEUE_OVERFLOW) {
+        if (attempt >= 6)
+            return ctx->fail(RTMC_ERR_CAPACITY, "run_batch: daughter queue overflow after six retries");
+        mult[0] *= 2; mult[1] *= 2;
+        ++retries;
+        continue;                        // new capacities change the key: the batch is recorded again
+    }
     if (status & (ST_STACK_OVERFLOW | ST_LOOP_LIMIT | ST_COLUMN))
         return ctx->fail(RTMC_ERR_DEVICE_CHECK, "run_batch: traversal stack overflow or iteration bound");
+    break;
+    }
     const Tally& all = t[(size_t)n_items];
     for (int64_t k = 0; k < n_items; ++k) {
         fill_result(out[k], t[(size_t)k], batch->n_primaries);
@@ -344,6 +357,7 @@ extern "C" int rtmc_run_batch(rtmc_ctx* ctx, const rtmc_batch* batch, const rtmc
         out[k].retested = (int64_t)all.retested;
         out[k].column_rays = (int64_t)all.col_rays;
         out[k].launches = launches;
+        out[k].queue_retries = retries;
         out[k].traverse_launches = trav_launches;
         out[k].ms_generate = kms[0];
         out[k].ms_traverse = kms[1];

@@ -56,7 +56,35 @@ struct Tuning {
     int traversal = 0;             // 0/2: while-while with ray refill, 1: one ray per lane per tile
     int stack_depth = 16;          // shared-memory stack entries per ray (8, 16, 32)
     int fetch_threshold = 0;       // refill when fewer lanes are active (0: default 20)
+    int max_visits = 0;            // lower bound on inner-node visits per cell traversal (0: the tree's own)
 };
+
+// Tuning of a run from its descriptor (the controls rtmc_run honours).
+inline Tuning tuning_from(const rtmc_run_desc& d)
+{
+    Tuning t;
+    if (d.block_threads > 0) t.block_threads = d.block_threads;
+    t.blocks_per_sm = d.blocks_per_sm;
+    t.traversal = d.traversal;
+    if (d.stack_depth > 0) t.stack_depth = d.stack_depth;
+    t.fetch_threshold = d.fetch_threshold;
+    t.max_visits = d.max_visits;
+    return t;
+}
+
+// Daughter-queue capacities per primary of a chunk, for the buffer of even
+// generations (index 0, generation 0 included) and of odd ones (index 1).
+// First attempt: from the largest expected yield y of the loaded emission at
+// energies up to e_max_ev, a margin of two over the expectation per generation
+// (generation g of a tree holds at most about y^g rays per primary, and for
+// chunks of thousands of primaries the count stays far below twice that),
+// capped at k_max for generation 1 and 16 beyond; desc.queue_factor > 0
+// replaces the odd buffer's factor (test hook).  A chunk that still overflows sets ST_QUEUE_OVERFLOW and
+// is run again with both factors doubled.
+struct QueueFactors {
+    double f[2] = {1.0, 1.0};
+};
+QueueFactors queue_factors(const rtmc_ctx* ctx, const rtmc_run_desc& d, double e_max_ev);
 
 }  // namespace rtmc
 
@@ -77,6 +105,8 @@ struct rtmc_ctx {
     cudaGraphExec_t batch_graph = nullptr;    // captured batch launch sequence
     std::string batch_key;                    // what the captured graph was built for
     int64_t batch_launches = 0;               // kernel launches in the captured graph
+    void* noalloc_scratch = nullptr;          // device address of rtmc_run_noalloc's static array
+    double yield_max = 1.0;                   // largest expected daughter count per emission (loaded emission)
     std::string err;
     int fail(int code, const std::string& msg) { err = msg; return code; }
 };

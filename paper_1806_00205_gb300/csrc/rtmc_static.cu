@@ -13,7 +13,6 @@
 
 #include <cmath>
 #include <cstring>
-#include <mutex>
 
 #include "rtmc_internal.h"
 
@@ -37,22 +36,19 @@ constexpr size_t kBytes = kHist + al(8 * kMaxBins);
 // The scratch: one copy per device that loads the library, held until exit.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_dev_ptr[kMaxDevices] = {};
-
-// Device address of the static array on the current device (looked up once).
-cudaError_t scratch_address(int device, void** out)
+// Device address of the static array, looked up with the context's device
+// current on the context's first call and kept in the context: a device reset
+// ends the context's other device state too, so the cache never outlives the
+// module load it came from while the context is usable.
+cudaError_t scratch_address(rtmc_ctx* ctx, void** out)
 {
-    if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_dev_ptr[device]) {
+    if (!ctx->noalloc_scratch) {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
-        g_dev_ptr[device] = p;
+        ctx->noalloc_scratch = p;
     }
-    *out = g_dev_ptr[device];
+    *out = ctx->noalloc_scratch;
     return cudaSuccess;
 }
 
@@ -107,21 +103,14 @@ extern "C" int rtmc_run_noalloc(rtmc_ctx* ctx, int32_t mesh_id, double energy_ev
         d.n_abins = 18;
         d.hist_e_max_ev = 50.0;
     }
-    if (d.n_ebins <= 0 || d.n_abins <= 0 || d.n_zbins < 0 || d.n_ebins + d.n_abins + d.n_zbins > kMaxBins ||
-        !(d.hist_e_max_ev > 0.0) || (d.n_zbins > 0 && !d.hist_z))
-        return ctx->fail(RTMC_ERR_INVALID_ARG,
-                         "run_noalloc: histogram bins must satisfy n_ebins + n_abins + n_zbins <= 1024 "
-                         "(hist_z needed when n_zbins > 0)");
-    if (d.max_wraps < 0 || d.max_wraps > (1 << 20))
-        return ctx->fail(RTMC_ERR_INVALID_ARG, "run_noalloc: max_wraps out of range");
-    if (d.block_threads != 0 && (d.block_threads % 32 != 0 || d.block_threads < 32 || d.block_threads > 128))
-        return ctx->fail(RTMC_ERR_INVALID_ARG, "run_noalloc: block_threads must be a multiple of 32 in [32, 128]");
-    if (d.blocks_per_sm < 0 || d.blocks_per_sm > 64)
-        return ctx->fail(RTMC_ERR_INVALID_ARG, "run_noalloc: blocks_per_sm out of range");
+    const int vrc = check_run_desc(ctx, d);     // the descriptor contract of rtmc_run
+    if (vrc) return vrc;
+    if (d.n_ebins + d.n_abins + d.n_zbins > kMaxBins)
+        return ctx->fail(RTMC_ERR_INVALID_ARG, "run_noalloc: histogram bins must satisfy n_ebins + n_abins + n_zbins <= 1024");
 
     CurrentDevice guard(ctx->device);
     void* base_v = nullptr;
-    cudaError_t ce = scratch_address(ctx->device, &base_v);
+    cudaError_t ce = scratch_address(ctx, &base_v);
     if (ce != cudaSuccess)
         return ctx->fail(RTMC_ERR_CUDA, std::string("run_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(ce));
     char* base = static_cast<char*>(base_v);
@@ -196,9 +185,7 @@ extern "C" int rtmc_run_noalloc(rtmc_ctx* ctx, int32_t mesh_id, double energy_ev
     q.records = nullptr;
     q.rec_cap = 0;
 
-    Tuning tune;
-    if (d.block_threads > 0) tune.block_threads = d.block_threads;
-    tune.blocks_per_sm = d.blocks_per_sm;
+    const Tuning tune = tuning_from(d);
 
     // The array keeps the previous call's contents: clear everything that must start at zero.
     ce = cudaMemsetAsync(base + kCtl, 0, sizeof(Control), s);

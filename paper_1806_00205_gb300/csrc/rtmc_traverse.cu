@@ -303,7 +303,7 @@ __device__ __forceinline__ void test_leaf(const float4* __restrict__ tris, const
 template <int FMT, bool COUNT = false, bool TRI64 = false, int SMEM = kSmemStack>
 __device__ __forceinline__ int bvh_closest(const void* __restrict__ nodes, const float4* __restrict__ tris,
                                            const RaySetup& r, const RaySetup64& r64, int skip, StackRef st,
-                                           float& t_best, float& bu, float& bv, unsigned& status,
+                                           float& t_best, float& bu, float& bv, unsigned& status, int max_iter,
                                            Counts* cnt = nullptr)
 {
     int2 lstack[kStackMax - SMEM];
@@ -329,7 +329,7 @@ __device__ __forceinline__ int bvh_closest(const void* __restrict__ nodes, const
         return false;
     };
     for (int visits = 0;; ++visits) {
-        if (visits >= kMaxVisits) { status |= ST_LOOP_LIMIT; break; }
+        if (visits >= max_iter) { status |= ST_LOOP_LIMIT; break; }
         if constexpr (FMT == FMT_W4 || FMT == FMT_Q4) {
             if (node < 0) {                                  // a leaf: test it now
                 test_leaf<COUNT, TRI64>(tris, r, r64, node, skip, t_best, t_best64, best, best_orig, bu, bv, cnt);
@@ -390,6 +390,7 @@ struct Cell {
     float lx, ly, z_min, z_top;
     int max_wraps;
     float eps;      // 2^-20 M, M the largest cell coordinate: bound on FP32 face-distance errors
+    int max_visits; // inner-node visits of one cell traversal before the ray is abandoned (ST_LOOP_LIMIT)
 };
 
 // Trace one ray segment by segment through the periodic cell (Section 2.2,
@@ -410,7 +411,9 @@ __device__ __forceinline__ float4 trace_ray(const void* __restrict__ nodes, cons
         RaySetup64 r64;
         if (TRI64) r64 = setup_ray64(o, d);
         float t, u, v;
-        const int j = bvh_closest<FMT, COUNT, TRI64, SMEM>(nodes, tris, rs, r64, skip, st, t, u, v, status, cnt);
+        // loop passes of one cell: inner-node visits plus leaf tests (at most 4 per 4-wide node)
+        const int j = bvh_closest<FMT, COUNT, TRI64, SMEM>(nodes, tris, rs, r64, skip, st, t, u, v, status,
+                                                           5 * c.max_visits, cnt);
         if (j >= 0) return make_float4(t, u, v, __int_as_float(j));
         double tx = INFINITY, ty = INFINITY, tz = INFINITY;
         if (d.x > 0.f) tx = ((double)c.lx - ox) / d.x; else if (d.x < 0.f) tx = (0.0 - ox) / d.x;
@@ -643,7 +646,7 @@ k_traverse_ww(const void* __restrict__ nodes, const float4* __restrict__ tris, c
         bool cell_done = false;
         for (;;) {
             while (node >= 0 && node != kEntrySentinel) {
-                if (++visits > kMaxVisits) { status |= ST_LOOP_LIMIT; node = kEntrySentinel; leaf = 0; sp = 0; break; }
+                if (++visits > cell.max_visits) { status |= ST_LOOP_LIMIT; node = kEntrySentinel; leaf = 0; sp = 0; break; }
                 if (COUNT) ++cnt.visits;
                 if constexpr (FMT == FMT_W4 || FMT == FMT_Q4) {
                     float tk[4];
@@ -934,7 +937,7 @@ template <int FMT>
 __global__ void __launch_bounds__(128)
 k_trace_rays(const void* __restrict__ nodes, const float4* __restrict__ tris, const int* __restrict__ inv_order,
              int n_tri, const float* __restrict__ o, const float* __restrict__ d, const int* __restrict__ skip,
-             int64_t n, rtmc_hit* __restrict__ hits, unsigned* __restrict__ status_out)
+             int64_t n, rtmc_hit* __restrict__ hits, unsigned* __restrict__ status_out, int max_iter)
 {
     extern __shared__ int2 s_stack[];
     const StackRef st{s_stack, (int)blockDim.x, (int)threadIdx.x};
@@ -946,7 +949,7 @@ k_trace_rays(const void* __restrict__ nodes, const float4* __restrict__ tris, co
     unsigned status = 0;
     float t, u, v;
     RaySetup64 r64;
-    const int j = bvh_closest<FMT>(nodes, tris, setup_ray(oo, dd), r64, sk, st, t, u, v, status);
+    const int j = bvh_closest<FMT>(nodes, tris, setup_ray(oo, dd), r64, sk, st, t, u, v, status, max_iter);
     rtmc_hit h;
     h.t = j >= 0 ? t : INFINITY;
     h.u = u; h.v = v;
@@ -956,6 +959,18 @@ k_trace_rays(const void* __restrict__ nodes, const float4* __restrict__ tris, co
 }
 
 }  // namespace
+
+// Inner-node visits one cell traversal may make: in a tree every inner node is
+// pushed by its one parent at most once, so a correct traversal visits each at
+// most once; more means a broken hierarchy, and the ray is abandoned with
+// ST_LOOP_LIMIT instead of looping.  `cap` > 0 lowers the bound (test hook).
+static int visit_bound(const DeviceMesh& m, int cap)
+{
+    const int64_t inner = (m.kind == FMT_W4 || m.kind == FMT_Q4) ? m.n_w4 : m.n_nodes;
+    int64_t b = std::min<int64_t>(inner + 1, (int64_t)kMaxVisits);
+    if (cap > 0) b = std::min<int64_t>(b, cap);
+    return (int)b;
+}
 
 template <int F, bool R, bool C, int SS>
 static cudaError_t ww_launch(const DeviceMesh& m, const Cell& cell, const Queues& q, int buf, int gen, int num_sms,
@@ -987,7 +1002,7 @@ static cudaError_t traverse_t(const DeviceMesh& m, const RunParams& p, const Que
                               int num_sms, const Tuning& tune, bool retest, cudaStream_t s)
 {
     const float big = fmaxf(fmaxf(fabsf(p.lx), fabsf(p.ly)), fmaxf(fabsf(p.z_min), fabsf(p.z_top)));
-    const Cell cell{p.lx, p.ly, p.z_min, p.z_top, p.max_wraps, ldexpf(big, -20)};
+    const Cell cell{p.lx, p.ly, p.z_min, p.z_top, p.max_wraps, ldexpf(big, -20), visit_bound(m, tune.max_visits)};
     const void* nodes = F == FMT_Q8 ? m.q8 : (F == FMT_W4 ? m.w4 : (F == FMT_Q4 ? m.q4 : (const void*)m.nodes));
     const int bt = tune.block_threads;
     int per_sm = tune.blocks_per_sm;
@@ -1030,7 +1045,7 @@ cudaError_t launch_columns(const DeviceMesh& m, const RunParams& p, const Queues
 {
     if (!m.col_ok) return cudaErrorInvalidValue;
     const float big = fmaxf(fmaxf(fabsf(p.lx), fabsf(p.ly)), fmaxf(fabsf(p.z_min), fabsf(p.z_top)));
-    const Cell cell{p.lx, p.ly, p.z_min, p.z_top, p.max_wraps, ldexpf(big, -20)};
+    const Cell cell{p.lx, p.ly, p.z_min, p.z_top, p.max_wraps, ldexpf(big, -20), visit_bound(m, 0)};
     const int tb = 128;
     int per_sm = 0;
     if (record) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, retest ? k_trace_columns<true, true>
@@ -1057,16 +1072,16 @@ cudaError_t launch_trace_rays(const DeviceMesh& m, const float* o, const float* 
     const int64_t gb = (n + tb - 1) / tb;
     if (gb > 0 && m.kind == FMT_Q8)
         k_trace_rays<FMT_Q8><<<(unsigned)gb, tb, smem, s>>>(m.q8, m.tris, m.inv_order, (int)m.n_tri, o, d, skip, n,
-                                                            hits, status);
+                                                            hits, status, 5 * visit_bound(m, 0));
     else if (gb > 0 && m.kind == FMT_W4)
         k_trace_rays<FMT_W4><<<(unsigned)gb, tb, smem, s>>>(m.w4, m.tris, m.inv_order, (int)m.n_tri, o, d, skip, n,
-                                                            hits, status);
+                                                            hits, status, 5 * visit_bound(m, 0));
     else if (gb > 0 && m.kind == FMT_Q4)
         k_trace_rays<FMT_Q4><<<(unsigned)gb, tb, smem, s>>>(m.q4, m.tris, m.inv_order, (int)m.n_tri, o, d, skip, n,
-                                                            hits, status);
+                                                            hits, status, 5 * visit_bound(m, 0));
     else if (gb > 0)
         k_trace_rays<FMT_FP32><<<(unsigned)gb, tb, smem, s>>>(m.nodes, m.tris, m.inv_order, (int)m.n_tri, o, d, skip,
-                                                              n, hits, status);
+                                                              n, hits, status, 5 * visit_bound(m, 0));
     return cudaGetLastError();
 }
 

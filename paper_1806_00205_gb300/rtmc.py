@@ -64,7 +64,7 @@ class RunDesc(C.Structure):
                 ("traversal", C.c_int32), ("fp64_retest", C.c_int32), ("item_base", C.c_uint32),
                 ("no_graph", C.c_int32), ("stack_depth", C.c_int32), ("fetch_threshold", C.c_int32),
                 ("random_polar", C.c_int32), ("n_zbins", C.c_int32), ("hist_z", C.c_void_p),
-                ("id_order", C.c_int32)]
+                ("id_order", C.c_int32), ("max_visits", C.c_int32), ("queue_factor", C.c_double)]
 
 
 class Batch(C.Structure):
@@ -82,7 +82,7 @@ class Result(C.Structure):
         (n, C.c_int64) for n in ("launches", "node_visits", "tri_tests")] + [
         (n, C.c_double) for n in ("ms_generate", "ms_traverse", "ms_shade", "ms_finalize")] + [
         ("traverse_launches", C.c_int64), ("retested", C.c_int64), ("ms_column", C.c_double),
-        ("column_rays", C.c_int64)]
+        ("column_rays", C.c_int64), ("queue_retries", C.c_int64)]
 
 
 class Record(C.Structure):
@@ -170,7 +170,8 @@ def paper_emission(e_c_ev=10.0, max_generation=6):
 def run_desc(n_ebins=64, n_abins=18, hist_e_max_ev=50.0, primary_offset=0, random_azimuth=False,
              max_wraps=1024, window=None, chunk=0, block_threads=0, blocks_per_sm=0, prim_hash=None,
              profile=False, count_visits=False, traversal=0, fp64_retest=False, item_base=0, no_graph=False,
-             stack_depth=0, fetch_threshold=0, id_order=False, random_polar=False, n_zbins=0):
+             stack_depth=0, fetch_threshold=0, id_order=False, random_polar=False, n_zbins=0, max_visits=0,
+             queue_factor=0.0):
     """Run descriptor.  ``random_polar`` draws each primary's polar angle from
     the cosine law (the item angle is ignored); ``n_zbins`` > 0 adds the
     penetration-depth histogram, returned as ``hist_z`` in each result dict
@@ -185,7 +186,7 @@ def run_desc(n_ebins=64, n_abins=18, hist_e_max_ev=50.0, primary_offset=0, rando
                    fp64_retest=int(bool(fp64_retest)), item_base=int(item_base), no_graph=int(bool(no_graph)),
                    stack_depth=int(stack_depth), fetch_threshold=int(fetch_threshold),
                    random_polar=int(bool(random_polar)), n_zbins=int(n_zbins), hist_z=None,
-                   id_order=int(bool(id_order)))
+                   id_order=int(bool(id_order)), max_visits=int(max_visits), queue_factor=float(queue_factor))
 
 
 def _with_hist_z(desc, n_items):

@@ -127,3 +127,45 @@ def test_batch_graph_follows_angles_and_rebuilds(setup):
     c, _, _ = ctx.run_batch([mid], [300.0], [0.0], n, 9)
     for k in INT_KEYS:
         assert c[0][k] == a[0][k], k
+
+
+@pytest.mark.parametrize("model", ["tertiaries", "paper_fit"])
+def test_batch_deeper_trees_equal_plain_runs(model):
+    """Every generation the emission allows runs batched (Section 2.2's ray tree):
+    tertiaries above 20 eV (the large config's physics) and the paper's own fits
+    with up to 6 generations give each item the tallies of a plain run, on all
+    four node formats, with and without the column grid for generation 0."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1806_00205_gb300 import rtmc
+    em = rtmc.Emission(regen_min_ev=20.0, max_generation=2) if model == "tertiaries" else rtmc.paper_emission()
+    energies = [500.0, 1500.0] if model == "tertiaries" else [416.0, 2000.0]
+    with rtmc.Context(0) as c:
+        c.load_see_tables(TABLE, em)
+        meshes = [I.grf_foam(16, 0.6, seed=6), I.grf_foam(24, 0.9, seed=7)]
+        for kind in (rtmc.BVH_FP32, rtmc.BVH_Q8, rtmc.BVH_W4, rtmc.BVH_Q4):
+            ids = []
+            for m in meshes:
+                mid = c.load_mesh(m.tri, m.box)
+                c.build_bvh(mid, kind=kind)
+                ids.append(mid)
+            for thetas in ([0.0], [0.0, 50.0]):
+                n = 15_000
+                res, he, ha = c.run_batch(ids, energies, thetas, n, 19, desc=rtmc.run_desc(chunk=40_000))
+                per_mesh = len(energies) * len(thetas)
+                deep = 0
+                for mi, mid in enumerate(ids):
+                    plain, phe, pha = c.run(mid, energies, thetas, n, 19,
+                                            desc=rtmc.run_desc(item_base=mi * per_mesh))
+                    for j in range(per_mesh):
+                        b = res[mi * per_mesh + j]
+                        for k in INT_KEYS + ("regenerated",):
+                            assert b[k] == plain[j][k], (kind, thetas, mi, j, k, b[k], plain[j][k])
+                        assert abs(b["e_sum"] - plain[j]["e_sum"]) <= 1e-9 * max(1.0, plain[j]["e_sum"])
+                        assert np.array_equal(he[mi * per_mesh + j], phe[j])
+                        assert np.array_equal(ha[mi * per_mesh + j], pha[j])
+                        deep += b["regenerated"]
+                assert deep > 0
+            for mid in ids:
+                c.unload_mesh(mid)

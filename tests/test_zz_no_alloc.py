@@ -87,6 +87,42 @@ def test_noalloc_fp64_retest_equals_run(setup):
     assert total > 0
 
 
+@pytest.mark.parametrize("opts", [dict(traversal=1), dict(traversal=2, stack_depth=8),
+                                  dict(traversal=2, stack_depth=32, fetch_threshold=12, block_threads=64),
+                                  dict(traversal=0, stack_depth=8, blocks_per_sm=2)])
+def test_noalloc_traversal_controls_equal_run(setup, opts):
+    """The traversal controls of the descriptor reach the kernels as in rtmc_run:
+    the same tallies and histograms at normal incidence (where traversal 2 keeps
+    generation 0 on the hierarchy) and at 40 degrees."""
+    ctx, mid, rtmc = setup
+    n = 3000
+    for theta in (0.0, 40.0):
+        desc = rtmc.run_desc(**opts)
+        ref, he, ha = ctx.run(mid, [350.0], [theta], n, 29, desc=desc)
+        got, ge, ga = ctx.run_noalloc(mid, 350.0, theta, n, 29, desc=desc)
+        for k in INT_KEYS + ("column_rays",):
+            assert got[k] == ref[0][k], (opts, theta, k, got[k], ref[0][k])
+        assert np.array_equal(ge, he[0]) and np.array_equal(ga, ha[0])
+
+
+def test_noalloc_checks_the_descriptor_as_run_does(setup):
+    ctx, mid, rtmc = setup
+    for bad in (dict(traversal=3), dict(stack_depth=12), dict(fetch_threshold=40), dict(chunk=-1),
+                dict(traversal=1, fp64_retest=True)):
+        with pytest.raises(rtmc.RtmcError) as e:
+            ctx.run(mid, [300.0], [0.0], 10, 1, desc=rtmc.run_desc(**bad))
+        with pytest.raises(rtmc.RtmcError) as f:
+            ctx.run_noalloc(mid, 300.0, 0.0, 10, 1, desc=rtmc.run_desc(**bad))
+        assert e.value.code == f.value.code == -1, bad
+    # the visit bound reaches the traversal kernels of both entry points
+    for opts in (dict(), dict(traversal=1)):
+        with pytest.raises(rtmc.RtmcError) as e:
+            ctx.run_noalloc(mid, 300.0, 30.0, 500, 1, desc=rtmc.run_desc(max_visits=2, **opts))
+        assert e.value.code == -8
+    ok, _, _ = ctx.run_noalloc(mid, 300.0, 30.0, 500, 1)
+    assert ok["rays"] == 500 + ok["emitted"]
+
+
 def test_noalloc_rejects_sizes_beyond_the_limit(setup):
     ctx, mid, rtmc = setup
     with pytest.raises(rtmc.RtmcError) as e:
