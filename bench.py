@@ -1,18 +1,23 @@
-"""Benchmark: RTMC secondary-electron yield, paper-scale plain configuration.
+"""Benchmark: RTMC secondary-electron yield, large configuration (the default).
 
-Workload (one step): a 128^3 periodic Gaussian-random-field foam (10 nm voxels,
-porosity 0.6, correlation length 2 voxels, seed 1806) meshed by marching cubes
-into ~1.39M FP32 triangles; 20 primary energies 50..1000 eV at normal
-incidence, 1e7 primaries each, tallying yield plus 64-bin energy and 18-bin
-polar-angle histograms of the escaped electrons.
+Workload (one step): a 256^3 periodic Gaussian-random-field foam (10 nm voxels,
+porosity 0.7, correlation length 2 voxels, seed 1806) meshed by marching cubes
+into ~9.9M FP32 triangles under a compressed (4-wide, 8-bit) BVH; 1e8 primaries
+at 500 eV at each of 9 incidence angles 0..80 deg, tertiaries for secondaries
+above 20 eV; 128-bin escaped-energy and 36-bin polar-angle histograms with FP64
+energy moments.  All items run batched (rtmc_run_batch).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--config large|paper|precision]
 
 Prints one JSON line.  ``value`` is traced rays per second over all ranks with
 the mesh, BVH and tables resident on the device; ``e2e`` is the same metric
 through the C ABI from pinned host buffers (mesh upload, BVH build, run and the
 result read-back inside the timed region).  ``--impl reference`` times the CPU
-FP64 oracle on a bounded sample of the same workload.
+FP64 oracle on a bounded sample of the same workload.  ``--config paper`` is
+the 128^3 foam x 20 energies at normal incidence (also reported, shorter, as
+``paper_config`` in the default line); ``--config precision`` the 8-bit-node
+precision form with the FP64 re-test.
 """
 from __future__ import annotations
 
@@ -40,6 +45,26 @@ NODE_BYTES = {0: 64, 1: 32, 2: 128, 3: 64}      # node fetch per visit: FP32 bin
 PREC_NODES = {"q4": 3, "q8": 1}                 # precision config: 8-bit node formats
 PREC_NODE_NAME = {3: "4-wide Q8", 1: "Q8"}
 MAIN_KIND = 2                                   # the paper-config workload runs on 4-wide FP32 nodes
+# large configuration (the default): 256^3 foam, compressed BVH, tertiaries, 9 angles
+LARGE_GRID, LARGE_POROSITY = 256, 0.7
+LARGE_E, LARGE_THETAS = 500.0, [10.0 * j for j in range(9)]
+LARGE_N_PRIM = 100_000_000
+LARGE_KIND = 3                                  # 4-wide nodes with 8-bit child boxes (compressed)
+LARGE_BINS = (128, 36)
+NODE_NAME = {0: "binary FP32", 1: "binary Q8", 2: "4-wide FP32", 3: "4-wide Q8"}
+
+
+def large_emission(rtmc_or_oracle):
+    """Tertiaries: secondaries at or above 20 eV re-emit once (max_generation 2)."""
+    return rtmc_or_oracle.Emission(regen_min_ev=20.0, max_generation=2)
+
+
+def large_workload_name(n_tri, n_prim):
+    return (f"large: {LARGE_GRID}^3 periodic GRF foam (10 nm voxels, porosity {LARGE_POROSITY}, corr {CORR:g} vox, "
+            f"seed {SEED}) -> {n_tri} FP32 triangles, {NODE_NAME[LARGE_KIND]} BVH (compressed); {n_prim:.3g} "
+            f"primaries at {LARGE_E:g} eV x {len(LARGE_THETAS)} angles {LARGE_THETAS[0]:g}-{LARGE_THETAS[-1]:g} deg; "
+            f"tertiaries above 20 eV (max_generation 2); {LARGE_BINS[0]} energy / {LARGE_BINS[1]} angle bins, "
+            "FP64 moments")
 
 
 def workload_name(n_tri, n_prim, energies=ENERGIES):
@@ -108,14 +133,14 @@ def kernel_sha():
     return h.hexdigest()[:16]
 
 
-def measured_traffic():
-    """DRAM bytes per traversal launch from a committed ncu summary, if it matches this kernel."""
-    path = os.path.join(ROOT, "profiles", "traverse_dram_traffic.json")
+def measured_traffic(tag="paper_config", node_format=MAIN_KIND):
+    """DRAM bytes per traversal ray from a committed ncu summary, if it matches this kernel."""
+    name = "traverse_dram_traffic.json" if tag == "paper_config" else f"traverse_dram_traffic_{tag}.json"
     try:
-        d = json.load(open(path))
+        d = json.load(open(os.path.join(ROOT, "profiles", name)))
     except (OSError, ValueError):
         return None
-    if d.get("kernel_sha") != kernel_sha() or d.get("node_format") != MAIN_KIND:
+    if d.get("kernel_sha") != kernel_sha() or d.get("node_format") != node_format:
         return None
     return d.get("dram_bytes_per_ray")
 
@@ -132,81 +157,122 @@ def make_mesh():
     return I.grf_foam(GRID, POROSITY, CORR, SEED), I.see_table()
 
 
-def cpu_oracle_sample(mesh, table, n_sample, energy=500.0, seed=SEED):
+def cpu_oracle_sample(mesh, table, n_sample, energy=500.0, seed=SEED, theta=0.0, item=0, emission=None,
+                      bins=(64, 18), records=False):
     import oracle as O
     threads = os.cpu_count() or 1
     t0 = time.perf_counter()
-    r = O.run(mesh, table, energy, 0.0, n_sample, seed, primary_offset=0, n_threads=threads)
+    r = O.run(mesh, table, energy, theta, n_sample, seed, primary_offset=0, n_threads=threads, item=item,
+              emission=emission or O.Emission(), n_ebins=bins[0], n_abins=bins[1], records=records)
     dt = time.perf_counter() - t0
     return r, dt, threads
 
 
+def large_oracle_sample(mesh, table, per_angle):
+    """The oracle on the first `per_angle` primaries of every angle of the large config
+    (item k = angle k, the batch's random streams); returns per-item results, rays, s, threads."""
+    import oracle as O
+    out, rays, secs, thr = [], 0, 0.0, 1
+    for k, th in enumerate(LARGE_THETAS):
+        r, dt, thr = cpu_oracle_sample(mesh, table, per_angle, LARGE_E, SEED, th, k, large_emission(O),
+                                       LARGE_BINS, records=True)
+        out.append(r)
+        rays += r["rays"]
+        secs += dt
+    return out, rays, secs, thr
+
+
 def run_reference(args):
+    """The reference arm: the FP64 oracle (the paper has no code) on a bounded sample
+    of the configuration's workload, on the host's cores, rank 0 only."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    mesh, table = make_mesh()
-    n_sample = args.ref_sample
-    for _ in range(args.warmup):
-        cpu_oracle_sample(mesh, table, max(16, n_sample // 8))
-    rays, secs, prims = 0, 0.0, 0
-    for _ in range(args.steps):
-        r, dt, threads = cpu_oracle_sample(mesh, table, n_sample)
-        rays += r["rays"]
-        secs += dt
-        prims += n_sample
+    from paper_1806_00205_gb300 import inputs as I
+    import oracle as O
+    table = I.see_table()
+    if args.config == "large":
+        mesh = I.grf_foam(LARGE_GRID, LARGE_POROSITY, CORR, SEED)
+        per_angle = max(1, args.ref_sample // len(LARGE_THETAS))
+        for _ in range(args.warmup):
+            cpu_oracle_sample(mesh, table, 1, LARGE_E, SEED, LARGE_THETAS[-1], len(LARGE_THETAS) - 1,
+                              large_emission(O), LARGE_BINS)
+        rays, secs, prims = 0, 0.0, 0
+        for _ in range(args.steps):
+            for k, th in enumerate(LARGE_THETAS):
+                r, dt, threads = cpu_oracle_sample(mesh, table, per_angle, LARGE_E, SEED, th, k, large_emission(O),
+                                                   LARGE_BINS)
+                rays += r["rays"]
+                secs += dt
+                prims += per_angle
+        workload = large_workload_name(mesh.n_tri, LARGE_N_PRIM)
+        sample = (f"{per_angle} primaries per angle x {len(LARGE_THETAS)} angles at {LARGE_E:g} eV per step, "
+                  f"tertiaries (brute force over all {mesh.n_tri} triangles per ray segment)")
+    else:
+        mesh, table = make_mesh()
+        n_sample = args.ref_sample
+        for _ in range(args.warmup):
+            cpu_oracle_sample(mesh, table, max(16, n_sample // 8))
+        rays, secs, prims = 0, 0.0, 0
+        for _ in range(args.steps):
+            r, dt, threads = cpu_oracle_sample(mesh, table, n_sample)
+            rays += r["rays"]
+            secs += dt
+            prims += n_sample
+        workload = workload_name(mesh.n_tri, N_PRIM)
+        sample = (f"{n_sample} primaries at 500 eV, normal incidence, per step "
+                  f"(brute force over all {mesh.n_tri} triangles per ray segment)")
     v = rays / secs
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "rays/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "primaries_per_s": prims / secs,
-            "config": {"workload": workload_name(mesh.n_tri, N_PRIM), "n_tri": mesh.n_tri},
-            "cpu_baseline": {"value": v, "unit": "rays/s", "cores": threads, "kind": "oracle",
-                             "sample": f"{n_sample} primaries at 500 eV, normal incidence, per step "
-                                       f"(brute force over all {mesh.n_tri} triangles per ray segment)"},
+            "config": {"workload": workload, "n_tri": mesh.n_tri},
+            "cpu_baseline": {"value": v, "unit": "rays/s", "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def run_forms(ctx, rtmc, autotune, n_prim):
+def run_forms(rtmc, autotune, n_prim, device=0):
     """Batched config: 16 foams (48^3..128^3, porosity 0.3..0.9) x 20 energies x 9 angles.
 
-    Compares the batched form (multi-item queues, one CUDA graph, autotuned,
-    Q8 or FP32 nodes) with the plain form (rtmc_run item by item, FP32 nodes)."""
+    Compares the batched form (multi-item queues, one CUDA graph, autotuned, 8-bit
+    or FP32 nodes, binary or 4-wide) with the plain form (rtmc_run item by item,
+    binary FP32 nodes), on a context of its own (the configuration's emission)."""
     import torch
     from paper_1806_00205_gb300 import inputs as I
     cfg = I.batched_foams()
     meshes = [I.grf_foam(g, p, CORR, sd) for g, p, sd in cfg]
     energies = [50.0 * i for i in range(1, 21)]
     thetas = [10.0 * j for j in range(9)]
-    ids32, idsq, idsw = [], [], []
+    ctx = rtmc.Context(device)
+    ctx.load_see_tables(I.see_table())
+    kinds = {"batched_q8": rtmc.BVH_Q8, "batched_q4": rtmc.BVH_Q4, "batched_fp32": rtmc.BVH_FP32,
+             "batched_w4": rtmc.BVH_W4}
+    ids = {name: [] for name in kinds}
     for m in meshes:
-        for ids, kind in ((ids32, rtmc.BVH_FP32), (idsq, rtmc.BVH_Q8), (idsw, rtmc.BVH_W4)):
+        for name, kind in kinds.items():
             a = ctx.load_mesh(m.tri, m.box)
             ctx.build_bvh(a, kind=kind)
-            ids.append(a)
+            ids[name].append(a)
     ntri = [m.n_tri for m in meshes]
-    pq = autotune.tune(ctx, idsq, ntri, energies, thetas, kind=1, cache_path=None, device_name="gb300")
-    p32 = autotune.tune(ctx, ids32, ntri, energies, thetas, kind=0, cache_path=None, device_name="gb300")
-    pw = autotune.tune(ctx, idsw, ntri, energies, thetas, kind=2, cache_path=None, device_name="gb300")
+    tuned = {name: autotune.tune(ctx, ids[name], ntri, energies, thetas, kind=kind, cache_path=None,
+                                 device_name="gb300") for name, kind in kinds.items()}
     per_mesh = len(energies) * len(thetas)
 
     def plain():
         out = []
-        for mi, mid in enumerate(ids32):
+        for mi, mid in enumerate(ids["batched_fp32"]):
             r, _, _ = ctx.run(mid, energies, thetas, n_prim, SEED, desc=rtmc.run_desc(item_base=mi * per_mesh))
             out += r
         return out
 
-    forms = {}
-    results = {}
-    for name, fn in (("batched_q8", lambda: ctx.run_batch(idsq, energies, thetas, n_prim, SEED,
-                                                          desc=rtmc.run_desc(**pq))[0]),
-                     ("batched_fp32", lambda: ctx.run_batch(ids32, energies, thetas, n_prim, SEED,
-                                                            desc=rtmc.run_desc(**p32))[0]),
-                     ("batched_w4", lambda: ctx.run_batch(idsw, energies, thetas, n_prim, SEED,
-                                                          desc=rtmc.run_desc(**pw))[0]),
-                     ("plain_fp32", plain)):
+    def batched(name):
+        return lambda: ctx.run_batch(ids[name], energies, thetas, n_prim, SEED,
+                                     desc=rtmc.run_desc(**tuned[name]))[0]
+
+    forms, results = {}, {}
+    for name, fn in [(n, batched(n)) for n in kinds] + [("plain_fp32", plain)]:
         fn()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -216,97 +282,316 @@ def run_forms(ctx, rtmc, autotune, n_prim):
         rays = sum(x["rays"] for x in r)
         forms[name] = {"rays_per_s": rays / dt, "primaries_per_s": len(r) * n_prim / dt, "s": dt}
         results[name] = r
-    d_sey = max(abs(a["sey"] - b["sey"]) for a, b in zip(results["batched_q8"], results["plain_fp32"]))
-    for mid in ids32 + idsq + idsw:
-        ctx.unload_mesh(mid)
+    d_sey = {name: max(abs(a["sey"] - b["sey"]) for a, b in zip(results[name], results["plain_fp32"]))
+             for name in kinds}
+    ctx.close()
     return {"workload": f"16 GRF foams (grids 48^3..128^3, porosity 0.30..0.90, {min(ntri)}..{max(ntri)} "
                         f"triangles) x 20 energies (50..1000 eV) x 9 angles (0..80 deg) x {n_prim:.0e} primaries",
-            "forms": forms, "max_abs_sey_diff_batched_q8_vs_plain_fp32": d_sey,
+            "forms": forms, "max_abs_sey_diff_vs_plain_fp32": d_sey,
             "speedup_batched_q8_vs_plain_fp32": forms["plain_fp32"]["s"] / forms["batched_q8"]["s"],
-            "autotuned": {"batched_q8": pq, "batched_fp32": p32, "batched_w4": pw}}
+            "speedup_batched_q4_vs_plain_fp32": forms["plain_fp32"]["s"] / forms["batched_q4"]["s"],
+            "autotuned": tuned}
+
+
+def kernel_fields(ms, launches, algo_bytes, peak, bound, extra=None):
+    """Roofline fields of one kernel from its summed CUDA-event time and algorithmic bytes."""
+    achieved = algo_bytes / (ms / 1e3) / 1e9 if ms > 0 else None
+    out = {"bound": bound, "ms": ms, "launches": launches, "ms_per_launch": ms / max(1, launches),
+           "algorithmic_bytes": algo_bytes, "achieved": achieved, "peak": peak, "unit": "GB/s",
+           "frac": achieved / peak if achieved else None}
+    if extra:
+        out.update(extra)
+    return out
+
+
+def paper_config_summary(rtmc, I, dev, l2_gbs, hbm_peak, steps=3):
+    """The paper-scale configuration (128^3 foam, 20 energies x 1e7 primaries at normal
+    incidence, 4-wide FP32 nodes) on its own context: rays/s and the traversal roofline."""
+    import torch
+    mesh, table = make_mesh()
+    stream = torch.cuda.Stream(device=dev)
+    ctx = rtmc.Context(dev.index or 0, stream=stream)
+    ctx.load_see_tables(table)
+    mid = ctx.load_mesh(mesh.tri, mesh.box)
+    ctx.build_bvh(mid, kind=MAIN_KIND)
+    desc = rtmc.run_desc(profile=True, no_graph=True)
+    ctx.run_batch([mid], ENERGIES, [0.0], N_PRIM, SEED, desc=desc)
+    torch.cuda.synchronize(dev)
+    rays = trav_ms = col_ms = col_rays = shade_ms = 0.0
+    trav_l = 0
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        res, _, _ = ctx.run_batch([mid], ENERGIES, [0.0], N_PRIM, SEED, desc=desc)
+        rays += sum(r["rays"] for r in res)
+        trav_ms += res[0]["ms_traverse"]
+        trav_l += res[0]["traverse_launches"]
+        col_ms += res[0]["ms_column"]
+        col_rays += res[0]["column_rays"]
+        shade_ms += res[0]["ms_shade"]
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    cres, _, _ = ctx.run_batch([mid], ENERGIES, [0.0], N_PRIM // 5, SEED,
+                               desc=rtmc.run_desc(count_visits=True, no_graph=True))
+    c_rays = sum(r["rays"] for r in cres) - cres[0]["column_rays"]
+    visits, tests = cres[0]["node_visits"] / c_rays, cres[0]["tri_tests"] / c_rays
+    b_ray = visits * NODE_BYTES[MAIN_KIND] + tests * TRI_BYTES + RAY_BYTES
+    h_rays = rays - col_rays
+    ctx.close()
+    tr = measured_traffic("paper_config", MAIN_KIND)
+    return {"workload": workload_name(mesh.n_tri, N_PRIM), "rays_per_s": rays / dt,
+            "primaries_per_s": steps * len(ENERGIES) * N_PRIM / dt, "ms_per_step": 1e3 * dt / steps,
+            "k_traverse_ww": kernel_fields(trav_ms, trav_l, h_rays * b_ray, l2_gbs, "l2", {
+                "node_format": NODE_NAME[MAIN_KIND], "bytes_per_ray": b_ray, "node_visits_per_ray": visits,
+                "tri_tests_per_ray": tests, "dram_bytes_per_ray": tr,
+                "frac_of_measured_hbm": (tr * h_rays / (trav_ms / 1e3) / 1e9 / hbm_peak) if tr else None}),
+            "k_trace_columns": {"ms": col_ms, "rays": col_rays, "rays_per_s": col_rays / (col_ms / 1e3)},
+            "k_shade_ms": shade_ms}
 
 
 def run_large(args):
-    """Large config: 256^3 foam at porosity 0.7 (~8M triangles, Q8 BVH), tertiaries for
-    secondaries above 20 eV, 1e8 primaries at 500 eV x 9 incidence angles, 128 energy
-    bins and 36 angle bins, FP64 moments."""
+    """Large config (the default line): 256^3 foam at porosity 0.7 (~9.9M triangles) under the
+    compressed 4-wide 8-bit BVH, 1e8 primaries at 500 eV x 9 incidence angles, tertiaries for
+    secondaries above 20 eV, 128 energy and 36 angle bins, FP64 moments; every item batched."""
     import torch
+    import torch.distributed as dist
+    import oracle as O
+    from paper_1806_00205_gb300 import autotune, rtmc, shard
     from paper_1806_00205_gb300 import inputs as I
-    from paper_1806_00205_gb300 import rtmc
-    dev = torch.device("cuda", 0)
-    n_prim = args.primaries if args.primaries != N_PRIM else 100_000_000
-    thetas = [10.0 * j for j in range(9)]
-    mesh = I.grf_foam(256, 0.7, CORR, SEED)
+    from tests.parity import primary_hashes
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n_prim = args.primaries if args.primaries else LARGE_N_PRIM
+    nt = len(LARGE_THETAS)
+    mesh = I.grf_foam(LARGE_GRID, LARGE_POROSITY, CORR, SEED)
     table = I.see_table()
-    em = rtmc.Emission(regen_min_ev=20.0, max_generation=2)
     stream = torch.cuda.Stream(device=dev)
-    ctx = rtmc.Context(0, stream=stream)
-    ctx.load_see_tables(table, em)
+    ctx = rtmc.Context(local, stream=stream)
+    ctx.load_see_tables(table, large_emission(rtmc))
+    free0, total_mem = torch.cuda.mem_get_info(dev)
     mid = ctx.load_mesh(mesh.tri, mesh.box)
-    ctx.build_bvh(mid, kind=rtmc.BVH_Q8)
-    desc = rtmc.run_desc(n_ebins=128, n_abins=36, profile=True)
+    ctx.build_bvh(mid, kind=LARGE_KIND)
+    offset = shard.primary_offset(rank, n_prim)     # weak scaling: each rank its own primary ids
+    if args.no_autotune:
+        tuned = {}
+    else:
+        tuned = autotune.tune(ctx, [mid], [mesh.n_tri], [LARGE_E], LARGE_THETAS, kind=LARGE_KIND, cache_path=None,
+                              device_name=torch.cuda.get_device_name(dev), n_sample=100_000)
+    nb = dict(n_ebins=LARGE_BINS[0], n_abins=LARGE_BINS[1])
+    desc = rtmc.run_desc(primary_offset=offset, profile=True, no_graph=True, **nb, **tuned)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def step(d=desc, m=mid):
+        return ctx.run_batch([m], [LARGE_E], LARGE_THETAS, n_prim, SEED, desc=d)
+
     for _ in range(args.warmup):
-        ctx.run(mid, [500.0], thetas, n_prim // 10, SEED, desc=desc)
-    clocks = ClockSampler(0)
-    torch.cuda.synchronize(dev)
+        step()
+    clocks = ClockSampler(local)
+    barrier()
     clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    rays = prims = launches = col_rays = 0
-    trav_ms, trav_l = 0.0, 0
+    rays = prims = launches = 0
+    k = dict(trav_ms=0.0, trav_l=0, shade_ms=0.0, gen_ms=0.0, fin_ms=0.0, col_ms=0.0, col_rays=0, shade_bytes=0.0,
+             retries=0)
+    results = None
     for _ in range(args.steps):
-        res, he, ha = ctx.run(mid, [500.0], thetas, n_prim, SEED, desc=desc)
-        rays += sum(r["rays"] for r in res)
-        col_rays += sum(r["column_rays"] for r in res)
-        prims += sum(r["n_primaries"] for r in res)
-        launches += sum(r["launches"] for r in res)
-        trav_ms += sum(r["ms_traverse"] for r in res)
-        trav_l += sum(r["traverse_launches"] for r in res)
+        results, he, ha = step()
+        r0 = results[0]
+        rays += sum(r["rays"] for r in results)
+        prims += sum(r["n_primaries"] for r in results)
+        launches += r0["launches"]
+        k["trav_ms"] += r0["ms_traverse"]
+        k["trav_l"] += r0["traverse_launches"]
+        k["shade_ms"] += r0["ms_shade"]
+        k["gen_ms"] += r0["ms_generate"]
+        k["fin_ms"] += r0["ms_finalize"]
+        k["col_ms"] += r0["ms_column"]
+        k["col_rays"] += r0["column_rays"]
+        k["retries"] += r0["queue_retries"]
+        # shade: queue entry (48 B) + hit (16 B) per ray, facet + normal (64 B) per facet stop,
+        # 48 B per daughter written
+        stops = sum(r["rays"] - r["escaped"] - r["lost"] for r in results)
+        k["shade_bytes"] += sum(r["rays"] for r in results) * 64.0 + stops * 64.0 + \
+            sum(r["emitted"] for r in results) * 48.0
     ev1.record(stream)
-    torch.cuda.synchronize(dev)
+    barrier()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
-    cres, _, _ = ctx.run(mid, [500.0], thetas[:1], n_prim // 10, SEED,
-                         desc=rtmc.run_desc(n_ebins=128, n_abins=36, count_visits=True))
-    h_rays = cres[0]["rays"] - cres[0]["column_rays"]          # the hierarchy's rays (counters cover these)
-    visits = cres[0]["node_visits"] / h_rays
-    tests = cres[0]["tri_tests"] / h_rays
-    b_ray = visits * 32 + tests * TRI_BYTES + RAY_BYTES
-    achieved = (rays - col_rays) * b_ray / (trav_ms / 1e3) / 1e9
+    mem_used = (total_mem - torch.cuda.mem_get_info(dev)[0]) / 1e9
+    t = torch.tensor([ms, rays, prims], dtype=torch.float64, device=dev)
+    if world > 1:
+        tmax = t[:1].clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = t[1:].clone()
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        ms, rays, prims = tmax.item(), tsum[0].item(), tsum[1].item()
+    value = rays / (ms / 1e3)
+    local_rays = sum(r["rays"] for r in results) * args.steps
+
+    # the same step replayed from the captured CUDA graph
+    gdesc = rtmc.run_desc(primary_offset=offset, **nb, **tuned)
+    step(gdesc)
+    barrier()
+    g0 = time.perf_counter()
+    g_steps = min(args.steps, 3)
+    for _ in range(g_steps):
+        step(gdesc)
+    barrier()
+    graph_ms = (time.perf_counter() - g0) * 1e3 / g_steps
+
+    # plain form (rtmc_run item by item) and uncompressed 4-wide nodes on the same workload
+    pdesc = rtmc.run_desc(primary_offset=offset, **nb)
+    barrier()
+    p0 = time.perf_counter()
+    pres, _, _ = ctx.run(mid, [LARGE_E], LARGE_THETAS, n_prim, SEED, desc=pdesc)
+    barrier()
+    plain_s = time.perf_counter() - p0
+    assert all(a["sum_k"] == b["sum_k"] for a, b in zip(pres, results)), "batched and plain tallies differ"
+    w4 = ctx.load_mesh(mesh.tri, mesh.box)
+    ctx.build_bvh(w4, kind=rtmc.BVH_W4)
+    step(gdesc, w4)
+    barrier()
+    w0 = time.perf_counter()
+    wres, _, _ = step(gdesc, w4)
+    barrier()
+    w4_s = time.perf_counter() - w0
+    assert all(a["sum_k"] == b["sum_k"] for a, b in zip(wres, results)), "4-wide FP32 and 8-bit tallies differ"
+    ctx.unload_mesh(w4)
+
+    # node-visit counts of a sample of the same workload (counting variant, untimed)
+    cres, _, _ = ctx.run_batch([mid], [LARGE_E], LARGE_THETAS, max(n_prim // 20, 1), SEED,
+                               desc=rtmc.run_desc(primary_offset=offset, count_visits=True, no_graph=True, **nb,
+                                                  **tuned))
+    c_rays = sum(r["rays"] for r in cres) - cres[0]["column_rays"]     # the hierarchy's rays
+    visits, tests = cres[0]["node_visits"] / c_rays, cres[0]["tri_tests"] / c_rays
+    b_ray = visits * NODE_BYTES[LARGE_KIND] + tests * TRI_BYTES + RAY_BYTES
+    h_rays = local_rays - k["col_rays"]
     pk, pk_kind = peaks()
-    peak = float(pk.get("hbm_gbs", 6800.0))
+    hbm_peak = float(pk.get("hbm_gbs", 6800.0))
+    l2_gbs = ctx.probe_bandwidth(32 << 20, 10)          # L2-resident streaming read (own probe)
+    hbm_read_gbs = ctx.probe_bandwidth(4 << 30, 5)      # HBM streaming read (own probe)
+    rays_per_launch = h_rays / max(1, k["trav_l"])
+    tr = measured_traffic("large_config", LARGE_KIND)
+    trav = kernel_fields(k["trav_ms"], k["trav_l"], h_rays * b_ray, l2_gbs, "l2", {
+        "kernel": f"k_traverse_ww ({NODE_NAME[LARGE_KIND]} nodes)", "bytes_per_ray": b_ray,
+        "node_visits_per_ray": visits, "tri_tests_per_ray": tests, "rays_per_launch": rays_per_launch,
+        "peak_kind": "own L2-resident streaming read probe (rtmc_probe_bandwidth, 32 MiB), this run",
+        "dram_bytes_per_ray": tr,
+        "hbm_achieved": tr * h_rays / (k["trav_ms"] / 1e3) / 1e9 if tr else None,
+        "frac_of_measured_hbm": tr * h_rays / (k["trav_ms"] / 1e3) / 1e9 / hbm_peak if tr else None,
+        "hbm_peak": hbm_peak, "hbm_peak_kind": f"{pk_kind} hbm_gbs (MEASURED_PEAKS.json)"})
+    roofline = {"bound": "l2", "kernel": trav["kernel"], "achieved": trav["achieved"], "peak": l2_gbs,
+                "unit": "GB/s", "frac": trav["frac"],
+                "traffic": tr * rays_per_launch if tr is not None else None,
+                "peak_kind": trav["peak_kind"], "bytes_per_ray": b_ray, "node_visits_per_ray": visits,
+                "tri_tests_per_ray": tests, "traverse_ms_per_launch": trav["ms_per_launch"],
+                "rays_per_launch": rays_per_launch, "traffic_bytes_per_ray": tr,
+                "hbm_frac": trav["frac_of_measured_hbm"], "hbm_peak": hbm_peak,
+                "hbm_read_probe_gbs": hbm_read_gbs, "l2_read_probe_gbs": l2_gbs}
+    kernels = {"k_traverse_ww": trav,
+               "k_shade": kernel_fields(k["shade_ms"], 0, k["shade_bytes"], hbm_peak, "hbm", {
+                   "peak_kind": f"{pk_kind} hbm_gbs", "note": "queue entry + hit per ray, facet + normal per "
+                                                              "stop, 48 B per daughter written"}),
+               "generate_ms": k["gen_ms"], "finalize_ms": k["fin_ms"],
+               "k_trace_columns": {"ms": k["col_ms"], "rays": k["col_rays"],
+                                   "note": "the 0-degree item's primaries"}}
+
+    # end to end through the C ABI from pinned host memory
     tri_host = torch.from_numpy(mesh.tri.reshape(-1, 9)).pin_memory()
-    torch.cuda.synchronize(dev)
-    e0 = time.perf_counter()
-    m2 = ctx.load_mesh(tri_host, mesh.box)
-    ctx.build_bvh(m2, kind=rtmc.BVH_Q8)
-    rr, _, _ = ctx.run(m2, [500.0], thetas, n_prim, SEED, desc=rtmc.run_desc(n_ebins=128, n_abins=36))
-    ctx.unload_mesh(m2)
-    e_dt = time.perf_counter() - e0
-    cpu = None
-    if not args.no_cpu:
-        r, dt, threads = cpu_oracle_sample(mesh, table, 48)
-        cpu = {"value": r["rays"] / dt, "unit": "rays/s", "cores": threads, "kind": "oracle",
-               "sample": f"48 primaries at 500 eV, normal incidence, max_generation 1 (brute force over "
-                         f"{mesh.n_tri} triangles per segment); {dt:.1f} s"}
-    line = {"metric": METRIC, "value": rays / (ms / 1e3), "unit": "rays/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "primaries_per_s": prims / (ms / 1e3),
-            "config": {"workload": f"large: 256^3 periodic GRF foam (porosity 0.7) -> {mesh.n_tri} triangles, "
-                                   f"Q8 BVH; {n_prim:.0e} primaries at 500 eV x 9 angles (0..80 deg); "
-                                   "tertiaries above 20 eV (max_generation 2); 128 energy / 36 angle bins",
-                       "n_tri": mesh.n_tri, "l2": "inputs larger than L2 (Q8 nodes + triangles ~0.6 GB)"},
-            "sey": [round(r["sey"], 6) for r in res], "regenerated": sum(r["regenerated"] for r in res),
-            "roofline": {"bound": "hbm", "kernel": "k_traverse_ww (Q8)", "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                         "peak_kind": f"{pk_kind} hbm_gbs", "bytes_per_ray": b_ray,
-                         "node_visits_per_ray": visits, "tri_tests_per_ray": tests},
-            "e2e": {"value": sum(r["rays"] for r in rr) / e_dt, "unit": "rays/s",
-                    "h2d_bytes_per_step": tri_host.numel() * 4 + table.delta.nbytes,
-                    "d2h_bytes_per_step": 9 * (rtmc.C.sizeof(rtmc.Result) + 8 * (128 + 36))},
-            "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu}
-    print(json.dumps(line), flush=True)
+    h2d = tri_host.numel() * 4 + table.delta.nbytes + 8 * (1 + nt)
+    d2h = nt * (rtmc.C.sizeof(rtmc.Result) + 8 * sum(LARGE_BINS))
+    e2e_desc = rtmc.run_desc(primary_offset=offset, **nb, **tuned)
+    barrier()
+    e_t0 = time.perf_counter()
+    e_rays = 0
+    for _ in range(args.e2e_steps):
+        m2 = ctx.load_mesh(tri_host, mesh.box)
+        ctx.build_bvh(m2, kind=LARGE_KIND)
+        rr, _, _ = ctx.run_batch([m2], [LARGE_E], LARGE_THETAS, n_prim, SEED, desc=e2e_desc)
+        ctx.unload_mesh(m2)
+        e_rays += sum(r["rays"] for r in rr)
+    barrier()
+    e_dt = time.perf_counter() - e_t0
+    et = torch.tensor([e_dt, e_rays], dtype=torch.float64, device=dev)
+    if world > 1:
+        a = et[:1].clone(); dist.all_reduce(a, op=dist.ReduceOp.MAX)
+        b = et[1:].clone(); dist.all_reduce(b, op=dist.ReduceOp.SUM)
+        e_dt, e_rays = a.item(), b.item()
+
+    extra = {}
+    if rank == 0 and not args.no_paper:
+        extra["paper_config"] = paper_config_summary(rtmc, I, dev, l2_gbs, hbm_peak)
+    if rank == 0 and not args.no_forms:
+        extra["batched_config"] = run_forms(rtmc, autotune, args.forms_primaries, local)
+
+    cpu, sampled = None, None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        per = args.cpu_sample_per_angle
+        outs, o_rays, o_secs, thr = large_oracle_sample(mesh, table, per)
+        cpu = {"value": o_rays / o_secs, "unit": "rays/s", "cores": thr, "kind": "oracle",
+               "sample": f"the first {per} primaries of each of the {nt} angles at {LARGE_E:g} eV, tertiaries, "
+                         f"same mesh (brute force over all {mesh.n_tri} triangles per ray segment); "
+                         f"{o_secs:.1f} s"}
+        same, esc_g, esc_o = 0, 0, 0
+        ids = np.arange(per, dtype=np.uint64)
+        for j, (th, o) in enumerate(zip(LARGE_THETAS, outs)):
+            h = torch.zeros(per, dtype=torch.int64, device=dev)
+            g, _, _ = ctx.run(mid, [LARGE_E], [th], per, SEED, desc=rtmc.run_desc(item_base=j, prim_hash=h, **nb))
+            same += int(np.sum(h.cpu().numpy().view(np.uint64) == primary_hashes(o["records"], ids)))
+            esc_g += g[0]["escaped"]
+            esc_o += o["escaped"]
+        sampled = {"primaries": per * nt, "per_primary_event_hashes_equal": same,
+                   "escapes_gpu": esc_g, "escapes_oracle": esc_o,
+                   "note": "same primary ids and random streams on both sides; a hash covers every ray of the "
+                           "primary's tree (fate, facet, count, energy and angle bins, wraps)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "primaries_per_s": prims / (ms / 1e3),
+            "config": {"workload": large_workload_name(mesh.n_tri, n_prim), "n_tri": mesh.n_tri,
+                       "energy_ev": LARGE_E, "theta_deg": LARGE_THETAS, "primaries_per_angle": n_prim,
+                       "primaries_per_step": n_prim * nt * world,
+                       "engine": f"rtmc_run_batch (multi-item queues), {NODE_NAME[LARGE_KIND]} BVH nodes, autotuned",
+                       "autotuned": tuned,
+                       "l2": "inputs larger than L2 (8-bit 4-wide nodes + triangles + normals "
+                             f"{mesh.n_tri * (64 / 3 + 48 + 16) / 1e9:.2f} GB, ray queues several GB)",
+                       "device_memory_gb": mem_used},
+            "sey": [round(r["sey"], 6) for r in results],
+            "sey_se": [round(r["sey_se"], 7) for r in results],
+            "sey_error": {"statistical_se_max": max(r["sey_se"] for r in results),
+                          "oracle_sample": sampled,
+                          "parity_tests": "tests/test_gpu_parity.py (per-ray records, hit distances within a "
+                                          "per-ray FP32 error bound, FP64 moments against the oracle)"},
+            "graph_ms_per_step": graph_ms,
+            "plain_form_rays_per_s": sum(r["rays"] for r in pres) / plain_s,
+            "uncompressed_4wide_fp32_rays_per_s": sum(r["rays"] for r in wres) / w4_s,
+            "queue_retries": k["retries"],
+            "roofline": roofline,
+            "kernels": kernels,
+            "e2e": {"value": e_rays / e_dt, "unit": "rays/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        line.update(extra)
+        print(json.dumps(line), flush=True)
     ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
 
 
 PREC_POROSITY = (0.4, 0.6, 0.8)
@@ -608,7 +893,7 @@ def run_ours(args):
 
     forms = None
     if rank == 0 and not args.no_forms:
-        forms = run_forms(ctx, rtmc, autotune, args.forms_primaries)
+        forms = run_forms(rtmc, autotune, args.forms_primaries, local)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -667,23 +952,32 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--primaries", type=int, default=N_PRIM, help="primaries per energy")
+    ap.add_argument("--primaries", type=int, default=0,
+                    help="primaries per item (0: the configuration's own, 1e8 large / 1e7 paper and precision)")
     ap.add_argument("--energies", type=int, default=len(ENERGIES))
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-sample", type=int, default=1024)
-    ap.add_argument("--ref-sample", type=int, default=256)
+    ap.add_argument("--ref-sample", type=int, default=0,
+                    help="reference arm: primaries per step (0: 9 large, 256 paper)")
+    ap.add_argument("--cpu-sample-per-angle", type=int, default=6,
+                    help="large config: primaries per angle for the CPU baseline and the sampled parity")
+    ap.add_argument("--no-paper", action="store_true", help="skip the paper-config summary of the default line")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched-config form comparison")
     ap.add_argument("--forms-primaries", type=int, default=1_000_000)
     ap.add_argument("--no-autotune", action="store_true", help="default launch parameters (profiling runs)")
-    ap.add_argument("--config", choices=("paper", "large", "precision"), default="paper",
-                    help="paper: 128^3 foam, 20 energies x 1e7 (default); large: 256^3 foam, tertiaries; "
-                         "precision: 3 porosities, 8-bit nodes + FP64 re-test, 3 energies x 2 angles")
+    ap.add_argument("--config", choices=("paper", "large", "precision"), default="large",
+                    help="large: 256^3 foam, 9 angles x 1e8, tertiaries (default); paper: 128^3 foam, 20 energies "
+                         "x 1e7; precision: 3 porosities, 8-bit nodes + FP64 re-test, 3 energies x 2 angles")
     ap.add_argument("--prec-nodes", choices=tuple(PREC_NODES), default="q4",
                     help="precision config: 8-bit node format (q4: 4-wide 64-byte nodes, q8: binary 32-byte)")
     ap.add_argument("--prec-oracle", type=int, default=64,
                     help="precision config: primaries per item checked against the oracle")
     args = ap.parse_args()
+    if args.ref_sample <= 0:
+        args.ref_sample = 9 if args.config == "large" else 256
+    if args.primaries <= 0 and args.config != "large":
+        args.primaries = N_PRIM
     if args.impl == "reference":
         run_reference(args)
     elif args.config == "large":

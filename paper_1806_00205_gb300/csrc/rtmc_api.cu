@@ -79,7 +79,9 @@ RunParams make_params(const DeviceMesh& m, const rtmc_run_desc& d, uint64_t seed
     p.seed = seed;
     p.item = item;
     p.energy = (float)energy;
-    p.theta_rad = (float)(theta_deg * kPi / 180.0);
+    // the FP32 direction nearest the exact one: sin and cos of the FP64 angle, rounded once
+    p.sin_t = (float)std::sin(theta_deg * kPi / 180.0);
+    p.cos_t = (float)std::cos(theta_deg * kPi / 180.0);
     p.random_azimuth = d.random_azimuth;
     p.random_polar = d.random_polar;
     const bool full = d.src_x0 == 0.0 && d.src_x1 == 0.0 && d.src_y0 == 0.0 && d.src_y1 == 0.0;

@@ -66,6 +66,37 @@ struct KernelTimer {
     }
 };
 
+// Chunks of one mesh's items over the item-major linear index of (item,
+// primary) pairs.  Generation 0 of a chunk whose items are all at normal
+// incidence (and no random polar angle) runs parallel to z through the column
+// grid; so that the others do not hold it back, the chunks are cut where that
+// property changes from one item to the next, then into pieces of at most
+// `chunk` pairs.
+struct BatchChunk {
+    int64_t g0;
+    unsigned n;
+    bool vertical;
+};
+
+std::vector<BatchChunk> batch_chunks(const rtmc_batch& b, const rtmc_run_desc& d, const rtmc::DeviceMesh& m,
+                                     int64_t chunk)
+{
+    const int64_t per_mesh = (int64_t)b.n_e * b.n_theta;
+    const bool can = d.traversal == 0 && !d.random_polar && m.col_ok;
+    auto vert = [&](int64_t item) { return can && b.theta_deg[item % b.n_theta] == 0.0; };
+    std::vector<BatchChunk> out;
+    int64_t i0 = 0;
+    while (i0 < per_mesh) {
+        int64_t i1 = i0 + 1;
+        while (i1 < per_mesh && vert(i1) == vert(i0)) ++i1;
+        const int64_t lo = i0 * b.n_primaries, hi = i1 * b.n_primaries;
+        for (int64_t g0 = lo; g0 < hi; g0 += chunk)
+            out.push_back({g0, (unsigned)std::min<int64_t>(chunk, hi - g0), vert(i0)});
+        i0 = i1;
+    }
+    return out;
+}
+
 // Record the launch sequence of the whole batch on `s`.
 cudaError_t record_batch(rtmc_ctx* ctx, const rtmc_batch& b, const rtmc_run_desc& d, const rtmc::Queues& q,
                          rtmc::ItemDev* d_items, rtmc::Tally* d_tallies, unsigned long long* d_hists,
@@ -79,21 +110,19 @@ cudaError_t record_batch(rtmc_ctx* ctx, const rtmc_batch& b, const rtmc_run_desc
     const TableDesc tab = make_table(ctx);
     const Emission em = make_emission(ctx->emission);
     const int64_t per_mesh = (int64_t)b.n_e * b.n_theta;
-    // generation 0 runs parallel to z when every item is at normal incidence
-    bool vertical = d.traversal == 0 && !d.random_polar;
-    for (int it = 0; it < b.n_theta; ++it) vertical = vertical && b.theta_deg[it] == 0.0;
     for (int mi = 0; mi < b.n_meshes && ce == cudaSuccess; ++mi) {
         const DeviceMesh& m = ctx->meshes[b.mesh_ids[mi]];
-        const bool columns = vertical && m.col_ok;
         const RunParams p = make_params(m, d, b.seed, 0u, 1.0, 0.0);
         ItemCtx ic;
         ic.items = d_items + mi * per_mesh;
         ic.n_per_item = (unsigned long long)b.n_primaries;
         ic.tallies = d_tallies;
         ic.hists = d_hists;
-        const int64_t total = per_mesh * b.n_primaries;
-        for (int64_t g0 = 0; g0 < total && ce == cudaSuccess; g0 += chunk) {
-            const unsigned n = (unsigned)std::min<int64_t>(chunk, total - g0);
+        for (const BatchChunk& c : batch_chunks(b, d, m, chunk)) {
+            if (ce != cudaSuccess) break;
+            const int64_t g0 = c.g0;
+            const unsigned n = c.n;
+            const bool columns = c.vertical;
             ic.g0 = (unsigned long long)g0;
             ic.it_lo = (unsigned)(g0 / b.n_primaries);
             ic.n_items = (unsigned)((g0 + n - 1) / b.n_primaries) - ic.it_lo + 1;
@@ -281,9 +310,8 @@ extern "C" int rtmc_run_batch(rtmc_ctx* ctx, const rtmc_batch* batch, const rtmc
                           (const void*)m.col_off, (const void*)m.col_ent, m.kind, (int)m.col_ok);
             key += buf;
         }
-        bool vertical = true;                             // the column grid is recorded for generation 0
-        for (int it = 0; it < batch->n_theta; ++it) vertical = vertical && batch->theta_deg[it] == 0.0;
-        key += vertical ? "|v1" : "|v0";
+        key += "|v";                                      // angles at which generation 0 takes the column grid
+        for (int it = 0; it < batch->n_theta; ++it) key += batch->theta_deg[it] == 0.0 ? '1' : '0';
         std::snprintf(buf, sizeof buf, "|cv%d|io%d|%p", d.count_visits, d.id_order, (const void*)ctx->delta);
         key += buf;
     }

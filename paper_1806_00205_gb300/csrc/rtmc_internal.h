@@ -132,7 +132,7 @@ int build_lbvh(rtmc_ctx* ctx, DeviceMesh& m);
 struct RunParams {
     unsigned long long seed = 0;
     unsigned item = 0;
-    float energy = 0.f, theta_rad = 0.f;
+    float energy = 0.f;
     int random_azimuth = 0;
     int random_polar = 0;        // 1: cosine-law polar angle of incidence (second Philox block, path 0)
     float src_x0 = 0.f, src_x1 = 0.f, src_y0 = 0.f, src_y1 = 0.f;
@@ -144,7 +144,7 @@ struct RunParams {
     float inv_abin = 0.f;        // bins per radian of polar angle
     float inv_zbin = 0.f;        // bins per nm of depth
     unsigned long long prim_offset = 0;
-    float sin_t = 0.f, cos_t = 1.f;   // incidence (single-item runs)
+    float sin_t = 0.f, cos_t = 1.f;   // incidence (single-item runs): the FP64 angle's sine and cosine, rounded once
 };
 
 struct Queues {

@@ -123,7 +123,8 @@ extern "C" int rtmc_run_noalloc(rtmc_ctx* ctx, int32_t mesh_id, double energy_ev
     p.seed = seed;
     p.item = item;
     p.energy = (float)energy_ev;
-    p.theta_rad = (float)(theta_deg * kPi / 180.0);
+    p.sin_t = (float)std::sin(theta_deg * kPi / 180.0);
+    p.cos_t = (float)std::cos(theta_deg * kPi / 180.0);
     p.random_azimuth = d.random_azimuth;
     p.random_polar = d.random_polar;
     const bool full = d.src_x0 == 0.0 && d.src_x1 == 0.0 && d.src_y0 == 0.0 && d.src_y1 == 0.0;

@@ -864,11 +864,9 @@ __global__ void k_philox(const uint4* __restrict__ ctr, int64_t n, unsigned long
 cudaError_t launch_generate(const RunParams& p, const Queues& q, int buf, unsigned long long first,
                             unsigned n, cudaStream_t s)
 {
-    const double th = (double)p.theta_rad;
     const int tb = 256;
     const unsigned gb = n ? (n + tb - 1) / tb : 1;
-    k_generate<<<gb, tb, 0, s>>>(p, (float)sin(th), (float)cos(th), first, n, q.oe[buf], q.dt[buf],
-                                 q.id[buf], q.ctl);
+    k_generate<<<gb, tb, 0, s>>>(p, p.sin_t, p.cos_t, first, n, q.oe[buf], q.dt[buf], q.id[buf], q.ctl);
     return cudaGetLastError();
 }
 
@@ -922,10 +920,7 @@ static cudaError_t generate_sorted(const RunParams& p, const ItemCtx& ic, const 
 cudaError_t launch_generate_sorted(const RunParams& p, const Queues& q, unsigned long long first, unsigned n,
                                    cudaStream_t s)
 {
-    RunParams pp = p;
-    pp.sin_t = (float)sin((double)p.theta_rad);
-    pp.cos_t = (float)cos((double)p.theta_rad);
-    return generate_sorted<false>(pp, ItemCtx{}, q, first, n, kSortCells, s);
+    return generate_sorted<false>(p, ItemCtx{}, q, first, n, kSortCells, s);
 }
 
 cudaError_t launch_generate_items_sorted(const RunParams& p, const ItemCtx& ic, const Queues& q, unsigned n,

@@ -68,9 +68,9 @@ def test_batch_fp64_retest_equals_plain_runs(setup):
     """The FP64 re-test decides each ambiguous facet against the best hit of its cell, so a
     ray's result does not depend on the launch: batched items equal plain runs with the
     re-test on, on binary FP32, Q8 and 4-wide meshes, and the batch's re-test count (a
-    batch total) is the sum of the plain runs'.  A batch with an oblique angle traces
-    every generation through the hierarchy, so the plain runs do too (traversal 2): the
-    count depends on which facets a path tests."""
+    batch total) is the sum of the plain runs'.  Both send the normal-incidence items'
+    primaries through the column grid and every other ray through the hierarchy (the
+    count depends on which facets a path tests)."""
     ctx, ids, rtmc = setup
     energies, thetas, n = [120.0, 600.0], [0.0, 70.0], 40_000
     res, he, _ = ctx.run_batch(ids, energies, thetas, n, 13, desc=rtmc.run_desc(fp64_retest=True, chunk=70_000))
@@ -78,7 +78,7 @@ def test_batch_fp64_retest_equals_plain_runs(setup):
     total = 0
     for mi, mid in enumerate(ids):
         plain, phe, _ = ctx.run(mid, energies, thetas, n, 13,
-                                desc=rtmc.run_desc(fp64_retest=True, item_base=mi * per_mesh, traversal=2))
+                                desc=rtmc.run_desc(fp64_retest=True, item_base=mi * per_mesh))
         total += sum(r["retested"] for r in plain)
         for j in range(per_mesh):
             b = res[mi * per_mesh + j]
@@ -110,6 +110,25 @@ def test_batch_rejects_what_it_cannot_do(setup):
         ctx.run_batch([12345], [300.0], [0.0], 10, 1)
     with pytest.raises(rtmc.RtmcError):
         ctx.run_batch(ids, [300.0], [95.0], 10, 1)
+
+
+def test_batch_column_grid_for_normal_incidence_items_only(setup):
+    """In a batch that mixes angles, the chunks of the normal-incidence items take the
+    column grid for their primaries and the others the hierarchy; every item keeps the
+    tallies of its plain run."""
+    ctx, ids, rtmc = setup
+    energies, thetas, n = [200.0, 650.0], [0.0, 30.0, 0.0, 60.0], 12_000
+    res, he, _ = ctx.run_batch(ids, energies, thetas, n, 41, desc=rtmc.run_desc(chunk=20_000))
+    per_mesh = len(energies) * len(thetas)
+    n_vertical = sum(1 for t in thetas if t == 0.0) * len(energies)
+    assert res[0]["column_rays"] == len(ids) * n_vertical * n
+    for mi, mid in enumerate(ids):
+        plain, phe, _ = ctx.run(mid, energies, thetas, n, 41, desc=rtmc.run_desc(item_base=mi * per_mesh))
+        for j in range(per_mesh):
+            b = res[mi * per_mesh + j]
+            for k in INT_KEYS:
+                assert b[k] == plain[j][k], (mi, j, k, b[k], plain[j][k])
+            assert np.array_equal(he[mi * per_mesh + j], phe[j])
 
 
 def test_batch_graph_follows_angles_and_rebuilds(setup):
@@ -169,3 +188,17 @@ def test_batch_deeper_trees_equal_plain_runs(model):
                 assert deep > 0
             for mid in ids:
                 c.unload_mesh(mid)
+
+
+def test_batch_equals_plain_runs_at_oblique_angles_at_scale(setup):
+    """1e6 primaries per angle at nine angles: the batched and the plain path give each
+    item identical tallies (both take the incidence direction as the FP64 angle's sine
+    and cosine rounded once to FP32, the direction nearest the oracle's)."""
+    ctx, ids, rtmc = setup
+    thetas = [10.0 * j for j in range(9)]
+    res, he, ha = ctx.run_batch([ids[3]], [500.0], thetas, 1_000_000, 1806)
+    plain, phe, pha = ctx.run(ids[3], [500.0], thetas, 1_000_000, 1806)
+    for j in range(len(thetas)):
+        for k in INT_KEYS:
+            assert res[j][k] == plain[j][k], (j, k, res[j][k], plain[j][k])
+    assert np.array_equal(he, phe) and np.array_equal(ha, pha)
