@@ -292,7 +292,11 @@ int rtmc_trace_rays(rtmc_ctx* ctx, int32_t mesh_id, const float* o, const float*
                     const int32_t* skip_tri, int64_t n, rtmc_hit* hits);
 
 /* Copy a built BVH to host memory for inspection: which = 0 FP32 nodes
-   (n_nodes x 64 B), 1 Q8 nodes (n_nodes x 32 B, RTMC_BVH_Q8 meshes only),
+   (n_nodes x 64 B; every child box widened outward by M 2^-22, M the
+   largest coordinate of the cell, so that a ray with a zero direction
+   component lying in a face plane of the exact box is still inside it),
+   1 Q8 nodes (n_nodes x 32 B, RTMC_BVH_Q8 meshes only; the widened boxes,
+   quantised outward),
    2 triangles in leaf order (n_tri x 48 B), 3 4-wide nodes (RTMC_BVH_W4
    meshes only, n_w4 x 128 B: rows lo.x, hi.x, lo.y, hi.y, lo.z, hi.z of the
    four child boxes, each widened outward by M 2^-22 with M the largest

@@ -220,8 +220,13 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
 
     const RunParams p = make_params(m, d, seed, item, energy, theta_deg);
     const TableDesc tab = make_table(ctx);
-    // generation 0 at normal incidence runs parallel to z: the column grid
+    // generation 0 at normal incidence runs parallel to z: the column grid;
+    // at a fixed oblique incidence (azimuth 0) the slanted grid of that direction
     const bool columns = m.col_ok && d.traversal == 0 && theta_deg == 0.0 && !d.random_polar;
+    GridDev slant{};
+    const bool slanted = !columns && m.col_ok && d.traversal == 0 && !d.random_polar && !d.random_azimuth &&
+                         !d.fp64_retest && theta_deg > 0.0 && n_prim > 0 &&
+                         slant_grid(ctx, m, p.sin_t, -p.cos_t, slant);
     const Emission e = make_emission(em);
 
     // Queue capacities: buffer 0 holds even generations, buffer 1 odd ones,
@@ -258,6 +263,9 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
         if (ce == cudaSuccess) ce = scratch_reserve(ctx->tally, sizeof(Tally));
         if (ce == cudaSuccess) ce = scratch_reserve(ctx->hist, (size_t)(d.n_ebins + d.n_abins + d.n_zbins) * 8);
         if (ce == cudaSuccess && record) ce = scratch_reserve(ctx->records, (size_t)std::max<int64_t>(o.rec_cap, 1) * sizeof(rtmc_record));
+        if (ce == cudaSuccess && slanted) ce = scratch_reserve(ctx->grids, sizeof(GridDev));
+        if (ce == cudaSuccess && slanted)
+            ce = cudaMemcpyAsync(ctx->grids.ptr, &slant, sizeof(GridDev), cudaMemcpyHostToDevice, s);
         if (ce != cudaSuccess) return ctx->fail(RTMC_ERR_OOM, std::string("run: scratch: ") + cudaGetErrorString(ce));
 
         Queues q;
@@ -311,11 +319,16 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
             launches += d.id_order ? 1 : 4;      // sorted: count, scan, scatter, write
             for (int g = 0; g <= em.max_generation && ce == cudaSuccess; ++g) {
                 const int buf = g & 1;
-                const bool col = columns && g == 0;
+                const bool col = (columns || slanted) && g == 0;
                 h = tick(col ? 4 : 1);
-                ce = col ? launch_columns(m, p, q, buf, g, ctx->num_sms, need_wraps, d.fp64_retest != 0, s)
-                         : launch_traverse(m, p, q, buf, g, ctx->num_sms, tune, need_wraps, d.count_visits != 0,
-                                           d.fp64_retest != 0, s);
+                if (columns && g == 0)
+                    ce = launch_columns(m, p, q, buf, g, ctx->num_sms, need_wraps, d.fp64_retest != 0, s);
+                else if (slanted && g == 0)
+                    ce = launch_slant(m, p, (const GridDev*)ctx->grids.ptr, false, q, buf, g, ctx->num_sms,
+                                      need_wraps, s);
+                else
+                    ce = launch_traverse(m, p, q, buf, g, ctx->num_sms, tune, need_wraps, d.count_visits != 0,
+                                         d.fp64_retest != 0, s);
                 tock(h);
                 h = tick(2);
                 if (ce == cudaSuccess)
@@ -472,7 +485,7 @@ void rtmc_destroy(rtmc_ctx* ctx)
     rtmc::Scratch* all[] = {&ctx->q_oe[0], &ctx->q_oe[1], &ctx->q_dt[0], &ctx->q_dt[1], &ctx->q_id[0],
                             &ctx->q_id[1], &ctx->hits, &ctx->kcount, &ctx->ctl, &ctx->tally, &ctx->hist,
                             &ctx->wraps, &ctx->records, &ctx->tmp, &ctx->items,
-                            &ctx->sort_counts};
+                            &ctx->sort_counts, &ctx->grids};
     for (auto* s : all) rtmc::scratch_free(*s);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;

@@ -67,31 +67,40 @@ struct KernelTimer {
 };
 
 // Chunks of one mesh's items over the item-major linear index of (item,
-// primary) pairs.  Generation 0 of a chunk whose items are all at normal
-// incidence (and no random polar angle) runs parallel to z through the column
-// grid; so that the others do not hold it back, the chunks are cut where that
-// property changes from one item to the next, then into pieces of at most
-// `chunk` pairs.
+// primary) pairs.  Generation 0 of an item at normal incidence can run parallel
+// to z through the column grid, one at a fixed oblique incidence through the
+// slanted grid of its direction (class 1 and 2; class 0: the hierarchy).  A
+// chunk whose items all have a grid traces generation 0 through the grids (the
+// vertical kernel when all are at normal incidence), else through the
+// hierarchy; so that neither holds the other back, the chunks are cut where an
+// item without a grid follows one with a grid or the reverse, then into pieces
+// of at most `chunk` pairs.
 struct BatchChunk {
     int64_t g0;
     unsigned n;
-    bool vertical;
+    int method;          // generation 0: 0 hierarchy, 1 vertical column grid, 2 per-item grids
 };
 
-std::vector<BatchChunk> batch_chunks(const rtmc_batch& b, const rtmc_run_desc& d, const rtmc::DeviceMesh& m,
-                                     int64_t chunk)
+std::vector<BatchChunk> batch_chunks(const rtmc_batch& b, const int* cls, int64_t chunk)
 {
     const int64_t per_mesh = (int64_t)b.n_e * b.n_theta;
-    const bool can = d.traversal == 0 && !d.random_polar && m.col_ok;
-    auto vert = [&](int64_t item) { return can && b.theta_deg[item % b.n_theta] == 0.0; };
     std::vector<BatchChunk> out;
     int64_t i0 = 0;
     while (i0 < per_mesh) {
+        const bool grid = cls[i0] != 0;
         int64_t i1 = i0 + 1;
-        while (i1 < per_mesh && vert(i1) == vert(i0)) ++i1;
+        while (i1 < per_mesh && (cls[i1] != 0) == grid) ++i1;
         const int64_t lo = i0 * b.n_primaries, hi = i1 * b.n_primaries;
-        for (int64_t g0 = lo; g0 < hi; g0 += chunk)
-            out.push_back({g0, (unsigned)std::min<int64_t>(chunk, hi - g0), vert(i0)});
+        for (int64_t g0 = lo; g0 < hi; g0 += chunk) {
+            const unsigned n = (unsigned)std::min<int64_t>(chunk, hi - g0);
+            int method = 0;
+            if (grid && n > 0) {
+                const int64_t a = g0 / b.n_primaries, z = (g0 + n - 1) / b.n_primaries;
+                method = 1;
+                for (int64_t it = a; it <= z; ++it) if (cls[it] != 1) method = 2;
+            }
+            out.push_back({g0, n, method});
+        }
         i0 = i1;
     }
     return out;
@@ -100,6 +109,7 @@ std::vector<BatchChunk> batch_chunks(const rtmc_batch& b, const rtmc_run_desc& d
 // Record the launch sequence of the whole batch on `s`.
 cudaError_t record_batch(rtmc_ctx* ctx, const rtmc_batch& b, const rtmc_run_desc& d, const rtmc::Queues& q,
                          rtmc::ItemDev* d_items, rtmc::Tally* d_tallies, unsigned long long* d_hists,
+                         const std::vector<int>& cls, const rtmc::GridDev* d_grids,
                          int64_t chunk, const rtmc::Tuning& tune, int64_t n_items, cudaStream_t s,
                          KernelTimer& kt, int64_t& launches)
 {
@@ -118,11 +128,10 @@ cudaError_t record_batch(rtmc_ctx* ctx, const rtmc_batch& b, const rtmc_run_desc
         ic.n_per_item = (unsigned long long)b.n_primaries;
         ic.tallies = d_tallies;
         ic.hists = d_hists;
-        for (const BatchChunk& c : batch_chunks(b, d, m, chunk)) {
+        for (const BatchChunk& c : batch_chunks(b, cls.data() + mi * per_mesh, chunk)) {
             if (ce != cudaSuccess) break;
             const int64_t g0 = c.g0;
             const unsigned n = c.n;
-            const bool columns = c.vertical;
             ic.g0 = (unsigned long long)g0;
             ic.it_lo = (unsigned)(g0 / b.n_primaries);
             ic.n_items = (unsigned)((g0 + n - 1) / b.n_primaries) - ic.it_lo + 1;
@@ -137,11 +146,15 @@ cudaError_t record_batch(rtmc_ctx* ctx, const rtmc_batch& b, const rtmc_run_desc
             launches += sorted ? 4 : 1;          // sorted: count, scan, scatter, write
             for (int g = 0; g <= ctx->emission.max_generation && ce == cudaSuccess; ++g) {
                 const int buf = g & 1;
-                const bool col = columns && g == 0;
-                h = kt.tick(col ? 4 : 1, s);
-                ce = col ? launch_columns(m, p, qq, buf, g, ctx->num_sms, true, d.fp64_retest != 0, s)
-                         : launch_traverse(m, p, qq, buf, g, ctx->num_sms, tune, true, d.count_visits != 0,
-                                           d.fp64_retest != 0, s);
+                const int method = g == 0 ? c.method : 0;
+                h = kt.tick(method ? 4 : 1, s);
+                if (method == 1)
+                    ce = launch_columns(m, p, qq, buf, g, ctx->num_sms, true, d.fp64_retest != 0, s);
+                else if (method == 2)
+                    ce = launch_slant(m, p, d_grids + mi * per_mesh, true, qq, buf, g, ctx->num_sms, true, s);
+                else
+                    ce = launch_traverse(m, p, qq, buf, g, ctx->num_sms, tune, true, d.count_visits != 0,
+                                         d.fp64_retest != 0, s);
                 kt.tock(h, s);
                 h = kt.tick(2, s);
                 if (ce == cudaSuccess) ce = launch_shade_items(m, p, tab, em, ic, qq, buf, g, ctx->num_sms, s);
@@ -218,6 +231,26 @@ extern "C" int rtmc_run_batch(rtmc_ctx* ctx, const rtmc_batch* batch, const rtmc
                 x.pad = 0;
             }
 
+    // generation 0 of each item: the column grid (normal incidence), the slanted
+    // grid of its direction (fixed oblique incidence), or the hierarchy; slanted
+    // grids are built here, before any capture
+    std::vector<int> cls((size_t)n_items, 0);
+    std::vector<GridDev> gdev((size_t)n_items);
+    for (int mi = 0; mi < batch->n_meshes; ++mi) {
+        DeviceMesh& m = ctx->meshes[batch->mesh_ids[mi]];
+        if (d.traversal != 0 || d.random_polar || !m.col_ok) continue;
+        for (int64_t j = 0; j < per_mesh; ++j) {
+            const int64_t k = mi * per_mesh + j;
+            const ItemDev& x = items[(size_t)k];
+            if (batch->theta_deg[j % batch->n_theta] == 0.0) {
+                cls[(size_t)k] = 1;
+                gdev[(size_t)k] = grid_dev(m, nullptr);
+            } else if (!d.random_azimuth && !d.fp64_retest && slant_grid(ctx, m, x.sin_t, -x.cos_t, gdev[(size_t)k])) {
+                cls[(size_t)k] = 2;
+            }
+        }
+    }
+
     // scratch: queues for one chunk, sized from the expected yield as in rtmc_run;
     // an overflow records the batch again with doubled capacities
     int64_t chunk = d.chunk > 0 ? d.chunk : ((int64_t)1 << 23);
@@ -240,10 +273,10 @@ extern "C" int rtmc_run_batch(rtmc_ctx* ctx, const rtmc_batch* batch, const rtmc
         return ctx->fail(RTMC_ERR_CAPACITY, "run_batch: queue capacity exceeds 2^32 rays; lower chunk");
     const int64_t capmax = std::max(cap0, cap1);
     cudaError_t ce = cudaSuccess;
-    const void* before[14] = {ctx->q_oe[0].ptr, ctx->q_oe[1].ptr, ctx->q_dt[0].ptr, ctx->q_dt[1].ptr,
+    const void* before[15] = {ctx->q_oe[0].ptr, ctx->q_oe[1].ptr, ctx->q_dt[0].ptr, ctx->q_dt[1].ptr,
                               ctx->q_id[0].ptr, ctx->q_id[1].ptr, ctx->hits.ptr, ctx->kcount.ptr,
                               ctx->ctl.ptr, ctx->tally.ptr, ctx->hist.ptr, ctx->items.ptr, ctx->wraps.ptr,
-                              ctx->sort_counts.ptr};
+                              ctx->sort_counts.ptr, ctx->grids.ptr};
     for (int bb = 0; bb < 2 && ce == cudaSuccess; ++bb) {
         const int64_t c = bb ? cap1 : cap0;
         ce = scratch_reserve(ctx->q_oe[bb], (size_t)c * 16);
@@ -261,11 +294,12 @@ extern "C" int rtmc_run_batch(rtmc_ctx* ctx, const rtmc_batch* batch, const rtmc
     if (ce == cudaSuccess) ce = scratch_reserve(ctx->items, (size_t)n_items * sizeof(ItemDev));
     if (ce == cudaSuccess && !d.id_order)
         ce = scratch_reserve(ctx->sort_counts, (size_t)kChunkItems * kSortBucketsPerItem * 4);
+    if (ce == cudaSuccess) ce = scratch_reserve(ctx->grids, (size_t)n_items * sizeof(GridDev));
     if (ce != cudaSuccess) return ctx->fail(RTMC_ERR_OOM, std::string("run_batch: scratch: ") + cudaGetErrorString(ce));
-    const void* after[14] = {ctx->q_oe[0].ptr, ctx->q_oe[1].ptr, ctx->q_dt[0].ptr, ctx->q_dt[1].ptr,
+    const void* after[15] = {ctx->q_oe[0].ptr, ctx->q_oe[1].ptr, ctx->q_dt[0].ptr, ctx->q_dt[1].ptr,
                              ctx->q_id[0].ptr, ctx->q_id[1].ptr, ctx->hits.ptr, ctx->kcount.ptr,
                              ctx->ctl.ptr, ctx->tally.ptr, ctx->hist.ptr, ctx->items.ptr, ctx->wraps.ptr,
-                             ctx->sort_counts.ptr};
+                             ctx->sort_counts.ptr, ctx->grids.ptr};
     const bool moved = std::memcmp(before, after, sizeof before) != 0;
 
     Queues q;
@@ -289,6 +323,9 @@ extern "C" int rtmc_run_batch(rtmc_ctx* ctx, const rtmc_batch* batch, const rtmc
     q.rec_cap = 0;
 
     ce = cudaMemcpyAsync(ctx->items.ptr, items.data(), items.size() * sizeof(ItemDev), cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(ctx->grids.ptr, gdev.data(), gdev.size() * sizeof(GridDev), cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);     // the host copies of the tables go out of scope
     if (ce != cudaSuccess) return ctx->fail(RTMC_ERR_CUDA, std::string("run_batch: ") + cudaGetErrorString(ce));
 
     // graph key: everything the recorded launch parameters depend on
@@ -310,8 +347,11 @@ extern "C" int rtmc_run_batch(rtmc_ctx* ctx, const rtmc_batch* batch, const rtmc
                           (const void*)m.col_off, (const void*)m.col_ent, m.kind, (int)m.col_ok);
             key += buf;
         }
-        key += "|v";                                      // angles at which generation 0 takes the column grid
-        for (int it = 0; it < batch->n_theta; ++it) key += batch->theta_deg[it] == 0.0 ? '1' : '0';
+        key += "|g";                                      // which grid generation 0 of each item takes
+        for (size_t k = 0; k < cls.size(); ++k) {
+            std::snprintf(buf, sizeof buf, "%d:%p,", cls[k], cls[k] ? (const void*)gdev[k].ent : nullptr);
+            key += buf;
+        }
         std::snprintf(buf, sizeof buf, "|cv%d|io%d|%p", d.count_visits, d.id_order, (const void*)ctx->delta);
         key += buf;
     }
@@ -330,7 +370,8 @@ extern "C" int rtmc_run_batch(rtmc_ctx* ctx, const rtmc_batch* batch, const rtmc
     cudaEventRecord(ev0, s);
     if (d.no_graph) {
         ce = record_batch(ctx, *batch, d, q, (ItemDev*)ctx->items.ptr, (Tally*)ctx->tally.ptr,
-                          (unsigned long long*)ctx->hist.ptr, chunk, tune, n_items, s, kt, launches);
+                          (unsigned long long*)ctx->hist.ptr, cls, (const GridDev*)ctx->grids.ptr, chunk, tune,
+                          n_items, s, kt, launches);
     } else {
         if (!ctx->batch_graph) {
             cudaGraph_t graph = nullptr;
@@ -339,7 +380,8 @@ extern "C" int rtmc_run_batch(rtmc_ctx* ctx, const rtmc_batch* batch, const rtmc
                 KernelTimer none;
                 const cudaError_t rec = record_batch(ctx, *batch, d, q, (ItemDev*)ctx->items.ptr,
                                                      (Tally*)ctx->tally.ptr, (unsigned long long*)ctx->hist.ptr,
-                                                     chunk, tune, n_items, s, none, ctx->batch_launches);
+                                                     cls, (const GridDev*)ctx->grids.ptr, chunk, tune, n_items, s,
+                                                     none, ctx->batch_launches);
                 ce = cudaStreamEndCapture(s, &graph);
                 if (ce == cudaSuccess) ce = rec;
             }

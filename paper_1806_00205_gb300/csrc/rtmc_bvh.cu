@@ -191,6 +191,20 @@ __global__ void k_karras(const unsigned* __restrict__ keys, int n, int2* __restr
 
 struct Box3 { float3 lo, hi; };
 
+// A box widened outward by m on every face, rounded outward.  Every stored
+// child box carries m = M 2^-22 (M the largest cell coordinate): the 4-wide
+// slab test evaluates planes with one FMA and relies on it, and for every
+// format it keeps a ray with a zero direction component that lies in a face
+// plane of a box inside the box (a slab test of such a ray sees the face at
+// distance 0 and would reject the box).
+__device__ __forceinline__ Box3 widen(const Box3& b, float m)
+{
+    Box3 w;
+    w.lo = make_float3(__fsub_rd(b.lo.x, m), __fsub_rd(b.lo.y, m), __fsub_rd(b.lo.z, m));
+    w.hi = make_float3(__fadd_ru(b.hi.x, m), __fadd_ru(b.hi.y, m), __fadd_ru(b.hi.z, m));
+    return w;
+}
+
 __device__ __forceinline__ Box3 tri_box(const float* __restrict__ tri, unsigned t)
 {
     const float* p = tri + 9ll * t;
@@ -230,7 +244,7 @@ __global__ void k_refit(const float* __restrict__ tri, const unsigned* __restric
                         const int2* __restrict__ child, const int2* __restrict__ range,
                         const int* __restrict__ parent, const int* __restrict__ leaf_parent,
                         unsigned* __restrict__ flag, float4* __restrict__ aabb, float4* __restrict__ nodes,
-                        int leaf_max)
+                        int leaf_max, float margin)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
@@ -251,7 +265,8 @@ __global__ void k_refit(const float* __restrict__ tri, const unsigned* __restric
                 b[s].hi = make_float3(hi.x, hi.y, hi.z);
             }
         }
-        store_node(nodes, node, b[0], b[1], child_ref(c.x, range, leaf_max), child_ref(c.y, range, leaf_max));
+        store_node(nodes, node, widen(b[0], margin), widen(b[1], margin), child_ref(c.x, range, leaf_max),
+                   child_ref(c.y, range, leaf_max));
         __stcg(aabb + 2ll * node, make_float4(fminf(b[0].lo.x, b[1].lo.x), fminf(b[0].lo.y, b[1].lo.y),
                                               fminf(b[0].lo.z, b[1].lo.z), 0.f));
         __stcg(aabb + 2ll * node + 1, make_float4(fmaxf(b[0].hi.x, b[1].hi.x), fmaxf(b[0].hi.y, b[1].hi.y),
@@ -263,9 +278,9 @@ __global__ void k_refit(const float* __restrict__ tri, const unsigned* __restric
 
 // A one-triangle mesh: the root's two children are the same leaf (the repeat
 // test cannot change the closest hit).
-__global__ void k_single_leaf(const float* __restrict__ tri, float4* __restrict__ nodes)
+__global__ void k_single_leaf(const float* __restrict__ tri, float4* __restrict__ nodes, float margin)
 {
-    const Box3 b = tri_box(tri, 0);
+    const Box3 b = widen(tri_box(tri, 0), margin);
     store_node(nodes, 0, b, b, ~0, ~0);
 }
 
@@ -319,10 +334,10 @@ __device__ unsigned quant_hi(float v, float o_shift, float sc)
 
 __device__ void child_info(int raw, const float* __restrict__ tri, const unsigned* __restrict__ order,
                            const int2* __restrict__ range, const float4* __restrict__ aabb, int leaf_max,
-                           Box3& b, bool& leaf, int& count)
+                           float margin, Box3& b, bool& leaf, int& count)
 {
     if (raw < 0) {
-        b = tri_box(tri, order[~raw]);
+        b = widen(tri_box(tri, order[~raw]), margin);
         leaf = true;
         count = 1;
         return;
@@ -330,6 +345,7 @@ __device__ void child_info(int raw, const float* __restrict__ tri, const unsigne
     const float4 lo = __ldcg(aabb + 2ll * raw), hi = __ldcg(aabb + 2ll * raw + 1);
     b.lo = make_float3(lo.x, lo.y, lo.z);
     b.hi = make_float3(hi.x, hi.y, hi.z);
+    b = widen(b, margin);
     const int2 r = range[raw];
     count = r.y - r.x + 1;
     leaf = count <= leaf_max;
@@ -337,7 +353,7 @@ __device__ void child_info(int raw, const float* __restrict__ tri, const unsigne
 
 __global__ void k_quantize(const float* __restrict__ tri, const unsigned* __restrict__ order, int n_inner,
                            const int2* __restrict__ child, const int2* __restrict__ range,
-                           const float4* __restrict__ aabb, int leaf_max, uint4* __restrict__ q8)
+                           const float4* __restrict__ aabb, int leaf_max, float margin, uint4* __restrict__ q8)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_inner) return;
@@ -345,8 +361,8 @@ __global__ void k_quantize(const float* __restrict__ tri, const unsigned* __rest
     Box3 b[2];
     bool leaf[2];
     int count[2];
-    child_info(c.x, tri, order, range, aabb, leaf_max, b[0], leaf[0], count[0]);
-    child_info(c.y, tri, order, range, aabb, leaf_max, b[1], leaf[1], count[1]);
+    child_info(c.x, tri, order, range, aabb, leaf_max, margin, b[0], leaf[0], count[0]);
+    child_info(c.y, tri, order, range, aabb, leaf_max, margin, b[1], leaf[1], count[1]);
     const int gamma = c.x < 0 ? ~c.x : c.x;
     const float3 plo = make_float3(fminf(b[0].lo.x, b[1].lo.x), fminf(b[0].lo.y, b[1].lo.y), fminf(b[0].lo.z, b[1].lo.z));
     const float3 phi = make_float3(fmaxf(b[0].hi.x, b[1].hi.x), fmaxf(b[0].hi.y, b[1].hi.y), fmaxf(b[0].hi.z, b[1].hi.z));
@@ -374,9 +390,9 @@ __global__ void k_quantize(const float* __restrict__ tri, const unsigned* __rest
 
 // One-triangle mesh in Q8 form: left leaf = triangle 0, right leaf = the
 // degenerate padding triangle 1 (never hit).
-__global__ void k_quantize_single(const float* __restrict__ tri, uint4* __restrict__ q8)
+__global__ void k_quantize_single(const float* __restrict__ tri, float margin, uint4* __restrict__ q8)
 {
-    const Box3 b = tri_box(tri, 0);
+    const Box3 b = widen(tri_box(tri, 0), margin);
     const int ex = frame_exponent(b.lo.x, b.hi.x), ey = frame_exponent(b.lo.y, b.hi.y), ez = frame_exponent(b.lo.z, b.hi.z);
     const unsigned meta = 1u | 16u;
     const unsigned packed = (unsigned)(ex + 127) | ((unsigned)(ey + 127) << 8) | ((unsigned)(ez + 127) << 16) |
@@ -749,16 +765,6 @@ __device__ __forceinline__ void w4_store(float4* __restrict__ w4, int w, const B
     nd[7] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-// A box widened outward by m on every face, rounded outward (the 4-wide slab
-// test evaluates planes with one FMA and relies on this margin).
-__device__ __forceinline__ Box3 widen(const Box3& b, float m)
-{
-    Box3 w;
-    w.lo = make_float3(__fsub_rd(b.lo.x, m), __fsub_rd(b.lo.y, m), __fsub_rd(b.lo.z, m));
-    w.hi = make_float3(__fadd_ru(b.hi.x, m), __fadd_ru(b.hi.y, m), __fadd_ru(b.hi.z, m));
-    return w;
-}
-
 __global__ void k_w4_emit(const int2* __restrict__ front, int nf, const int* __restrict__ off, int base,
                           const int2* __restrict__ child, const int2* __restrict__ range,
                           const float4* __restrict__ aabb, const float* __restrict__ tri,
@@ -977,6 +983,94 @@ __global__ void __launch_bounds__(128) k_col_sort(const int* __restrict__ off, u
     for (int i = threadIdx.x; i < L; i += blockDim.x) ent[b + i] = col_unkey(key[i]);
 }
 
+// ---- slanted column grid ---------------------------------------------------
+// Rays of direction (dx, 0, dz), dz < 0, entering through z_top at x0 reach the
+// point (x, y, z) of the unwrapped line when x0 = x - (z_top - z) dx / |dz| + k lx
+// for the image k (the lateral wraps before that point).  A facet's footprint
+// is its vertices' sheared x' = x - (z_top - z) s, s = dx / |dz|, and y; it is
+// listed, with k, in every pixel its footprint shifted by k lx meets inside
+// [0, lx), for every k >= 0 that does.  The bounds are taken in FP64, widened
+// by `margin` (a bound on how far FP32 rounding moves the traced ray from the
+// exact line) and rounded outward to FP32 before the monotonic pixel floor.
+constexpr int kSlantMaxImages = 255;         // wraps a ray may make before its hit in a listed entry
+
+struct SlantSpan {
+    int k0, k1, y0, y1;
+    double lo, hi;      // sheared x' range, widened
+};
+
+__device__ __forceinline__ SlantSpan slant_span(const float4* __restrict__ tris, int j, double lx, double z_top,
+                                               double shear, double margin, int gy, float iwy, float& ztop)
+{
+    const float4 a = tris[3ll * j], b = tris[3ll * j + 1], c = tris[3ll * j + 2];
+    const double xa = (double)a.x - (z_top - (double)a.z) * shear;
+    const double xb = (double)b.x - (z_top - (double)b.z) * shear;
+    const double xc = (double)c.x - (z_top - (double)c.z) * shear;
+    SlantSpan sp;
+    sp.lo = fmin(xa, fmin(xb, xc)) - margin;
+    sp.hi = fmax(xa, fmax(xb, xc)) + margin;
+    sp.k0 = max(0, (int)ceil(-sp.hi / lx));              // images whose shifted footprint reaches [0, lx)
+    sp.k1 = (int)ceil((lx - sp.lo) / lx) - 1;
+    const float loy = __double2float_rd((double)fminf(a.y, fminf(b.y, c.y)) - margin);
+    const float hiy = __double2float_ru((double)fmaxf(a.y, fmaxf(b.y, c.y)) + margin);
+    sp.y0 = min(max((int)floorf(loy * iwy), 0), gy - 1);
+    sp.y1 = min(max((int)floorf(hiy * iwy), 0), gy - 1);
+    ztop = fmaxf(a.z, fmaxf(b.z, c.z));
+    return sp;
+}
+
+__device__ __forceinline__ void slant_xrange(const SlantSpan& sp, int k, double lx, int gx, float iwx, int& x0,
+                                             int& x1)
+{
+    const float lo = __double2float_rd(fmax(sp.lo + k * lx, 0.0));
+    const float hi = __double2float_ru(fmin(sp.hi + k * lx, lx));
+    x0 = min(max((int)floorf(lo * iwx), 0), gx - 1);
+    x1 = min(max((int)floorf(hi * iwx), 0), gx - 1);
+}
+
+__global__ void k_slant_count(const float4* __restrict__ tris, int n, int gx, int gy, float iwx, float iwy, double lx,
+                              double z_top, double shear, double margin, int* __restrict__ cnt, int* __restrict__ bad)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    float zt;
+    const SlantSpan sp = slant_span(tris, j, lx, z_top, shear, margin, gy, iwy, zt);
+    if (sp.k1 > kSlantMaxImages) { atomicOr(bad, 4); return; }
+    int total = 0;
+    for (int k = sp.k0; k <= sp.k1; ++k) {
+        int x0, x1;
+        slant_xrange(sp, k, lx, gx, iwx, x0, x1);
+        total += (x1 - x0 + 1) * (sp.y1 - sp.y0 + 1);
+    }
+    if (total > 4 * kColMaxSpan) { atomicOr(bad, 1); return; }
+    for (int k = sp.k0; k <= sp.k1; ++k) {
+        int x0, x1;
+        slant_xrange(sp, k, lx, gx, iwx, x0, x1);
+        for (int y = sp.y0; y <= sp.y1; ++y)
+            for (int x = x0; x <= x1; ++x) atomicAdd(&cnt[y * gx + x], 1);
+    }
+}
+
+__global__ void k_slant_fill(const float4* __restrict__ tris, int n, int gx, int gy, float iwx, float iwy, double lx,
+                             double z_top, double shear, double margin, int* __restrict__ cursor,
+                             uint2* __restrict__ ent)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    float zt;
+    const SlantSpan sp = slant_span(tris, j, lx, z_top, shear, margin, gy, iwy, zt);
+    if (sp.k1 > kSlantMaxImages) return;
+    for (int k = sp.k0; k <= sp.k1; ++k) {
+        int x0, x1;
+        slant_xrange(sp, k, lx, gx, iwx, x0, x1);
+        for (int y = sp.y0; y <= sp.y1; ++y)
+            for (int x = x0; x <= x1; ++x) {
+                const int slot = atomicAdd(&cursor[y * gx + x], 1);
+                ent[slot] = make_uint2((unsigned)j | ((unsigned)k << kSlantFacetBits), __float_as_uint(zt));
+            }
+    }
+}
+
 struct DevBuf {
     void* p = nullptr;
     ~DevBuf() { if (p) cudaFree(p); }
@@ -1037,7 +1131,7 @@ int build_lbvh(rtmc_ctx* ctx, DeviceMesh& m)
     if (e != cudaSuccess) return ctx->fail(RTMC_ERR_OOM, std::string("build_bvh scratch: ") + cudaGetErrorString(e));
 
     const rtmc_box& bx = m.box;
-    // outward margin of every 4-wide box: M 2^-22, M the largest coordinate a
+    // outward margin of every stored child box (all node formats): M 2^-22, M the largest coordinate a
     // ray origin in the cell can have (the FMA slab test's o * inv rounding moves
     // a plane by at most |o| 2^-24)
     const double big = std::max(std::max(std::fabs(bx.lx), std::fabs(bx.ly)),
@@ -1121,8 +1215,8 @@ int build_lbvh(rtmc_ctx* ctx, DeviceMesh& m)
         order = ord.as<unsigned>();
     }
     if (n == 1) {
-        k_single_leaf<<<1, 1, 0, s>>>(m.tri_in, m.nodes);
-        if (m.kind == FMT_Q8) k_quantize_single<<<1, 1, 0, s>>>(m.tri_in, reinterpret_cast<uint4*>(m.q8));
+        k_single_leaf<<<1, 1, 0, s>>>(m.tri_in, m.nodes, w4_margin);
+        if (m.kind == FMT_Q8) k_quantize_single<<<1, 1, 0, s>>>(m.tri_in, w4_margin, reinterpret_cast<uint4*>(m.q8));
         if (wide) {
             k_w4_single<<<1, 1, 0, s>>>(m.tri_in, w4_margin, reinterpret_cast<float4*>(m.w4));
             m.n_w4 = 1;
@@ -1136,11 +1230,12 @@ int build_lbvh(rtmc_ctx* ctx, DeviceMesh& m)
         if (!m.ploc)
             k_karras<<<gi, tb, 0, s>>>(ki, n, child.as<int2>(), range.as<int2>(), parent.as<int>(), leafp.as<int>());
         k_refit<<<gb, tb, 0, s>>>(m.tri_in, order, n, child.as<int2>(), range.as<int2>(), parent.as<int>(),
-                                  leafp.as<int>(), flag.as<unsigned>(), aabb.as<float4>(), m.nodes, m.leaf_max);
+                                  leafp.as<int>(), flag.as<unsigned>(), aabb.as<float4>(), m.nodes, m.leaf_max,
+                                  w4_margin);
         k_depth<<<gb, tb, 0, s>>>(parent.as<int>(), leafp.as<int>(), n, depth.as<int>());
         if (m.kind == FMT_Q8)
             k_quantize<<<gi, tb, 0, s>>>(m.tri_in, order, n - 1, child.as<int2>(), range.as<int2>(), aabb.as<float4>(),
-                                         m.leaf_max, reinterpret_cast<uint4*>(m.q8));
+                                         m.leaf_max, w4_margin, reinterpret_cast<uint4*>(m.q8));
         if (wide) {
             DevBuf fr[2], cnt, off, tot;
             e = fr[0].alloc(8ull * n_nodes);
@@ -1214,6 +1309,13 @@ int build_lbvh(rtmc_ctx* ctx, DeviceMesh& m)
 
 void free_columns(DeviceMesh& m)
 {
+    for (SlantGrid& g : m.slant) {
+        if (g.off) cudaFree(g.off);
+        if (g.ent) cudaFree(g.ent);
+    }
+    m.slant.clear();
+    m.slant_failed.clear();
+    m.slant_bytes = 0;
     if (m.col_off) cudaFree(m.col_off);
     if (m.col_ent) cudaFree(m.col_ent);
     m.col_off = nullptr;
@@ -1292,6 +1394,102 @@ int build_columns(rtmc_ctx* ctx, DeviceMesh& m)
     }
     free_columns(m);
     return RTMC_OK;
+}
+
+GridDev grid_dev(const DeviceMesh& m, const SlantGrid* g)
+{
+    GridDev d;
+    if (g) {
+        d.off = g->off; d.ent = g->ent; d.gx = g->gx; d.gy = g->gy; d.iwx = g->iwx; d.iwy = g->iwy;
+        d.dx = g->dx; d.dz = g->dz;
+    } else {
+        d.off = m.col_off; d.ent = m.col_ent; d.gx = m.col_gx; d.gy = m.col_gy; d.iwx = m.col_inv_wx;
+        d.iwy = m.col_inv_wy; d.dx = 0.f; d.dz = -1.f;
+    }
+    return d;
+}
+
+// The slanted grid keeps the vertical grid's y pixels and widens its x pixels
+// by 1 + s (s = dx / |dz|), so a facet's sheared footprint (x extent plus z
+// extent times s) covers about as many pixels as its vertical footprint; a
+// footprint over more than 4 x 64 pixels makes the build retry with half the x
+// pixels (up to four times).  All slanted grids of a mesh together stay below
+// a quarter of the free device memory and 32 GiB.
+bool slant_grid(rtmc_ctx* ctx, DeviceMesh& m, float dx, float dz, GridDev& out)
+{
+    for (const SlantGrid& g : m.slant)
+        if (g.dx == dx && g.dz == dz) { out = grid_dev(m, &g); return true; }
+    for (const float2& f : m.slant_failed)
+        if (f.x == dx && f.y == dz) return false;
+    auto fail = [&]() { m.slant_failed.push_back(make_float2(dx, dz)); return false; };
+    const int n = (int)m.n_tri;
+    if (!m.col_ok || !(dx > 0.f) || !(dz < 0.f) || n <= 0 || n > (1 << kSlantFacetBits)) return fail();
+    cudaStream_t s = ctx->stream;
+    const double lx = m.box.lx, ly = m.box.ly, z_top = m.box.z_top, z_min = m.box.z_min;
+    const double shear = (double)dx / -(double)dz;
+    const double big = std::max(std::max(std::fabs(lx), std::fabs(ly)), std::max(std::fabs(z_min), std::fabs(z_top)));
+    const double flight = (z_top - z_min) * std::sqrt(1.0 + shear * shear);
+    const double margin = std::ldexp(big + flight, -16);   // FP32 rounding of the traced ray, with room to spare
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    const size_t cap = std::min<size_t>((size_t)32 << 30, free_b / 4);
+    const int gy = m.col_gy;
+    int gx = std::max(1, (int)std::lround(m.col_gx / (1.0 + shear)));
+    for (int attempt = 0; attempt < 5; ++attempt, gx = std::max(1, gx / 2)) {
+        const int np = gx * gy;
+        const float iwx = (float)(gx / lx), iwy = (float)(gy / ly);
+        SlantGrid g;
+        g.dx = dx; g.dz = dz; g.gx = gx; g.gy = gy; g.iwx = iwx; g.iwy = iwy;
+        DevBuf cnt, tot, bad;
+        cudaError_t e = cnt.alloc(4ull * np);
+        if (e == cudaSuccess) e = tot.alloc(4);
+        if (e == cudaSuccess) e = bad.alloc(4);
+        if (e == cudaSuccess) e = cudaMalloc(&g.off, 4ull * (np + 1));
+        if (e == cudaSuccess) e = cudaMemsetAsync(cnt.p, 0, 4ull * np, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(bad.p, 0, 4, s);
+        const int tb = 256, gb = (n + tb - 1) / tb;
+        if (e == cudaSuccess) {
+            k_slant_count<<<gb, tb, 0, s>>>(m.tris, n, gx, gy, iwx, iwy, lx, z_top, shear, margin, cnt.as<int>(),
+                                            bad.as<int>());
+            k_w4_scan<<<1, 1024, 0, s>>>(cnt.as<int>(), np, reinterpret_cast<int*>(g.off), tot.as<int>());
+            e = cudaGetLastError();
+        }
+        int h_tot = 0, h_bad = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g.off + np, tot.p, 4, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&h_tot, tot.p, 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&h_bad, bad.p, 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        const size_t bytes = 8ull * (size_t)std::max(h_tot, 0) + 4ull * (np + 1);
+        if (e == cudaSuccess && (h_bad & 1) == 0 && (h_bad || h_tot <= 0 || m.slant_bytes + bytes > cap)) {
+            cudaFree(g.off);
+            return fail();                              // too many wraps, nothing listed, or no room
+        }
+        if (e == cudaSuccess && (h_bad & 1)) { cudaFree(g.off); continue; }   // a footprint too wide
+        if (e == cudaSuccess) {
+            e = cudaMalloc(&g.ent, 8ull * h_tot);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(cnt.p, g.off, 4ull * np, cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess) {
+                k_slant_fill<<<gb, tb, 0, s>>>(m.tris, n, gx, gy, iwx, iwy, lx, z_top, shear, margin, cnt.as<int>(),
+                                               g.ent);
+                k_col_sort<<<np, 128, 0, s>>>(reinterpret_cast<const int*>(g.off), g.ent, bad.as<int>());
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&h_bad, bad.p, 4, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        }
+        if (e != cudaSuccess || h_bad) {             // no memory, or a pixel list too long to sort
+            if (e != cudaSuccess) cudaGetLastError();
+            if (g.off) cudaFree(g.off);
+            if (g.ent) cudaFree(g.ent);
+            return fail();
+        }
+        g.entries = h_tot;
+        m.slant_bytes += bytes;
+        m.slant.push_back(g);
+        out = grid_dev(m, &g);
+        return true;
+    }
+    return fail();
 }
 
 }  // namespace rtmc

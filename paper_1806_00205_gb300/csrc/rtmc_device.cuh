@@ -76,6 +76,20 @@ struct ItemCtx {
 
 constexpr int kChunkItems = 16;      // per-block shared accumulators for up to this many items
 
+// A column grid as the traversal kernels read it.  Rays of direction
+// (dx, 0, dz), dz < 0, dx >= 0, enter through z_top; pixel p of the gx x gy grid
+// over [0, lx) x [0, ly) lists ent[off[p] .. off[p+1]) = (facet | k << 24, top z
+// bits), sorted by top z descending: the facets a ray entering in p can meet,
+// with the lateral wraps k it makes before it meets them (k = 0 when dx = 0).
+struct GridDev {
+    const unsigned* off;
+    const uint2* ent;
+    int gx, gy;
+    float iwx, iwy;
+    float dx, dz;
+};
+constexpr unsigned kSlantFacetBits = 24;    // facet index bits of a grid entry; the wrap count sits above
+
 struct Emission {
     float phi, e_cut, absorb_min, regen_min;
     int max_generation, k_max;
@@ -150,6 +164,19 @@ __device__ __forceinline__ float3 f3(float4 v) { return make_float3(v.x, v.y, v.
 __device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
 __device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 
+// The facet test's arithmetic with its rounding spelled out (one product, then
+// fused multiply-adds, in a fixed order): every kernel that inlines the test
+// rounds alike, so a ray through an edge shared by two facets gets the same
+// decision whichever traversal tests it.
+__device__ __forceinline__ float dot3_fixed(float3 a, float3 b)
+{
+    return __fmaf_rn(a.z, b.z, __fmaf_rn(a.y, b.y, __fmul_rn(a.x, b.x)));
+}
+__device__ __forceinline__ float cross2_fixed(float a, float b, float c, float d)   // a b - c d
+{
+    return __fmaf_rn(a, b, -__fmul_rn(c, d));
+}
+
 __host__ __device__ inline unsigned long long splitmix64(unsigned long long x)
 {
     unsigned long long z = x + 0x9E3779B97F4A7C15ull;
@@ -218,22 +245,22 @@ __device__ __forceinline__ bool intersect_tri(const RaySetup& r, float4 w0, floa
                                               float& t_best, int& best_orig, float& bu, float& bv)
 {
     const float3 A = f3(w0) - r.o, B = f3(w1) - r.o, C = f3(w2) - r.o;
-    const float ax = dot3(A, r.mx), ay = dot3(A, r.my);
-    const float bx = dot3(B, r.mx), by = dot3(B, r.my);
-    const float cx = dot3(C, r.mx), cy = dot3(C, r.my);
-    float U = cx * by - cy * bx;
-    float V = ax * cy - ay * cx;
-    float W = bx * ay - by * ax;
+    const float ax = dot3_fixed(A, r.mx), ay = dot3_fixed(A, r.my);
+    const float bx = dot3_fixed(B, r.mx), by = dot3_fixed(B, r.my);
+    const float cx = dot3_fixed(C, r.mx), cy = dot3_fixed(C, r.my);
+    float U = cross2_fixed(cx, by, cy, bx);
+    float V = cross2_fixed(ax, cy, ay, cx);
+    float W = cross2_fixed(bx, ay, by, ax);
     if (U == 0.f || V == 0.f || W == 0.f) {            // exact edge: decide in FP64
         U = (float)((double)cx * (double)by - (double)cy * (double)bx);
         V = (float)((double)ax * (double)cy - (double)ay * (double)cx);
         W = (float)((double)bx * (double)ay - (double)by * (double)ax);
     }
     if (U < 0.f || V < 0.f || W < 0.f) return false;   // outside or back-facing
-    const float det = U + V + W;
+    const float det = __fadd_rn(__fadd_rn(U, V), W);
     if (det == 0.f) return false;
-    const float az = dot3(A, r.mz), bz = dot3(B, r.mz), cz = dot3(C, r.mz);
-    const float T = U * az + V * bz + W * cz;
+    const float az = dot3_fixed(A, r.mz), bz = dot3_fixed(B, r.mz), cz = dot3_fixed(C, r.mz);
+    const float T = __fmaf_rn(W, cz, __fmaf_rn(V, bz, __fmul_rn(U, az)));
     if (T <= 0.f) return false;
     const float t = T / det;
     const int orig = __float_as_int(w0.w);

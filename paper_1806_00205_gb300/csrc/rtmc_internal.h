@@ -11,6 +11,17 @@
 
 namespace rtmc {
 
+// A slanted column grid (rays of one fixed oblique direction, see GridDev),
+// built on first use by a run at that incidence and kept with the mesh.
+struct SlantGrid {
+    float dx = 0.f, dz = -1.f;     // the FP32 direction it serves (d.y = 0)
+    int gx = 0, gy = 0;
+    float iwx = 0.f, iwy = 0.f;
+    unsigned* off = nullptr;
+    uint2* ent = nullptr;
+    int64_t entries = 0;
+};
+
 struct DeviceMesh {
     int64_t n_tri = 0;
     rtmc_box box{};
@@ -42,6 +53,9 @@ struct DeviceMesh {
     unsigned* col_off = nullptr;   // col_gx * col_gy + 1
     uint2* col_ent = nullptr;
     int64_t col_entries = 0;
+    std::vector<SlantGrid> slant;  // slanted grids built so far (freed with the column grid)
+    size_t slant_bytes = 0;
+    std::vector<float2> slant_failed;   // directions whose grid could not be built (not retried)
 };
 
 // Growable device scratch owned by the context.
@@ -102,6 +116,7 @@ struct rtmc_ctx {
     rtmc::Scratch q_oe[2], q_dt[2], q_id[2], hits, kcount, ctl, tally, hist, wraps, records, tmp;
     rtmc::Scratch items;                      // batched item table
     rtmc::Scratch sort_counts;                // spatial sort of primaries
+    rtmc::Scratch grids;                      // column-grid descriptors of the items (GridDev)
     cudaGraphExec_t batch_graph = nullptr;    // captured batch launch sequence
     std::string batch_key;                    // what the captured graph was built for
     int64_t batch_launches = 0;               // kernel launches in the captured graph
@@ -192,6 +207,18 @@ cudaError_t launch_columns(const DeviceMesh& m, const RunParams& p, const Queues
                            int num_sms, bool record, bool retest, cudaStream_t s);
 int build_columns(rtmc_ctx* ctx, DeviceMesh& m);
 void free_columns(DeviceMesh& m);
+// The slanted grid for primaries of direction (dx, 0, dz), dx > 0 > dz, built on
+// first use (synchronises the context's stream; never call it inside a stream
+// capture); its descriptor goes to `out`.  false when the mesh has none and
+// cannot get one: no column grid, too many facets, a footprint too wide even
+// for coarse pixels, more than 255 wraps before a facet, or the slanted grids'
+// memory cap -- such rays take the hierarchy.
+bool slant_grid(rtmc_ctx* ctx, DeviceMesh& m, float dx, float dz, GridDev& out);
+GridDev grid_dev(const DeviceMesh& m, const SlantGrid* g);   // g == nullptr: the vertical grid
+// Generation `gen` of primaries of fixed directions (one per item when `items`)
+// through their grids (device array; entry 0, or one per item of the mesh).
+cudaError_t launch_slant(const DeviceMesh& m, const RunParams& p, const GridDev* grids, bool items, const Queues& q,
+                         int buf, int gen, int num_sms, bool record, cudaStream_t s);
 cudaError_t launch_trace_rays(const DeviceMesh& m, const float* o, const float* d, const int* skip,
                               int64_t n, rtmc_hit* hits, unsigned* status, cudaStream_t s);
 cudaError_t launch_read_probe(const void* buf, size_t bytes, int passes, int num_sms, float* sink, cudaStream_t s);

@@ -16,6 +16,10 @@ namespace {
 
 constexpr int kSmemStack = 16;        // default stack entries held in shared memory per ray
 constexpr float kRobust = 1.0000004f; // 1 + 2 gamma_3 (Ize 2013): conservative slab test
+// Boxes are culled against the best facet distance widened by 2^-16: the FP32
+// facet test rounds too, and a box whose facet would tie the best FP32 distance
+// (met on a shared edge) must still be entered so the tie goes to the lower id.
+constexpr float kTieSlack = 1.0000152587890625f;
 
 __device__ __forceinline__ float4 ldg4(const float4* p) { return __ldg(p); }
 
@@ -324,7 +328,7 @@ __device__ __forceinline__ int bvh_closest(const void* __restrict__ nodes, const
         while (sp > 0) {
             --sp;
             const int2 e = sp < SMEM ? st.smem[sp * st.stride + st.tid] : lstack[sp - SMEM];
-            if (__int_as_float(e.y) <= t_best * kRobust) { node = e.x; return true; }
+            if (__int_as_float(e.y) <= t_best * kTieSlack * kRobust) { node = e.x; return true; }
         }
         return false;
     };
@@ -339,7 +343,7 @@ __device__ __forceinline__ int bvh_closest(const void* __restrict__ nodes, const
             if (COUNT) ++cnt->visits;
             float tk[4];
             int ck[4], nh;
-            node4_children<FMT>(nodes, node, FMT == FMT_Q4 ? q4_setup(r) : r, t_best, tk, ck, nh);
+            node4_children<FMT>(nodes, node, FMT == FMT_Q4 ? q4_setup(r) : r, t_best * kTieSlack, tk, ck, nh);
             if (nh > 3) push(ck[3], tk[3]);
             if (nh > 2) push(ck[2], tk[2]);
             if (nh > 1) push(ck[1], tk[1]);
@@ -351,7 +355,7 @@ __device__ __forceinline__ int bvh_closest(const void* __restrict__ nodes, const
         float tmin0, tmin1;
         bool h0, h1;
         int c0, c1;
-        node_children<FMT>(nodes, node, r, t_best, tmin0, tmin1, h0, h1, c0, c1);
+        node_children<FMT>(nodes, node, r, t_best * kTieSlack, tmin0, tmin1, h0, h1, c0, c1);
         if (h0 && c0 < 0) {
             test_leaf<COUNT, TRI64>(tris, r, r64, c0, skip, t_best, t_best64, best, best_orig, bu, bv, cnt);
             h0 = false;
@@ -378,7 +382,7 @@ __device__ __forceinline__ int bvh_closest(const void* __restrict__ nodes, const
         while (sp > 0) {
             --sp;
             const int2 e = sp < SMEM ? st.smem[sp * st.stride + st.tid] : lstack[sp - SMEM];
-            if (__int_as_float(e.y) <= t_best * kRobust) { node = e.x; found = true; break; }
+            if (__int_as_float(e.y) <= t_best * kTieSlack * kRobust) { node = e.x; found = true; break; }
         }
         if (!found) break;
     }
@@ -392,6 +396,55 @@ struct Cell {
     float eps;      // 2^-20 M, M the largest cell coordinate: bound on FP32 face-distance errors
     int max_visits; // inner-node visits of one cell traversal before the ray is abandoned (ST_LOOP_LIMIT)
 };
+
+// A ray that meets no facet in the cell leaves it through a face (reading R4).
+// The distances to the three faces ahead are estimated in FP32 from the FP32
+// origin o (slab reciprocals inv); they pick the face unless the two nearest
+// lie closer than the estimates' error bound (2^-20 M per unit of |1/d|, plus
+// 1e-5 relative), when the FP64 quotients from the FP64 origin (ox, oy, oz)
+// decide (the reference rule: z first if strictly nearest, then x on a tie
+// with y).  An exit through z_top or z_min returns HIT_ESCAPE / HIT_LOST with
+// its distance from the FP64 offset in tout; so does a wrap past max_wraps
+// (HIT_LOST).  A lateral wrap returns 0 with the FP64 re-entry point, the same
+// FP64 quotient as the reference, in (ox, oy, oz) and one more in wraps.  (FP64
+// is slow on this GPU; most daughters leave a cell at least once.)
+__device__ __forceinline__ int cell_exit(float3 o, float3 d, float3 inv, const Cell& cell, double& ox, double& oy,
+                                         double& oz, int& wraps, float& tout)
+{
+    const float ax = fabsf(inv.x), ay = fabsf(inv.y), az = fabsf(inv.z);
+    const float fx = d.x != 0.f ? (d.x > 0.f ? cell.lx - o.x : o.x) * ax : INFINITY;
+    const float fy = d.y != 0.f ? (d.y > 0.f ? cell.ly - o.y : o.y) * ay : INFINITY;
+    const float fz = d.z != 0.f ? (d.z > 0.f ? cell.z_top - o.z : o.z - cell.z_min) * az : INFINITY;
+    const float m1 = fminf(fx, fminf(fy, fz));
+    const float m2 = fmaxf(fminf(fx, fy), fminf(fmaxf(fx, fy), fz));   // second smallest
+    int face;                                                           // 0 x, 1 y, 2 z
+    if (m2 - m1 <= 1e-5f * m2 + cell.eps * (ax + ay + az)) {
+        double tx = INFINITY, ty = INFINITY, tz = INFINITY;
+        if (d.x > 0.f) tx = ((double)cell.lx - ox) / d.x; else if (d.x < 0.f) tx = (0.0 - ox) / d.x;
+        if (d.y > 0.f) ty = ((double)cell.ly - oy) / d.y; else if (d.y < 0.f) ty = (0.0 - oy) / d.y;
+        if (d.z > 0.f) tz = ((double)cell.z_top - oz) / d.z; else if (d.z < 0.f) tz = ((double)cell.z_min - oz) / d.z;
+        face = (tz < tx && tz < ty) ? 2 : (tx <= ty ? 0 : 1);
+    } else {
+        face = fz == m1 ? 2 : (fx == m1 ? 0 : 1);
+    }
+    if (face == 2) {
+        tout = (float)(d.z > 0.f ? (double)cell.z_top - oz : oz - (double)cell.z_min) * az;
+        return d.z > 0.f ? HIT_ESCAPE : HIT_LOST;
+    }
+    if (++wraps > cell.max_wraps) {
+        tout = fminf(fx, fy);
+        return HIT_LOST;
+    }
+    if (face == 0) {
+        const double tx = d.x > 0.f ? ((double)cell.lx - ox) / d.x : (0.0 - ox) / d.x;
+        oy = oy + tx * d.y; oz = oz + tx * d.z; ox = d.x > 0.f ? 0.0 : (double)cell.lx;
+    } else {
+        const double ty = d.y > 0.f ? ((double)cell.ly - oy) / d.y : (0.0 - oy) / d.y;
+        ox = ox + ty * d.x; oz = oz + ty * d.z; oy = d.y > 0.f ? 0.0 : (double)cell.ly;
+    }
+    tout = 0.f;
+    return 0;
+}
 
 // Trace one ray segment by segment through the periodic cell (Section 2.2,
 // last paragraph).  Returns the hit record; *wraps gets the lateral re-entries.
@@ -494,18 +547,18 @@ __device__ __forceinline__ int intersect_tri_rt(const RaySetup& r, float4 w0, fl
                                                 float& t_best, int& best_orig, float& bu, float& bv)
 {
     const float3 A = f3(w0) - r.o, B = f3(w1) - r.o, C = f3(w2) - r.o;
-    const float ax = dot3(A, r.mx), ay = dot3(A, r.my);
-    const float bx = dot3(B, r.mx), by = dot3(B, r.my);
-    const float cx = dot3(C, r.mx), cy = dot3(C, r.my);
-    const float U = cx * by - cy * bx, V = ax * cy - ay * cx, W = bx * ay - by * ax;
+    const float ax = dot3_fixed(A, r.mx), ay = dot3_fixed(A, r.my);
+    const float bx = dot3_fixed(B, r.mx), by = dot3_fixed(B, r.my);
+    const float cx = dot3_fixed(C, r.mx), cy = dot3_fixed(C, r.my);
+    const float U = cross2_fixed(cx, by, cy, bx), V = cross2_fixed(ax, cy, ay, cx), W = cross2_fixed(bx, ay, by, ax);
     const float m = fminf(fminf(U, V), W);
     const float e = edge_eps * (fabsf(U) + fabsf(V) + fabsf(W));
     if (m < -e) return 0;                          // clearly outside or back-facing
     if (m <= e && edge_eps > 0.f) return 2;        // near an edge: FP64 decides
-    const float det = U + V + W;
+    const float det = __fadd_rn(__fadd_rn(U, V), W);
     if (det == 0.f) return 0;
-    const float az = dot3(A, r.mz), bz = dot3(B, r.mz), cz = dot3(C, r.mz);
-    const float T = U * az + V * bz + W * cz;
+    const float az = dot3_fixed(A, r.mz), bz = dot3_fixed(B, r.mz), cz = dot3_fixed(C, r.mz);
+    const float T = __fmaf_rn(W, cz, __fmaf_rn(V, bz, __fmul_rn(U, az)));
     if (T <= 0.f) return 0;
     const float t = T / det;
     const int orig = __float_as_int(w0.w);
@@ -603,7 +656,7 @@ k_traverse_ww(const void* __restrict__ nodes, const float4* __restrict__ tris, c
         while (sp > 0) {
             --sp;
             const int2 e = sp < SSTACK ? s_stack[sp * B + tid] : lstack[sp - SSTACK];
-            if (__int_as_float(e.y) <= t_best * kRobust) return e.x;
+            if (__int_as_float(e.y) <= t_best * kTieSlack * kRobust) return e.x;
         }
         return kEntrySentinel;
     };
@@ -651,7 +704,7 @@ k_traverse_ww(const void* __restrict__ nodes, const float4* __restrict__ tris, c
                 if constexpr (FMT == FMT_W4 || FMT == FMT_Q4) {
                     float tk[4];
                     int ck[4], nh;
-                    node4_children<FMT>(nodes, node, rs, t_best, tk, ck, nh);
+                    node4_children<FMT>(nodes, node, rs, t_best * kTieSlack, tk, ck, nh);
                     if (nh > 3) push(ck[3], tk[3]);           // farthest first: the nearest stays on top
                     if (nh > 2) push(ck[2], tk[2]);
                     if (nh > 1) push(ck[1], tk[1]);
@@ -660,7 +713,7 @@ k_traverse_ww(const void* __restrict__ nodes, const float4* __restrict__ tris, c
                     float tmin0, tmin1;
                     bool h0, h1;
                     int c0, c1;
-                    node_children<FMT>(nodes, node, rs, t_best, tmin0, tmin1, h0, h1, c0, c1);
+                    node_children<FMT>(nodes, node, rs, t_best * kTieSlack, tmin0, tmin1, h0, h1, c0, c1);
                     if (h0 && h1) {
                         const bool first0 = tmin0 <= tmin1;
                         push(first0 ? c1 : c0, first0 ? tmin1 : tmin0);
@@ -731,52 +784,12 @@ k_traverse_ww(const void* __restrict__ nodes, const float4* __restrict__ tris, c
             }
             hits[ray] = make_float4(t_best, bu, bv, __int_as_float(best));
         } else {
-            // No facet in this cell: leave through a face.  The distances to the
-            // three faces ahead are estimated in FP32 from the FP32 origin; they
-            // pick the face unless the two nearest lie closer than the estimates'
-            // error bound (2^-20 M per unit of |1/d|, plus 1e-5 relative), when
-            // the FP64 quotients decide (the reference rule: z first if strictly
-            // nearest, then x on a tie with y).  An exit through z_top or z_min
-            // reports its distance from the FP64 offset; a wrap divides in FP64,
-            // because it moves the FP64 re-entry point.  (FP64 is slow on this
-            // GPU; most daughters leave a cell at least once.)
             double ox = s_o[tid], oy = s_o[B + tid], oz = s_o[2 * B + tid];
-            const float ax = fabsf(rs.inv.x), ay = fabsf(rs.inv.y), az = fabsf(rs.inv.z);
-            const float fx = d.x != 0.f ? (d.x > 0.f ? cell.lx - o.x : o.x) * ax : INFINITY;
-            const float fy = d.y != 0.f ? (d.y > 0.f ? cell.ly - o.y : o.y) * ay : INFINITY;
-            const float fz = d.z != 0.f ? (d.z > 0.f ? cell.z_top - o.z : o.z - cell.z_min) * az : INFINITY;
-            const float m1 = fminf(fx, fminf(fy, fz));
-            const float m2 = fmaxf(fminf(fx, fy), fminf(fmaxf(fx, fy), fz));   // second smallest
-            int face;                                                           // 0 x, 1 y, 2 z
-            if (m2 - m1 <= 1e-5f * m2 + cell.eps * (ax + ay + az)) {
-                double tx = INFINITY, ty = INFINITY, tz = INFINITY;
-                if (d.x > 0.f) tx = ((double)cell.lx - ox) / d.x; else if (d.x < 0.f) tx = (0.0 - ox) / d.x;
-                if (d.y > 0.f) ty = ((double)cell.ly - oy) / d.y; else if (d.y < 0.f) ty = (0.0 - oy) / d.y;
-                if (d.z > 0.f) tz = ((double)cell.z_top - oz) / d.z; else if (d.z < 0.f) tz = ((double)cell.z_min - oz) / d.z;
-                face = (tz < tx && tz < ty) ? 2 : (tx <= ty ? 0 : 1);
-            } else {
-                face = fz == m1 ? 2 : (fx == m1 ? 0 : 1);
-            }
-            int code = 0;
-            float tout = 0.f;
-            if (face == 2) {
-                code = d.z > 0.f ? HIT_ESCAPE : HIT_LOST;
-                tout = (float)(d.z > 0.f ? (double)cell.z_top - oz : oz - (double)cell.z_min) * az;
-            } else if (++wraps > cell.max_wraps) {
-                code = HIT_LOST;
-                tout = fminf(fx, fy);
-            }
+            float tout;
+            const int code = cell_exit(o, d, rs.inv, cell, ox, oy, oz, wraps, tout);
             if (code) {
                 hits[ray] = make_float4(tout, 0.f, 0.f, __int_as_float(code));
             } else {
-                // the same FP64 quotient as above (and as the reference) for the face taken
-                if (face == 0) {
-                    const double tx = d.x > 0.f ? ((double)cell.lx - ox) / d.x : (0.0 - ox) / d.x;
-                    oy = oy + tx * d.y; oz = oz + tx * d.z; ox = d.x > 0.f ? 0.0 : (double)cell.lx;
-                } else {
-                    const double ty = d.y > 0.f ? ((double)cell.ly - oy) / d.y : (0.0 - oy) / d.y;
-                    ox = ox + ty * d.x; oz = oz + ty * d.z; oy = d.y > 0.f ? 0.0 : (double)cell.ly;
-                }
                 s_o[tid] = ox; s_o[B + tid] = oy; s_o[2 * B + tid] = oz;
                 o = make_float3((float)ox, (float)oy, (float)oz);
                 skip = -1;
@@ -933,6 +946,113 @@ k_trace_columns(const unsigned* __restrict__ col_off, const uint2* __restrict__ 
     }
 }
 
+// --------------------------------------------------------------------------
+// a generation of rays of one fixed oblique direction through a slanted grid
+// --------------------------------------------------------------------------
+// Primaries at fixed incidence (dx, 0, dz) travel in straight lines through
+// the periodic images of the cell.  Projected along that direction onto the
+// top plane, every facet image covers the entry points of the rays that can
+// meet it, and the image fixes how many lateral wraps k the ray has made by
+// then.  The slanted grid lists, per pixel of entry points, those (facet, k)
+// pairs sorted by top z (their along-ray distance from the entry is at least
+// (z_top - top z) / |dz|).  A ray tests them in that order against the FP32 ray
+// of its segment k -- the FP32 re-entry point after k wraps, replayed with the
+// hierarchy's own cell exit -- keeps the best (k, t, original id) in that
+// order (the hierarchy ends at the first segment with a hit and takes the
+// nearest, then the lowest id, within it), and stops when the next facet lies
+// beyond the best hit by the column grid's margins.  The facet tests, wrap
+// replay and tie rule are the hierarchy's, so the hit record, wrap count
+// included, is the same.  With no facet met the replay carries the ray to its
+// exit, as the hierarchy does.
+template <bool RECORD, bool ITEMS>
+__global__ void __launch_bounds__(128)
+k_trace_slant(const GridDev* __restrict__ grids, const float4* __restrict__ tris, Cell cell,
+              const float4* __restrict__ oe, const float4* __restrict__ dt, const uint4* __restrict__ id,
+              float4* __restrict__ hits, int* __restrict__ wraps_out, Control* __restrict__ ctl, int gen,
+              unsigned cap, Tally* __restrict__ tally)
+{
+    const unsigned n = min(*((volatile unsigned*)&ctl->count[gen]), cap);
+    const float eps_abs = cell.eps * 16.f;
+    unsigned status = 0, my_rays = 0;
+    unsigned long long my_wraps = 0;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float4 a = oe[i], b = dt[i];
+        const float3 o = make_float3(a.x, a.y, a.z), d = make_float3(b.x, b.y, b.z);
+        const GridDev g = grids[ITEMS ? id[i].y : 0u];
+        ++my_rays;
+        if (d.y != 0.f || d.x != g.dx || d.z != g.dz || !(d.z < 0.f) || __float_as_int(b.w) != -1 ||
+            o.z != cell.z_top) {
+            status |= ST_COLUMN;           // not a ray this grid serves: the caller chose wrongly
+            hits[i] = make_float4(0.f, 0.f, 0.f, __int_as_float(HIT_LOST));
+            if (RECORD) wraps_out[i] = 0;
+            continue;
+        }
+        const float az = fabsf(1.0f / d.z);
+        const int px = min(max((int)floorf(o.x * g.iwx), 0), g.gx - 1);
+        const int py = min(max((int)floorf(o.y * g.iwy), 0), g.gy - 1);
+        const unsigned e0 = g.off[py * g.gx + px], e1 = g.off[py * g.gx + px + 1];
+        // segment state: the ray after kc wraps (FP32 origin oc, FP64 origin sx/sy/sz);
+        // k_end: the last segment the ray reaches (its exit or wrap limit ends it there)
+        int kc = 0, wr = 0, k_end = INT_MAX, end_code = 0;
+        float end_tout = 0.f;
+        float3 oc = o;
+        double sx = o.x, sy = o.y, sz = o.z;
+        RaySetup rs = setup_ray(oc, d);
+        auto advance = [&](int k) {                 // replay the wraps up to segment k
+            if (k < kc) { kc = 0; wr = 0; oc = o; sx = o.x; sy = o.y; sz = o.z; rs = setup_ray(oc, d); }
+            while (kc < k && kc < k_end) {
+                float tout;
+                const int code = cell_exit(oc, d, rs.inv, cell, sx, sy, sz, wr, tout);
+                if (code) { k_end = kc; end_code = code; end_tout = tout; break; }
+                oc = make_float3((float)sx, (float)sy, (float)sz);
+                rs = setup_ray(oc, d);
+                ++kc;
+            }
+        };
+        float t_best = kNoHit, bu = 0.f, bv = 0.f, reach = kNoHit;
+        int best = -1, best_orig = INT_MAX, k_best = INT_MAX;
+        for (unsigned e = e0; e < e1; ++e) {
+            const uint2 ent = g.ent[e];
+            if ((o.z - __uint_as_float(ent.y)) * az > reach) break;
+            const int k = (int)(ent.x >> kSlantFacetBits);
+            const int j = (int)(ent.x & ((1u << kSlantFacetBits) - 1u));
+            if (k > k_best || k > k_end) continue;             // a later segment cannot win
+            if (k != kc) advance(k);
+            if (kc != k) continue;                             // the ray ends before segment k
+            float t = k == k_best ? t_best : kNoHit, u = 0.f, v = 0.f;
+            int orig = k == k_best ? best_orig : INT_MAX;
+            const float4* tp = tris + 3ll * j;
+            if (intersect_tri(rs, ldg4(tp), ldg4(tp + 1), ldg4(tp + 2), t, orig, u, v)) {
+                t_best = t; best_orig = orig; bu = u; bv = v; best = j; k_best = k;
+                // along-ray distance of the best hit from the entry point, with the grid margins
+                reach = ((float)((double)o.z - sz) * az + t_best) * kColRel + eps_abs;
+            }
+        }
+        int w;
+        if (best >= 0) {
+            hits[i] = make_float4(t_best, bu, bv, __int_as_float(best));
+            w = k_best;
+        } else {
+            advance(INT_MAX);                                   // no facet: replay to the exit
+            hits[i] = make_float4(end_tout, 0.f, 0.f, __int_as_float(end_code ? end_code : HIT_LOST));
+            w = wr;
+        }
+        my_wraps += (unsigned)w;
+        if (RECORD) wraps_out[i] = w;
+    }
+    const int lane = threadIdx.x & 31;
+    for (int off = 16; off; off >>= 1) {
+        my_rays += __shfl_xor_sync(0xFFFFFFFFu, my_rays, off);
+        my_wraps += __shfl_xor_sync(0xFFFFFFFFu, my_wraps, off);
+        status |= __shfl_xor_sync(0xFFFFFFFFu, status, off);
+    }
+    if (lane == 0) {
+        if (my_rays) atomicAdd(&tally->col_rays, (unsigned long long)my_rays);
+        if (my_wraps) atomicAdd(&tally->wraps, my_wraps);
+        if (status) atomicOr(&tally->status, (unsigned long long)status);
+    }
+}
+
 template <int FMT>
 __global__ void __launch_bounds__(128)
 k_trace_rays(const void* __restrict__ nodes, const float4* __restrict__ tris, const int* __restrict__ inv_order,
@@ -1061,6 +1181,26 @@ cudaError_t launch_columns(const DeviceMesh& m, const RunParams& p, const Queues
     if (record) { if (retest) RTMC_COLUMNS(true, true); else RTMC_COLUMNS(true, false); }
     else { if (retest) RTMC_COLUMNS(false, true); else RTMC_COLUMNS(false, false); }
 #undef RTMC_COLUMNS
+    return cudaGetLastError();
+}
+
+cudaError_t launch_slant(const DeviceMesh& m, const RunParams& p, const GridDev* grids, bool items, const Queues& q,
+                         int buf, int gen, int num_sms, bool record, cudaStream_t s)
+{
+    const float big = fmaxf(fmaxf(fabsf(p.lx), fabsf(p.ly)), fmaxf(fabsf(p.z_min), fabsf(p.z_top)));
+    const Cell cell{p.lx, p.ly, p.z_min, p.z_top, p.max_wraps, ldexpf(big, -20), visit_bound(m, 0)};
+    const int tb = 128;
+    int per_sm = 0;
+    int* wr = record ? q.wraps : nullptr;
+#define RTMC_SLANT(R, I)                                                                                        \
+    do {                                                                                                        \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_slant<R, I>, tb, 0);                     \
+        k_trace_slant<R, I><<<(unsigned)num_sms * (unsigned)(per_sm > 0 ? per_sm : 1), tb, 0, s>>>(            \
+            grids, m.tris, cell, q.oe[buf], q.dt[buf], q.id[buf], q.hits, wr, q.ctl, gen, q.cap[buf], q.tally); \
+    } while (0)
+    if (record) { if (items) RTMC_SLANT(true, true); else RTMC_SLANT(true, false); }
+    else { if (items) RTMC_SLANT(false, true); else RTMC_SLANT(false, false); }
+#undef RTMC_SLANT
     return cudaGetLastError();
 }
 

@@ -112,16 +112,18 @@ def test_batch_rejects_what_it_cannot_do(setup):
         ctx.run_batch(ids, [300.0], [95.0], 10, 1)
 
 
-def test_batch_column_grid_for_normal_incidence_items_only(setup):
-    """In a batch that mixes angles, the chunks of the normal-incidence items take the
-    column grid for their primaries and the others the hierarchy; every item keeps the
-    tallies of its plain run."""
+def test_batch_column_grids_for_fixed_incidence_items(setup):
+    """In a batch that mixes angles, every fixed-incidence item's primaries take a column
+    grid (vertical or slanted, several directions in one chunk), random azimuths the
+    hierarchy; every item keeps the tallies of its plain run."""
     ctx, ids, rtmc = setup
     energies, thetas, n = [200.0, 650.0], [0.0, 30.0, 0.0, 60.0], 12_000
     res, he, _ = ctx.run_batch(ids, energies, thetas, n, 41, desc=rtmc.run_desc(chunk=20_000))
     per_mesh = len(energies) * len(thetas)
+    assert res[0]["column_rays"] == len(ids) * per_mesh * n
+    ra, _, _ = ctx.run_batch(ids, energies, thetas, n, 41, desc=rtmc.run_desc(chunk=20_000, random_azimuth=True))
     n_vertical = sum(1 for t in thetas if t == 0.0) * len(energies)
-    assert res[0]["column_rays"] == len(ids) * n_vertical * n
+    assert ra[0]["column_rays"] == len(ids) * n_vertical * n
     for mi, mid in enumerate(ids):
         plain, phe, _ = ctx.run(mid, energies, thetas, n, 41, desc=rtmc.run_desc(item_base=mi * per_mesh))
         for j in range(per_mesh):
@@ -136,10 +138,11 @@ def test_batch_graph_follows_angles_and_rebuilds(setup):
     (the column grid at normal incidence, the hierarchy otherwise) or a mesh is rebuilt."""
     ctx, ids, rtmc = setup
     mid, n = ids[2], 20_000
-    a, _, _ = ctx.run_batch([mid], [300.0], [0.0], n, 9)       # records the column grid
-    b, _, _ = ctx.run_batch([mid], [300.0], [35.0], n, 9)      # same shape, oblique
+    a, _, _ = ctx.run_batch([mid], [300.0], [0.0], n, 9)       # records the vertical column grid
+    b, _, _ = ctx.run_batch([mid], [300.0], [35.0], n, 9)      # same shape, oblique: the slanted grid
     pb, _, _ = ctx.run(mid, [300.0], [35.0], n, 9)
-    assert a[0]["column_rays"] == n and b[0]["column_rays"] == 0
+    r, _, _ = ctx.run_batch([mid], [300.0], [35.0], n, 9, desc=rtmc.run_desc(random_azimuth=True))
+    assert a[0]["column_rays"] == n and b[0]["column_rays"] == n and r[0]["column_rays"] == 0
     for k in INT_KEYS:
         assert b[0][k] == pb[0][k], k
     ctx.build_bvh(mid, kind=rtmc.BVH_W4)                         # new device arrays

@@ -1,6 +1,9 @@
-"""Column grid: generation 0 at normal incidence traced through per-pixel facet lists
-sorted by top z instead of the hierarchy (GB300).  Same facet tests, so the same hit
-records: every tally, histogram and per-primary event hash equals the hierarchy's."""
+"""Column grids: generation 0 at fixed incidence traced through per-pixel facet lists
+sorted by top z instead of the hierarchy (GB300) -- vertical lists at normal incidence,
+slanted lists (facets projected along the ray direction, with the wraps before each)
+at oblique incidence.  Same facet tests and the hierarchy's own wrap replay, so the
+same hit records: every tally, histogram and per-primary event hash equals the
+hierarchy's."""
 import numpy as np
 import pytest
 
@@ -58,14 +61,14 @@ def test_column_grid_equals_hierarchy(ctx, grid, porosity, kind, retest):
     ctx.unload_mesh(mid)
 
 
-def test_column_grid_only_at_normal_incidence(ctx):
+def test_vertical_grid_only_at_normal_incidence(ctx):
     from paper_1806_00205_gb300 import rtmc
     mesh = I.grf_foam(24, 0.6, seed=5)
     mid = ctx.load_mesh(mesh.tri, mesh.box)
     ctx.build_bvh(mid, kind=rtmc.BVH_W4)
     n = 20_000
-    r0, _, _ = ctx.run(mid, [300.0], [0.0, 30.0], n, 3)
-    assert r0[0]["column_rays"] == n and r0[1]["column_rays"] == 0
+    r0, _, _ = ctx.run(mid, [300.0], [0.0, 30.0], n, 3, desc=rtmc.run_desc(fp64_retest=True))
+    assert r0[0]["column_rays"] == n and r0[1]["column_rays"] == 0      # no slanted grid with the FP64 re-test
     rp, _, _ = ctx.run(mid, [300.0], [0.0], n, 3, desc=rtmc.run_desc(random_polar=True))
     assert rp[0]["column_rays"] == 0
     ra, _, _ = ctx.run(mid, [300.0], [0.0], n, 3, desc=rtmc.run_desc(random_azimuth=True))
@@ -144,3 +147,92 @@ def test_column_grid_retries_coarser_for_a_wide_facet(ctx):
     for k in INT_KEYS[:-1]:
         assert a[0][k] == c[0][k], k
     assert np.array_equal(ha, hc)
+
+
+def _slant_vs_hierarchy(ctx, mid, energies, thetas, n, seed, **kw):
+    import torch
+    from paper_1806_00205_gb300 import rtmc
+    out = []
+    for e in energies:
+        for th in thetas:
+            hs = torch.zeros(n, dtype=torch.int64, device="cuda")
+            hb = torch.zeros(n, dtype=torch.int64, device="cuda")
+            a = ctx.run(mid, [e], [th], n, seed, desc=rtmc.run_desc(prim_hash=hs, **kw))
+            b = ctx.run(mid, [e], [th], n, seed, desc=rtmc.run_desc(prim_hash=hb, traversal=2, **kw))
+            out.append((th, a, b, hs, hb))
+    return out
+
+
+@pytest.mark.parametrize("grid,porosity,kind", [(16, 0.5, 0), (48, 0.3, 1), (48, 0.8, 2), (128, 0.6, 3)])
+def test_slanted_grid_equals_hierarchy(ctx, grid, porosity, kind):
+    """Oblique primaries through the slanted grid of their direction: every tally,
+    histogram and per-primary hash (wraps included) equals the hierarchy's."""
+    import torch
+    mesh = I.grf_foam(grid, porosity)
+    mid = ctx.load_mesh(mesh.tri, mesh.box)
+    ctx.build_bvh(mid, kind=kind)
+    n = 200_000 if grid < 128 else 1_000_000
+    for th, (ra, hea, haa), (rb, heb, hab), hs, hb in _slant_vs_hierarchy(
+            ctx, mid, [80.0, 500.0], [5.0, 37.0, 60.0, 80.0, 89.0], n, 17):
+        for a, b in zip(ra, rb):
+            # at 89 degrees a facet's slanted footprint can be wider than the cell: then no grid
+            assert (a["column_rays"] == n or th > 85.0) and a["column_rays"] in (0, n), th
+            assert b["column_rays"] == 0, th
+            for k in INT_KEYS:
+                assert a[k] == b[k], (th, k, a[k], b[k])
+            assert abs(a["e_sum"] - b["e_sum"]) <= 1e-9 * max(1.0, b["e_sum"])
+        assert np.array_equal(hea, heb) and np.array_equal(haa, hab)
+        assert torch.equal(hs, hb), th
+    ctx.unload_mesh(mid)
+
+
+def test_slanted_grid_many_wraps(ctx):
+    """A square well 400 nm deep in a 100 nm periodic cell at 85
+    degrees: primaries wrap many times before they meet a wall or the floor; the replayed
+    wraps give the hierarchy's records."""
+    import torch
+    from paper_1806_00205_gb300 import rtmc
+    well = I.square_well(90.0, 400.0, rim=5.0)
+    mid = ctx.load_mesh(well.tri, well.box)
+    ctx.build_bvh(mid, kind=rtmc.BVH_W4)
+    n = 100_000
+    for th, (ra, _, _), (rb, _, _), hs, hb in _slant_vs_hierarchy(ctx, mid, [300.0], [45.0, 75.0, 85.0], n, 3,
+                                                                    window=(0.0, 100.0, 0.0, 100.0)):
+        a, b = ra[0], rb[0]
+        assert a["column_rays"] == n
+        for k in INT_KEYS:
+            assert a[k] == b[k], (th, k, a[k], b[k])
+        assert torch.equal(hs, hb), th
+    assert b["wraps"] > n            # at 85 degrees primaries wrap more than once on average
+    ctx.unload_mesh(mid)
+
+
+def test_slanted_grid_records_match_oracle(ctx):
+    """Per-ray records of oblique primaries through the slanted grid against the FP64 oracle."""
+    import oracle as O
+    from tests.parity import check_moments, compare_records
+    mesh = I.grf_foam(16, 0.5)
+    mid = ctx.load_mesh(mesh.tri, mesh.box)
+    ctx.build_bvh(mid)
+    n = 30_000
+    for th in (50.0, 80.0):
+        g = ctx.run_records(mid, 300.0, th, n, seed=1806)
+        assert g["column_rays"] == n
+        o = O.run(mesh, TABLE, 300.0, th, n, seed=1806, records=True)
+        st = compare_records(g["records"], o["records"], mesh=mesh)
+        assert st["frac_same"] >= 0.9999, {k: v for k, v in st.items() if k != "mismatch"}
+        assert st["t_bound_violations"] == 0, (st["t_bound_ratio_max"], st["t_bound_worst"])
+        check_moments(g, o, st)
+    ctx.unload_mesh(mid)
+
+
+def test_slanted_grid_not_for_random_directions(ctx):
+    from paper_1806_00205_gb300 import rtmc
+    mesh = I.grf_foam(16, 0.5)
+    mid = ctx.load_mesh(mesh.tri, mesh.box)
+    ctx.build_bvh(mid)
+    n = 20_000
+    for kw in (dict(random_azimuth=True), dict(random_polar=True), dict(traversal=1), dict(fp64_retest=True)):
+        r, _, _ = ctx.run(mid, [300.0], [40.0], n, 3, desc=rtmc.run_desc(**kw))
+        assert r[0]["column_rays"] == 0, kw
+    ctx.unload_mesh(mid)

@@ -64,7 +64,7 @@ def _decode_fp32(raw):
 
 @pytest.mark.parametrize("n,p,leaf", [(16, 0.5, 4), (48, 0.3, 1), (128, 0.6, 4)])
 def test_q8_boxes_contain_fp32_boxes(ctx, n, p, leaf):
-    """Exhaustive: every decoded 8-bit child box contains its exact FP32 box."""
+    """Exhaustive: every decoded 8-bit child box contains its FP32 box (both widened by M 2^-22)."""
     from paper_1806_00205_gb300 import rtmc
     mesh = I.grf_foam(n, p)
     mid = ctx.load_mesh(mesh.tri, mesh.box)

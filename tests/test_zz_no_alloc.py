@@ -100,7 +100,8 @@ def test_noalloc_traversal_controls_equal_run(setup, opts):
         desc = rtmc.run_desc(**opts)
         ref, he, ha = ctx.run(mid, [350.0], [theta], n, 29, desc=desc)
         got, ge, ga = ctx.run_noalloc(mid, 350.0, theta, n, 29, desc=desc)
-        for k in INT_KEYS + ("column_rays",):
+        # the scratch-free entry builds no slanted grid: oblique primaries take the hierarchy
+        for k in INT_KEYS + (("column_rays",) if theta == 0.0 else ()):
             assert got[k] == ref[0][k], (opts, theta, k, got[k], ref[0][k])
         assert np.array_equal(ge, he[0]) and np.array_equal(ga, ha[0])
 
