@@ -996,16 +996,18 @@ k_trace_slant(const GridDev* __restrict__ grids, const float4* __restrict__ tris
         int kc = 0, wr = 0, k_end = INT_MAX, end_code = 0;
         float end_tout = 0.f;
         float3 oc = o;
+        float drop = 0.f;                           // z of the entry minus z of the segment's origin
         double sx = o.x, sy = o.y, sz = o.z;
         RaySetup rs = setup_ray(oc, d);
         auto advance = [&](int k) {                 // replay the wraps up to segment k
-            if (k < kc) { kc = 0; wr = 0; oc = o; sx = o.x; sy = o.y; sz = o.z; rs = setup_ray(oc, d); }
+            if (k < kc) { kc = 0; wr = 0; oc = o; sx = o.x; sy = o.y; sz = o.z; rs = setup_ray(oc, d); drop = 0.f; }
             while (kc < k && kc < k_end) {
                 float tout;
                 const int code = cell_exit(oc, d, rs.inv, cell, sx, sy, sz, wr, tout);
                 if (code) { k_end = kc; end_code = code; end_tout = tout; break; }
                 oc = make_float3((float)sx, (float)sy, (float)sz);
                 rs = setup_ray(oc, d);
+                drop = (float)((double)o.z - sz);
                 ++kc;
             }
         };
@@ -1025,7 +1027,7 @@ k_trace_slant(const GridDev* __restrict__ grids, const float4* __restrict__ tris
             if (intersect_tri(rs, ldg4(tp), ldg4(tp + 1), ldg4(tp + 2), t, orig, u, v)) {
                 t_best = t; best_orig = orig; bu = u; bv = v; best = j; k_best = k;
                 // along-ray distance of the best hit from the entry point, with the grid margins
-                reach = ((float)((double)o.z - sz) * az + t_best) * kColRel + eps_abs;
+                reach = (drop * az + t_best) * kColRel + eps_abs;
             }
         }
         int w;
