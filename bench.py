@@ -544,6 +544,7 @@ def run_large(args):
                          f"same mesh (brute force over all {mesh.n_tri} triangles per ray segment); "
                          f"{o_secs:.1f} s"}
         same, esc_g, esc_o = 0, 0, 0
+        mom = np.zeros((2, 2))                   # [gpu, oracle] x [sum E, sum E^2]
         ids = np.arange(per, dtype=np.uint64)
         for j, (th, o) in enumerate(zip(LARGE_THETAS, outs)):
             h = torch.zeros(per, dtype=torch.int64, device=dev)
@@ -551,8 +552,12 @@ def run_large(args):
             same += int(np.sum(h.cpu().numpy().view(np.uint64) == primary_hashes(o["records"], ids)))
             esc_g += g[0]["escaped"]
             esc_o += o["escaped"]
+            mom += [[g[0]["e_sum"], g[0]["e2_sum"]], [o["e_sum"], o["e2_sum"]]]
         sampled = {"primaries": per * nt, "per_primary_event_hashes_equal": same,
                    "escapes_gpu": esc_g, "escapes_oracle": esc_o,
+                   "sey_gpu": esc_g / (per * nt), "sey_oracle": esc_o / (per * nt),
+                   "e_sum_rel_err": abs(mom[0, 0] - mom[1, 0]) / max(mom[1, 0], 1e-300),
+                   "e2_sum_rel_err": abs(mom[0, 1] - mom[1, 1]) / max(mom[1, 1], 1e-300),
                    "note": "same primary ids and random streams on both sides; a hash covers every ray of the "
                            "primary's tree (fate, facet, count, energy and angle bins, wraps)"}
 
