@@ -435,7 +435,8 @@ k_shade(const float4* __restrict__ tris, const float4* __restrict__ normals, Tab
     __shared__ unsigned long long s_red[10][kShadeThreads / 32];
     __shared__ double s_dred[2][kShadeThreads / 32];
     __shared__ unsigned s_icnt[kChunkItems][10];      // multi-item chunks: per-item counters
-    __shared__ double s_isum[kChunkItems][2];
+    __shared__ double s_isum[kChunkItems][2];       // multi-item warps (rare): FP64 shared atomics
+    __shared__ float s_iff[kShadeThreads / 32][kChunkItems][4];   // per warp and item: sum E, sum E^2 as float pairs
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nbins = p.n_ebins + p.n_abins + p.n_zbins;
@@ -449,6 +450,7 @@ k_shade(const float4* __restrict__ tris, const float4* __restrict__ normals, Tab
         for (int b = tid; b < kChunkItems * 10; b += kShadeThreads) {
             (&s_icnt[0][0])[b] = 0u;
             if (b < kChunkItems * 2) (&s_isum[0][0])[b] = 0.0;
+            if (b < kChunkItems * 4) for (int w = 0; w < kShadeThreads / 32; ++w) s_iff[w][0][b] = 0.f;
         }
     unsigned *sh_e = s_hist, *sh_a = s_hist + p.n_ebins;
     const unsigned n = min(*((volatile unsigned*)&ctl->count[gen]), cap_in);
@@ -626,8 +628,13 @@ k_shade(const float4* __restrict__ tris, const float4* __restrict__ normals, Tab
                 if (__any_sync(0xFFFFFFFFu, r.esc != 0u)) {
                     const FF es = ff_warp_sum(r.es), e2 = ff_warp_sum(r.e2);
                     if (lane == 0) {
-                        atomicAdd(&s_isum[j0][0], ff_double(es));
-                        atomicAdd(&s_isum[j0][1], ff_double(e2));
+                        // the warp's own slots: no atomics, and FP64 only once per item at the end
+                        float* f = s_iff[warp][j0];
+                        FF a, b;
+                        a.hi = f[0]; a.lo = f[1]; b.hi = f[2]; b.lo = f[3];
+                        a = ff_add(a, es);
+                        b = ff_add(b, e2);
+                        f[0] = a.hi; f[1] = a.lo; f[2] = b.hi; f[3] = b.lo;
                     }
                 }
             } else if (jslot >= 0) {
@@ -731,7 +738,13 @@ k_shade(const float4* __restrict__ tris, const float4* __restrict__ normals, Tab
                     atomicAdd(dst[tid], (unsigned long long)v);
                 }
             } else if (tid == 32 || tid == 33) {
-                const double v = s_isum[j][tid - 32];
+                double v = s_isum[j][tid - 32];
+                for (int w = 0; w < kShadeThreads / 32; ++w) {
+                    FF x;
+                    x.hi = s_iff[w][j][2 * (tid - 32)];
+                    x.lo = s_iff[w][j][2 * (tid - 32) + 1];
+                    v += ff_double(x);
+                }
                 if (v != 0.0) atomicAdd(tid == 32 ? &t->e_sum : &t->e2_sum, v);
             }
             unsigned long long* hh = ic.hists + (size_t)slot * nbins;
