@@ -73,29 +73,130 @@ __global__ void k_radix_hist(const unsigned* __restrict__ keys, int n, int shift
     hist[(long long)threadIdx.x * n_tiles + blockIdx.x] = cnt[threadIdx.x];
 }
 
-// ---- radix sort: exclusive scan of the digit-major histogram (one block) --
-__global__ void k_radix_scan(unsigned* __restrict__ hist, long long total)
+// ---- device-wide exclusive scan of 32-bit counts --------------------------
+// Tiles of kScanThreads threads x kScanPer consecutive elements.  Pass 1 sums
+// each tile, pass 2 scans the tile sums in one block, pass 3 rescans every tile
+// from its offset.  A whole tile moves as 16-byte vectors (the arrays come from
+// cudaMalloc, so a tile start is 16-byte aligned).  In place (in == out) is
+// fine: a tile is read before it is written, and only by its own block.
+constexpr int kScanThreads = 256, kScanPer = 16, kScanTile = kScanThreads * kScanPer;
+
+__device__ __forceinline__ void scan_load(const unsigned* __restrict__ in, long long n, long long i0,
+                                          unsigned (&v)[kScanPer])
+{
+    if (i0 + kScanPer <= n) {
+        const uint4* p = reinterpret_cast<const uint4*>(in + i0);
+#pragma unroll
+        for (int q = 0; q < kScanPer / 4; ++q) {
+            const uint4 w = p[q];
+            v[4 * q] = w.x; v[4 * q + 1] = w.y; v[4 * q + 2] = w.z; v[4 * q + 3] = w.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kScanPer; ++k) v[k] = i0 + k < n ? in[i0 + k] : 0u;
+    }
+}
+
+// Exclusive prefix of x over the block (kScanThreads threads); *sum gets the block total.
+__device__ __forceinline__ unsigned block_exclusive(unsigned x, unsigned* s_warp, unsigned& sum)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned incl = x;
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned y = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+        if (lane >= off) incl += y;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    unsigned before = 0, tot = 0;
+    for (int w = 0; w < kScanThreads / 32; ++w) {
+        const unsigned t = s_warp[w];
+        before += w < warp ? t : 0u;
+        tot += t;
+    }
+    sum = tot;
+    return before + incl - x;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_tiles(const unsigned* __restrict__ in, long long n, unsigned* __restrict__ part)
+{
+    __shared__ unsigned s_warp[kScanThreads / 32];
+    unsigned v[kScanPer];
+    scan_load(in, n, (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanPer, v);
+    unsigned t = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) t += v[k];
+    unsigned sum;
+    block_exclusive(t, s_warp, sum);
+    if (threadIdx.x == 0) part[blockIdx.x] = sum;
+}
+
+// One block: exclusive scan of the nb tile sums in place; the grand total to *total.
+__global__ void k_scan_parts(unsigned* __restrict__ part, long long nb, unsigned* __restrict__ total)
 {
     __shared__ unsigned sums[1024];
-    const long long per = (total + blockDim.x - 1) / blockDim.x;
-    const long long lo = threadIdx.x * per;
-    const long long hi = lo + per < total ? lo + per : total;
-    unsigned s = 0;
-    for (long long i = lo; i < hi; ++i) s += hist[i];
-    sums[threadIdx.x] = s;
+    const long long per = (nb + blockDim.x - 1) / blockDim.x;
+    const long long lo = threadIdx.x * per, hi = lo + per < nb ? lo + per : nb;
+    unsigned t = 0;
+    for (long long i = lo; i < hi; ++i) t += part[i];
+    sums[threadIdx.x] = t;
     __syncthreads();
     for (int off = 1; off < (int)blockDim.x; off <<= 1) {
-        unsigned v = threadIdx.x >= (unsigned)off ? sums[threadIdx.x - off] : 0u;
+        const unsigned v = threadIdx.x >= (unsigned)off ? sums[threadIdx.x - off] : 0u;
         __syncthreads();
         sums[threadIdx.x] += v;
         __syncthreads();
     }
-    unsigned run = sums[threadIdx.x] - s;       // exclusive prefix of this segment
+    unsigned run = sums[threadIdx.x] - t;
     for (long long i = lo; i < hi; ++i) {
-        const unsigned v = hist[i];
-        hist[i] = run;
+        const unsigned v = part[i];
+        part[i] = run;
         run += v;
     }
+    if (total && threadIdx.x == blockDim.x - 1) *total = sums[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_apply(const unsigned* in, unsigned* out, long long n, const unsigned* __restrict__ part)
+{
+    __shared__ unsigned s_warp[kScanThreads / 32];
+    const long long i0 = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanPer;
+    unsigned v[kScanPer];
+    scan_load(in, n, i0, v);
+    unsigned t = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) t += v[k];
+    unsigned sum;
+    unsigned run = part[blockIdx.x] + block_exclusive(t, s_warp, sum);
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+        const unsigned x = v[k];
+        v[k] = run;
+        run += x;
+    }
+    if (i0 + kScanPer <= n) {
+        uint4* p = reinterpret_cast<uint4*>(out + i0);
+#pragma unroll
+        for (int q = 0; q < kScanPer / 4; ++q) p[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < kScanPer; ++k)
+            if (i0 + k < n) out[i0 + k] = v[k];
+    }
+}
+
+// Tile sums needed by scan_exclusive for n elements.
+inline long long scan_parts(long long n) { return std::max<long long>((n + kScanTile - 1) / kScanTile, 1); }
+
+// out[i] = in[0] + ... + in[i-1] for i < n (in == out allowed); *total (device,
+// optional) = the sum of all n.  part: device scratch of scan_parts(n) words.
+void scan_exclusive(const unsigned* in, unsigned* out, long long n, unsigned* total, unsigned* part, cudaStream_t s)
+{
+    const long long nb = (n + kScanTile - 1) / kScanTile;
+    if (nb > 0) k_scan_tiles<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, part);
+    k_scan_parts<<<1, 1024, 0, s>>>(part, nb, total);
+    if (nb > 0) k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, part);
 }
 
 // ---- radix sort: stable scatter ------------------------------------------
@@ -730,27 +831,6 @@ __global__ void k_w4_count(const int2* __restrict__ front, int nf, const int2* _
     cnt[f] = m;
 }
 
-// Exclusive scan of cnt[0..n) into off, total to *tot (one block).
-__global__ void k_w4_scan(const int* __restrict__ cnt, int n, int* __restrict__ off, int* __restrict__ tot)
-{
-    __shared__ int sums[1024];
-    const int per = (n + (int)blockDim.x - 1) / (int)blockDim.x;
-    const int lo = threadIdx.x * per, hi = min(lo + per, n);
-    int t = 0;
-    for (int i = lo; i < hi; ++i) t += cnt[i];
-    sums[threadIdx.x] = t;
-    __syncthreads();
-    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
-        const int v = threadIdx.x >= (unsigned)o ? sums[threadIdx.x - o] : 0;
-        __syncthreads();
-        sums[threadIdx.x] += v;
-        __syncthreads();
-    }
-    int run = sums[threadIdx.x] - t;
-    for (int i = lo; i < hi; ++i) { off[i] = run; run += cnt[i]; }
-    if (threadIdx.x == blockDim.x - 1) *tot = sums[threadIdx.x];
-}
-
 __device__ __forceinline__ void w4_store(float4* __restrict__ w4, int w, const Box3 (&b)[4], const int (&ref)[4])
 {
     float4* nd = w4 + 8ll * w;
@@ -1115,12 +1195,13 @@ int build_lbvh(rtmc_ctx* ctx, DeviceMesh& m)
     cudaEventRecord(ev0, s);
 
     const int n_tiles = (n + kSortTile - 1) / kSortTile;
-    DevBuf k0, k1, v0, v1, hist, child, range, parent, leafp, flag, aabb, depth;
+    DevBuf k0, k1, v0, v1, hist, part, child, range, parent, leafp, flag, aabb, depth;
     e = k0.alloc(4ull * n);
     if (e == cudaSuccess) e = k1.alloc(4ull * n);
     if (e == cudaSuccess) e = v0.alloc(4ull * n);
     if (e == cudaSuccess) e = v1.alloc(4ull * n);
     if (e == cudaSuccess) e = hist.alloc(4ull * 256 * n_tiles);
+    if (e == cudaSuccess) e = part.alloc(4ull * scan_parts(256ll * n_tiles));
     if (e == cudaSuccess) e = child.alloc(8ull * n_nodes);
     if (e == cudaSuccess) e = range.alloc(8ull * n_nodes);
     if (e == cudaSuccess) e = parent.alloc(4ull * n_nodes);
@@ -1147,7 +1228,7 @@ int build_lbvh(rtmc_ctx* ctx, DeviceMesh& m)
     for (int pass = 0; pass < 4; ++pass) {
         const int shift = 8 * pass;
         k_radix_hist<<<n_tiles, kSortThreads, 0, s>>>(ki, n, shift, n_tiles, hist.as<unsigned>());
-        k_radix_scan<<<1, 1024, 0, s>>>(hist.as<unsigned>(), 256ll * n_tiles);
+        scan_exclusive(hist.as<unsigned>(), hist.as<unsigned>(), 256ll * n_tiles, nullptr, part.as<unsigned>(), s);
         k_radix_scatter<<<n_tiles, kSortThreads, 0, s>>>(ki, vi, ko, vo, n, shift, n_tiles, hist.as<unsigned>());
         unsigned* t = ki; ki = ko; ko = t;
         t = vi; vi = vo; vo = t;
@@ -1237,12 +1318,13 @@ int build_lbvh(rtmc_ctx* ctx, DeviceMesh& m)
             k_quantize<<<gi, tb, 0, s>>>(m.tri_in, order, n - 1, child.as<int2>(), range.as<int2>(), aabb.as<float4>(),
                                          m.leaf_max, w4_margin, reinterpret_cast<uint4*>(m.q8));
         if (wide) {
-            DevBuf fr[2], cnt, off, tot;
+            DevBuf fr[2], cnt, off, tot, part;
             e = fr[0].alloc(8ull * n_nodes);
             if (e == cudaSuccess) e = fr[1].alloc(8ull * n_nodes);
             if (e == cudaSuccess) e = cnt.alloc(4ull * n_nodes);
             if (e == cudaSuccess) e = off.alloc(4ull * n_nodes);
             if (e == cudaSuccess) e = tot.alloc(4);
+            if (e == cudaSuccess) e = part.alloc(4ull * scan_parts(n_nodes));
             if (e != cudaSuccess)
                 return ctx->fail(RTMC_ERR_OOM, std::string("build_bvh (4-wide) scratch: ") + cudaGetErrorString(e));
             const int2 root = make_int2(0, 0);
@@ -1253,7 +1335,7 @@ int build_lbvh(rtmc_ctx* ctx, DeviceMesh& m)
                 const int gf = (nf + kW4Block - 1) / kW4Block;
                 k_w4_count<<<gf, kW4Block, 0, s>>>(fr[cur].as<int2>(), nf, child.as<int2>(), range.as<int2>(),
                                                    aabb.as<float4>(), m.leaf_max, cnt.as<int>());
-                k_w4_scan<<<1, 1024, 0, s>>>(cnt.as<int>(), nf, off.as<int>(), tot.as<int>());
+                scan_exclusive(cnt.as<unsigned>(), off.as<unsigned>(), nf, tot.as<unsigned>(), part.as<unsigned>(), s);
                 k_w4_emit<<<gf, kW4Block, 0, s>>>(fr[cur].as<int2>(), nf, off.as<int>(), base, child.as<int2>(),
                                                   range.as<int2>(), aabb.as<float4>(), m.tri_in, order, m.leaf_max,
                                                   w4_margin, reinterpret_cast<float4*>(m.w4), fr[1 - cur].as<int2>());
@@ -1346,17 +1428,19 @@ int build_columns(rtmc_ctx* ctx, DeviceMesh& m)
         const int gy = std::min(2048, std::max(1, (int)std::lround(pix / gx)));
         const int np = gx * gy;
         const float iwx = (float)(gx / lx), iwy = (float)(gy / ly);
-        DevBuf cnt, tot, bad;
+        DevBuf cnt, tot, bad, part;
         cudaError_t e = cnt.alloc(4ull * np);
         if (e == cudaSuccess) e = tot.alloc(4);
         if (e == cudaSuccess) e = bad.alloc(4);
+        if (e == cudaSuccess) e = part.alloc(4ull * scan_parts(np));
         if (e == cudaSuccess) e = cudaMalloc(&m.col_off, 4ull * (np + 1));
         if (e == cudaSuccess) e = cudaMemsetAsync(cnt.p, 0, 4ull * np, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(bad.p, 0, 4, s);
         const int tb = 256, gb = (n + tb - 1) / tb;
         if (e == cudaSuccess) {
             k_col_count<<<gb, tb, 0, s>>>(m.tris, n, gx, gy, iwx, iwy, cnt.as<int>(), bad.as<int>());
-            k_w4_scan<<<1, 1024, 0, s>>>(cnt.as<int>(), np, reinterpret_cast<int*>(m.col_off), tot.as<int>());
+            scan_exclusive(cnt.as<unsigned>(), reinterpret_cast<unsigned*>(m.col_off), np, tot.as<unsigned>(),
+                           part.as<unsigned>(), s);
             e = cudaGetLastError();
         }
         int h_tot = 0, h_bad = 0;
@@ -1440,10 +1524,11 @@ bool slant_grid(rtmc_ctx* ctx, DeviceMesh& m, float dx, float dz, GridDev& out)
         const float iwx = (float)(gx / lx), iwy = (float)(gy / ly);
         SlantGrid g;
         g.dx = dx; g.dz = dz; g.gx = gx; g.gy = gy; g.iwx = iwx; g.iwy = iwy;
-        DevBuf cnt, tot, bad;
+        DevBuf cnt, tot, bad, part;
         cudaError_t e = cnt.alloc(4ull * np);
         if (e == cudaSuccess) e = tot.alloc(4);
         if (e == cudaSuccess) e = bad.alloc(4);
+        if (e == cudaSuccess) e = part.alloc(4ull * scan_parts(np));
         if (e == cudaSuccess) e = cudaMalloc(&g.off, 4ull * (np + 1));
         if (e == cudaSuccess) e = cudaMemsetAsync(cnt.p, 0, 4ull * np, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(bad.p, 0, 4, s);
@@ -1451,7 +1536,8 @@ bool slant_grid(rtmc_ctx* ctx, DeviceMesh& m, float dx, float dz, GridDev& out)
         if (e == cudaSuccess) {
             k_slant_count<<<gb, tb, 0, s>>>(m.tris, n, gx, gy, iwx, iwy, lx, z_top, shear, margin, cnt.as<int>(),
                                             bad.as<int>());
-            k_w4_scan<<<1, 1024, 0, s>>>(cnt.as<int>(), np, reinterpret_cast<int*>(g.off), tot.as<int>());
+            scan_exclusive(cnt.as<unsigned>(), reinterpret_cast<unsigned*>(g.off), np, tot.as<unsigned>(),
+                           part.as<unsigned>(), s);
             e = cudaGetLastError();
         }
         int h_tot = 0, h_bad = 0;
