@@ -381,7 +381,7 @@ def run_large(args):
         tuned = {}
     else:
         tuned = autotune.tune(ctx, [mid], [mesh.n_tri], [LARGE_E], LARGE_THETAS, kind=LARGE_KIND, cache_path=None,
-                              device_name=torch.cuda.get_device_name(dev), n_sample=100_000)
+                              device_name=torch.cuda.get_device_name(dev), n_sample=1_000_000)
     nb = dict(n_ebins=LARGE_BINS[0], n_abins=LARGE_BINS[1])
     desc = rtmc.run_desc(primary_offset=offset, profile=True, no_graph=True, **nb, **tuned)
 

@@ -102,7 +102,7 @@ typedef struct {
     int32_t max_wraps;             /* lateral re-entries before a ray counts as lost (0 -> 1024) */
     double src_x0, src_x1, src_y0, src_y1;   /* primary source window; all 0 -> whole cell */
     int64_t chunk;                 /* primaries per wavefront chunk (0 -> automatic) */
-    int32_t block_threads;         /* traversal block size (0 -> 128) */
+    int32_t block_threads;         /* traversal block size (0 -> 64) */
     int32_t blocks_per_sm;         /* persistent traversal blocks per SM (0 -> occupancy) */
     uint64_t* prim_hash;           /* optional DEVICE array [n_primaries]: per-primary
                                       sum of record hashes (see rtmc_record_hash) */
@@ -120,7 +120,7 @@ typedef struct {
     uint32_t item_base;            /* added to every item index (Philox counter word 3) */
     int32_t no_graph;              /* rtmc_run_batch: 1 = launch eagerly, no CUDA graph */
     int32_t stack_depth;           /* shared-memory traversal stack entries: 8, 16 or 32 (0 -> 16) */
-    int32_t fetch_threshold;       /* warp refills rays when fewer lanes than this are busy (0 -> 20) */
+    int32_t fetch_threshold;       /* warp refills rays when fewer lanes than this are busy (0 -> 28) */
     int32_t random_polar;          /* 1: random incidence -- polar angle from the cosine law
                                       (sin^2 theta = u of a second Philox block, path 0) and
                                       uniform azimuth; the item angle is ignored */

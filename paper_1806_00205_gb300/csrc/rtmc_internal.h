@@ -65,11 +65,11 @@ struct Scratch {
 };
 
 struct Tuning {
-    int block_threads = 128;
+    int block_threads = 64;
     int blocks_per_sm = 0;         // 0: from occupancy
     int traversal = 0;             // 0/2: while-while with ray refill, 1: one ray per lane per tile
     int stack_depth = 16;          // shared-memory stack entries per ray (8, 16, 32)
-    int fetch_threshold = 0;       // refill when fewer lanes are active (0: default 20)
+    int fetch_threshold = 0;       // refill when fewer lanes are active (0: default 28)
     int max_visits = 0;            // lower bound on inner-node visits per cell traversal (0: the tree's own)
 };
 

@@ -609,7 +609,7 @@ __device__ __noinline__ Hit64 facet_fp64(float3 o, float3 d, float4 w0, float4 w
 // decision.
 // --------------------------------------------------------------------------
 constexpr int kEntrySentinel = 0x76543210;   // "stack empty" (never a node index)
-constexpr int kFetchThreshold = 20;          // default: refill when fewer lanes than this are active
+constexpr int kFetchThreshold = 28;          // default: refill when fewer lanes than this are active
 constexpr float kEdgeEps = 1e-5f;
 constexpr float kGrazeCos = 1e-3f;
 constexpr int kAmbMax = 4;

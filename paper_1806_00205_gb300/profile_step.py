@@ -9,7 +9,9 @@ BVH and column grids, runs ``--warmup`` batched steps (``rtmc_run_batch``: every
 angle one item, tertiaries for secondaries above ``--regen-min`` eV), then brackets
 ``--steps`` more with ``cudaProfilerStart`` / ``cudaProfilerStop`` so that ``ncu
 --profile-from-start off`` sees only those launches, and prints one JSON line with the
-rays traced and the device time of each phase.
+rays traced and the device time of each phase.  With ``--build`` the bracket covers the mesh
+upload, the BVH and vertical-grid build and one step instead, whose first use of each
+oblique angle builds that angle's slanted grid (no warm-up).
 
 Summary modes (no GPU)::
 
@@ -50,19 +52,25 @@ def run_step(a):
     mesh = I.grf_foam(a.grid, a.porosity, 2.0, a.seed)
     ctx = rtmc.Context(0)
     ctx.load_see_tables(I.see_table(), rtmc.Emission(regen_min_ev=a.regen_min, max_generation=a.max_generation))
-    mid = ctx.load_mesh(mesh.tri, mesh.box)
-    ctx.build_bvh(mid, kind=a.kind)
     thetas = [float(x) for x in a.angles.split(",")]
     desc = rtmc.run_desc(n_ebins=128, n_abins=36, no_graph=True, profile=True, chunk=a.chunk)
+    cudart = torch.cuda.cudart()
+    if a.build:
+        # the profiled range: mesh upload, BVH and vertical grid, then one step,
+        # whose first use of each oblique angle builds that angle's slanted grid
+        torch.cuda.synchronize()
+        cudart.cudaProfilerStart()
+    mid = ctx.load_mesh(mesh.tri, mesh.box)
+    ctx.build_bvh(mid, kind=a.kind)
 
     def step():
         return ctx.run_batch([mid], [a.energy], thetas, a.primaries, a.seed, desc=desc)
 
-    for _ in range(a.warmup):
-        step()
-    torch.cuda.synchronize()
-    cudart = torch.cuda.cudart()
-    cudart.cudaProfilerStart()
+    if not a.build:
+        for _ in range(a.warmup):
+            step()
+        torch.cuda.synchronize()
+        cudart.cudaProfilerStart()
     out = []
     for _ in range(a.steps):
         res, _, _ = step()
@@ -164,6 +172,8 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=1806)
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--build", action="store_true",
+                    help="profile the mesh upload, the BVH and grid builds and one step instead (no warm-up)")
     ap.add_argument("--launches", metavar="CSV", help="summarise an ncu launch list")
     ap.add_argument("--traffic", metavar="CSV", help="DRAM bytes per traversal ray from an ncu capture")
     ap.add_argument("--step-json", metavar="FILE", help="run-mode output belonging to --traffic")

@@ -14,7 +14,8 @@ def autotune():
 
 
 class FakeCtx:
-    """run_batch returns a time that is smallest at stack 16, threshold 20, 64 threads, 0 blocks/SM."""
+    """run_batch returns a time that is smallest at stack 16, threshold 20, 64 threads, 0 blocks/SM
+    (the library defaults use threshold 28, 2 ms slower here)."""
 
     def __init__(self):
         self.calls = []
@@ -66,3 +67,25 @@ def test_tune_caches_per_device_format_and_sizes(autotune, tmp_path):
     assert len(ctx.calls) == 2 * n                               # another node format is tuned anew
     autotune.tune(ctx, [0, 1], [100, 7000], [300.0], [0.0], kind=1, cache_path=path, device_name="a")
     assert len(ctx.calls) == 3 * n                               # so are other mesh sizes
+
+
+class FlatCtx:
+    """The defaults take 10 ms, every other candidate 10.05 ms, except (8, 12, 128, 0): `fast` ms."""
+
+    def __init__(self, defaults, fast):
+        self.defaults, self.fast = defaults, fast
+
+    def run_batch(self, ids, energies, thetas, n, seed, desc):
+        p = (desc.stack_depth, desc.fetch_threshold, desc.block_threads, desc.blocks_per_sm)
+        ms = 10.0 if p == self.defaults else (self.fast if p == (8, 12, 128, 0) else 10.05)
+        return [{"gpu_ms": ms}], None, None
+
+
+def test_tune_keeps_the_defaults_unless_clearly_faster(autotune):
+    d = autotune.DEFAULTS
+    defaults = (d["stack_depth"], d["fetch_threshold"], d["block_threads"], d["blocks_per_sm"])
+    assert autotune.MARGIN == 0.02
+    kept = autotune.tune(FlatCtx(defaults, 9.9), [0], [100], [300.0], [0.0], cache_path=None)
+    assert kept == d                                              # 1 % faster: within the margin
+    moved = autotune.tune(FlatCtx(defaults, 9.7), [0], [100], [300.0], [0.0], cache_path=None)
+    assert moved == {"stack_depth": 8, "fetch_threshold": 12, "block_threads": 128, "blocks_per_sm": 0}
