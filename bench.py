@@ -51,12 +51,13 @@ LARGE_E, LARGE_THETAS = 500.0, [10.0 * j for j in range(9)]
 LARGE_N_PRIM = 100_000_000
 LARGE_KIND = 3                                  # 4-wide nodes with 8-bit child boxes (compressed)
 LARGE_BINS = (128, 36)
+LARGE_MAX_GEN = 2                               # tertiaries: secondaries above 20 eV re-emit once
 NODE_NAME = {0: "binary FP32", 1: "binary Q8", 2: "4-wide FP32", 3: "4-wide Q8"}
 
 
 def large_emission(rtmc_or_oracle):
     """Tertiaries: secondaries at or above 20 eV re-emit once (max_generation 2)."""
-    return rtmc_or_oracle.Emission(regen_min_ev=20.0, max_generation=2)
+    return rtmc_or_oracle.Emission(regen_min_ev=20.0, max_generation=LARGE_MAX_GEN)
 
 
 def large_workload_name(n_tri, n_prim):
@@ -499,7 +500,10 @@ def run_large(args):
                 "hbm_frac": trav["frac_of_measured_hbm"], "hbm_peak": hbm_peak,
                 "hbm_read_probe_gbs": hbm_read_gbs, "l2_read_probe_gbs": l2_gbs}
     kernels = {"k_traverse_ww": trav,
-               "k_shade": kernel_fields(k["shade_ms"], 0, k["shade_bytes"], hbm_peak, "hbm", {
+               # one shade launch per generation of every chunk; every chunk of this workload runs
+               # the hierarchy once per generation after the first
+               "k_shade": kernel_fields(k["shade_ms"], k["trav_l"] // LARGE_MAX_GEN * (LARGE_MAX_GEN + 1),
+                                        k["shade_bytes"], hbm_peak, "hbm", {
                    "peak_kind": f"{pk_kind} hbm_gbs", "note": "queue entry + hit per ray, facet + normal per "
                                                               "stop, 48 B per daughter written"}),
                "generate_ms": k["gen_ms"], "finalize_ms": k["fin_ms"],

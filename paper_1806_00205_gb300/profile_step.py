@@ -6,7 +6,7 @@ Run mode (the command a profiler wraps)::
 
 builds a periodic GRF foam (the synthetic porous-surface recipe of the inputs module), its
 BVH and column grids, runs ``--warmup`` batched steps (``rtmc_run_batch``: every incidence
-angle one item, tertiaries for secondaries above ``--regen-min`` eV), then brackets
+energy and angle one item, tertiaries for secondaries above ``--regen-min`` eV), then brackets
 ``--steps`` more with ``cudaProfilerStart`` / ``cudaProfilerStop`` so that ``ncu
 --profile-from-start off`` sees only those launches, and prints one JSON line with the
 rays traced and the device time of each phase.  With ``--build`` the bracket covers the mesh
@@ -53,6 +53,7 @@ def run_step(a):
     ctx = rtmc.Context(0)
     ctx.load_see_tables(I.see_table(), rtmc.Emission(regen_min_ev=a.regen_min, max_generation=a.max_generation))
     thetas = [float(x) for x in a.angles.split(",")]
+    energies = [float(x) for x in a.energies.split(",")]
     desc = rtmc.run_desc(n_ebins=128, n_abins=36, no_graph=True, profile=True, chunk=a.chunk)
     cudart = torch.cuda.cudart()
     if a.build:
@@ -64,7 +65,7 @@ def run_step(a):
     ctx.build_bvh(mid, kind=a.kind)
 
     def step():
-        return ctx.run_batch([mid], [a.energy], thetas, a.primaries, a.seed, desc=desc)
+        return ctx.run_batch([mid], energies, thetas, a.primaries, a.seed, desc=desc)
 
     if not a.build:
         for _ in range(a.warmup):
@@ -82,8 +83,9 @@ def run_step(a):
                         launches=r0["launches"], traverse_launches=r0["traverse_launches"]))
     torch.cuda.synchronize()
     cudart.cudaProfilerStop()
-    print(json.dumps(dict(grid=a.grid, porosity=a.porosity, n_tri=mesh.n_tri, kind=a.kind, energy=a.energy,
-                          angles=thetas, primaries=a.primaries, steps=out, kernel_sha=traverse_sha())),
+    print(json.dumps(dict(grid=a.grid, porosity=a.porosity, n_tri=mesh.n_tri, kind=a.kind, energies=energies,
+                          angles=thetas, primaries=a.primaries, max_generation=a.max_generation, steps=out,
+                          kernel_sha=traverse_sha())),
           flush=True)
     ctx.close()
 
@@ -153,7 +155,8 @@ def summarize_traffic(path, step_json, kind):
     tot = sum(d.get("dram_read_bytes", 0.0) + d.get("dram_write_bytes", 0.0) for d in lst)
     rec = dict(kernel=lst[0]["kernel"] if lst else None, kernel_sha=step["kernel_sha"], node_format=kind,
                dram_bytes_per_ray=tot / hier if hier else None, hierarchy_rays=hier,
-               workload=dict((k, step[k]) for k in ("grid", "porosity", "n_tri", "energy", "angles", "primaries")),
+               workload=dict((k, step[k]) for k in ("grid", "porosity", "n_tri", "energies", "angles", "primaries",
+                                                    "max_generation")),
                launches=lst)
     print(json.dumps(rec, indent=1))
 
@@ -163,9 +166,9 @@ def main(argv=None):
     ap.add_argument("--grid", type=int, default=192, help="foam voxels per side")
     ap.add_argument("--porosity", type=float, default=0.7)
     ap.add_argument("--kind", type=int, default=3, help="BVH node format (3: 4-wide 8-bit boxes)")
-    ap.add_argument("--primaries", type=int, default=2_000_000, help="per incidence angle")
+    ap.add_argument("--primaries", type=int, default=2_000_000, help="per item (energy, angle)")
     ap.add_argument("--angles", default="0,40,80", help="incidence angles, degrees")
-    ap.add_argument("--energy", type=float, default=500.0)
+    ap.add_argument("--energies", default="500", help="primary energies, eV (every energy x angle is one item)")
     ap.add_argument("--regen-min", type=float, default=20.0)
     ap.add_argument("--max-generation", type=int, default=2)
     ap.add_argument("--chunk", type=int, default=0)

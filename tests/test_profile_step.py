@@ -43,7 +43,8 @@ def test_traffic_record_per_hierarchy_ray(tmp_path, capsys):
                  row(2, TRAV, "dram__bytes_write.sum", "byte", "0"))
     step = tmp_path / "s.json"
     step.write_text("warming up\n" + json.dumps(dict(
-        grid=8, porosity=0.7, n_tri=100, energy=500.0, angles=[0.0], primaries=10, kernel_sha="abc",
+        grid=8, porosity=0.7, n_tri=100, energies=[500.0], angles=[0.0], primaries=10, max_generation=2,
+        kernel_sha="abc",
         steps=[dict(hierarchy_rays=30000, rays=40000)])) + "\n")
     P.summarize_traffic(str(f), str(step), 3)
     rec = json.loads(capsys.readouterr().out)
