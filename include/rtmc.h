@@ -215,8 +215,9 @@ int rtmc_load_see_tables(rtmc_ctx* ctx, const float* delta, const rtmc_grid* gri
    four children; leaves are those of the binary hierarchy), level by level,
    one host synchronisation per level.  RTMC_BVH_Q4 builds that 4-wide
    hierarchy and quantises every node to 64 bytes: per axis a quantum
-   s = 2^e and a frame origin, and per child and plane one byte, rounded
-   outward by at least s + M 2^-21 (M the largest cell coordinate) so that the
+   s = 2^e and a frame origin, and per child and plane one byte: each plane is
+   moved outward by M 2^-21 + s 2^-7 beyond the 4-wide box (M the largest cell
+   coordinate), then rounded outward to the quantum grid, so that the
    traversal may evaluate each plane with one FMA.  RTMC_ERR_INVALID_ARG if a
    node would need a quantum above 2^40 (coordinates beyond about 2^47).
    Every kind also gets a column grid for rays parallel to z (generation 0 at
@@ -302,10 +303,11 @@ int rtmc_trace_rays(rtmc_ctx* ctx, int32_t mesh_id, const float* o, const float*
    four child boxes, each widened outward by M 2^-22 with M the largest
    coordinate of the cell, then the four child refs; an empty slot has ref
    INT_MIN and the box [+inf, +inf]^3), 4 quantised 4-wide nodes
-   (RTMC_BVH_Q4 meshes only, n_w4 x 64 B: floats o'.x, o'.y, o'.z, s.x | s.y,
-   s.z, then six words lo.x, hi.x, lo.y, hi.y, lo.z, hi.z whose byte c is
-   child c's code q, then the four child refs; a plane is o' + (2^23 + q) s,
-   an empty slot has codes lo 255, hi 0 and ref INT_MIN).  Layouts as in the library's
+   (RTMC_BVH_Q4 meshes only, n_w4 x 64 B: floats o'.x, o'.y, o'.z, S.x | S.y,
+   S.z, then six words lo.x, hi.x, lo.y, hi.y, lo.z, hi.z whose byte c is
+   child c's code q, then the four child refs; S = 2^15 s with s the quantum,
+   a plane is o' + (1 + q 2^-15) S, an empty slot has codes lo 255, hi 0 and
+   ref INT_MIN).  Layouts as in the library's
    device code; a Q8 node holds per axis a shifted origin o' (float) and a
    biased exponent byte b (scale s = 2^(b - 127)), and child bound q decodes
    as fmaf(2^23 + q, s, o') in FP32.  With out == NULL only *bytes_needed is written; otherwise

@@ -905,11 +905,15 @@ __global__ void k_w4_single(const float* __restrict__ tri, float margin, float4*
 // ---- 4-wide nodes quantised to 8 bits ---------------------------------------
 // Per axis a quantum s = 2^e and an integer frame start m (origin m s); child
 // plane codes q in [0, 255] stand for (m + q) s.  The traversal evaluates a
-// plane as fmaf(2^23 + q, s / d, (o' - o) / d) with o' = (m - 2^23) s: the
+// plane as fmaf(1 + q 2^-15, S / d, (o' - o) / d) with S = 2^15 s and
+// o' = (m - 2^15) s, both exact in FP32 (|m - 2^15| < 2^24).  The product
+// (1 + q 2^-15) S / d is exact inside the FMA (S is a power of two); the
 // rounding of o' - o and of its quotient moves a plane by at most
-// |o' - o| 2^-23 <= s + M 2^-22 (|o'| < 2^23 s + M, |o| <= M), so every code
-// is rounded outward by k = 1 + ceil(M 2^-21 / s) quanta beyond the FP32
-// 4-wide box.  All of it is exact in FP64: s is a power of two, |m| < 2^23.
+// |o' - o| 2^-23 <= M 2^-22 + s 2^-8 (|m s| <= M, |o| <= M), so every plane
+// is rounded outward from the FP32 4-wide box by twice that, M 2^-21 + s 2^-7,
+// before it is rounded to the quantum grid -- a small fraction of a quantum
+// where the shifted origin (m - 2^23) s of the 0x4B0000qq decode needed one
+// whole quantum.  All of it is exact in FP64: s is a power of two, |m| < 2^23.
 // Returns false when no quantum up to 2^kQ4MaxExp fits (coordinates too large).
 __device__ bool q4_axis(const float4& lo_row, const float4& hi_row, const bool (&real)[4], double big,
                         float& o_shift, float& scale, unsigned& w_lo, unsigned& w_hi)
@@ -925,21 +929,21 @@ __device__ bool q4_axis(const float4& lo_row, const float4& hi_row, const bool (
     if (mag > 0.0) e = max(e, ilogb(mag) - 22);
     for (; e <= kQ4MaxExp; ++e) {
         const double sc = ldexp(1.0, e);
-        const double k = 1.0 + ceil(big * 0x1p-21 / sc);
-        const double m = floor(L / sc) - k;
-        if (!(fabs(m) < 0x1p23) || ceil((H - m * sc) / sc) + k > 255.0) continue;
+        const double margin = big * 0x1p-21 + sc * 0x1p-7;
+        const double m = floor((L - margin) / sc);
+        if (!(fabs(m) < 0x1p23) || ceil((H + margin - m * sc) / sc) > 255.0) continue;
         w_lo = w_hi = 0u;
         for (int c = 0; c < 4; ++c) {
             unsigned ql = 255u, qh = 0u;                 // empty slot: lo above hi
             if (real[c]) {
-                ql = (unsigned)(floor(((double)lo[c] - m * sc) / sc) - k);
-                qh = (unsigned)(ceil(((double)hi[c] - m * sc) / sc) + k);
+                ql = (unsigned)floor(((double)lo[c] - margin - m * sc) / sc);
+                qh = (unsigned)ceil(((double)hi[c] + margin - m * sc) / sc);
             }
             w_lo |= ql << (8 * c);
             w_hi |= qh << (8 * c);
         }
-        o_shift = (float)((m - 0x1p23) * sc);
-        scale = (float)sc;
+        o_shift = (float)((m - 0x1p15) * sc);
+        scale = (float)(sc * 0x1p15);
         return true;
     }
     return false;

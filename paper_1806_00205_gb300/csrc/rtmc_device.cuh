@@ -109,7 +109,7 @@ constexpr int FMT_FP32 = 0;
 constexpr int FMT_Q8 = 1;
 constexpr int FMT_W4 = 2;         // 4-wide nodes, FP32 child boxes (128 B)
 constexpr int FMT_Q4 = 3;         // 4-wide nodes, 8-bit child boxes (64 B)
-// A 4-wide 8-bit node keeps its shifted frame origin (|o'| about 2^23 quanta)
+// A 4-wide 8-bit node keeps its shifted frame origin (|o'| below 2^24 quanta)
 // finite after the slab test multiplies it by 1/d: the quantum stays below
 // 2^kQ4MaxExp and the traversal clamps |1/d| to 2^kQ4MaxInvExp.
 constexpr int kQ4MaxExp = 40;
@@ -126,6 +126,12 @@ __device__ __forceinline__ float exp2_int(int e) { return __int_as_float((e + 12
 __device__ __forceinline__ float byte_m(unsigned w, int k)
 {
     return __int_as_float(__byte_perm(w, 0x4B000000u, (unsigned)k | 0x7540u));
+}
+
+// Byte q = byte k of w as the float 0x3F80qq00, i.e. 1 + q 2^-15 (exact).
+__device__ __forceinline__ float byte_f(unsigned w, int k)
+{
+    return __int_as_float(__byte_perm(w, 0x3F800000u, 0x7604u | ((unsigned)k << 4)));
 }
 
 // --------------------------------------------------------------------------

@@ -135,14 +135,15 @@ __device__ __forceinline__ void node4_children(const void* __restrict__ nodes, i
 {
     bool h0, h1, h2, h3;
     if constexpr (FMT == FMT_Q4) {
-        // Plane (m + q) s evaluated as fmaf(2^23 + q, s / d, (o' - o) / d): one
-        // FMA per plane on the code byte made a float by __byte_perm.  The
-        // codes are rounded outward far enough to cover the rounding of
-        // (o' - o) / d (see the quantiser); the near row of each axis is
-        // chosen by the sign of the direction, as for FP32 nodes.
+        // Plane (m + q) s evaluated as fmaf(1 + q 2^-15, S / d, (o' - o) / d)
+        // with S = 2^15 s and o' = (m - 2^15) s: one FMA per plane on the code
+        // byte made a float by __byte_perm.  The codes are rounded outward far
+        // enough to cover the rounding of (o' - o) / d (see the quantiser); the
+        // near row of each axis is chosen by the sign of the direction, as for
+        // FP32 nodes.
         const float4* np = reinterpret_cast<const float4*>(nodes) + 4ll * node;
         float4 a, b, c, cr;
-        ldg8(np, a, b);                          // o'.xyz, s.x | s.y, s.z, row lo.x, row hi.x
+        ldg8(np, a, b);                          // o'.xyz, S.x | S.y, S.z, row lo.x, row hi.x
         ldg8(np + 2, c, cr);                     // rows lo.y, hi.y, lo.z, hi.z | refs
         const float kx = a.w * r.inv.x, ky = b.x * r.inv.y, kz = b.y * r.inv.z;
         const float ox = (a.x - r.o.x) * r.inv.x, oy = (a.y - r.o.y) * r.inv.y, oz = (a.z - r.o.z) * r.inv.z;
@@ -156,9 +157,9 @@ __device__ __forceinline__ void node4_children(const void* __restrict__ nodes, i
         ck[0] = __float_as_int(cr.x); ck[1] = __float_as_int(cr.y);
         ck[2] = __float_as_int(cr.z); ck[3] = __float_as_int(cr.w);
         auto child = [&](int j, float& tmin, bool& hit) {
-            const float tnx = fmaf(byte_m(nxw, j), kx, ox), tfx = fmaf(byte_m(fxw, j), kx, ox);
-            const float tny = fmaf(byte_m(nyw, j), ky, oy), tfy = fmaf(byte_m(fyw, j), ky, oy);
-            const float tnz = fmaf(byte_m(nzw, j), kz, oz), tfz = fmaf(byte_m(fzw, j), kz, oz);
+            const float tnx = fmaf(byte_f(nxw, j), kx, ox), tfx = fmaf(byte_f(fxw, j), kx, ox);
+            const float tny = fmaf(byte_f(nyw, j), ky, oy), tfy = fmaf(byte_f(fyw, j), ky, oy);
+            const float tnz = fmaf(byte_f(nzw, j), kz, oz), tfz = fmaf(byte_f(fzw, j), kz, oz);
             tmin = fmaxf(fmaxf(tnx, tny), fmaxf(tnz, 0.f));
             const float tmax = fminf(fminf(tfx, tfy), fminf(tfz, t_best));
             hit = tmin <= tmax * kRobust;
