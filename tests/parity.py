@@ -47,7 +47,7 @@ U32 = 2.0 ** -24           # unit roundoff of FP32
 # normal incidence.
 E_REL = 1e-5
 E_ABS = 1e-4               # eV
-T_REL = 1e-5               # FP32 intersection of one ray against FP64 (the benchmark spec tolerance)
+T_REL = 1e-5               # FP32 intersection of one ray against FP64 (the stated hit-distance tolerance)
 K_SETUP = 16.0             # FP32 roundings per ray set-up step (see t_error_bound)
 
 
