@@ -65,7 +65,7 @@ def test_device_philox_matches_oracle(ctx):
 
 # ------------------------------------------------------------- BVH hits ----
 
-def _rays_for(mesh, n, rng):
+def _rays_for(mesh, n, rng, reach=5.0):
     box = mesh.box
     o = np.stack([rng.uniform(0, box.lx, n), rng.uniform(0, box.ly, n),
                   rng.uniform(box.z_min + 0.3 * (box.z_top - box.z_min), box.z_top, n)], axis=1)
@@ -76,7 +76,7 @@ def _rays_for(mesh, n, rng):
     k = n // 4
     pick = rng.integers(0, mesh.n_tri, k)
     tgt = np.where(rng.random(k)[:, None] < 0.5, tri[pick, 0], 0.5 * (tri[pick, 0] + tri[pick, 1]))
-    o2 = tgt + rng.normal(size=(k, 3)) * 5.0
+    o2 = tgt + rng.normal(size=(k, 3)) * reach
     d2 = tgt - o2
     d2 /= np.linalg.norm(d2, axis=1)[:, None]
     return np.concatenate([o, o2]).astype(np.float32), np.concatenate([d, d2]).astype(np.float32)
@@ -118,6 +118,36 @@ def test_bvh_closest_hit_matches_brute_force(ctx, which, kind, leaf, ploc):
             near.append(min(g["u"], g["v"], 1 - g["u"] - g["v"]) < 1e-4)
         assert any(near), (i, g, (t, j, u, v))
     assert same_rand >= 0.999 * n_rand
+
+
+@pytest.mark.parametrize("kind", [2, 3])
+@pytest.mark.parametrize("h", [1.0e-3, 1.0e4])
+def test_four_wide_closest_hit_at_extreme_scales(ctx, kind, h):
+    """The 4-wide nodes' one-FMA planes and the 8-bit codes' margins (M 2^-21 + s 2^-7) at voxel
+    sizes 1e-3 and 1e4 (cells of 8e-3 and 8e4): closest hits still equal brute force."""
+    mesh = I.grf_foam(8, 0.7, 1.5, 3, h=h)
+    mid = ctx.load_mesh(mesh.tri, mesh.box)
+    ctx.build_bvh(mid, kind=kind)
+    rng = np.random.default_rng(7)
+    o, d = _rays_for(mesh, 3000, rng, reach=0.5 * h)       # aimed rays start a few voxels away
+    hits = ctx.trace_rays(mid, o, d, np.full(o.shape[0], -1, dtype=np.int32))
+    ctx.unload_mesh(mid)
+    same = 0
+    for i in range(o.shape[0]):
+        t, j, u, v = O.closest_hit(mesh, o[i].astype(np.float64), d[i].astype(np.float64), -1)
+        g = hits[i]
+        if g["tri"] == j:
+            same += i < 3000                            # the random rays (the rest aim at vertices and edges)
+            if j >= 0:
+                assert abs(g["t"] - t) <= 1e-5 * max(t, h), (i, g, t)
+            continue
+        near = []
+        if j >= 0:
+            near.append(min(u, v, 1 - u - v) < 1e-4)
+        if g["tri"] >= 0:
+            near.append(min(g["u"], g["v"], 1 - g["u"] - g["v"]) < 1e-4)
+        assert any(near), (i, g, (t, j, u, v))
+    assert same >= 0.999 * 3000
 
 
 # ---------------------------------------------------------- full runs ------
