@@ -429,13 +429,7 @@ def run_large(args):
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     mem_used = (total_mem - torch.cuda.mem_get_info(dev)[0]) / 1e9
-    t = torch.tensor([ms, rays, prims], dtype=torch.float64, device=dev)
-    if world > 1:
-        tmax = t[:1].clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        tsum = t[1:].clone()
-        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
-        ms, rays, prims = tmax.item(), tsum[0].item(), tsum[1].item()
+    ms, (rays, prims) = shard.reduce_timing(ms, [rays, prims], device=dev)     # max time, summed work
     value = rays / (ms / 1e3)
     local_rays = sum(r["rays"] for r in results) * args.steps
 
@@ -527,11 +521,7 @@ def run_large(args):
         e_rays += sum(r["rays"] for r in rr)
     barrier()
     e_dt = time.perf_counter() - e_t0
-    et = torch.tensor([e_dt, e_rays], dtype=torch.float64, device=dev)
-    if world > 1:
-        a = et[:1].clone(); dist.all_reduce(a, op=dist.ReduceOp.MAX)
-        b = et[1:].clone(); dist.all_reduce(b, op=dist.ReduceOp.SUM)
-        e_dt, e_rays = a.item(), b.item()
+    e_dt, (e_rays,) = shard.reduce_timing(e_dt, [e_rays], device=dev)
 
     extra = {}
     if rank == 0 and not args.no_paper:
@@ -835,13 +825,7 @@ def run_ours(args):
     barrier()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms, rays, prims], dtype=torch.float64, device=dev)
-    if world > 1:
-        tmax = t[:1].clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        tsum = t[1:].clone()
-        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
-        ms, rays, prims = tmax.item(), tsum[0].item(), tsum[1].item()
+    ms, (rays, prims) = shard.reduce_timing(ms, [rays, prims], device=dev)     # max time, summed work
     value = rays / (ms / 1e3)
 
     # the same steps replayed from the captured CUDA graph
@@ -900,11 +884,7 @@ def run_ours(args):
         e_rays += sum(r["rays"] for r in rr)
     barrier()
     e_dt = time.perf_counter() - e_t0
-    et = torch.tensor([e_dt, e_rays], dtype=torch.float64, device=dev)
-    if world > 1:
-        a = et[:1].clone(); dist.all_reduce(a, op=dist.ReduceOp.MAX)
-        b = et[1:].clone(); dist.all_reduce(b, op=dist.ReduceOp.SUM)
-        e_dt, e_rays = a.item(), b.item()
+    e_dt, (e_rays,) = shard.reduce_timing(e_dt, [e_rays], device=dev)
 
     forms = None
     if rank == 0 and not args.no_forms:

@@ -57,3 +57,21 @@ def gather_merge(result, group=None):
     plain = {k: (v.tolist() if hasattr(v, "tolist") else v) for k, v in result.items() if k != "records"}
     dist.gather_object(plain, parts, dst=0, group=group)
     return merge_results(parts) if rank == 0 else None
+
+
+def reduce_timing(ms, counts, device=None, group=None):
+    """Whole-job timing of a sharded step: the slowest rank's time and the summed counts.
+
+    Every rank passes its own elapsed time `ms` and its counts (rays, primaries, ...); all
+    ranks get back (max ms over ranks, [sum of each count over ranks]).  One all-reduce of
+    each kind, on `device` (the rank's GPU under NCCL, the CPU under gloo).  Without an
+    initialised process group the inputs come back unchanged."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size(group) == 1:
+        return float(ms), [float(c) for c in counts]
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    c = torch.tensor([float(x) for x in counts], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM, group=group)
+    return t.item(), c.tolist()

@@ -66,3 +66,38 @@ def test_two_gloo_ranks_equal_one_run():
     assert merged["hist_e"] == full["hist_e"].tolist()
     assert abs(merged["e_sum"] - full["e_sum"]) <= 1e-9 * max(1.0, full["e_sum"])
     assert merged["sey"] == full["sey"]
+
+
+def _timing_worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    # rank r took 10 + 5 r ms and traced 1000 (r + 1) rays of 100 primaries
+    ms, counts = shard.reduce_timing(10.0 + 5.0 * rank, [1000.0 * (rank + 1), 100.0], device="cpu")
+    q.put((rank, ms, counts))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_reduce_timing_takes_the_slowest_rank_and_sums_the_work():
+    import torch.multiprocessing as mp
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_timing_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    got = sorted(q.get(timeout=180) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, ms, counts in got:                 # every rank sees the whole-job numbers
+        assert ms == 15.0 and counts == [3000.0, 200.0]
+    # throughput as the bench reports it: summed work over the slowest rank's time
+    assert counts[0] / (ms / 1e3) == 200000.0
+
+
+def test_reduce_timing_without_a_process_group_is_the_identity():
+    assert shard.reduce_timing(12.5, [7, 3]) == (12.5, [7.0, 3.0])
