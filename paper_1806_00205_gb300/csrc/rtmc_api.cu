@@ -259,7 +259,7 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
         if (ce == cudaSuccess) ce = scratch_reserve(ctx->kcount, (size_t)chunk * 4);
         if (ce == cudaSuccess && kc_new) ce = cudaMemsetAsync(ctx->kcount.ptr, 0, ctx->kcount.bytes, s);
         if (ce == cudaSuccess) ce = scratch_reserve(ctx->ctl, sizeof(Control));
-        if (ce == cudaSuccess && !d.id_order) ce = scratch_reserve(ctx->sort_counts, (size_t)kSortBucketsPerItem * 4);
+        if (ce == cudaSuccess && !d.id_order) ce = scratch_reserve(ctx->sort_counts, sort_scratch_bytes(1));
         if (ce == cudaSuccess) ce = scratch_reserve(ctx->tally, sizeof(Tally));
         if (ce == cudaSuccess) ce = scratch_reserve(ctx->hist, (size_t)(d.n_ebins + d.n_abins + d.n_zbins) * 8);
         if (ce == cudaSuccess && record) ce = scratch_reserve(ctx->records, (size_t)std::max<int64_t>(o.rec_cap, 1) * sizeof(rtmc_record));
@@ -316,7 +316,7 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
                 ce = d.id_order ? launch_generate(p, q, 0, (unsigned long long)first, nc, s)
                                 : launch_generate_sorted(p, q, (unsigned long long)first, nc, s);
             tock(h);
-            launches += d.id_order ? 1 : 4;      // sorted: count, scan, scatter, write
+            launches += d.id_order ? 1 : 6;      // sorted: count, scan (three kernels), scatter, write
             for (int g = 0; g <= em.max_generation && ce == cudaSuccess; ++g) {
                 const int buf = g & 1;
                 const bool col = (columns || slanted) && g == 0;

@@ -143,7 +143,7 @@ cudaError_t record_batch(rtmc_ctx* ctx, const rtmc_batch& b, const rtmc_run_desc
             if (ce == cudaSuccess)
                 ce = sorted ? launch_generate_items_sorted(p, ic, qq, n, s) : launch_generate_items(p, ic, qq, n, s);
             kt.tock(h, s);
-            launches += sorted ? 4 : 1;          // sorted: count, scan, scatter, write
+            launches += sorted ? 6 : 1;          // sorted: count, scan (three kernels), scatter, write
             for (int g = 0; g <= ctx->emission.max_generation && ce == cudaSuccess; ++g) {
                 const int buf = g & 1;
                 const int method = g == 0 ? c.method : 0;
@@ -293,7 +293,7 @@ extern "C" int rtmc_run_batch(rtmc_ctx* ctx, const rtmc_batch* batch, const rtmc
     if (ce == cudaSuccess) ce = scratch_reserve(ctx->hist, (size_t)n_items * nbins * 8);
     if (ce == cudaSuccess) ce = scratch_reserve(ctx->items, (size_t)n_items * sizeof(ItemDev));
     if (ce == cudaSuccess && !d.id_order)
-        ce = scratch_reserve(ctx->sort_counts, (size_t)kChunkItems * kSortBucketsPerItem * 4);
+        ce = scratch_reserve(ctx->sort_counts, sort_scratch_bytes(kChunkItems));
     if (ce == cudaSuccess) ce = scratch_reserve(ctx->grids, (size_t)n_items * sizeof(GridDev));
     if (ce != cudaSuccess) return ctx->fail(RTMC_ERR_OOM, std::string("run_batch: scratch: ") + cudaGetErrorString(ce));
     const void* after[15] = {ctx->q_oe[0].ptr, ctx->q_oe[1].ptr, ctx->q_dt[0].ptr, ctx->q_dt[1].ptr,

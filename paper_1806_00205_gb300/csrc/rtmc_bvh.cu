@@ -186,19 +186,6 @@ k_scan_apply(const unsigned* in, unsigned* out, long long n, const unsigned* __r
     }
 }
 
-// Tile sums needed by scan_exclusive for n elements.
-inline long long scan_parts(long long n) { return std::max<long long>((n + kScanTile - 1) / kScanTile, 1); }
-
-// out[i] = in[0] + ... + in[i-1] for i < n (in == out allowed); *total (device,
-// optional) = the sum of all n.  part: device scratch of scan_parts(n) words.
-void scan_exclusive(const unsigned* in, unsigned* out, long long n, unsigned* total, unsigned* part, cudaStream_t s)
-{
-    const long long nb = (n + kScanTile - 1) / kScanTile;
-    if (nb > 0) k_scan_tiles<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, part);
-    k_scan_parts<<<1, 1024, 0, s>>>(part, nb, total);
-    if (nb > 0) k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, part);
-}
-
 // ---- radix sort: stable scatter ------------------------------------------
 // Element e = tile*1024 + it*256 + warp*32 + lane.  Its rank among equal
 // digits of the tile = (equal digits in earlier (it, warp) slots) + (equal
@@ -1163,6 +1150,19 @@ struct DevBuf {
 };
 
 }  // namespace
+
+// Tile sums needed by scan_exclusive for n elements.
+long long scan_parts(long long n) { return std::max<long long>((n + kScanTile - 1) / kScanTile, 1); }
+
+// out[i] = in[0] + ... + in[i-1] for i < n (in == out allowed); *total (device,
+// optional) = the sum of all n.  part: device scratch of scan_parts(n) words.
+void scan_exclusive(const unsigned* in, unsigned* out, long long n, unsigned* total, unsigned* part, cudaStream_t s)
+{
+    const long long nb = (n + kScanTile - 1) / kScanTile;
+    if (nb > 0) k_scan_tiles<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, part);
+    k_scan_parts<<<1, 1024, 0, s>>>(part, nb, total);
+    if (nb > 0) k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, part);
+}
 
 int build_lbvh(rtmc_ctx* ctx, DeviceMesh& m)
 {

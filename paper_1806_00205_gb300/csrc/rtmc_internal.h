@@ -143,6 +143,12 @@ void scratch_free(Scratch& s);
 // LBVH build (rtmc_bvh.cu).
 int build_lbvh(rtmc_ctx* ctx, DeviceMesh& m);
 
+// Device-wide exclusive scan of 32-bit counts: out[i] = in[0] + ... + in[i-1]
+// (in == out allowed), *total (device, optional) = the sum of all n.  part:
+// device scratch of scan_parts(n) words.  Three launches on s.
+long long scan_parts(long long n);
+void scan_exclusive(const unsigned* in, unsigned* out, long long n, unsigned* total, unsigned* part, cudaStream_t s);
+
 // Wavefront launchers (rtmc_trace.cu).
 struct RunParams {
     unsigned long long seed = 0;
@@ -191,9 +197,15 @@ cudaError_t launch_shade(const DeviceMesh& m, const RunParams& p, const TableDes
 cudaError_t launch_finalize(const Queues& q, unsigned n, cudaStream_t s);
 cudaError_t launch_generate_items(const RunParams& p, const ItemCtx& ic, const Queues& q, unsigned n,
                                   cudaStream_t s);
-// Spatially sorted primaries (Morton-ordered 128 x 128 entry cells; per item in
-// multi-item chunks, at most kChunkItems items).
-constexpr unsigned kSortBucketsPerItem = 1u << 14;
+// Spatially sorted primaries (Morton-ordered 512 x 512 entry cells; per item in
+// multi-item chunks, at most kChunkItems items).  The sort scratch holds the
+// counts of up to `items` items followed by the scan's tile sums.
+constexpr unsigned kSortBucketsPerItem = 1u << 18;
+inline size_t sort_scratch_bytes(unsigned items)
+{
+    const long long b = (long long)items * kSortBucketsPerItem;
+    return (size_t)(b + scan_parts(b)) * 4;
+}
 cudaError_t launch_generate_sorted(const RunParams& p, const Queues& q, unsigned long long first, unsigned n,
                                    cudaStream_t s);
 cudaError_t launch_generate_items_sorted(const RunParams& p, const ItemCtx& ic, const Queues& q, unsigned n,
