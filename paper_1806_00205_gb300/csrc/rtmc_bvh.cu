@@ -1027,14 +1027,65 @@ __device__ __forceinline__ uint2 col_unkey(unsigned long long k)
     return make_uint2((unsigned)k, u);
 }
 
-// One block per pixel: bitonic sort of its list in shared memory.
-__global__ void __launch_bounds__(128) k_col_sort(const int* __restrict__ off, uint2* __restrict__ ent,
-                                                 int* __restrict__ bad)
+// Pixel lists of up to kRankSortMax entries: one warp per pixel (grid-stride,
+// pixels in order) loads the list into shared memory and every lane ranks its
+// R keys against all of them (rank = number of smaller keys; the keys are
+// distinct, so the ranks are a permutation), then writes each entry to its
+// rank.  About L^2 / 32 comparisons per lane and no block barrier.  Longer
+// lists are left to k_col_sort_long.
+constexpr int kRankSortMax = 256;
+constexpr int kRankWarps = 4;                 // warps per block
+
+template <int R>
+__device__ __forceinline__ void rank_list(const unsigned long long* key, uint2* __restrict__ ent, int b, int L,
+                                          int lane)
+{
+    unsigned long long mine[R];
+    int rank[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int e = lane + 32 * r;
+        mine[r] = e < L ? key[e] : ~0ull;
+        rank[r] = 0;
+    }
+    for (int j = 0; j < L; ++j) {
+        const unsigned long long kj = key[j];         // the same word for every lane: a broadcast
+#pragma unroll
+        for (int r = 0; r < R; ++r) rank[r] += kj < mine[r] ? 1 : 0;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        if (lane + 32 * r < L) ent[b + rank[r]] = col_unkey(mine[r]);
+}
+
+__global__ void __launch_bounds__(32 * kRankWarps) k_col_rank_sort(const int* __restrict__ off,
+                                                                   uint2* __restrict__ ent, int np)
+{
+    __shared__ unsigned long long s_key[kRankWarps][kRankSortMax];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned long long* key = s_key[w];
+    for (int p = blockIdx.x * kRankWarps + w; p < np; p += gridDim.x * kRankWarps) {
+        const int b = off[p], L = off[p + 1] - b;
+        if (L <= 1 || L > kRankSortMax) continue;
+        __syncwarp();                                  // the previous list's ranks are read
+        for (int i = lane; i < L; i += 32) key[i] = col_key(ent[b + i]);
+        __syncwarp();
+        if (L <= 32) rank_list<1>(key, ent, b, L, lane);
+        else if (L <= 64) rank_list<2>(key, ent, b, L, lane);
+        else if (L <= 128) rank_list<4>(key, ent, b, L, lane);
+        else rank_list<8>(key, ent, b, L, lane);
+    }
+}
+
+// Lists longer than kRankSortMax, one block per pixel: bitonic sort in shared
+// memory; lists beyond kColSortMax refuse the grid (*bad |= 2).
+__global__ void __launch_bounds__(128) k_col_sort_long(const int* __restrict__ off, uint2* __restrict__ ent,
+                                                      int* __restrict__ bad)
 {
     __shared__ unsigned long long key[kColSortMax];
     const int p = blockIdx.x;
     const int b = off[p], L = off[p + 1] - b;
-    if (L <= 1) return;
+    if (L <= kRankSortMax) return;
     if (L > kColSortMax) { if (threadIdx.x == 0) atomicOr(bad, 2); return; }
     int m = 1;
     while (m < L) m <<= 1;
@@ -1052,6 +1103,13 @@ __global__ void __launch_bounds__(128) k_col_sort(const int* __restrict__ off, u
             __syncthreads();
         }
     for (int i = threadIdx.x; i < L; i += blockDim.x) ent[b + i] = col_unkey(key[i]);
+}
+
+// Sort every pixel list of a grid by col_key.
+void sort_lists(const int* off, uint2* ent, int np, int* bad, int num_sms, cudaStream_t s)
+{
+    k_col_rank_sort<<<num_sms * 16, 32 * kRankWarps, 0, s>>>(off, ent, np);
+    k_col_sort_long<<<np, 128, 0, s>>>(off, ent, bad);
 }
 
 // ---- slanted column grid ---------------------------------------------------
@@ -1458,7 +1516,7 @@ int build_columns(rtmc_ctx* ctx, DeviceMesh& m)
             if (e == cudaSuccess) e = cudaMemcpyAsync(cnt.p, m.col_off, 4ull * np, cudaMemcpyDeviceToDevice, s);
             if (e == cudaSuccess) {
                 k_col_fill<<<gb, tb, 0, s>>>(m.tris, n, gx, gy, iwx, iwy, cnt.as<int>(), m.col_ent);
-                k_col_sort<<<np, 128, 0, s>>>(reinterpret_cast<const int*>(m.col_off), m.col_ent, bad.as<int>());
+                sort_lists(reinterpret_cast<const int*>(m.col_off), m.col_ent, np, bad.as<int>(), ctx->num_sms, s);
                 e = cudaGetLastError();
             }
             if (e == cudaSuccess) e = cudaMemcpyAsync(&h_bad, bad.p, 4, cudaMemcpyDeviceToHost, s);
@@ -1561,7 +1619,7 @@ bool slant_grid(rtmc_ctx* ctx, DeviceMesh& m, float dx, float dz, GridDev& out)
             if (e == cudaSuccess) {
                 k_slant_fill<<<gb, tb, 0, s>>>(m.tris, n, gx, gy, iwx, iwy, lx, z_top, shear, margin, cnt.as<int>(),
                                                g.ent);
-                k_col_sort<<<np, 128, 0, s>>>(reinterpret_cast<const int*>(g.off), g.ent, bad.as<int>());
+                sort_lists(reinterpret_cast<const int*>(g.off), g.ent, np, bad.as<int>(), ctx->num_sms, s);
                 e = cudaGetLastError();
             }
             if (e == cudaSuccess) e = cudaMemcpyAsync(&h_bad, bad.p, 4, cudaMemcpyDeviceToHost, s);
