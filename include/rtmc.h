@@ -254,6 +254,10 @@ int rtmc_run(rtmc_ctx* ctx, int32_t mesh_id, const double* energies_ev, int32_t 
    identical to that run's.  Every generation the loaded emission allows
    (max_generation <= 6) is traced, one traversal and one shade launch per
    generation and chunk; a generation with no rays ends its launches at once.
+   With desc->chunk = 0 a chunk is the largest power of two up to 2^26
+   primaries whose queues take at most a quarter of the free device memory
+   (the queues the context already holds counted as free), and at most 15
+   items' worth of primaries.
    Queues are sized as in rtmc_run (desc->queue_factor); if a chunk overflows,
    the whole batch is recorded again with twice the capacity and run again
    (up to six times; queue_retries counts the repeats).  Writes
