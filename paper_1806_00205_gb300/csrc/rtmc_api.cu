@@ -161,6 +161,20 @@ QueueFactors queue_factors(const rtmc_ctx* ctx, const rtmc_run_desc& d, double e
     return q;
 }
 
+int64_t default_chunk(const rtmc_ctx* ctx, const QueueFactors& qf)
+{
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { cudaGetLastError(); free_b = 0; }
+    double avail = (double)free_b;
+    for (int b = 0; b < 2; ++b) avail += (double)(ctx->q_oe[b].bytes + ctx->q_dt[b].bytes + ctx->q_id[b].bytes);
+    avail += (double)(ctx->hits.bytes + ctx->wraps.bytes + ctx->kcount.bytes);
+    // queue entries (48 B) in both buffers, hit record and wrap count per slot, escape count per primary
+    const double per_primary = 48.0 * (qf.f[0] + qf.f[1]) + 20.0 * std::max(qf.f[0], qf.f[1]) + 4.0;
+    int64_t chunk = (int64_t)1 << 26;
+    while (chunk > ((int64_t)1 << 20) && per_primary * (double)chunk > 0.25 * avail) chunk >>= 1;
+    return chunk;
+}
+
 void fill_result(rtmc_result& r, const Tally& t, int64_t n_prim)
 {
     std::memset(&r, 0, sizeof r);
@@ -232,10 +246,9 @@ int run_item(rtmc_ctx* ctx, DeviceMesh& m, double energy, double theta_deg, unsi
     // Queue capacities: buffer 0 holds even generations, buffer 1 odd ones,
     // sized from the expected yield (queue_factors); a chunk whose daughters
     // overflow is run again with doubled capacities.
-    int64_t chunk = d.chunk > 0 ? d.chunk : ((int64_t)1 << 22);
-    if (em.max_generation >= 2 && d.chunk <= 0) chunk = (int64_t)1 << 20;
-    chunk = std::min<int64_t>(chunk, std::max<int64_t>(n_prim, 1));
     const QueueFactors qf = queue_factors(ctx, d, energy);
+    int64_t chunk = d.chunk > 0 ? d.chunk : default_chunk(ctx, qf);
+    chunk = std::min<int64_t>(chunk, std::max<int64_t>(n_prim, 1));
     double mult[2] = {qf.f[0], qf.f[1]};
     const Tuning tune = tuning_from(d);
     int64_t retries = 0;

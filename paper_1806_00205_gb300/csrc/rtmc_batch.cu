@@ -259,20 +259,9 @@ extern "C" int rtmc_run_batch(rtmc_ctx* ctx, const rtmc_batch* batch, const rtmc
     double mult[2] = {qf.f[0], qf.f[1]};
     int64_t chunk = d.chunk;
     if (chunk <= 0) {
-        // The largest power of two up to 2^26 primaries whose queues take at most a
-        // quarter of the device memory not held by other buffers (the queues this
-        // context already holds count as free, so the choice is the same call after
-        // call).  Longer chunks mean fewer launches and shorter launch tails: 2^26
-        // against 2^23 traced a 9e8-primary step 6 % faster.
-        size_t free_b = 0, total_b = 0;
-        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { cudaGetLastError(); free_b = 0; }
-        double avail = (double)free_b;
-        for (int bb = 0; bb < 2; ++bb)
-            avail += (double)(ctx->q_oe[bb].bytes + ctx->q_dt[bb].bytes + ctx->q_id[bb].bytes);
-        avail += (double)(ctx->hits.bytes + ctx->wraps.bytes + ctx->kcount.bytes);
-        const double per_primary = 48.0 * (mult[0] + mult[1]) + 20.0 * std::max(mult[0], mult[1]) + 4.0;
-        chunk = (int64_t)1 << 26;
-        while (chunk > ((int64_t)1 << 20) && per_primary * (double)chunk > 0.25 * avail) chunk >>= 1;
+        // longer chunks mean fewer launches and shorter launch tails: 2^26 against
+        // 2^23 traced a 9e8-primary step 6 % faster
+        chunk = default_chunk(ctx, qf);
         // and at most kChunkItems items per chunk (a chunk may start inside an item), so that
         // shade keeps its per-item shared accumulators and the primaries stay spatially sorted
         chunk = std::min<int64_t>(chunk, std::max<int64_t>((int64_t)(kChunkItems - 1) * batch->n_primaries,

@@ -99,6 +99,11 @@ struct QueueFactors {
     double f[2] = {1.0, 1.0};
 };
 QueueFactors queue_factors(const rtmc_ctx* ctx, const rtmc_run_desc& d, double e_max_ev);
+// Default primaries per chunk: the largest power of two up to 2^26 whose queues
+// (capacities f[0], f[1] per primary) take at most a quarter of the device memory
+// not held by other buffers; the queues the context already holds count as free,
+// so the choice is the same from call to call.
+int64_t default_chunk(const rtmc_ctx* ctx, const QueueFactors& qf);
 
 }  // namespace rtmc
 
