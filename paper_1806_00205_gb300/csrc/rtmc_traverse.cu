@@ -125,10 +125,10 @@ __device__ __forceinline__ void slab_near_far(float nxp, float fxp, float nyp, f
 
 // 4-wide node (128 B): rows lo.x, hi.x, lo.y, hi.y, lo.z, hi.z of the four
 // child boxes, then the four child refs.  The 8-bit form (64 B) holds per
-// axis a shifted origin o' and a quantum s, then the same six rows as one
+// axis a frame origin o' and a scale S = 2^15 s, then the same six rows as one
 // code byte per child, then the refs.  The hit children come back sorted by
 // entry distance (nearest first); *nh is their number.  An empty slot holds
-// the box [+inf, +inf]^3 (FP32) or the ref kEmptyChild (8-bit), never hit.
+// the box [+inf, +inf]^3 (FP32) or the codes lo 255, hi 0 (8-bit), never hit.
 template <int FMT>
 __device__ __forceinline__ void node4_children(const void* __restrict__ nodes, int node, const RaySetup& r,
                                                float t_best, float (&tk)[4], int (&ck)[4], int& nh)
@@ -168,9 +168,8 @@ __device__ __forceinline__ void node4_children(const void* __restrict__ nodes, i
         child(1, tk[1], h1);
         child(2, tk[2], h2);
         child(3, tk[3], h3);
-        h1 = h1 && ck[1] != kEmptyChild;
-        h2 = h2 && ck[2] != kEmptyChild;
-        h3 = h3 && ck[3] != kEmptyChild;
+        // an empty slot (codes lo 255, hi 0) is never hit: its near plane lies beyond its far
+        // plane along the ray whatever the direction's sign, also where both saturate to +-inf
     } else {
         // Per axis the lane loads the near row first (lo when the direction is
         // positive, hi when negative), so (near - o) * inv <= (far - o) * inv and no
